@@ -264,12 +264,56 @@ _NULL1 = scipy.linalg.null_space(np.ones((1, 4)))   # basis of 1-perp in R^4
 
 def c_definition(Kn, S) -> float:
     """Largest finite generalized eigenvalue of the local pencil K v = C M v
-    (Sec. 5.2) with K = Kn, M = S.  Both annihilate constants, so the pencil is
-    singular; following the rank-based definition (Sec. 4.4) the common null
-    vector is deflated and the regular 3x3 pencil is solved."""
+    (Sec. 5.2) with K = Kn, M = S given on the nodal basis.  Both annihilate
+    constants, so the pencil is singular; following the rank-based
+    definition (Sec. 4.4) the common null vector is deflated and the regular
+    3x3 pencil is solved.  (Loses accuracy on thin cut regions, where the
+    deflated nodal basis is ill conditioned; ``c_definition_pieces`` is the
+    accurate form used by the assembly.)"""
     Kq = _NULL1.T @ Kn @ _NULL1
     Mq = _NULL1.T @ S @ _NULL1
     return float(scipy.linalg.eigh(Kq, Mq, eigvals_only=True)[-1])
+
+
+def c_definition_pieces(pieces, xc, yc, h) -> float:
+    """The same largest generalized eigenvalue, with Q1 modulo constants
+    spanned by b1 = (x - xb)/s, b2 = (y - yb)/s, b3 = (x - xb)(y - yb)/s^2,
+    (xb, yb) the area centroid of K cap Omega_h and s^2 its area.  Centring
+    on the centroid makes the M-block diagonal, so the 3x3 pencil stays well
+    conditioned for thin or small cut regions.
+      M3_ab = int_{K cap Omega} grad b_a . grad b_b,
+      K3_ab = int_{K cap Gamma} (n . grad b_a)(n . grad b_b)."""
+    to_phys = lambda r: np.array([xc, yc]) + h * np.asarray(r, float)
+    P, W = [], []
+    for pc in pieces:
+        X, w = polygon_rule(np.array([to_phys(r) for r in pc.poly]))
+        P.append(X); W.append(w)
+    X = np.concatenate(P); W = np.concatenate(W)
+    area = W.sum()
+    xb, yb = (W * X[:, 0]).sum() / area, (W * X[:, 1]).sum() / area
+    sc = np.sqrt(area)
+
+    def grads(x, y):      # (n, 3, 2)
+        n = len(x)
+        g = np.zeros((n, 3, 2))
+        g[:, 0, 0] = 1.0 / sc
+        g[:, 1, 1] = 1.0 / sc
+        g[:, 2, 0] = (y - yb) / sc ** 2
+        g[:, 2, 1] = (x - xb) / sc ** 2
+        return g
+
+    g = grads(X[:, 0], X[:, 1])
+    M3 = np.einsum("q,qia,qja->ij", W, g, g)
+    K3 = np.zeros((3, 3))
+    for pc in pieces:
+        for (pr, qr) in pc.segments:
+            p, q = to_phys(pr), to_phys(qr)
+            d = q - p
+            n = np.array([d[1], -d[0]]) / np.hypot(*d)
+            Xs, Ws = segment_rule(p, q)
+            dn = grads(Xs[:, 0], Xs[:, 1]) @ n         # (n, 3)
+            K3 += np.einsum("q,qi,qj->ij", Ws, dn, dn)
+    return float(scipy.linalg.eigh(K3, M3, eigvals_only=True)[-1])
 
 
 def c_triangle(theta1, theta2, h) -> float:
@@ -286,14 +330,14 @@ def c_pentagon(h) -> float:
     return 3.0 * np.sqrt(2.0) / h
 
 
-def stabilisation_C(config, psi4, ints: CellIntegrals, h) -> float:
+def stabilisation_C(config, psi4, pieces, ints: CellIntegrals, xc, yc, h) -> float:
     if config == "triangle":
         return c_triangle(*triangle_legs(psi4), h)
     if config in ("pentagon", "hexagon"):
         return c_pentagon(h)
     if ints.length == 0.0:
         return 0.0
-    return c_definition(ints.Kn, ints.S)
+    return c_definition_pieces(pieces, xc, yc, h)
 
 
 # ----------------------------------------------------------------------------
@@ -315,10 +359,13 @@ class CutCell:
 
 
 def cut_cell(psi4, ic, jc, x0, y0, h, gamma) -> CutCell:
+    """Element matrices of cut cell (ic, jc).  The integrals are invariant
+    under translation, so they are taken in cell-local coordinates (origin
+    at the cell's lower-left corner, side h): absolute coordinates would add
+    cancellation of order |x0 + ic h| / (size of the cut region)."""
     config, pieces, thetas = cut_pieces(psi4)
-    xc, yc = x0 + ic * h, y0 + jc * h
-    ints = cell_integrals(pieces, xc, yc, h)
-    C = stabilisation_C(config, psi4, ints, h)
+    ints = cell_integrals(pieces, 0.0, 0.0, h)
+    C = stabilisation_C(config, psi4, pieces, ints, 0.0, 0.0, h)
     lam = gamma * C
     # a_h(phi_j, phi_i) on K: grad.grad + lam phi phi - (n.grad phi_j) phi_i
     #                          - (n.grad phi_i) phi_j           (Eq. disc_bil_form)
@@ -410,10 +457,27 @@ def assemble_problem(prob, gamma=2.0, alpha=1.75) -> System:
     return assemble(prob.psi, prob.N, prob.x0, prob.y0, prob.h, gamma, alpha)
 
 
-def direct_solve(system: System, F: np.ndarray) -> np.ndarray:
-    """Sparse direct solution of A u = F on the DOFs (u = 0 elsewhere)."""
+def direct_solve(system: System, F: np.ndarray, refine: int = 4) -> np.ndarray:
+    """Solution of A u = F on the DOFs (u = 0 elsewhere): sparse LU, then
+    iterative refinement (Wilkinson) with the residual F - A u accumulated in
+    extended precision (numpy longdouble), so the result is the exact
+    solution rounded to fp64 even when cond(A) ~ 1e8 (small cut cells),
+    where a plain fp64 solve is only good to about cond(A) eps."""
     import scipy.sparse.linalg as spla
     d = np.flatnonzero(system.dof)
     u = np.zeros(system.n_nodes)
-    u[d] = spla.spsolve(system.A[d][:, d].tocsc(), F[d])
+    if len(d) == 0:
+        return u
+    A = system.A[d][:, d].tocsr()
+    lu = spla.splu(A.tocsc())
+    x = lu.solve(F[d])
+    Al = sp.csr_matrix((A.data.astype(np.longdouble), A.indices, A.indptr), shape=A.shape)
+    Fl = F[d].astype(np.longdouble)
+    for _ in range(refine):
+        r = Fl - Al @ x.astype(np.longdouble)
+        dx = lu.solve(np.asarray(r, dtype=np.float64))
+        x = np.asarray(x.astype(np.longdouble) + dx, dtype=np.float64)
+        if np.abs(dx).max() <= 4 * np.finfo(np.float64).eps * np.abs(x).max():
+            break
+    u[d] = x
     return u

@@ -93,6 +93,79 @@ def test_c_triangle_equals_eigen_definition(t1, t2):
     assert c_def == pytest.approx(gf.c_triangle(t1, t2, h), rel=1e-10)
 
 
+@pytest.mark.parametrize("t1,t2", [(1.0, 1.0), (0.3, 0.7), (0.05, 0.9), (0.01, 0.02), (0.9, 0.002)])
+def test_c_definition_pieces_equals_c_triangle(t1, t2):
+    # cell-local coordinates (origin at the cell corner), as the assembly uses
+    h = 0.02
+    psi4 = np.array([-1.0, (1 - t1) / t1, (1 - t2) / t2, 3.0])
+    cfg, pieces, _ = gf.cut_pieces(psi4)
+    assert gf.c_definition_pieces(pieces, 0.0, 0.0, h) == pytest.approx(
+        gf.c_triangle(t1, t2, h), rel=1e-13)
+
+
+@pytest.mark.parametrize("theta", [0.9, 0.3, 0.03, 0.004])
+def test_c_definition_pieces_straight_cut(theta):
+    # Sec. 5.3 rectangle / Sec. 4.4: C = 1/(theta h) for the straight-cut quad
+    h = 0.05
+    psi4 = np.array([1.0 - theta, -theta, 1.0 - theta, -theta])
+    cfg, pieces, _ = gf.cut_pieces(psi4)
+    assert gf.c_definition_pieces(pieces, 0.0, 0.0, h) == pytest.approx(1 / (theta * h), rel=1e-13)
+
+
+def _c_mp(pieces, dps=40):
+    """Brute-force C(K) h in mpmath: exact 3-point Gauss on degree <= 2
+    integrands of the monomials x, y, xy (reference cell), 40 digits."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = dps
+    r = mp.sqrt(mp.mpf(3) / 5) / 2
+    S3 = [mp.mpf(1) / 2 - r, mp.mpf(1) / 2, mp.mpf(1) / 2 + r]
+    W3 = [mp.mpf(5) / 18, mp.mpf(8) / 18, mp.mpf(5) / 18]
+    g = lambda x, y: [(1, 0), (0, 1), (y, x)]
+    M = mp.zeros(3, 3); K = mp.zeros(3, 3)
+    for pc in pieces:
+        P = [(mp.mpf(a), mp.mpf(b)) for a, b in pc.poly]
+        for k in range(1, len(P) - 1):
+            A, B, C = P[0], P[k], P[k + 1]
+            jac = abs((B[0] - A[0]) * (C[1] - A[1]) - (B[1] - A[1]) * (C[0] - A[0]))
+            for s_, ws in zip(S3, W3):
+                for t_, wt in zip(S3, W3):
+                    x = A[0] + s_ * (1 - t_) * (B[0] - A[0]) + s_ * t_ * (C[0] - A[0])
+                    y = A[1] + s_ * (1 - t_) * (B[1] - A[1]) + s_ * t_ * (C[1] - A[1])
+                    G = g(x, y)
+                    for i in range(3):
+                        for j in range(3):
+                            M[i, j] += jac * s_ * ws * wt * (G[i][0] * G[j][0] + G[i][1] * G[j][1])
+        for pr, qr in pc.segments:
+            pa = [mp.mpf(v) for v in pr]; qa = [mp.mpf(v) for v in qr]
+            dx, dy = qa[0] - pa[0], qa[1] - pa[1]
+            L = mp.sqrt(dx * dx + dy * dy)
+            for s_, ws in zip(S3, W3):
+                G = g(pa[0] + s_ * dx, pa[1] + s_ * dy)
+                dn = [(dy * G[i][0] - dx * G[i][1]) / L for i in range(3)]
+                for i in range(3):
+                    for j in range(3):
+                        K[i, j] += L * ws * dn[i] * dn[j]
+    Li = mp.inverse(mp.cholesky(M))
+    return float(max(mp.eigsy(Li * K * Li.T)[0]))
+
+
+def test_c_definition_pieces_high_precision_on_thin_quads():
+    # thin and slanted quadrilaterals, and two-triangle saddles: 1e-14
+    # against a 40-digit evaluation of the same definition
+    rng = np.random.default_rng(7)
+    cases = [np.array([-0.02542, -0.033139, 0.97458, 0.966861]),
+             np.array([-0.001, -0.3, 0.999, 0.7]),
+             np.array([-0.5, 0.9, 0.9, -0.4])]
+    for _ in range(6):
+        a, b = rng.uniform(1e-3, 0.2, 2)
+        cases.append(np.array([-a, -b, 1 - a, 1 - b]))
+    for psi4 in cases:
+        cfg, pieces, _ = gf.cut_pieces(psi4)
+        assert cfg in ("quad", "two_triangles")
+        ref = _c_mp(pieces)
+        assert gf.c_definition_pieces(pieces, 0.0, 0.0, 1.0) == pytest.approx(ref, rel=1e-14)
+
+
 def test_c_pentagon_is_triangle_at_one():
     h = 0.1
     assert gf.c_pentagon(h) == pytest.approx(gf.c_triangle(1.0, 1.0, h), rel=1e-15)

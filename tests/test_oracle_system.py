@@ -67,6 +67,24 @@ def test_second_order_convergence(make):
     assert slope > 1.8, (e, slope)
 
 
+def test_refined_direct_solve_is_exact_to_fp64():
+    # residual accumulated in extended precision is at rounding level, and the
+    # refined solution agrees with a dense solve to within cond(A) eps
+    p = wl.flower(64)
+    s = gf.assemble_problem(p)
+    F = s.rhs(p.f, p.g)
+    u = gf.direct_solve(s, F)
+    d = np.flatnonzero(s.dof)
+    A = s.A[d][:, d].toarray()
+    r = F[d].astype(np.longdouble) - A.astype(np.longdouble) @ u[d].astype(np.longdouble)
+    eps = np.finfo(np.float64).eps
+    assert float(np.abs(r).max()) <= 8 * eps * float(np.abs(A).sum(1).max() * np.abs(u).max())
+    ev = np.linalg.eigvalsh(A)
+    kappa = ev[-1] / ev[0]
+    ud = np.linalg.solve(A, F[d])
+    assert np.abs(ud - u[d]).max() <= 4 * kappa * eps * np.abs(u).max()
+
+
 def test_rhs_linear_in_data():
     p = wl.flower(32)
     s = gf.assemble_problem(p)
