@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark: DOF/s to 1e-10 relative residual for the ghost-FEM multigrid
+solve on one GB300 (fp32 V-cycle inside fp64 iterative refinement, with the
+plain fp64 V-cycle beside it), and the HBM roofline fraction of the dominant
+kernel.
+
+A step is one mg_solve of the flower problem (r - 0.3 - 0.1 sin 5 theta on
+[-0.5, 0.5]^2, 4096^2 cells, u = sin 3x cos 2y) from u = 0 until
+||F - A u||_inf / ||F||_inf <= 1e-10, with f, g, u resident in HBM.  L2 is
+flushed (a 512 MB write) between steps, outside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun with N > 1 every rank solves its own replica (no collective
+on the data path); value = the DOFs all ranks solved / the slowest rank's
+time.  ``--impl reference`` times the CPU oracle on a bounded sample of the
+same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF/s to 1e-10 rel. residual (mixed vs FP64 V-cycle, 1 GB300); % HBM roofline"
+UNIT = "DOF/s"
+TOL = 1e-10
+
+# algorithmic bytes per fine-level DOF moved by one launch of each kernel:
+# the method must read u, F and one byte of node class and write u (sweep);
+# restriction writes a quarter-size coarse array, prolongation reads one.
+ALGO_BYTES = {
+    ("sweep", "f32"): 4 + 4 + 1 + 4,
+    ("sweep", "f64"): 8 + 8 + 1 + 8,
+    ("restrict", "f32"): 4 + 4 + 1 + 1,
+    ("restrict", "f64"): 8 + 8 + 1 + 2,
+    ("prolong", "f32"): 4 + 4 + 1 + 1,
+    ("prolong", "f64"): 8 + 8 + 1 + 2,
+    ("residual", "mixed"): 8 + 8 + 1 + 4,     # fp64 u, F in; fp32 scaled r out
+    ("residual", "f64"): 8 + 8 + 1,
+    ("update", "mixed"): 8 + 4 + 1 + 8,       # u64 in, e32 in, u64 out
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(N):
+    return f"flower r-0.3-0.1sin(5theta) on [-0.5,0.5]^2, {N}x{N} cells, u=sin3x cos2y"
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    src = os.path.join(ROOT, "paper_2505_05105_gb300", "csrc", "cycle.cu")
+    try:
+        txt = open(path).read()
+        want = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+        t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        if m and t and m.group(1) == want:
+            return float(t.group(1))
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(N_sample, steps, warmup):
+    """Time the CPU oracle (fp64 4-colour V(2,1) with eta = 4, same stopping
+    test) on the flower level set with N_sample cells per side; setup is
+    excluded, like the GPU metric.  Returns (DOF/s, dofs, per-solve s, cycles)."""
+    from oracle import ghostfem as gf
+    from oracle import multigrid as mg
+    from paper_2505_05105_gb300 import workloads as wl
+    p = wl.flower(N_sample)
+    s = gf.assemble_problem(p)
+    lev = mg.build_hierarchy(s)
+    F = s.rhs(p.f, p.g)
+    times, cyc = [], 0
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        u, hist, cyc = mg.solve(lev, F, tol=TOL)
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+    ndof = int(s.dof.sum())
+    return ndof / statistics.mean(times), ndof, statistics.mean(times), cyc
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((d.get("num_threads", 1) for d in threadpool_info()), default=1)
+    except Exception:
+        n = 1
+    # the oracle's sparse kernels (SciPy CSR) are single-threaded
+    return 1 if n >= 1 else 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    Ns = 2048
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    val, ndof, sec, cyc = oracle_sample(Ns, steps, warm)
+    sample = (f"flower level set at {Ns}x{Ns} cells ({ndof} DOFs, 1/{(args.N // Ns) ** 2} of the "
+              f"nodes), full fp64 solve to 1e-10 ({cyc} V(2,1) cycles), setup excluded")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": steps, "warmup": warm, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.N), "N": args.N, "tol": TOL,
+                   "sample_N": Ns},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2505_05105_gb300 import ghostmg, workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ghostmg.load()
+
+    N = args.N
+    p = wl.flower(N)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(dev)
+    psi, f, g = t(p.psi), t(p.f), t(p.g)
+    stream = torch.cuda.current_stream(dev)
+    solvers = {
+        "mixed": ghostmg.Solver(psi, N, p.x0, p.y0, p.h, precision="mixed",
+                                stream=stream.cuda_stream),
+        "fp64": ghostmg.Solver(psi, N, p.x0, p.y0, p.h, precision="fp64",
+                               stream=stream.cuda_stream),
+    }
+    n_levels, ndof, ncut, nbnd = solvers["mixed"].counts()
+    u = torch.zeros_like(f)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(S, steps, warm, prof=False):
+        for _ in range(warm):
+            u.zero_()
+            S.solve(f, g, u, tol=TOL)
+        if prof:
+            ghostmg.mg_set_profiling(S.handle, True)
+        ms, cycles = [], []
+        barrier()
+        for k in range(steps):
+            u.zero_()
+            flush.fill_(float(k))               # evict L2 (512 MB write), untimed
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = S.solve(f, g, u, tol=TOL)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            cycles.append(info.cycles)
+        barrier()
+        prof_out = ghostmg.mg_get_profile(S.handle) if prof else None
+        if prof:
+            ghostmg.mg_set_profiling(S.handle, False)
+        total = sum(ms)
+        if dist is not None:
+            tt = torch.tensor([total], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total = float(tt.item())
+        return total, ms, cycles, prof_out, info
+
+    with ClockSampler(local) as clk:
+        total_mx, ms_mx, cyc_mx, prof, info_mx = timed(solvers["mixed"], args.steps, args.warmup,
+                                                       prof=True)
+    clocks = clk.summary()
+    total_64, ms_64, cyc_64, _, info_64 = timed(solvers["fp64"], args.steps, args.warmup)
+
+    value = world * ndof * args.steps / (total_mx / 1e3)
+    value64 = world * ndof * args.steps / (total_64 / 1e3)
+
+    # roofline of the dominant fine-level kernel (live CUDA-event timing)
+    launches, slots = prof
+    kinds = {"sweep": "f32", "restrict": "f32", "prolong": "f32", "residual": "mixed",
+             "update": "mixed"}
+    cand = {k: v for k, v in slots.items() if k in kinds and v[0] > 0}
+    dom = max(cand, key=lambda k: cand[k][1])
+    n_launch, dom_ms = cand[dom]
+    per_launch_s = dom_ms / n_launch / 1e3
+    algo = ALGO_BYTES[(dom, kinds[dom])] * ndof
+    peak, peak_src = measured_peaks()
+    achieved = algo / per_launch_s / 1e9
+    traffic = profile_traffic(f"{dom}_f32_flower{N}")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": f"k_gs_sweep<float> (fine level)" if dom == "sweep" else dom,
+                "algorithmic_bytes_per_launch": algo, "launches": n_launch,
+                "avg_launch_us": per_launch_s * 1e6, "peak_source": f"{peak_src} hbm_gbs"}
+    breakdown = {k: {"launch_groups": v[0], "ms_per_step": v[1] / args.steps}
+                 for k, v in slots.items()}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(np.ascontiguousarray(p.f, dtype=np.float64).ravel()).pin_memory()
+        gh = torch.from_numpy(np.ascontiguousarray(p.g, dtype=np.float64).ravel()).pin_memory()
+        uh = torch.zeros(fh.numel(), dtype=torch.float64).pin_memory()
+        S = solvers["mixed"]
+        for _ in range(max(1, args.warmup)):
+            uh.zero_()
+            S.solve(fh.data_ptr(), gh.data_ptr(), uh.data_ptr(), tol=TOL)
+        barrier()
+        tot = 0.0
+        for k in range(args.steps):
+            uh.zero_()
+            flush.fill_(float(k))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            S.solve(fh.data_ptr(), gh.data_ptr(), uh.data_ptr(), tol=TOL)
+            tot += time.perf_counter() - t0
+        barrier()
+        if dist is not None:
+            tt = torch.tensor([tot], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tot = float(tt.item())
+        nb = fh.numel() * 8
+        e2e = {"value": world * ndof * args.steps / tot, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * nb, "d2h_bytes_per_step": nb}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        Ns = 2048
+        val, sdof, sec, scyc = oracle_sample(Ns, steps=2, warmup=0)
+        cpu = {"value": val, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"flower level set at {Ns}x{Ns} cells ({sdof} DOFs), full fp64 "
+                         f"4-colour V(2,1) solve to 1e-10 ({scyc} cycles), setup excluded"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_mx / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle in f64 refinement",
+            "data": "synthetic",
+            "config": {"workload": workload_name(N), "N": N, "n_dof": ndof, "n_cut": ncut,
+                       "n_levels": n_levels, "tol": TOL, "precision": "mixed",
+                       "cycles_per_solve": cyc_mx[-1], "V": "V(2,1), eta=4, gamma=2",
+                       "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "fp64": {"value": value64, "unit": UNIT, "ms_per_step": total_64 / args.steps,
+                     "cycles_per_solve": cyc_64[-1], "dtype": "f64"},
+            "mixed_over_fp64": value / value64,
+            "roofline": roofline,
+            "kernel_breakdown_mixed": breakdown,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    for S in solvers.values():
+        S.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * ghostmg.h - C ABI of the GB300 (sm_103a) geometric multigrid solver for the
+ * nodal ghost finite element method of Dilip & Coco, "Multigrid methods for
+ * the ghost finite element approximation of elliptic problems"
+ * (arXiv 2505.05105).
+ *
+ * Problem (Sec. 2, Eq. poisson_model_prob with a Dirichlet boundary):
+ *     -Laplace u = f in Omega = {psi < 0},   u = g on {psi = 0},
+ * discretised with Q1 elements on the active cells of an N x N Cartesian grid
+ * (Eq. Vhact) and Nitsche terms on the cut cells (Eq. disc_bil_form,
+ * Eq. disc_rhs), with the local stabilisation lambda_K = gamma C(K) of
+ * Sec. 5.2 and snapping back to grid with threshold h^alpha (Sec. 2).  The
+ * system A u = F is solved by V(nu1, nu2)-cycles (Sec. 3.2) with a 4-colour
+ * Gauss-Seidel smoother (Sec. 4.1) plus eta extra sweeps on the cut-cell
+ * vertices (Sec. 5.3), bilinear prolongation P and restriction R = P^T
+ * (Sec. 5.1) and Galerkin coarse operators (Eq. galerkin).
+ *
+ * Arrays: every nodal array has (N+1)^2 doubles, row-major with node index
+ * k = i + j (N+1) (Sec. 5.1), node (i, j) at (x0 + i h, y0 + j h).
+ * Array arguments may be device pointers (used on the handle's stream) or
+ * host pointers (pageable or pinned; staged through handle-owned device
+ * buffers, and the call returns after the copies back have completed).
+ * The caller owns every array; no pointer is kept after a call returns.
+ *
+ * Errors: every int-returning call returns MG_OK (0) or one of the MG_ERR_*
+ * codes below; nothing is thrown across the ABI.  After MG_ERR_CUDA the
+ * handle should be destroyed.  mg_strerror() gives a message, including the
+ * last CUDA error text when there was one.
+ *
+ * Threading: one handle per CUDA stream; calls on different handles are
+ * independent.  A handle must not be used from two threads at once.
+ */
+#ifndef GHOSTMG_H
+#define GHOSTMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,    /* bad size, NULL pointer, NaN/Inf input,
+                                domain touching the outer ring of nodes */
+  MG_ERR_CUDA = 2,           /* a CUDA runtime call or kernel failed */
+  MG_ERR_NOT_CONVERGED = 3,  /* max_cycles reached; outputs and info filled */
+  MG_ERR_DIVERGED = 4,       /* residual grew for 3 consecutive cycles */
+  MG_ERR_NOT_SPD = 5,        /* coarsest Cholesky met a pivot <= 0 */
+  MG_ERR_TIMEOUT = 6,        /* reserved for bounded device waits */
+  MG_ERR_UNIMPLEMENTED = 7,  /* option not supported (e.g. Neumann data) */
+  MG_ERR_INTERNAL = 8,       /* internal consistency check failed */
+  MG_ERR_OUT_OF_MEMORY = 9   /* device allocation failed */
+};
+
+enum { MG_BC_DIRICHLET = 0 };     /* weak Dirichlet on the whole of {psi = 0} */
+enum { MG_LAMBDA_LOCAL = 0 };     /* lambda_K = gamma C(K) per cut cell (Sec. 5.2) */
+enum { MG_FP64 = 0,               /* fp64 V-cycles */
+       MG_MIXED = 1 };            /* fp32 V-cycle inside fp64 iterative refinement */
+
+typedef struct mg_ctx* mg_handle;
+
+/* Grid of Omega_art (Sec. 2): n_cells x n_cells cells of side h with the
+ * lower-left node at (x0, y0).  n_cells is a power of two >= 8;
+ * coarsest_cells (a power of two, 2..32, dividing n_cells; default 8) is the
+ * size of the level solved exactly (Alg. 1, step 3). */
+typedef struct {
+  int n_cells;
+  double x0, y0;
+  double h;
+  int coarsest_cells;
+} mg_grid;
+
+/* Boundary conditions.  kind must be MG_BC_DIRICHLET and neumann_mask NULL:
+ * the Neumann term of Eq. disc_rhs is not implemented (MG_ERR_UNIMPLEMENTED). */
+typedef struct {
+  int kind;
+  const uint8_t* neumann_mask;
+} mg_bc;
+
+/* Method parameters (defaults from mg_default_stab):
+ *   gamma = 2     lambda_K = gamma C(K)                       (Sec. 5.3)
+ *   alpha = 1.75  snapping threshold h^alpha                   (Sec. 5.3)
+ *   eta = 4       extra cut-cell sweeps per smoothing step     (Sec. 5.3), 0..8
+ *   nu1 = 2, nu2 = 1  pre/post smoothing steps                 (Sec. 5.3), 0..8
+ *   lambda_mode = MG_LAMBDA_LOCAL
+ *   precision = MG_FP64 or MG_MIXED
+ *   max_cycles = 100  cycles (MG_FP64) or refinement steps (MG_MIXED)      */
+typedef struct {
+  double gamma, alpha;
+  int eta, nu1, nu2;
+  int lambda_mode, precision, max_cycles;
+} mg_stab;
+
+/* Result summary of a solve. */
+typedef struct {
+  int cycles;             /* V-cycles (MG_FP64) or refinement steps (MG_MIXED) */
+  double rel_res;         /* final ||F - A u||_inf / ||F||_inf, in fp64 */
+  double res_hist[64];    /* rel_res before cycle 1, after cycle 1, ... */
+  int n_dof;              /* fine-level DOFs (vertices of active cells) */
+  int n_cut;              /* fine-level cut cells */
+  int n_levels;           /* levels including the coarsest */
+  float setup_ms;         /* wall time of mg_setup */
+  float solve_ms;         /* wall time of the last mg_solve (device events) */
+} mg_info;
+
+/* Fills *out with the defaults above.  Returns MG_ERR_INVALID_ARG if out is
+ * NULL. */
+int mg_default_stab(mg_stab* out);
+
+/* Builds the discretisation and the multigrid hierarchy on the GPU.
+ *   levelset  (N+1)^2 nodal psi (Omega = {psi < 0}); copied, then snapped
+ *             (Sec. 2) and classified (Sec. 5.2).  psi after snapping must be
+ *             >= 0 on the outer ring of nodes (i or j equal to 0 or N).
+ *   grid, bc, stab  as documented above; stab may be NULL (defaults).
+ *   cuda_stream     cudaStream_t to run on (NULL = legacy default stream).
+ * Runs: snapping and cell classes (Sec. 2); cut geometry, element matrices
+ * with exact quadrature and C(K) (Sec. 5.2, Eq. c_triangle, Eq. c_pentagon,
+ * the local eigenvalue definition for quadrilaterals); per-node operator
+ * rows; Galerkin coarse levels A_2h = P^T A_h P (Eq. galerkin); the
+ * coarsest-level inverse.  On success *out owns all device memory of the
+ * hierarchy; release it with mg_destroy.  Errors: MG_ERR_INVALID_ARG,
+ * MG_ERR_UNIMPLEMENTED, MG_ERR_NOT_SPD, MG_ERR_OUT_OF_MEMORY, MG_ERR_CUDA
+ * (*out is left NULL). */
+int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const mg_bc* bc,
+             const mg_stab* stab, void* cuda_stream);
+
+/* Solves A u = F with F = M f + G g (Eq. disc_rhs; f and g enter through
+ * their Q1 interpolants, g being any extension of the Dirichlet data to the
+ * nodes).  u holds the initial guess on entry (non-DOF entries ignored) and
+ * the solution on exit, with 0 on nodes that are not DOFs.  Cycles stop when
+ * ||F - A u||_inf / ||F||_inf <= tol (fp64 residual) or after max_cycles.
+ * info may be NULL.  f, g, u: (N+1)^2 doubles, device or host.
+ * Errors: MG_ERR_INVALID_ARG (NULL pointer, NaN/Inf in f, g or u),
+ * MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED (u and info still filled),
+ * MG_ERR_CUDA. */
+int mg_solve(mg_handle h, const double* f, const double* g, double* u, double tol,
+             mg_info* info);
+
+/* Adjoint of mg_solve for a loss L(u): solves A w = dL/du (A is symmetric,
+ * Sec. 4.1) to the tolerance of the last mg_solve (1e-10 if none), then
+ * dL/df = M^T w and dL/dg = G^T w (F is linear in f and g, Eq. disc_rhs).
+ * dLdu, dLdf, dLdg: (N+1)^2 doubles, device or host; dLdf or dLdg may be
+ * NULL to skip it.  Errors as mg_solve. */
+int mg_adjoint(mg_handle h, const double* dLdu, double* dLdf, double* dLdg);
+
+/* Releases the handle and its device memory (NULL is ignored). */
+void mg_destroy(mg_handle h);
+
+/* Static message for a status code (with the last CUDA error text after
+ * MG_ERR_CUDA). */
+const char* mg_strerror(int code);
+
+/* ---------------------------------------------------------------------------
+ * Step-level entry points (the same kernels as mg_solve, exposed so that
+ * each step can be checked on its own).  Arrays as above.
+ * ------------------------------------------------------------------------- */
+
+/* Sizes of the hierarchy: levels, fine DOFs, fine cut cells, boundary nodes
+ * (vertices of cut cells) on the fine level.  Any pointer may be NULL. */
+int mg_get_counts(mg_handle h, int* n_levels, int* n_dof, int* n_cut, int* n_boundary);
+
+/* Cells per side of level `level` (0 = finest), or -1 for a bad level. */
+int mg_level_cells(mg_handle h, int level);
+
+/* The 9-point rows of the level-`level` operator: out[9 k + s] = A_{k, k'}
+ * with k' the neighbour at offset (s mod 3 - 1, s / 3 - 1), k = i + j (n+1);
+ * zero rows on nodes that are not DOFs.  out: 9 (n+1)^2 doubles. */
+int mg_export_stencil(mg_handle h, int level, double* out);
+
+/* Fine-level cut cells in increasing cell index c = ic + jc N.  For each of
+ * the first max_cells: cells[t] = c; data[52 t ..] = C(K), lambda_K,
+ * |K cap Omega_h|, |Gamma_h cap K|, Ke (16, row-major, local vertex order
+ * (0,0),(1,0),(0,1),(1,1)), Mk (16), Gk (16).  Returns the number of cut
+ * cells in *n_total.  cells/data: host or device. */
+int mg_export_cut_cells(mg_handle h, int max_cells, int* cells, double* data, int* n_total);
+
+/* F = M f + G g on the fine level (Eq. disc_rhs), zero off the DOFs. */
+int mg_rhs(mg_handle h, const double* f, const double* g, double* F);
+
+/* Exactly k cycles from u with right-hand side F (no stopping test):
+ * precision MG_FP64 runs k V-cycles; MG_MIXED runs k refinement steps (fp64
+ * residual, one fp32 V-cycle, fp64 update).  u in/out. */
+int mg_cycles(mg_handle h, const double* F, double* u, int k, int precision);
+
+/* r = F - A u on the fine level (fp64); norms[0] = ||r||_inf,
+ * norms[1] = ||r||_2 (host array of 2, may be NULL); r may be NULL. */
+int mg_residual(mg_handle h, const double* F, const double* u, double* r, double* norms);
+
+/* ---------------------------------------------------------------------------
+ * Profiling: device time per kernel class, measured with CUDA events
+ * recorded around each launch on the handle's stream while enabled, and a
+ * count of every kernel the handle launches.  Slots:
+ * ------------------------------------------------------------------------- */
+enum {
+  MG_PROF_SWEEP = 0,     /* fine-level Gauss-Seidel sweeps */
+  MG_PROF_BAND = 1,      /* fine-level extra sweeps on cut-cell vertices */
+  MG_PROF_RESTRICT = 2,  /* fine-level residual + restriction */
+  MG_PROF_PROLONG = 3,   /* fine-level prolongation + correction */
+  MG_PROF_RESIDUAL = 4,  /* fine-level fp64 residual (stopping test, refinement) */
+  MG_PROF_UPDATE = 5,    /* refinement update u += e */
+  MG_PROF_COARSE = 6,    /* every kernel on the coarser levels */
+  MG_PROF_IO = 7,        /* right-hand side, input checks, pack/unpack */
+  MG_PROF_SLOTS = 8
+};
+
+/* enable != 0: clear the accumulators and start recording; 0: stop. */
+int mg_set_profiling(mg_handle h, int enable);
+
+/* Kernel launches since profiling was last enabled (*launches), and per
+ * slot the number of timed launch groups (counts[MG_PROF_SLOTS]) and their
+ * total device milliseconds (ms[MG_PROF_SLOTS]).  Any pointer may be NULL. */
+int mg_get_profile(mg_handle h, long long* launches, long long* counts, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GHOSTMG_H */

@@ -1,0 +1,848 @@
+// C ABI of the ghost-FEM multigrid solver: handle, setup pipeline, V-cycle
+// driver (Alg. 1 applied recursively, Sec. 3.2) and mixed-precision
+// iterative refinement.  See include/ghostmg.h for the contract.
+#include "ghostmg.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "cycle.cuh"
+#include "setup.cuh"
+
+namespace {
+
+thread_local char g_cuda_msg[256] = "";
+
+struct Level {
+  Layout L{};
+  int n = 0;
+  // cells
+  uint8_t* cls = nullptr;
+  int* cell_cut = nullptr;
+  int n_cut = 0;
+  int* cut_list = nullptr;
+  double* Ke = nullptr;
+  // nodes
+  uint16_t* code = nullptr;
+  int* tile_base = nullptr;
+  int n_bnd = 0;
+  int* bnode = nullptr;
+  double* rows64 = nullptr;
+  float* rows32 = nullptr;
+  int n_active = 0;
+  int* active = nullptr;
+  int n_band = 0;
+  int* band = nullptr;
+  int nbx = 0;
+  int n_dof = 0;
+  // vectors
+  double* u64[2] = {nullptr, nullptr};
+  double* F64 = nullptr;
+  double* bval64 = nullptr;
+  float* u32[2] = {nullptr, nullptr};
+  float* F32 = nullptr;
+  float* bval32 = nullptr;
+  int cur64 = 0, cur32 = 0;
+};
+
+}  // namespace
+
+struct mg_ctx {
+  cudaStream_t st = nullptr;
+  mg_grid grid{};
+  mg_stab stab{};
+  int N = 0;
+  double h = 0.0;
+  std::vector<Level> lev;
+  double* psi_s = nullptr;
+  double* Mk = nullptr;
+  double* Gk = nullptr;
+  double* Cl = nullptr;
+  int* cfg = nullptr;
+  double* Adense = nullptr;
+  double* Ainv = nullptr;
+  unsigned* d_err = nullptr;
+  double* d_norms = nullptr;     // 8 slots of (max, sum)
+  double* h_norms = nullptr;     // pinned mirror
+  double* stage[3] = {nullptr, nullptr, nullptr};
+  std::vector<void*> allocs;
+  double last_tol = 1e-10;
+  float setup_ms = 0.f;
+  float solve_ms = 0.f;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // profiling: device time per kernel class between event pairs
+  bool prof = false;
+  long long launches = 0;
+  struct Pend { int cls; cudaEvent_t a, b; };
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> evpool;
+  long long kcount[MG_PROF_SLOTS] = {};
+  double kms[MG_PROF_SLOTS] = {};
+};
+
+int mg_cuda_fail(cudaError_t e) {
+  snprintf(g_cuda_msg, sizeof(g_cuda_msg), "CUDA error: %s", cudaGetErrorString(e));
+  return MG_ERR_CUDA;
+}
+
+namespace {
+
+template <class T>
+int dalloc(mg_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return MG_ERR_OUT_OF_MEMORY;
+  }
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  c->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, count * sizeof(T), c->st);
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  return MG_OK;
+}
+
+#define TRY(expr)                 \
+  do {                            \
+    int rc__ = (expr);            \
+    if (rc__ != MG_OK) return rc__; \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int sync_check(mg_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  unsigned err = 0;
+  e = cudaMemcpy(&err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  if (err) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->st);
+    cudaStreamSynchronize(c->st);
+    if (err & DEV_ERR_NOT_SPD) return MG_ERR_NOT_SPD;
+    if (err & (DEV_ERR_NAN | DEV_ERR_EDGE)) return MG_ERR_INVALID_ARG;
+    return MG_ERR_INTERNAL;
+  }
+  return MG_OK;
+}
+
+int read_int(mg_ctx* c, const int* d, int* out) {
+  cudaError_t e = cudaMemcpyAsync(out, d, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  return MG_OK;
+}
+
+// --- profiling ----------------------------------------------------------------
+
+cudaEvent_t ev_get(mg_ctx* c) {
+  if (!c->evpool.empty()) {
+    cudaEvent_t e = c->evpool.back();
+    c->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Counts `nk` kernel launches and, when profiling, brackets them with events
+// attributed to class `cls`.
+struct Launch {
+  mg_ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Launch(mg_ctx* ctx, int k, int nk) : c(ctx), cls(k) {
+    c->launches += nk;
+    if (c->prof) {
+      a = ev_get(c);
+      cudaEventRecord(a, c->st);
+    }
+  }
+  ~Launch() {
+    if (c->prof) {
+      cudaEvent_t b = ev_get(c);
+      cudaEventRecord(b, c->st);
+      c->pend.push_back({cls, a, b});
+    }
+  }
+};
+
+// Accumulates the finished event pairs (call after a stream synchronize).
+void harvest(mg_ctx* c) {
+  for (auto& p : c->pend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->kms[p.cls] += ms;
+      c->kcount[p.cls] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->evpool.push_back(p.a);
+    c->evpool.push_back(p.b);
+  }
+  c->pend.clear();
+}
+
+// Codes, boundary rows and tile lists of a level whose cells are ready.
+int build_nodes(mg_ctx* c, Level& V) {
+  const Layout& L = V.L;
+  const int ntiles = L.ntx * L.nty;
+  int *tile_cnt, *d_cnt, *tmp;
+  uint8_t* tile_active;
+  TRY(dalloc(c, &tile_cnt, ntiles));
+  TRY(dalloc(c, &V.tile_base, ntiles));
+  TRY(dalloc(c, &tile_active, ntiles));
+  TRY(dalloc(c, &d_cnt, 4));
+  size_t tmpn = scan_tmp_ints((size_t)ntiles);
+  int nbx = (V.n + 1 + 31) / 32, nby = nbx;
+  size_t tmpn2 = scan_tmp_ints((size_t)nbx * nby);
+  TRY(dalloc(c, &tmp, (tmpn > tmpn2 ? tmpn : tmpn2) + 8));
+  CellData cd{V.n, V.cls, V.cell_cut, V.Ke};
+  launch_tile_counts(cd, L, tile_cnt, tile_active, d_cnt + 0, c->st);
+  exclusive_scan_int(tile_cnt, V.tile_base, d_cnt + 1, (size_t)ntiles, tmp, c->st);
+  int h_cnt[2];
+  MG_CUDA_TRY(cudaMemcpyAsync(h_cnt, d_cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+  V.n_dof = h_cnt[0];
+  V.n_bnd = h_cnt[1];
+  TRY(dalloc(c, &V.code, L.size()));
+  TRY(dalloc(c, &V.rows64, (size_t)V.n_bnd * MG_ROW));
+  TRY(dalloc(c, &V.rows32, (size_t)V.n_bnd * MG_ROW));
+  TRY(dalloc(c, &V.bnode, (size_t)V.n_bnd));
+  launch_tile_assemble(cd, L, V.tile_base, V.code, V.rows64, V.bnode, c->d_err, c->st);
+  launch_rows_to_f32(V.rows64, V.rows32, (size_t)V.n_bnd * MG_ROW, c->st);
+  TRY(dalloc(c, &V.active, ntiles));
+  compact_flags_u8(tile_active, V.active, d_cnt + 2, (size_t)ntiles, tmp, nullptr, c->st);
+  TRY(read_int(c, d_cnt + 2, &V.n_active));
+  uint8_t* bflag;
+  TRY(dalloc(c, &bflag, (size_t)nbx * nby));
+  launch_band_flags(V.bnode, V.n_bnd, nbx, bflag, c->st);
+  TRY(dalloc(c, &V.band, (size_t)nbx * nby));
+  compact_flags_u8(bflag, V.band, d_cnt + 3, (size_t)nbx * nby, tmp, nullptr, c->st);
+  TRY(read_int(c, d_cnt + 3, &V.n_band));
+  V.nbx = nbx;
+  size_t sz = L.size();
+  TRY(dalloc(c, &V.u64[0], sz));
+  TRY(dalloc(c, &V.u64[1], sz));
+  TRY(dalloc(c, &V.F64, sz));
+  TRY(dalloc(c, &V.bval64, (size_t)V.n_bnd));
+  TRY(dalloc(c, &V.u32[0], sz));
+  TRY(dalloc(c, &V.u32[1], sz));
+  TRY(dalloc(c, &V.F32, sz));
+  TRY(dalloc(c, &V.bval32, (size_t)V.n_bnd));
+  return MG_OK;
+}
+
+int build_cut_list(mg_ctx* c, Level& V, const uint8_t* cut_flag) {
+  size_t ncell = (size_t)V.n * V.n;
+  int *cnt, *tmp;
+  TRY(dalloc(c, &cnt, 1));
+  TRY(dalloc(c, &tmp, scan_tmp_ints(ncell) + 8));
+  TRY(dalloc(c, &V.cut_list, ncell));
+  compact_flags_u8(cut_flag, V.cut_list, cnt, ncell, tmp, nullptr, c->st);
+  TRY(read_int(c, cnt, &V.n_cut));
+  TRY(dalloc(c, &V.cell_cut, ncell));
+  launch_fill_int(V.cell_cut, ncell, -1, c->st);
+  launch_scatter_cut_id(V.cut_list, V.n_cut, V.cell_cut, c->st);
+  TRY(dalloc(c, &V.Ke, (size_t)V.n_cut * 16));
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle driver, templated on the arithmetic type
+// ---------------------------------------------------------------------------
+
+template <class T> struct P;
+template <> struct P<double> {
+  static double* u(Level& v, int b) { return v.u64[b]; }
+  static double* F(Level& v) { return v.F64; }
+  static double* bval(Level& v) { return v.bval64; }
+  static const double* rows(Level& v) { return v.rows64; }
+  static int& cur(Level& v) { return v.cur64; }
+};
+template <> struct P<float> {
+  static float* u(Level& v, int b) { return v.u32[b]; }
+  static float* F(Level& v) { return v.F32; }
+  static float* bval(Level& v) { return v.bval32; }
+  static const float* rows(Level& v) { return v.rows32; }
+  static int& cur(Level& v) { return v.cur32; }
+};
+
+template <class T>
+OpArgs<T> op_of(Level& v) {
+  OpArgs<T> o;
+  o.L = v.L;
+  o.code = v.code;
+  o.tile_base = v.tile_base;
+  o.rows = P<T>::rows(v);
+  return o;
+}
+
+template <class T>
+void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine) {
+  OpArgs<T> op = op_of<T>(v);
+  int& cur = P<T>::cur(v);
+  const int eta = c->stab.eta;
+  {
+    Launch k(c, fine ? MG_PROF_SWEEP : MG_PROF_COARSE, v.n_active > 0);
+    launch_gs_sweep<T>(op, v.active, v.n_active, P<T>::u(v, cur), P<T>::u(v, cur ^ 1), P<T>::F(v),
+                       eta > 0 ? P<T>::bval(v) : (T*)nullptr, zero_in, c->st);
+  }
+  cur ^= 1;
+  if (eta > 0 && v.n_band > 0) {
+    Launch k(c, fine ? MG_PROF_BAND : MG_PROF_COARSE, 1);
+    launch_band<T>(op, v.band, v.n_band, v.nbx, eta, P<T>::u(v, cur), P<T>::F(v), P<T>::bval(v),
+                   c->st);
+  }
+}
+
+template <class T>
+void vcycle(mg_ctx* c, int l, bool zero_init) {
+  Level& v = c->lev[l];
+  const int nlev = (int)c->lev.size();
+  if (l == nlev - 1) {
+    Launch k(c, MG_PROF_COARSE, 1);
+    launch_coarse_solve<T>(v.L, c->Ainv, P<T>::F(v), P<T>::u(v, 0), c->st);
+    P<T>::cur(v) = 0;
+    return;
+  }
+  const bool fine = l == 0;
+  int& cur = P<T>::cur(v);
+  if (zero_init && c->stab.nu1 == 0)
+    cudaMemsetAsync(P<T>::u(v, cur), 0, v.L.size() * sizeof(T), c->st);
+  for (int s = 0; s < c->stab.nu1; ++s) smooth<T>(c, v, zero_init && s == 0, fine);
+  Level& w = c->lev[l + 1];
+  OpArgs<T> op = op_of<T>(v);
+  {
+    Launch k(c, fine ? MG_PROF_RESTRICT : MG_PROF_COARSE, w.n_active > 0);
+    launch_resid_restrict<T>(op, P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
+                             P<T>::F(w), nullptr, c->st);
+  }
+  vcycle<T>(c, l + 1, true);
+  {
+    Launch k(c, fine ? MG_PROF_PROLONG : MG_PROF_COARSE, v.n_active > 0);
+    launch_prolong<T>(op, v.active, v.n_active, P<T>::u(v, cur), w.L, P<T>::u(w, P<T>::cur(w)),
+                      c->st);
+  }
+  for (int s = 0; s < c->stab.nu2; ++s) smooth<T>(c, v, false, fine);
+}
+
+// ||F - A u||_inf of the fine level in fp64 (host value); optionally writes
+// sigma (F - A u) in fp32 to the fine level's fp32 right-hand side.
+int fine_residual(mg_ctx* c, double sigma, bool to_f32, double* rmax) {
+  Level& v = c->lev[0];
+  MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
+  OpArgs<double> op = op_of<double>(v);
+  {
+    Launch k(c, MG_PROF_RESIDUAL, v.n_active > 0);
+    if (to_f32)
+      launch_residual<double, float>(op, v.active, v.n_active, v.u64[v.cur64], v.F64, v.F32,
+                                     sigma, c->d_norms, c->st);
+    else
+      launch_residual<double, double>(op, v.active, v.n_active, v.u64[v.cur64], v.F64,
+                                      (double*)nullptr, 1.0, c->d_norms, c->st);
+  }
+  MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->st));
+  MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (c->prof) harvest(c);
+  *rmax = c->h_norms[0];
+  return MG_OK;
+}
+
+double pow2_near_inverse(double x) {
+  if (!(x > 0.0) || !std::isfinite(x)) return 1.0;
+  int e;
+  std::frexp(x, &e);
+  return std::ldexp(1.0, -e);
+}
+
+// One refinement step: r = F - A u (fp64) -> sigma r in fp32, one fp32
+// V-cycle from e = 0, u += e / sigma.  rmax is ||F - A u||_inf before it.
+void refinement_step(mg_ctx* c, double sigma) {
+  Level& v = c->lev[0];
+  vcycle<float>(c, 0, true);
+  Launch k(c, MG_PROF_UPDATE, v.n_active > 0);
+  launch_update(v.L, v.active, v.n_active, v.code, v.u64[v.cur64], v.u32[v.cur32], 1.0 / sigma,
+                c->st);
+}
+
+// Cycles from the current fine-level u64 with F64 set; Fn = ||F||_inf.
+// In MG_MIXED the fp32 residual is scaled by a power of two sigma chosen
+// from the previous residual norm (times an expected reduction of 0.1), so
+// the fp32 V-cycle works on O(1) values; the update divides by the same
+// sigma exactly.
+int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info) {
+  const bool mixed = c->stab.precision == MG_MIXED;
+  double rmax;
+  int k = 0, grow = 0, status = MG_OK;
+  double sigma = mixed ? pow2_near_inverse(Fn) : 1.0;
+  TRY(fine_residual(c, sigma, mixed, &rmax));
+  double rel = rmax / Fn, prev = rel;
+  if (info) info->res_hist[0] = rel;
+  while (rel > tol) {
+    if (k >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
+    if (mixed) refinement_step(c, sigma);
+    else vcycle<double>(c, 0, false);
+    ++k;
+    if (mixed) sigma = pow2_near_inverse(rmax * 0.1);
+    TRY(fine_residual(c, sigma, mixed, &rmax));
+    rel = rmax / Fn;
+    if (info && k < 64) info->res_hist[k] = rel;
+    if (!std::isfinite(rel)) { status = MG_ERR_DIVERGED; break; }
+    grow = rel > prev ? grow + 1 : 0;
+    if (grow >= 3) { status = MG_ERR_DIVERGED; break; }
+    prev = rel;
+  }
+  if (info) {
+    info->cycles = k;
+    info->rel_res = rel;
+  }
+  return status;
+}
+
+struct Staged {
+  const double* dev = nullptr;
+  bool host = false;
+};
+
+int stage_in(mg_ctx* c, int slot, const double* p, Staged& s) {
+  size_t m = (size_t)(c->N + 1) * (c->N + 1);
+  if (is_device_ptr(p)) {
+    s.dev = p;
+    s.host = false;
+    return MG_OK;
+  }
+  if (!c->stage[slot]) TRY(dalloc(c, &c->stage[slot], m));
+  MG_CUDA_TRY(cudaMemcpyAsync(c->stage[slot], p, m * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  s.dev = c->stage[slot];
+  s.host = true;
+  return MG_OK;
+}
+
+// output pointer: device pointer as is, host pointer via a staging slot
+int stage_out(mg_ctx* c, int slot, double* p, double** dev, bool* host) {
+  size_t m = (size_t)(c->N + 1) * (c->N + 1);
+  if (is_device_ptr(p)) {
+    *dev = p;
+    *host = false;
+    return MG_OK;
+  }
+  if (!c->stage[slot]) TRY(dalloc(c, &c->stage[slot], m));
+  *dev = c->stage[slot];
+  *host = true;
+  return MG_OK;
+}
+
+int finish_out(mg_ctx* c, double* user, const double* dev, bool host) {
+  size_t m = (size_t)(c->N + 1) * (c->N + 1);
+  if (host)
+    MG_CUDA_TRY(cudaMemcpyAsync(user, dev, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  return MG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// public API
+// ===========================================================================
+
+extern "C" {
+
+int mg_default_stab(mg_stab* out) {
+  if (!out) return MG_ERR_INVALID_ARG;
+  out->gamma = 2.0;
+  out->alpha = 1.75;
+  out->eta = 4;
+  out->nu1 = 2;
+  out->nu2 = 1;
+  out->lambda_mode = MG_LAMBDA_LOCAL;
+  out->precision = MG_FP64;
+  out->max_cycles = 100;
+  return MG_OK;
+}
+
+const char* mg_strerror(int code) {
+  switch (code) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID_ARG: return "invalid argument";
+    case MG_ERR_CUDA: return g_cuda_msg[0] ? g_cuda_msg : "CUDA error";
+    case MG_ERR_NOT_CONVERGED: return "not converged within max_cycles";
+    case MG_ERR_DIVERGED: return "diverged";
+    case MG_ERR_NOT_SPD: return "coarsest matrix not positive definite";
+    case MG_ERR_TIMEOUT: return "device wait timed out";
+    case MG_ERR_UNIMPLEMENTED: return "not implemented";
+    case MG_ERR_INTERNAL: return "internal error";
+    case MG_ERR_OUT_OF_MEMORY: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+void mg_destroy(mg_handle c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_norms) cudaFreeHost(c->h_norms);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  harvest(c);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  delete c;
+}
+
+static int setup_impl(mg_ctx* c, const double* levelset) {
+  const int N = c->N;
+  MG_CUDA_TRY(cudaMallocHost((void**)&c->h_norms, 16 * sizeof(double)));
+  MG_CUDA_TRY(cudaEventCreate(&c->ev0));
+  MG_CUDA_TRY(cudaEventCreate(&c->ev1));
+  TRY(dalloc(c, &c->d_err, 4));
+  TRY(dalloc(c, &c->d_norms, 16));
+  // level set on the device
+  Staged ps;
+  TRY(stage_in(c, 0, levelset, ps));
+  TRY(dalloc(c, &c->psi_s, (size_t)(N + 1) * (N + 1)));
+  launch_snap(ps.dev, c->psi_s, N, std::pow(c->h, c->stab.alpha), c->d_err, c->st);
+  // fine level cells
+  c->lev.emplace_back();
+  {
+    Level& v = c->lev[0];
+    v.n = N;
+    v.L = make_layout(N);
+    uint8_t* cut_flag;
+    TRY(dalloc(c, &v.cls, (size_t)N * N));
+    TRY(dalloc(c, &cut_flag, (size_t)N * N));
+    launch_cell_class(c->psi_s, N, v.cls, cut_flag, c->st);
+    TRY(sync_check(c));
+    TRY(build_cut_list(c, v, cut_flag));
+    TRY(dalloc(c, &c->Mk, (size_t)v.n_cut * 16));
+    TRY(dalloc(c, &c->Gk, (size_t)v.n_cut * 16));
+    TRY(dalloc(c, &c->Cl, (size_t)v.n_cut * 4));
+    TRY(dalloc(c, &c->cfg, (size_t)v.n_cut));
+    launch_cut_cells(c->psi_s, N, c->h, c->stab.gamma, v.cut_list, v.n_cut, v.Ke, c->Mk, c->Gk,
+                     c->Cl, c->cfg, c->st);
+    TRY(build_nodes(c, v));
+  }
+  // coarse levels by element-wise Galerkin products
+  while (c->lev.back().n > c->grid.coarsest_cells) {
+    c->lev.emplace_back();
+    Level& f = c->lev[c->lev.size() - 2];
+    Level& v = c->lev.back();
+    v.n = f.n / 2;
+    v.L = make_layout(v.n);
+    uint8_t* cut_flag;
+    TRY(dalloc(c, &v.cls, (size_t)v.n * v.n));
+    TRY(dalloc(c, &cut_flag, (size_t)v.n * v.n));
+    launch_coarse_class(f.cls, f.n, v.cls, cut_flag, c->st);
+    TRY(build_cut_list(c, v, cut_flag));
+    CellData fd{f.n, f.cls, f.cell_cut, f.Ke};
+    launch_coarse_cut(fd, v.cut_list, v.n_cut, v.n, v.Ke, c->st);
+    TRY(build_nodes(c, v));
+  }
+  {
+    Level& v = c->lev.back();
+    int m = (v.n + 1) * (v.n + 1);
+    TRY(dalloc(c, &c->Adense, (size_t)m * m));
+    TRY(dalloc(c, &c->Ainv, (size_t)m * m));
+    CellData cd{v.n, v.cls, v.cell_cut, v.Ke};
+    launch_coarsest(cd, c->Adense, c->Ainv, c->d_err, c->st);
+  }
+  MG_CUDA_TRY(configure_kernels<double>(c->stab.eta));
+  MG_CUDA_TRY(configure_kernels<float>(c->stab.eta));
+  TRY(sync_check(c));
+  return MG_OK;
+}
+
+int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const mg_bc* bc,
+             const mg_stab* stab, void* cuda_stream) {
+  if (!out) return MG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!levelset || !grid) return MG_ERR_INVALID_ARG;
+  mg_stab s;
+  mg_default_stab(&s);
+  if (stab) s = *stab;
+  if (bc && (bc->kind != MG_BC_DIRICHLET || bc->neumann_mask)) return MG_ERR_UNIMPLEMENTED;
+  mg_grid g = *grid;
+  if (g.coarsest_cells <= 0) g.coarsest_cells = 8;
+  if (!pow2(g.n_cells) || g.n_cells < 8 || g.n_cells > 32768) return MG_ERR_INVALID_ARG;
+  if (!pow2(g.coarsest_cells) || g.coarsest_cells < 2 || g.coarsest_cells > 32 ||
+      g.coarsest_cells > g.n_cells)
+    return MG_ERR_INVALID_ARG;
+  if (!(g.h > 0.0) || !std::isfinite(g.h) || !std::isfinite(g.x0) || !std::isfinite(g.y0))
+    return MG_ERR_INVALID_ARG;
+  if (!(s.gamma > 0.0) || !(s.alpha > 0.0) || s.eta < 0 || s.eta > 8 || s.nu1 < 0 || s.nu1 > 8 ||
+      s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0)
+    return MG_ERR_INVALID_ARG;
+  if (s.lambda_mode != MG_LAMBDA_LOCAL) return MG_ERR_UNIMPLEMENTED;
+  if (s.precision != MG_FP64 && s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
+  mg_ctx* c = new mg_ctx();
+  c->st = (cudaStream_t)cuda_stream;
+  c->grid = g;
+  c->stab = s;
+  c->N = g.n_cells;
+  c->h = g.h;
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = setup_impl(c, levelset);
+  if (rc != MG_OK) {
+    mg_destroy(c);
+    return rc;
+  }
+  c->setup_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = c;
+  return MG_OK;
+}
+
+int mg_get_counts(mg_handle c, int* n_levels, int* n_dof, int* n_cut, int* n_boundary) {
+  if (!c) return MG_ERR_INVALID_ARG;
+  if (n_levels) *n_levels = (int)c->lev.size();
+  if (n_dof) *n_dof = c->lev[0].n_dof;
+  if (n_cut) *n_cut = c->lev[0].n_cut;
+  if (n_boundary) *n_boundary = c->lev[0].n_bnd;
+  return MG_OK;
+}
+
+int mg_level_cells(mg_handle c, int level) {
+  if (!c || level < 0 || level >= (int)c->lev.size()) return -1;
+  return c->lev[level].n;
+}
+
+static int fill_info(mg_ctx* c, mg_info* info) {
+  if (!info) return MG_OK;
+  info->n_dof = c->lev[0].n_dof;
+  info->n_cut = c->lev[0].n_cut;
+  info->n_levels = (int)c->lev.size();
+  info->setup_ms = c->setup_ms;
+  info->solve_ms = c->solve_ms;
+  return MG_OK;
+}
+
+int mg_solve(mg_handle c, const double* f, const double* g, double* u, double tol, mg_info* info) {
+  if (!c || !f || !g || !u || !(tol >= 0.0)) return MG_ERR_INVALID_ARG;
+  if (info) memset(info, 0, sizeof(*info));
+  c->last_tol = tol;
+  Level& v = c->lev[0];
+  MG_CUDA_TRY(cudaEventRecord(c->ev0, c->st));
+  Staged sf, sg, su;
+  TRY(stage_in(c, 0, f, sf));
+  TRY(stage_in(c, 1, g, sg));
+  TRY(stage_in(c, 2, u, su));
+  size_t m = (size_t)(c->N + 1) * (c->N + 1);
+  MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
+  {
+    Launch k(c, MG_PROF_IO, 4);
+    launch_check_finite(sf.dev, m, c->d_err, c->st);
+    launch_check_finite(sg.dev, m, c->d_err, c->st);
+    RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
+    launch_rhs(ra, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
+    v.cur64 = 0;
+    launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st);
+  }
+  MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->st));
+  TRY(sync_check(c));
+  double Fn = c->h_norms[0];
+  int status = MG_OK;
+  if (Fn == 0.0) {
+    // F = 0: the solution is u = 0
+    MG_CUDA_TRY(cudaMemsetAsync(v.u64[0], 0, v.L.size() * sizeof(double), c->st));
+    if (info) info->rel_res = 0.0;
+  } else {
+    status = solve_loop(c, Fn, tol, c->stab.max_cycles, info);
+    if (status == MG_ERR_CUDA) return status;
+  }
+  double* ud = const_cast<double*>(su.dev);
+  {
+    Launch k(c, MG_PROF_IO, 1);
+    launch_unpack(v.L, v.code, v.u64[v.cur64], ud, c->st);
+  }
+  if (su.host) TRY(finish_out(c, u, ud, true));
+  MG_CUDA_TRY(cudaEventRecord(c->ev1, c->st));
+  TRY(sync_check(c));
+  harvest(c);
+  MG_CUDA_TRY(cudaEventElapsedTime(&c->solve_ms, c->ev0, c->ev1));
+  fill_info(c, info);
+  return status;
+}
+
+int mg_rhs(mg_handle c, const double* f, const double* g, double* F) {
+  if (!c || !f || !g || !F) return MG_ERR_INVALID_ARG;
+  Level& v = c->lev[0];
+  Staged sf, sg;
+  TRY(stage_in(c, 0, f, sf));
+  TRY(stage_in(c, 1, g, sg));
+  double* Fd;
+  bool Fh;
+  TRY(stage_out(c, 2, F, &Fd, &Fh));
+  MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
+  RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
+  launch_rhs(ra, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
+  launch_unpack(v.L, v.code, v.F64, Fd, c->st);
+  TRY(finish_out(c, F, Fd, Fh));
+  return sync_check(c);
+}
+
+int mg_cycles(mg_handle c, const double* F, double* u, int k, int precision) {
+  if (!c || !F || !u || k < 0) return MG_ERR_INVALID_ARG;
+  if (precision != MG_FP64 && precision != MG_MIXED) return MG_ERR_INVALID_ARG;
+  Level& v = c->lev[0];
+  Staged sF, su;
+  TRY(stage_in(c, 0, F, sF));
+  TRY(stage_in(c, 2, u, su));
+  launch_pack<double>(v.L, v.code, sF.dev, v.F64, c->d_err, c->st);
+  v.cur64 = 0;
+  launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st);
+  for (int s = 0; s < k; ++s) {
+    if (precision == MG_FP64) {
+      vcycle<double>(c, 0, false);
+    } else {
+      double rmax;
+      // scale by the residual's magnitude (exact power of two)
+      TRY(fine_residual(c, 1.0, false, &rmax));
+      double sigma = pow2_near_inverse(rmax);
+      OpArgs<double> op = op_of<double>(v);
+      launch_residual<double, float>(op, v.active, v.n_active, v.u64[v.cur64], v.F64, v.F32, sigma,
+                                     (double*)nullptr, c->st);
+      refinement_step(c, sigma);
+    }
+  }
+  double* ud = const_cast<double*>(su.dev);
+  launch_unpack(v.L, v.code, v.u64[v.cur64], ud, c->st);
+  if (su.host) TRY(finish_out(c, u, ud, true));
+  return sync_check(c);
+}
+
+int mg_residual(mg_handle c, const double* F, const double* u, double* r, double* norms) {
+  if (!c || !F || !u) return MG_ERR_INVALID_ARG;
+  Level& v = c->lev[0];
+  Staged sF, su;
+  TRY(stage_in(c, 0, F, sF));
+  TRY(stage_in(c, 1, u, su));
+  launch_pack<double>(v.L, v.code, sF.dev, v.F64, c->d_err, c->st);
+  v.cur64 = 0;
+  launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st);
+  MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
+  OpArgs<double> op = op_of<double>(v);
+  launch_residual<double, double>(op, v.active, v.n_active, v.u64[0], v.F64, v.u64[1], 1.0,
+                                  c->d_norms, c->st);
+  if (r) {
+    double* rd;
+    bool rh;
+    TRY(stage_out(c, 2, r, &rd, &rh));
+    launch_unpack(v.L, v.code, v.u64[1], rd, c->st);
+    TRY(finish_out(c, r, rd, rh));
+  }
+  MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->st));
+  TRY(sync_check(c));
+  if (norms) {
+    norms[0] = c->h_norms[0];
+    norms[1] = std::sqrt(c->h_norms[1]);
+  }
+  return MG_OK;
+}
+
+int mg_export_stencil(mg_handle c, int level, double* out) {
+  if (!c || !out || level < 0 || level >= (int)c->lev.size()) return MG_ERR_INVALID_ARG;
+  Level& v = c->lev[level];
+  size_t m = (size_t)(v.n + 1) * (v.n + 1) * 9;
+  double* d = out;
+  bool host = !is_device_ptr(out);
+  if (host) MG_CUDA_TRY(cudaMalloc((void**)&d, m * sizeof(double)));
+  launch_export_stencil<double>(op_of<double>(v), d, c->st);
+  int rc = MG_OK;
+  if (host) {
+    cudaError_t e = cudaMemcpyAsync(out, d, m * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(d);
+    if (e != cudaSuccess) rc = mg_cuda_fail(e);
+  }
+  if (rc != MG_OK) return rc;
+  return sync_check(c);
+}
+
+int mg_export_cut_cells(mg_handle c, int max_cells, int* cells, double* data, int* n_total) {
+  if (!c || max_cells < 0) return MG_ERR_INVALID_ARG;
+  Level& v = c->lev[0];
+  if (n_total) *n_total = v.n_cut;
+  int m = max_cells < v.n_cut ? max_cells : v.n_cut;
+  if (m == 0) return MG_OK;
+  std::vector<int> hc(m);
+  std::vector<double> cl((size_t)m * 4), ke((size_t)m * 16), mk((size_t)m * 16), gk((size_t)m * 16);
+  MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+  MG_CUDA_TRY(cudaMemcpy(hc.data(), v.cut_list, m * sizeof(int), cudaMemcpyDeviceToHost));
+  MG_CUDA_TRY(cudaMemcpy(cl.data(), c->Cl, cl.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  MG_CUDA_TRY(cudaMemcpy(ke.data(), v.Ke, ke.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  MG_CUDA_TRY(cudaMemcpy(mk.data(), c->Mk, mk.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  MG_CUDA_TRY(cudaMemcpy(gk.data(), c->Gk, gk.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  std::vector<double> d((size_t)m * 52);
+  for (int t = 0; t < m; ++t) {
+    double* o = d.data() + (size_t)t * 52;
+    for (int q = 0; q < 4; ++q) o[q] = cl[(size_t)t * 4 + q];
+    for (int q = 0; q < 16; ++q) {
+      o[4 + q] = ke[(size_t)t * 16 + q];
+      o[20 + q] = mk[(size_t)t * 16 + q];
+      o[36 + q] = gk[(size_t)t * 16 + q];
+    }
+  }
+  if (cells) {
+    if (is_device_ptr(cells))
+      MG_CUDA_TRY(cudaMemcpy(cells, hc.data(), m * sizeof(int), cudaMemcpyHostToDevice));
+    else
+      memcpy(cells, hc.data(), m * sizeof(int));
+  }
+  if (data) {
+    if (is_device_ptr(data))
+      MG_CUDA_TRY(cudaMemcpy(data, d.data(), d.size() * sizeof(double), cudaMemcpyHostToDevice));
+    else
+      memcpy(data, d.data(), d.size() * sizeof(double));
+  }
+  return MG_OK;
+}
+
+int mg_set_profiling(mg_handle c, int enable) {
+  if (!c) return MG_ERR_INVALID_ARG;
+  MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+  harvest(c);
+  if (enable) {
+    for (int k = 0; k < MG_PROF_SLOTS; ++k) { c->kcount[k] = 0; c->kms[k] = 0.0; }
+    c->launches = 0;
+  }
+  c->prof = enable != 0;
+  return MG_OK;
+}
+
+int mg_get_profile(mg_handle c, long long* launches, long long* counts, double* ms) {
+  if (!c) return MG_ERR_INVALID_ARG;
+  MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+  harvest(c);
+  if (launches) *launches = c->launches;
+  for (int k = 0; k < MG_PROF_SLOTS; ++k) {
+    if (counts) counts[k] = c->kcount[k];
+    if (ms) ms[k] = c->kms[k];
+  }
+  return MG_OK;
+}
+
+int mg_adjoint(mg_handle c, const double* dLdu, double* dLdf, double* dLdg) {
+  if (!c || !dLdu) return MG_ERR_INVALID_ARG;
+  return MG_ERR_UNIMPLEMENTED;
+}
+
+}  // extern "C"

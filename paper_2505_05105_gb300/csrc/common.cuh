@@ -1,0 +1,135 @@
+// Shared definitions of the ghost-FEM multigrid library (CUDA, sm_103a).
+//
+// Node layout of every level (n cells per side, nodes 0..n in each direction):
+// a padded row-major array, node (i, j) at (j + MG_G) * pitch + (i + MG_G).
+// The node index of Sec. 5.1, k = i + j (n+1), is the unpadded version of the
+// same row-major order.  Everything outside [0, n]^2 holds zero (code 0), so
+// stencil kernels read halos without bounds checks.
+//
+// Per node a uint16 "code": 0 = not a DOF, 1 = interior DOF (all four adjacent
+// cells internal: constant Q1 stencil 8/3, -1/3), >= 2 = boundary DOF (vertex
+// of a cut cell), whose 9-point row is row[tile_base[tile] + code - 2] in a
+// table compacted per 64 x 32 node tile.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#define MG_TX 64          // tile width in nodes
+#define MG_TY 32          // tile height in nodes
+#define MG_G 8            // zero margin around the node array
+#define MG_ROW 10         // boundary row: 9 stencil coefficients + 1/diagonal
+
+// 3 x 3 stencil offset order used by boundary rows: s = (di + 1) + 3 (dj + 1)
+
+enum CellClass : uint8_t { CELL_EXT = 0, CELL_INT = 1, CELL_CUT = 2 };
+
+// device error bits (ORed into a device word, turned into status codes)
+enum : unsigned {
+  DEV_ERR_NAN = 1u,          // NaN / Inf in an input array
+  DEV_ERR_EDGE = 2u,         // Omega_h touches the outer ring of the box
+  DEV_ERR_NOT_SPD = 4u,      // coarsest Cholesky pivot <= 0
+  DEV_ERR_TILE = 8u,         // more boundary nodes in a tile than codes allow
+  DEV_ERR_GEOM = 16u,        // unexpected cut configuration
+};
+
+struct Layout {
+  int n;       // cells per side
+  int ntx;     // tiles along x covering nodes 0..n
+  int nty;
+  int pitch;   // elements per padded row
+  int rows;    // padded rows
+  __host__ __device__ __forceinline__ size_t idx(int i, int j) const {
+    return (size_t)(j + MG_G) * (size_t)pitch + (size_t)(i + MG_G);
+  }
+  __host__ __device__ __forceinline__ size_t size() const {
+    return (size_t)pitch * (size_t)rows;
+  }
+  __host__ __device__ __forceinline__ int tile_of(int i, int j) const {
+    return (j / MG_TY) * ntx + (i / MG_TX);
+  }
+};
+
+inline Layout make_layout(int n) {
+  Layout L;
+  L.n = n;
+  L.ntx = (n + 1 + MG_TX - 1) / MG_TX;
+  L.nty = (n + 1 + MG_TY - 1) / MG_TY;
+  // one spare tile column/row so that regions of the next finer level's
+  // restriction blocks stay inside the allocation
+  int w = (L.ntx + 1) * MG_TX + 2 * MG_G;
+  L.pitch = (w + 31) / 32 * 32;
+  L.rows = (L.nty + 1) * MG_TY + 2 * MG_G;
+  return L;
+}
+
+// Operator data of one level, precision independent part.
+struct LevelOp {
+  Layout L;
+  const uint16_t* code;     // padded layout
+  const int* tile_base;     // per tile: first boundary row
+};
+
+template <class T> struct Vec2;
+template <> struct Vec2<double> { typedef double2 type; };
+template <> struct Vec2<float> { typedef float2 type; };
+
+// Block-wide reductions ------------------------------------------------------
+
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// non-negative doubles order like their bit patterns
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr),
+            (unsigned long long)__double_as_longlong(v));
+}
+
+// Reduce (max, sum) over the block and add to out[0] (max) / out[1] (sum).
+// Requires blockDim.x a multiple of 32, <= 1024.
+__device__ __forceinline__ void block_norms_to_global(double vmax, double vsum, double* out) {
+  __shared__ double s_max[32], s_sum[32];
+  vmax = warp_max(vmax);
+  vsum = warp_sum(vsum);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { s_max[w] = vmax; s_sum[w] = vsum; }
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    vmax = l < nw ? s_max[l] : 0.0;
+    vsum = l < nw ? s_sum[l] : 0.0;
+    vmax = warp_max(vmax);
+    vsum = warp_sum(vsum);
+    if (l == 0) {
+      atomic_max_nonneg(out, vmax);
+      atomicAdd(out + 1, vsum);
+    }
+  }
+}
+
+// Host helpers ----------------------------------------------------------------
+
+#define MG_CUDA_TRY(expr)                                  \
+  do {                                                     \
+    cudaError_t e__ = (expr);                              \
+    if (e__ != cudaSuccess) return mg_cuda_fail(e__);      \
+  } while (0)
+
+int mg_cuda_fail(cudaError_t e);   // records the message, returns MG_ERR_CUDA
+
+// scan.cu: exclusive scan / compaction on the device
+// out[i] = sum_{k<i} in[i]; *total (device) = sum of all.  tmp must hold
+// scan_tmp_ints(n) ints.
+size_t scan_tmp_ints(size_t n);
+void exclusive_scan_int(const int* in, int* out, int* total, size_t n, int* tmp,
+                        cudaStream_t st);
+// list of indices i with flag[i] != 0, in increasing order; *count on device
+void compact_flags_u8(const uint8_t* flag, int* list, int* count, size_t n, int* tmp,
+                      int* tmp_offsets, cudaStream_t st);

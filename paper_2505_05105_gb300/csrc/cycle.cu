@@ -1,0 +1,594 @@
+// V-cycle kernels (Alg. 1 applied recursively, Sec. 3.2) for one level of
+// the ghost-FEM hierarchy, templated on the arithmetic type T (double or
+// float).  All are matrix-free stencil passes over 64 x 32 node tiles:
+//
+//   k_gs_sweep        one Gauss-Seidel sweep (Sec. 4.1), 4 colours
+//                     (i mod 2, j mod 2) in the order (0,0),(1,0),(0,1),(1,1),
+//                     temporally blocked in shared memory with a 4-node halo;
+//                     reads u_in, writes u_out (ping-pong buffers)
+//   k_band            the eta extra sweeps restricted to the vertices of cut
+//                     cells (Sec. 5.3), 4 eta colour phases per 32 x 32 band
+//                     tile with a (4 eta + 1)-node halo, in place
+//   k_resid_restrict  r = F - A u and r_2h = P^T r (Sec. 5.1 weights 1, 1/2,
+//                     1/4), optionally with ||r||_inf and ||r||_2^2
+//   k_residual        r = F - A u on one level with norms, optional scaled
+//                     copy of r in another precision (refinement residual)
+//   k_prolong         u += P e_2h on the DOFs (bilinear interpolation)
+//   k_coarse_solve    u = A^{-1} F on the coarsest level (dense inverse)
+//   k_rhs             F = M f + G g (Eq. disc_rhs with Q1 interpolants)
+#include "cycle.cuh"
+
+namespace {
+
+constexpr int SW_H = 4;
+constexpr int SW_RX = MG_TX + 2 * SW_H;   // 72
+constexpr int SW_RY = MG_TY + 2 * SW_H;   // 40
+constexpr int SW_PX = SW_RX / 2;          // 36
+constexpr int SW_PY = SW_RY / 2;          // 20
+constexpr int SW_PLANE = SW_PX * SW_PY;   // nodes per parity plane
+constexpr int kThreads = 256;
+
+template <class T>
+__device__ __forceinline__ const T* row_of(const OpArgs<T>& op, int i, int j, int cd) {
+  int r = op.tile_base[op.L.tile_of(i, j)] + cd - 2;
+  return op.rows + (size_t)r * MG_ROW;
+}
+
+template <class T, bool ZERO_IN>
+__global__ void __launch_bounds__(kThreads)
+k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ uin,
+           T* __restrict__ uout, const T* __restrict__ F, T* __restrict__ bval) {
+  typedef typename Vec2<T>::type T2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);            // [4][PY][PX] parity planes
+  T* sF = sU + 4 * SW_PLANE;
+  uint16_t* sC = reinterpret_cast<uint16_t*>(sF + 4 * SW_PLANE);
+
+  const int t = tiles[blockIdx.x];
+  const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
+  const int ri0 = i0 - SW_H, rj0 = j0 - SW_H;
+
+  for (int it = threadIdx.x; it < SW_RY * SW_PX; it += blockDim.x) {
+    int rj = it / SW_PX, a = it - rj * SW_PX;
+    size_t g = op.L.idx(ri0 + 2 * a, rj0 + rj);
+    int pl = (rj & 1) * 2 * SW_PLANE + (rj >> 1) * SW_PX + a;
+    T2 f2 = *reinterpret_cast<const T2*>(F + g);
+    sF[pl] = f2.x;
+    sF[pl + SW_PLANE] = f2.y;
+    if (ZERO_IN) {
+      sU[pl] = T(0);
+      sU[pl + SW_PLANE] = T(0);
+    } else {
+      T2 u2 = *reinterpret_cast<const T2*>(uin + g);
+      sU[pl] = u2.x;
+      sU[pl + SW_PLANE] = u2.y;
+    }
+    uint32_t c2 = *reinterpret_cast<const uint32_t*>(op.code + g);
+    sC[pl] = (uint16_t)(c2 & 0xffffu);
+    sC[pl + SW_PLANE] = (uint16_t)(c2 >> 16);
+  }
+  __syncthreads();
+
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    const int ci = k & 1, cj = k >> 1;
+    T* P = sU + (cj * 2 + ci) * SW_PLANE;
+    const T* PXn = sU + (cj * 2 + (ci ^ 1)) * SW_PLANE;
+    const T* PYn = sU + ((cj ^ 1) * 2 + ci) * SW_PLANE;
+    const T* PDn = sU + ((cj ^ 1) * 2 + (ci ^ 1)) * SW_PLANE;
+    const T* PF = sF + (cj * 2 + ci) * SW_PLANE;
+    const uint16_t* PC = sC + (cj * 2 + ci) * SW_PLANE;
+    const int lo = k + 1, hix = SW_RX - 1 - k, hiy = SW_RY - 1 - k;
+    for (int it = threadIdx.x; it < SW_PLANE; it += blockDim.x) {
+      int b = it / SW_PX, a = it - b * SW_PX;
+      int ri = 2 * a + ci, rj = 2 * b + cj;
+      if (ri < lo || ri >= hix || rj < lo || rj >= hiy) continue;
+      uint16_t cd = PC[it];
+      if (cd == 0) continue;
+      int xm = a + ci - 1, xp = a + ci, ym = b + cj - 1, yp = b + cj;
+      T w = PXn[b * SW_PX + xm], e = PXn[b * SW_PX + xp];
+      T s = PYn[ym * SW_PX + a], n = PYn[yp * SW_PX + a];
+      T sw = PDn[ym * SW_PX + xm], se = PDn[ym * SW_PX + xp];
+      T nw = PDn[yp * SW_PX + xm], ne = PDn[yp * SW_PX + xp];
+      T f = PF[it];
+      T unew;
+      if (cd == 1) {
+        // interior row: 8/3 u_p - 1/3 (sum of 8 neighbours) = F_p
+        unew = (T(3) * f + ((w + e) + (s + n)) + ((sw + se) + (nw + ne))) * T(0.125);
+      } else {
+        const T* R = row_of(op, ri0 + ri, rj0 + rj, cd);
+        T uc = P[it];
+        T acc = R[0] * sw + R[1] * s + R[2] * se + R[3] * w + R[4] * uc + R[5] * e +
+                R[6] * nw + R[7] * n + R[8] * ne;
+        unew = uc + (f - acc) * R[9];
+      }
+      P[it] = unew;
+    }
+    __syncthreads();
+  }
+
+  const int base = op.tile_base[t];
+  for (int it = threadIdx.x; it < MG_TY * (MG_TX / 2); it += blockDim.x) {
+    int rr = it / (MG_TX / 2), a2 = it - rr * (MG_TX / 2);
+    int rj = SW_H + rr, a = SW_H / 2 + a2;
+    int pl = (rj & 1) * 2 * SW_PLANE + (rj >> 1) * SW_PX + a;
+    T2 v;
+    v.x = sU[pl];
+    v.y = sU[pl + SW_PLANE];
+    *reinterpret_cast<T2*>(uout + op.L.idx(i0 + 2 * a2, j0 + rr)) = v;
+    if (bval) {
+      uint16_t c0 = sC[pl], c1 = sC[pl + SW_PLANE];
+      if (c0 >= 2) bval[base + c0 - 2] = v.x;
+      if (c1 >= 2) bval[base + c1 - 2] = v.y;
+    }
+  }
+}
+
+// Extra Gauss-Seidel sweeps on the cut-cell vertices (boundary nodes).  Each
+// block owns the boundary nodes of a 32 x 32 band tile and recomputes the
+// 4 eta colour phases redundantly on a halo of 4 eta + 1 nodes, so the owned
+// values equal those of the global sweep.  Boundary values are read from
+// bval (written by the preceding full sweep) and never from u, which other
+// blocks update concurrently.
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __restrict__ u,
+       const T* __restrict__ F, const T* __restrict__ bval) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int H = 4 * eta + 1;
+  const int RB = 32 + 2 * H;
+  const int cap = ((RB + 1) / 2) * ((RB + 1) / 2);
+  T* sU = reinterpret_cast<T*>(smem_raw);
+  uint16_t* sC = reinterpret_cast<uint16_t*>(sU + RB * RB);
+  uint16_t* sL = sC + RB * RB;                      // [4][cap]
+  __shared__ int cnt[4];
+  if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+  const int bt = btiles[blockIdx.x];
+  const int bi0 = (bt % nbx) * 32 - H, bj0 = (bt / nbx) * 32 - H;
+  const int n = op.L.n;
+  __syncthreads();
+  for (int p = threadIdx.x; p < RB * RB; p += blockDim.x) {
+    int y = p / RB, x = p - y * RB;
+    int gi = bi0 + x, gj = bj0 + y;
+    uint16_t cd = 0;
+    T v = T(0);
+    if (gi >= 0 && gj >= 0 && gi <= n && gj <= n) {
+      size_t g = op.L.idx(gi, gj);
+      cd = op.code[g];
+      if (cd >= 2) {
+        int r = op.tile_base[op.L.tile_of(gi, gj)] + cd - 2;
+        v = bval[r];
+        if (x > 0 && y > 0 && x < RB - 1 && y < RB - 1) {
+          int c = (gi & 1) + 2 * (gj & 1);
+          int pos = atomicAdd(&cnt[c], 1);
+          sL[c * cap + pos] = (uint16_t)p;
+        }
+      } else {
+        v = u[g];
+      }
+    }
+    sU[p] = v;
+    sC[p] = cd;
+  }
+  __syncthreads();
+  for (int ph = 0; ph < 4 * eta; ++ph) {
+    const int c = ph & 3;
+    const int m = cnt[c];
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+      int p = sL[c * cap + e];
+      int y = p / RB, x = p - y * RB;
+      int gi = bi0 + x, gj = bj0 + y;
+      const T* R = row_of(op, gi, gj, sC[p]);
+      const T* Up = sU + p;
+      T acc = R[0] * Up[-RB - 1] + R[1] * Up[-RB] + R[2] * Up[-RB + 1] + R[3] * Up[-1] +
+              R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[RB - 1] + R[7] * Up[RB] + R[8] * Up[RB + 1];
+      T f = F[op.L.idx(gi, gj)];
+      sU[p] = Up[0] + (f - acc) * R[9];
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < 4; ++c) {
+    const int m = cnt[c];
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+      int p = sL[c * cap + e];
+      int y = p / RB, x = p - y * RB;
+      if (x >= H && x < H + 32 && y >= H && y < H + 32)
+        u[op.L.idx(bi0 + x, bj0 + y)] = sU[p];
+    }
+  }
+}
+
+// Residual of one node from a plain 2D shared-memory region (row stride RS).
+template <class T, int RS>
+__device__ __forceinline__ T node_residual(const OpArgs<T>& op, const T* Up, uint16_t cd, T f,
+                                           int gi, int gj) {
+  if (cd == 0) return T(0);
+  if (cd == 1) {
+    T s8 = ((Up[-1] + Up[1]) + (Up[-RS] + Up[RS])) +
+           ((Up[-RS - 1] + Up[-RS + 1]) + (Up[RS - 1] + Up[RS + 1]));
+    return f - (T(8) * Up[0] - s8) / T(3);
+  }
+  const T* R = row_of(op, gi, gj, cd);
+  T acc = R[0] * Up[-RS - 1] + R[1] * Up[-RS] + R[2] * Up[-RS + 1] + R[3] * Up[-1] +
+          R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[RS - 1] + R[7] * Up[RS] + R[8] * Up[RS + 1];
+  return f - acc;
+}
+
+constexpr int RR_X = 68, RR_Y = 36;   // region of a 64 x 32 fine block with 2-node halo
+
+template <class T, bool NORM>
+__global__ void __launch_bounds__(kThreads)
+k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F, Layout Lc,
+                 const int* __restrict__ ctiles, T* __restrict__ Fc, double* __restrict__ norms) {
+  typedef typename Vec2<T>::type T2;
+  __shared__ __align__(16) T sU[RR_Y * RR_X];
+  __shared__ __align__(16) T sR[RR_Y * RR_X];
+  __shared__ uint16_t sC[RR_Y * RR_X];
+  const int t = ctiles[blockIdx.x >> 2], sub = blockIdx.x & 3;
+  const int I0 = (t % Lc.ntx) * MG_TX + (sub & 1) * 32;
+  const int J0 = (t / Lc.ntx) * MG_TY + (sub >> 1) * 16;
+  if (I0 > Lc.n || J0 > Lc.n) return;
+  const int fi0 = 2 * I0 - 2, fj0 = 2 * J0 - 2;
+  for (int it = threadIdx.x; it < RR_Y * (RR_X / 2); it += blockDim.x) {
+    int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
+    size_t g = op.L.idx(fi0 + 2 * a, fj0 + rj);
+    T2 u2 = *reinterpret_cast<const T2*>(u + g);
+    uint32_t c2 = *reinterpret_cast<const uint32_t*>(op.code + g);
+    sU[rj * RR_X + 2 * a] = u2.x;
+    sU[rj * RR_X + 2 * a + 1] = u2.y;
+    sC[rj * RR_X + 2 * a] = (uint16_t)(c2 & 0xffffu);
+    sC[rj * RR_X + 2 * a + 1] = (uint16_t)(c2 >> 16);
+  }
+  __syncthreads();
+  double vmax = 0.0, vsum = 0.0;
+  for (int it = threadIdx.x; it < (RR_Y - 2) * (RR_X - 2); it += blockDim.x) {
+    int rj = 1 + it / (RR_X - 2), ri = 1 + it % (RR_X - 2);
+    int p = rj * RR_X + ri;
+    uint16_t cd = sC[p];
+    T r = T(0);
+    if (cd) {
+      int gi = fi0 + ri, gj = fj0 + rj;
+      r = node_residual<T, RR_X>(op, sU + p, cd, F[op.L.idx(gi, gj)], gi, gj);
+    }
+    sR[p] = r;
+    if (NORM && ri >= 2 && ri < RR_X - 2 && rj >= 2 && rj < RR_Y - 2) {
+      double rd = (double)r;
+      vmax = fmax(vmax, fabs(rd));
+      vsum += rd * rd;
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < 32 * 16; it += blockDim.x) {
+    int cy = it / 32, cx = it - cy * 32;
+    int I = I0 + cx, J = J0 + cy;
+    if (I > Lc.n || J > Lc.n) continue;
+    const T* R = sR + (2 * cy + 2) * RR_X + (2 * cx + 2);
+    T rc = R[0] + T(0.5) * ((R[-1] + R[1]) + (R[-RR_X] + R[RR_X])) +
+           T(0.25) * ((R[-RR_X - 1] + R[-RR_X + 1]) + (R[RR_X - 1] + R[RR_X + 1]));
+    Fc[Lc.idx(I, J)] = rc;
+  }
+  if (NORM) block_norms_to_global(vmax, vsum, norms);
+}
+
+template <class T, class TR>
+__global__ void __launch_bounds__(kThreads)
+k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
+           const T* __restrict__ F, TR* __restrict__ rout, T scale, double* __restrict__ norms) {
+  typedef typename Vec2<T>::type T2;
+  __shared__ __align__(16) T sU[RR_Y * RR_X];
+  __shared__ uint16_t sC[RR_Y * RR_X];
+  const int t = tiles[blockIdx.x];
+  const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
+  const int fi0 = i0 - 2, fj0 = j0 - 2;
+  for (int it = threadIdx.x; it < RR_Y * (RR_X / 2); it += blockDim.x) {
+    int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
+    size_t g = op.L.idx(fi0 + 2 * a, fj0 + rj);
+    T2 u2 = *reinterpret_cast<const T2*>(u + g);
+    uint32_t c2 = *reinterpret_cast<const uint32_t*>(op.code + g);
+    sU[rj * RR_X + 2 * a] = u2.x;
+    sU[rj * RR_X + 2 * a + 1] = u2.y;
+    sC[rj * RR_X + 2 * a] = (uint16_t)(c2 & 0xffffu);
+    sC[rj * RR_X + 2 * a + 1] = (uint16_t)(c2 >> 16);
+  }
+  __syncthreads();
+  double vmax = 0.0, vsum = 0.0;
+  for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
+    int rr = it / MG_TX, ii = it - rr * MG_TX;
+    int p = (rr + 2) * RR_X + ii + 2;
+    int gi = i0 + ii, gj = j0 + rr;
+    size_t g = op.L.idx(gi, gj);
+    uint16_t cd = sC[p];
+    T r = cd ? node_residual<T, RR_X>(op, sU + p, cd, F[g], gi, gj) : T(0);
+    double rd = (double)r;
+    vmax = fmax(vmax, fabs(rd));
+    vsum += rd * rd;
+    if (rout) rout[g] = (TR)(r * scale);
+  }
+  if (norms) block_norms_to_global(vmax, vsum, norms);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+k_prolong(OpArgs<T> op, const int* __restrict__ tiles, T* __restrict__ uf, Layout Lc,
+          const T* __restrict__ ec) {
+  const int t = tiles[blockIdx.x];
+  const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
+  for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
+    int rr = it / MG_TX, ii = it - rr * MG_TX;
+    int i = i0 + ii, j = j0 + rr;
+    size_t g = op.L.idx(i, j);
+    if (op.code[g] == 0) continue;
+    int I = i >> 1, J = j >> 1;
+    const T* E = ec + Lc.idx(I, J);
+    T e;
+    if (!(i & 1) && !(j & 1)) e = E[0];
+    else if (!(j & 1)) e = T(0.5) * (E[0] + E[1]);
+    else if (!(i & 1)) e = T(0.5) * (E[0] + E[Lc.pitch]);
+    else e = T(0.25) * ((E[0] + E[1]) + (E[Lc.pitch] + E[Lc.pitch + 1]));
+    uf[g] += e;
+  }
+}
+
+template <class T>
+__global__ void k_coarse_solve(Layout Lc, const double* __restrict__ Ainv, const T* __restrict__ Fc,
+                               T* __restrict__ uc) {
+  extern __shared__ double sF[];
+  const int n = Lc.n, m = (n + 1) * (n + 1);
+  for (int p = threadIdx.x; p < m; p += blockDim.x)
+    sF[p] = (double)Fc[Lc.idx(p % (n + 1), p / (n + 1))];
+  __syncthreads();
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < m; ++c) s += Ainv[(size_t)c * m + p] * sF[c];
+    uc[Lc.idx(p % (n + 1), p / (n + 1))] = (T)s;
+  }
+}
+
+__global__ void k_rhs(RhsArgs a, const double* __restrict__ f, const double* __restrict__ g,
+                      double* __restrict__ F, double* __restrict__ norms) {
+  const int n = a.L.n;
+  const size_t m = (size_t)(n + 1) * (n + 1);
+  const double h2 = a.h * a.h / 36.0;
+  double vmax = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(k % (n + 1)), j = (int)(k / (n + 1));
+    size_t gk = a.L.idx(i, j);
+    double s = 0.0;
+    if (a.code[gk]) {
+      for (int q = 0; q < 4; ++q) {
+        int dx = q & 1, dy = q >> 1;
+        int ic = i - 1 + dx, jc = j - 1 + dy;
+        if (ic < 0 || jc < 0 || ic >= n || jc >= n) continue;
+        size_t c = (size_t)jc * n + ic;
+        uint8_t cl = a.cls[c];
+        if (cl == CELL_EXT) continue;
+        int av = (1 - dx) + 2 * (1 - dy);
+        size_t k0 = (size_t)jc * (n + 1) + ic;
+        size_t vk[4] = {k0, k0 + 1, k0 + n + 1, k0 + n + 2};
+        if (cl == CELL_INT) {
+          // whole-cell Q1 mass h^2/36 [[4,2,2,1],...]: 4 on the diagonal,
+          // 2 along edges, 1 across the diagonal
+          for (int b = 0; b < 4; ++b) {
+            int wgt = (b == av) ? 4 : ((b ^ av) == 3 ? 1 : 2);
+            s += h2 * wgt * f[vk[b]];
+          }
+        } else {
+          const double* Mk = a.Mk + (size_t)a.cell_cut[c] * 16 + av * 4;
+          const double* Gk = a.Gk + (size_t)a.cell_cut[c] * 16 + av * 4;
+          for (int b = 0; b < 4; ++b) s += Mk[b] * f[vk[b]] + Gk[b] * g[vk[b]];
+        }
+      }
+    }
+    F[gk] = s;
+    vmax = fmax(vmax, fabs(s));
+  }
+  block_norms_to_global(vmax, 0.0, norms);
+}
+
+template <class T>
+__global__ void k_pack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
+                       T* __restrict__ dst, unsigned* err) {
+  const int n = L.n;
+  const size_t m = (size_t)(n + 1) * (n + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(k % (n + 1)), j = (int)(k / (n + 1));
+    size_t g = L.idx(i, j);
+    double v = src[k];
+    if (err && !isfinite(v)) atomicOr(err, DEV_ERR_NAN);
+    dst[g] = code[g] ? (T)v : T(0);
+  }
+}
+
+__global__ void k_unpack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
+                         double* __restrict__ dst) {
+  const int n = L.n;
+  const size_t m = (size_t)(n + 1) * (n + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(k % (n + 1)), j = (int)(k / (n + 1));
+    size_t g = L.idx(i, j);
+    dst[k] = code[g] ? src[g] : 0.0;
+  }
+}
+
+__global__ void k_check_finite(const double* __restrict__ p, size_t m, unsigned* err) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(p[k])) atomicOr(err, DEV_ERR_NAN);
+}
+
+__global__ void k_update(Layout L, const int* __restrict__ tiles, const uint16_t* __restrict__ code,
+                         double* __restrict__ u, const float* __restrict__ e, double inv_scale) {
+  const int t = tiles[blockIdx.x];
+  const int i0 = (t % L.ntx) * MG_TX, j0 = (t / L.ntx) * MG_TY;
+  for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
+    int rr = it / MG_TX, ii = it - rr * MG_TX;
+    size_t g = L.idx(i0 + ii, j0 + rr);
+    if (code[g]) u[g] += (double)e[g] * inv_scale;
+  }
+}
+
+template <class T>
+__global__ void k_export_stencil(OpArgs<T> op, double* __restrict__ out) {
+  const int n = op.L.n;
+  const size_t m = (size_t)(n + 1) * (n + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(k % (n + 1)), j = (int)(k / (n + 1));
+    uint16_t cd = op.code[op.L.idx(i, j)];
+    double* o = out + k * 9;
+    for (int s = 0; s < 9; ++s) o[s] = 0.0;
+    if (cd == 1) {
+      for (int s = 0; s < 9; ++s) o[s] = -1.0 / 3.0;
+      o[4] = 8.0 / 3.0;
+    } else if (cd >= 2) {
+      const T* R = row_of(op, i, j, cd);
+      for (int s = 0; s < 9; ++s) o[s] = (double)R[s];
+    }
+  }
+}
+
+inline int grid_for(size_t m, int threads = kThreads) {
+  size_t b = (m + threads - 1) / threads;
+  return (int)(b < 65536 * 8 ? (b ? b : 1) : 65536 * 8);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------
+
+template <class T>
+size_t sweep_smem() { return 4 * SW_PLANE * (2 * sizeof(T) + sizeof(uint16_t)); }
+
+template <class T>
+size_t band_smem(int eta) {
+  int H = 4 * eta + 1, RB = 32 + 2 * H, cap = ((RB + 1) / 2) * ((RB + 1) / 2);
+  return (size_t)RB * RB * (sizeof(T) + sizeof(uint16_t)) + 4 * (size_t)cap * sizeof(uint16_t);
+}
+
+template <class T>
+cudaError_t configure_kernels(int eta) {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_gs_sweep<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sweep_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gs_sweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sweep_smem<T>());
+  if (e != cudaSuccess) return e;
+  // the largest eta allowed by the ABI, so handles with different eta coexist
+  (void)eta;
+  e = cudaFuncSetAttribute(k_band<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)band_smem<T>(8));
+  return e;
+}
+
+template <class T>
+void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T* uin, T* uout,
+                     const T* F, T* bval, bool zero_in, cudaStream_t st) {
+  if (!ntiles) return;
+  if (zero_in)
+    k_gs_sweep<T, true><<<ntiles, kThreads, sweep_smem<T>(), st>>>(op, tiles, uin, uout, F, bval);
+  else
+    k_gs_sweep<T, false><<<ntiles, kThreads, sweep_smem<T>(), st>>>(op, tiles, uin, uout, F, bval);
+}
+
+template <class T>
+void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
+                 const T* F, const T* bval, cudaStream_t st) {
+  if (!nbt || eta <= 0) return;
+  k_band<T><<<nbt, kThreads, band_smem<T>(eta), st>>>(op, btiles, nbx, eta, u, F, bval);
+}
+
+template <class T>
+void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const Layout& Lc,
+                           const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st) {
+  if (!nct) return;
+  if (norms)
+    k_resid_restrict<T, true><<<nct * 4, kThreads, 0, st>>>(op, u, F, Lc, ctiles, Fc, norms);
+  else
+    k_resid_restrict<T, false><<<nct * 4, kThreads, 0, st>>>(op, u, F, Lc, ctiles, Fc, norms);
+}
+
+template <class T, class TR>
+void launch_residual(const OpArgs<T>& op, const int* tiles, int ntiles, const T* u, const T* F,
+                     TR* rout, T scale, double* norms, cudaStream_t st) {
+  if (!ntiles) return;
+  k_residual<T, TR><<<ntiles, kThreads, 0, st>>>(op, tiles, u, F, rout, scale, norms);
+}
+
+template <class T>
+void launch_prolong(const OpArgs<T>& op, const int* tiles, int ntiles, T* uf, const Layout& Lc,
+                    const T* ec, cudaStream_t st) {
+  if (!ntiles) return;
+  k_prolong<T><<<ntiles, kThreads, 0, st>>>(op, tiles, uf, Lc, ec);
+}
+
+template <class T>
+void launch_coarse_solve(const Layout& Lc, const double* Ainv, const T* Fc, T* uc, cudaStream_t st) {
+  int m = (Lc.n + 1) * (Lc.n + 1);
+  k_coarse_solve<T><<<1, kThreads, m * sizeof(double), st>>>(Lc, Ainv, Fc, uc);
+}
+
+void launch_rhs(const RhsArgs& a, const double* f, const double* g, double* F, double* norms,
+                cudaStream_t st) {
+  size_t m = (size_t)(a.L.n + 1) * (a.L.n + 1);
+  k_rhs<<<grid_for(m), kThreads, 0, st>>>(a, f, g, F, norms);
+}
+
+template <class T>
+void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* dst, unsigned* err,
+                 cudaStream_t st) {
+  size_t m = (size_t)(L.n + 1) * (L.n + 1);
+  k_pack<T><<<grid_for(m), kThreads, 0, st>>>(L, code, src, dst, err);
+}
+
+void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
+                   cudaStream_t st) {
+  size_t m = (size_t)(L.n + 1) * (L.n + 1);
+  k_unpack<<<grid_for(m), kThreads, 0, st>>>(L, code, src, dst);
+}
+
+void launch_check_finite(const double* p, size_t m, unsigned* err, cudaStream_t st) {
+  k_check_finite<<<grid_for(m), kThreads, 0, st>>>(p, m, err);
+}
+
+void launch_update(const Layout& L, const int* tiles, int ntiles, const uint16_t* code, double* u,
+                   const float* e, double inv_scale, cudaStream_t st) {
+  if (!ntiles) return;
+  k_update<<<ntiles, kThreads, 0, st>>>(L, tiles, code, u, e, inv_scale);
+}
+
+template <class T>
+void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st) {
+  size_t m = (size_t)(op.L.n + 1) * (op.L.n + 1);
+  k_export_stencil<T><<<grid_for(m), kThreads, 0, st>>>(op, out);
+}
+
+#define MG_INSTANTIATE(T)                                                                        \
+  template size_t sweep_smem<T>();                                                               \
+  template size_t band_smem<T>(int);                                                             \
+  template cudaError_t configure_kernels<T>(int);                                                \
+  template void launch_gs_sweep<T>(const OpArgs<T>&, const int*, int, const T*, T*, const T*, T*, \
+                                   bool, cudaStream_t);                                          \
+  template void launch_band<T>(const OpArgs<T>&, const int*, int, int, int, T*, const T*,        \
+                               const T*, cudaStream_t);                                          \
+  template void launch_resid_restrict<T>(const OpArgs<T>&, const T*, const T*, const Layout&,    \
+                                         const int*, int, T*, double*, cudaStream_t);            \
+  template void launch_prolong<T>(const OpArgs<T>&, const int*, int, T*, const Layout&, const T*, \
+                                  cudaStream_t);                                                 \
+  template void launch_coarse_solve<T>(const Layout&, const double*, const T*, T*, cudaStream_t); \
+  template void launch_pack<T>(const Layout&, const uint16_t*, const double*, T*, unsigned*,     \
+                               cudaStream_t);                                                    \
+  template void launch_export_stencil<T>(const OpArgs<T>&, double*, cudaStream_t);
+
+MG_INSTANTIATE(double)
+MG_INSTANTIATE(float)
+template void launch_residual<double, float>(const OpArgs<double>&, const int*, int, const double*,
+                                             const double*, float*, double, double*, cudaStream_t);
+template void launch_residual<double, double>(const OpArgs<double>&, const int*, int,
+                                              const double*, const double*, double*, double,
+                                              double*, cudaStream_t);

@@ -1,0 +1,57 @@
+// V-cycle kernel launchers (see cycle.cu).
+#pragma once
+
+#include "common.cuh"
+
+// Operator of one level for kernels in arithmetic type T.
+template <class T> struct OpArgs {
+  Layout L;
+  const uint16_t* code;      // per node, padded layout
+  const int* tile_base;      // per tile: first boundary row
+  const T* rows;             // boundary rows, MG_ROW values each
+};
+
+// Level-0 data for the right-hand side F = M f + G g.
+struct RhsArgs {
+  Layout L;
+  double h;
+  const uint16_t* code;
+  const uint8_t* cls;        // n x n cell classes
+  const int* cell_cut;       // n x n, index into the cut list or -1
+  const double* Mk;          // 16 per cut cell, mass on K cap Omega_h
+  const double* Gk;          // 16 per cut cell, boundary load
+};
+
+template <class T> size_t sweep_smem();
+template <class T> size_t band_smem(int eta);
+template <class T> cudaError_t configure_kernels(int eta);
+
+template <class T>
+void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T* uin, T* uout,
+                     const T* F, T* bval, bool zero_in, cudaStream_t st);
+template <class T>
+void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
+                 const T* F, const T* bval, cudaStream_t st);
+template <class T>
+void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const Layout& Lc,
+                           const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st);
+template <class T, class TR>
+void launch_residual(const OpArgs<T>& op, const int* tiles, int ntiles, const T* u, const T* F,
+                     TR* rout, T scale, double* norms, cudaStream_t st);
+template <class T>
+void launch_prolong(const OpArgs<T>& op, const int* tiles, int ntiles, T* uf, const Layout& Lc,
+                    const T* ec, cudaStream_t st);
+template <class T>
+void launch_coarse_solve(const Layout& Lc, const double* Ainv, const T* Fc, T* uc, cudaStream_t st);
+void launch_rhs(const RhsArgs& a, const double* f, const double* g, double* F, double* norms,
+                cudaStream_t st);
+template <class T>
+void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* dst, unsigned* err,
+                 cudaStream_t st);
+void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
+                   cudaStream_t st);
+void launch_check_finite(const double* p, size_t m, unsigned* err, cudaStream_t st);
+void launch_update(const Layout& L, const int* tiles, int ntiles, const uint16_t* code, double* u,
+                   const float* e, double inv_scale, cudaStream_t st);
+template <class T>
+void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st);

@@ -1,0 +1,297 @@
+"""ctypes binding of libghostmg.so (declared in include/ghostmg.h).
+
+Argument marshalling only: every step runs in the CUDA library.  Array
+arguments may be CUDA torch tensors (float64, contiguous; used on the handle's
+stream), NumPy float64 C-contiguous host arrays, or raw integer addresses.
+Importing this module does not build anything; loading fails loudly when the
+library has not been built (``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libghostmg.so")
+
+MG_OK = 0
+MG_ERR_INVALID_ARG = 1
+MG_ERR_CUDA = 2
+MG_ERR_NOT_CONVERGED = 3
+MG_ERR_DIVERGED = 4
+MG_ERR_NOT_SPD = 5
+MG_ERR_TIMEOUT = 6
+MG_ERR_UNIMPLEMENTED = 7
+MG_ERR_INTERNAL = 8
+MG_ERR_OUT_OF_MEMORY = 9
+MG_BC_DIRICHLET = 0
+MG_LAMBDA_LOCAL = 0
+MG_FP64 = 0
+MG_MIXED = 1
+
+
+class mg_grid(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("h", ctypes.c_double), ("coarsest_cells", ctypes.c_int)]
+
+
+class mg_bc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("neumann_mask", ctypes.c_void_p)]
+
+
+class mg_stab(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("alpha", ctypes.c_double), ("eta", ctypes.c_int),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("lambda_mode", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int)]
+
+
+class mg_info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("res_hist", ctypes.c_double * 64), ("n_dof", ctypes.c_int),
+                ("n_cut", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("setup_ms", ctypes.c_float), ("solve_ms", ctypes.c_float)]
+
+    def history(self):
+        return [self.res_hist[k] for k in range(min(self.cycles + 1, 64))]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# name -> (restype, argtypes); the order of declaration in include/ghostmg.h
+SIGNATURES = {
+    "mg_default_stab": (_I, [ctypes.POINTER(mg_stab)]),
+    "mg_setup": (_I, [ctypes.POINTER(_P), _P, ctypes.POINTER(mg_grid), ctypes.POINTER(mg_bc),
+                      ctypes.POINTER(mg_stab), _P]),
+    "mg_solve": (_I, [_P, _P, _P, _P, _D, ctypes.POINTER(mg_info)]),
+    "mg_adjoint": (_I, [_P, _P, _P, _P]),
+    "mg_destroy": (None, [_P]),
+    "mg_strerror": (ctypes.c_char_p, [_I]),
+    "mg_get_counts": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                           ctypes.POINTER(_I)]),
+    "mg_level_cells": (_I, [_P, _I]),
+    "mg_export_stencil": (_I, [_P, _I, _P]),
+    "mg_export_cut_cells": (_I, [_P, _I, _P, _P, ctypes.POINTER(_I)]),
+    "mg_rhs": (_I, [_P, _P, _P, _P]),
+    "mg_cycles": (_I, [_P, _P, _P, _I, _I]),
+    "mg_residual": (_I, [_P, _P, _P, _P, _P]),
+    "mg_set_profiling": (_I, [_P, _I]),
+    "mg_get_profile": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _P, _P]),
+}
+
+PROF_SLOTS = ("sweep", "band", "restrict", "prolong", "residual", "update", "coarse", "io")
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libghostmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class GhostMGError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = load().mg_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (status {code})")
+
+
+def _check(code: int, where: str, ok=(MG_OK,)):
+    if code not in ok:
+        raise GhostMGError(code, where)
+    return code
+
+
+def _addr(x, writable=False):
+    """Address of an array argument (torch tensor, NumPy array or int)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if x.dtype not in (np.float64, np.int32) or not x.flags.c_contiguous:
+            raise TypeError("NumPy arrays must be C-contiguous float64 (int32 for cell lists)")
+        if writable and not x.flags.writeable:
+            raise TypeError("output array is read-only")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise TypeError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+# --- same-name wrappers of the C entry points ------------------------------------
+
+def mg_default_stab() -> mg_stab:
+    s = mg_stab()
+    _check(load().mg_default_stab(ctypes.byref(s)), "mg_default_stab")
+    return s
+
+
+def mg_setup(levelset, grid: mg_grid, bc: Optional[mg_bc] = None, stab: Optional[mg_stab] = None,
+             stream: int = 0) -> int:
+    h = _P()
+    _check(load().mg_setup(ctypes.byref(h), _addr(levelset), ctypes.byref(grid),
+                           ctypes.byref(bc) if bc is not None else None,
+                           ctypes.byref(stab) if stab is not None else None,
+                           _P(stream) if stream else None), "mg_setup")
+    return h.value
+
+
+def mg_solve(handle: int, f, g, u, tol: float, info: Optional[mg_info] = None,
+             ok=(MG_OK,)) -> int:
+    return _check(load().mg_solve(handle, _addr(f), _addr(g), _addr(u, True), tol,
+                                  ctypes.byref(info) if info is not None else None),
+                  "mg_solve", ok)
+
+
+def mg_adjoint(handle: int, dLdu, dLdf=None, dLdg=None) -> int:
+    return _check(load().mg_adjoint(handle, _addr(dLdu), _addr(dLdf, True), _addr(dLdg, True)),
+                  "mg_adjoint")
+
+
+def mg_destroy(handle: int) -> None:
+    if handle:
+        load().mg_destroy(handle)
+
+
+def mg_strerror(code: int) -> str:
+    return load().mg_strerror(code).decode()
+
+
+def mg_get_counts(handle: int):
+    vals = [_I() for _ in range(4)]
+    _check(load().mg_get_counts(handle, *[ctypes.byref(v) for v in vals]), "mg_get_counts")
+    return tuple(v.value for v in vals)
+
+
+def mg_level_cells(handle: int, level: int) -> int:
+    return load().mg_level_cells(handle, level)
+
+
+def mg_export_stencil(handle: int, level: int, out) -> int:
+    return _check(load().mg_export_stencil(handle, level, _addr(out, True)), "mg_export_stencil")
+
+
+def mg_export_cut_cells(handle: int, max_cells: int, cells, data) -> int:
+    n = _I()
+    _check(load().mg_export_cut_cells(handle, max_cells, _addr(cells, True), _addr(data, True),
+                                      ctypes.byref(n)), "mg_export_cut_cells")
+    return n.value
+
+
+def mg_rhs(handle: int, f, g, F) -> int:
+    return _check(load().mg_rhs(handle, _addr(f), _addr(g), _addr(F, True)), "mg_rhs")
+
+
+def mg_cycles(handle: int, F, u, k: int, precision: int = MG_FP64) -> int:
+    return _check(load().mg_cycles(handle, _addr(F), _addr(u, True), k, precision), "mg_cycles")
+
+
+def mg_residual(handle: int, F, u, r=None):
+    norms = np.zeros(2)
+    _check(load().mg_residual(handle, _addr(F), _addr(u), _addr(r, True), norms.ctypes.data),
+           "mg_residual")
+    return float(norms[0]), float(norms[1])
+
+
+def mg_set_profiling(handle: int, enable: bool) -> int:
+    return _check(load().mg_set_profiling(handle, int(bool(enable))), "mg_set_profiling")
+
+
+def mg_get_profile(handle: int):
+    """(total launches, {slot: (launch groups, device ms)})."""
+    n = ctypes.c_longlong()
+    counts = np.zeros(len(PROF_SLOTS), dtype=np.int64)
+    ms = np.zeros(len(PROF_SLOTS))
+    _check(load().mg_get_profile(handle, ctypes.byref(n), counts.ctypes.data, ms.ctypes.data),
+           "mg_get_profile")
+    return n.value, {k: (int(counts[i]), float(ms[i])) for i, k in enumerate(PROF_SLOTS)}
+
+
+# --- convenience object ------------------------------------------------------------
+
+class Solver:
+    """Owns one handle.  ``psi`` is the (N+1)^2 nodal level set (host or
+    device); arrays passed to the methods may live on host or device."""
+
+    def __init__(self, psi, n_cells: int, x0: float, y0: float, h: float, *,
+                 coarsest: int = 8, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
+                 nu1: int = 2, nu2: int = 1, precision: str = "fp64", max_cycles: int = 100,
+                 stream: int = 0):
+        self.N = n_cells
+        stab = mg_default_stab()
+        stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta
+        stab.nu1, stab.nu2, stab.max_cycles = nu1, nu2, max_cycles
+        stab.precision = {"fp64": MG_FP64, "mixed": MG_MIXED}[precision]
+        grid = mg_grid(n_cells, x0, y0, h, coarsest)
+        self.handle = mg_setup(psi, grid, mg_bc(MG_BC_DIRICHLET, None), stab, stream)
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        return cls(np.ascontiguousarray(prob.psi, dtype=np.float64).ravel(), prob.N, prob.x0,
+                   prob.y0, prob.h, **kw)
+
+    def counts(self):
+        return mg_get_counts(self.handle)
+
+    def solve(self, f, g, u, tol: float = 1e-10, allow_not_converged: bool = False) -> mg_info:
+        info = mg_info()
+        ok = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
+        mg_solve(self.handle, f, g, u, tol, info, ok)
+        return info
+
+    def rhs(self, f, g, F):
+        mg_rhs(self.handle, f, g, F)
+        return F
+
+    def cycles(self, F, u, k: int, precision: str = "fp64"):
+        mg_cycles(self.handle, F, u, k, {"fp64": MG_FP64, "mixed": MG_MIXED}[precision])
+        return u
+
+    def residual(self, F, u, r=None):
+        return mg_residual(self.handle, F, u, r)
+
+    def stencil(self, level: int) -> np.ndarray:
+        n = mg_level_cells(self.handle, level)
+        out = np.zeros((n + 1) * (n + 1) * 9)
+        mg_export_stencil(self.handle, level, out)
+        return out.reshape(-1, 9)
+
+    def cut_cells(self):
+        total = mg_export_cut_cells(self.handle, 0, None, None)
+        cells = np.zeros(total, dtype=np.int32)
+        data = np.zeros(total * 52)
+        mg_export_cut_cells(self.handle, total, cells, data)
+        return cells, data.reshape(-1, 52)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,232 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle.
+
+All calls go through the C ABI (paper_2505_05105_gb300.ghostmg).  Tolerances
+(fp64, derived from the arithmetic: both sides evaluate the same exact
+integrals and stencils in a different order, so entries agree to a few ulp):
+operator rows of every level to 1e-13 of the level's largest entry, cut-cell
+C, lambda, Ke, Mk, Gk to 1e-13 (relative / relative to the cell's largest
+entry), F to 1e-13; iterates of the 4-colour V(2,1)-cycle after k cycles to
+1e-10 of max|u|; solutions driven to ||F - Au||/||F|| <= 1e-13 to 1e-10 of
+the oracle's direct solution (refined to fp64 exactness).  Mixed precision
+(fp32 V-cycle inside fp64 refinement): driven to 1e-12, within 1e-9 max|u|;
+stopped at 1e-10, the oracle's own residual of the result is <= 1e-10 and
+the error is within 3x that of the fp64 V-cycle stopped at the same
+residual (the stopping test, not fp32, bounds the error there).
+"""
+import numpy as np
+import pytest
+
+from oracle import ghostfem as gf
+from oracle import multigrid as mg
+from paper_2505_05105_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2505_05105_gb300 import ghostmg
+    ghostmg.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def solver(p, **kw):
+    from paper_2505_05105_gb300 import ghostmg
+    return ghostmg.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h, **kw)
+
+
+def oracle_rows(A, n):
+    """9-point rows of a sparse operator over (n+1)^2 nodes."""
+    A = A.tocoo()
+    out = np.zeros(((n + 1) ** 2, 9))
+    di = A.col % (n + 1) - A.row % (n + 1)
+    dj = A.col // (n + 1) - A.row // (n + 1)
+    np.add.at(out, (A.row, (di + 1) + 3 * (dj + 1)), A.data)
+    return out
+
+
+PROBLEMS = {
+    "circle64": lambda: wl.circle64(64),
+    "flower128": lambda: wl.flower(128),
+    "hourglass64": lambda: wl.paper_hourglass(64),
+    "discs256": lambda: wl.three_discs(256, seed=0),
+    "batch3": lambda: wl.batch_geometry(3),
+}
+
+
+@pytest.fixture(scope="module")
+def oracle_cache():
+    return {}
+
+
+def oracle_for(name, cache):
+    if name not in cache:
+        p = PROBLEMS[name]()
+        s = gf.assemble_problem(p)
+        lev = mg.build_hierarchy(s)
+        cache[name] = (p, s, lev)
+    return cache[name]
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_counts(name, oracle_cache):
+    p, s, lev = oracle_for(name, oracle_cache)
+    with solver(p) as S:
+        nl, ndof, ncut, nbnd = S.counts()
+    assert nl == len(lev)
+    assert ndof == int(s.dof.sum())
+    assert ncut == len(s.cut)
+    assert nbnd == int((lev[0].cut_nodes & lev[0].dof).sum())
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_operator_rows_all_levels(name, oracle_cache):
+    p, s, lev = oracle_for(name, oracle_cache)
+    with solver(p) as S:
+        for l, L in enumerate(lev):
+            got = S.stencil(l)
+            ref = oracle_rows(L.A, L.n)
+            scale = np.abs(ref).max()
+            err = np.abs(got - ref).max() / scale
+            assert err <= 1e-13, (l, err)
+
+
+@pytest.mark.parametrize("name", ["circle64", "flower128", "discs256", "batch3"])
+def test_cut_cell_data(name, oracle_cache):
+    p, s, lev = oracle_for(name, oracle_cache)
+    with solver(p) as S:
+        cells, data = S.cut_cells()
+    assert len(cells) == len(s.cut)
+    ref_cells = np.array([c.ic + c.jc * p.N for c in s.cut])
+    np.testing.assert_array_equal(cells, ref_cells)
+    for t, c in enumerate(s.cut):
+        d = data[t]
+        assert d[0] == pytest.approx(c.C, rel=1e-13), (t, c.config)
+        assert d[1] == pytest.approx(c.lam, rel=1e-13)
+        assert d[2] == pytest.approx(c.ints.area, rel=1e-13, abs=1e-300)
+        assert d[3] == pytest.approx(c.ints.length, rel=1e-13, abs=1e-300)
+        for off, M in ((4, c.Ke), (20, c.Mk), (36, c.Gk)):
+            sc = np.abs(M).max()
+            assert np.abs(d[off:off + 16] - M.ravel()).max() <= 1e-13 * sc, (t, off, c.config)
+
+
+@pytest.mark.parametrize("name", ["circle64", "flower128", "discs256"])
+def test_rhs(name, oracle_cache):
+    p, s, lev = oracle_for(name, oracle_cache)
+    F_ref = s.rhs(p.f, p.g)
+    with solver(p) as S:
+        F = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
+        S.rhs(dev(p.f), dev(p.g), F)
+        got = host(F)
+    assert np.abs(got - F_ref).max() <= 1e-13 * np.abs(F_ref).max()
+
+
+@pytest.mark.parametrize("name", ["circle64", "flower128", "hourglass64", "discs256"])
+def test_residual(name, oracle_cache):
+    p, s, lev = oracle_for(name, oracle_cache)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(s.n_nodes) * s.dof
+    F = s.rhs(p.f, p.g)
+    r_ref = F - s.A @ u
+    r_ref[~s.dof] = 0
+    with solver(p) as S:
+        r = torch.zeros_like(dev(F))
+        nrm = S.residual(dev(F), dev(u), r)
+        got = host(r)
+    assert np.abs(got - r_ref).max() <= 1e-12 * np.abs(r_ref).max()
+    assert nrm[0] == pytest.approx(np.abs(r_ref).max(), rel=1e-12)
+    assert nrm[1] == pytest.approx(np.linalg.norm(r_ref), rel=1e-10)
+
+
+@pytest.mark.parametrize("name", ["circle64", "flower128", "hourglass64", "discs256", "batch3"])
+def test_iterate_parity_vcycles(name, oracle_cache):
+    p, s, lev = oracle_for(name, oracle_cache)
+    F = s.rhs(p.f, p.g)
+    if not np.abs(F).max() > 0:        # homogeneous data: seeded random F on the DOFs
+        F = np.random.default_rng(11).standard_normal(s.n_nodes) * s.dof
+    u_ref = np.zeros(s.n_nodes)
+    with solver(p) as S:
+        u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+        Fd = dev(F)
+        for k in range(1, 6):
+            u_ref = mg.mg_cycle(lev, 0, u_ref, F, nu1=2, nu2=1, eta=4, order="color4")
+            S.cycles(Fd, u, 1)
+            got = host(u)
+            err = np.abs(got - u_ref).max() / np.abs(u_ref).max()
+            assert err <= 1e-10, (k, err)
+
+
+@pytest.mark.parametrize("name", ["circle64", "flower128", "discs256"])
+def test_solution_parity_fp64(name, oracle_cache):
+    p, s, lev = oracle_for(name, oracle_cache)
+    ud = gf.direct_solve(s, s.rhs(p.f, p.g))
+    with solver(p) as S:
+        u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+        info = S.solve(dev(p.f), dev(p.g), u, tol=1e-13)
+        got = host(u)
+    assert info.rel_res <= 1e-13
+    assert np.abs(got - ud).max() <= 1e-10 * np.abs(ud).max()
+
+
+@pytest.mark.parametrize("name", ["circle64", "flower128", "discs256"])
+def test_solution_parity_mixed(name, oracle_cache):
+    p, s, lev = oracle_for(name, oracle_cache)
+    F = s.rhs(p.f, p.g)
+    ud = gf.direct_solve(s, F)
+    scale = np.abs(ud).max()
+    with solver(p, precision="mixed") as S:
+        u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+        info = S.solve(dev(p.f), dev(p.g), u, tol=1e-12)
+        tight = host(u)
+        u.zero_()
+        info10 = S.solve(dev(p.f), dev(p.g), u, tol=1e-10)
+        mixed10 = host(u)
+    with solver(p) as S:
+        u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+        S.solve(dev(p.f), dev(p.g), u, tol=1e-10)
+        fp64_10 = host(u)
+    assert info.rel_res <= 1e-12
+    assert np.abs(tight - ud).max() <= 1e-9 * scale
+    # stopped at 1e-10: the oracle's residual of the result, and no less
+    # accurate than the fp64 V-cycle at the same stopping residual
+    r = F - s.A @ mixed10
+    assert np.abs(r[s.dof]).max() <= 1e-10 * np.abs(F).max()
+    e_mixed = np.abs(mixed10 - ud).max() / scale
+    e_fp64 = np.abs(fp64_10 - ud).max() / scale
+    print(f"{name}: mixed error at 1e-10 {e_mixed:.2e}, fp64 {e_fp64:.2e}, "
+          f"{info10.cycles} refinement steps")
+    assert e_mixed <= 3 * e_fp64 + 1e-12
+
+
+def test_host_and_device_arrays_agree():
+    p = wl.flower(64)
+    with solver(p) as S:
+        u_h = np.zeros((p.N + 1) ** 2)
+        S.solve(np.ascontiguousarray(p.f.ravel()), np.ascontiguousarray(p.g.ravel()), u_h,
+                tol=1e-12)
+        u_d = torch.zeros_like(dev(u_h))
+        S.solve(dev(p.f), dev(p.g), u_d, tol=1e-12)
+        np.testing.assert_array_equal(u_h, host(u_d))
+
+
+def test_warm_start_and_repeat_are_deterministic():
+    p = wl.flower(128)
+    with solver(p) as S:
+        a = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
+        b = torch.zeros_like(a)
+        S.solve(dev(p.f), dev(p.g), a, tol=1e-11)
+        S.solve(dev(p.f), dev(p.g), b, tol=1e-11)
+        assert torch.equal(a, b)
+        info = S.solve(dev(p.f), dev(p.g), a, tol=1e-11)   # warm start: already converged
+        assert info.cycles == 0
