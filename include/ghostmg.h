@@ -188,6 +188,36 @@ int mg_cycles(mg_handle h, const double* F, double* u, int k, int precision);
 int mg_residual(mg_handle h, const double* F, const double* u, double* r, double* norms);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free residual.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory while they use the
+ * solver -- work being captured into a CUDA graph (cudaMalloc cannot be
+ * captured), real-time loops that cannot take the device-wide
+ * synchronisation an allocation may cause, frameworks whose own allocator
+ * must own all device memory.
+ *
+ * Same result as mg_residual (r = F - A u on the fine level, norms[0] =
+ * ||r||_inf, norms[1] = ||r||_2), but it allocates nothing and uses no
+ * handle-owned scratch: F, u and r are read and written in place in the
+ * caller's (N+1)^2 layout, and the norm reduction uses a file-scope device
+ * array of 2 MG_NOALLOC_MAX_TILES + 2 doubles (1 MiB), which every GPU that
+ * loads the library keeps until the process exits.  ||r||_2 is summed in a
+ * fixed order, so it is reproducible.
+ *   F, u, r  device pointers; r may be NULL (norms only); u is read as 0 on
+ *            nodes that are not DOFs; r gets 0 there.
+ *   norms    host or device array of 2 doubles, or NULL.
+ * The call returns after the results are written.  Errors:
+ * MG_ERR_INVALID_ARG for NULL or host F/u/r, or a fine level with more than
+ * MG_NOALLOC_MAX_TILES active 64 x 32-node tiles (every n_cells <= 8192
+ * fits); MG_ERR_CUDA.
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (other threads, streams or handles) race and must be serialised.
+ * ------------------------------------------------------------------------- */
+#define MG_NOALLOC_MAX_TILES 65536
+int mg_residual_static(mg_handle h, const double* F, const double* u, double* r, double* norms);
+
+/* ---------------------------------------------------------------------------
  * Profiling: device time per kernel class, measured with CUDA events
  * recorded around each launch on the handle's stream while enabled, and a
  * count of every kernel the handle launches.  Slots:

@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "cycle.cuh"
+#include "internal.h"
 #include "setup.cuh"
 
 namespace {
@@ -815,6 +816,24 @@ int mg_export_cut_cells(mg_handle c, int max_cells, int* cells, double* data, in
   }
   return MG_OK;
 }
+
+}  // extern "C"
+
+int mg_internal_fine_view(mg_handle c, FineOpView* out) {
+  if (!c || !out || c->lev.empty()) return MG_ERR_INVALID_ARG;
+  Level& v = c->lev[0];
+  out->L = v.L;
+  out->code = v.code;
+  out->tile_base = v.tile_base;
+  out->rows64 = v.rows64;
+  out->active = v.active;
+  out->n_active = v.n_active;
+  out->N = c->N;
+  out->st = c->st;
+  return MG_OK;
+}
+
+extern "C" {
 
 int mg_set_profiling(mg_handle c, int enable) {
   if (!c) return MG_ERR_INVALID_ARG;

@@ -78,6 +78,7 @@ SIGNATURES = {
     "mg_rhs": (_I, [_P, _P, _P, _P]),
     "mg_cycles": (_I, [_P, _P, _P, _I, _I]),
     "mg_residual": (_I, [_P, _P, _P, _P, _P]),
+    "mg_residual_static": (_I, [_P, _P, _P, _P, _P]),
     "mg_set_profiling": (_I, [_P, _I]),
     "mg_get_profile": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _P, _P]),
 }
@@ -206,6 +207,15 @@ def mg_residual(handle: int, F, u, r=None):
     norms = np.zeros(2)
     _check(load().mg_residual(handle, _addr(F), _addr(u), _addr(r, True), norms.ctypes.data),
            "mg_residual")
+    return float(norms[0]), float(norms[1])
+
+
+def mg_residual_static(handle: int, F, u, r=None):
+    """Allocation-free fine-level residual (device F, u, r); returns
+    (||r||_inf, ||r||_2).  See include/ghostmg.h."""
+    norms = np.zeros(2)
+    _check(load().mg_residual_static(handle, _addr(F), _addr(u), _addr(r, True),
+                                     norms.ctypes.data), "mg_residual_static")
     return float(norms[0]), float(norms[1])
 
 
