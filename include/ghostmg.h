@@ -45,7 +45,7 @@ enum {
                                 domain touching the outer ring of nodes */
   MG_ERR_CUDA = 2,           /* a CUDA runtime call or kernel failed */
   MG_ERR_NOT_CONVERGED = 3,  /* max_cycles reached; outputs and info filled */
-  MG_ERR_DIVERGED = 4,       /* residual grew for 3 consecutive cycles */
+  MG_ERR_DIVERGED = 4,       /* residual not finite or 1e3 x above its best */
   MG_ERR_NOT_SPD = 5,        /* coarsest Cholesky met a pivot <= 0 */
   MG_ERR_TIMEOUT = 6,        /* reserved for bounded device waits */
   MG_ERR_UNIMPLEMENTED = 7,  /* option not supported (e.g. Neumann data) */

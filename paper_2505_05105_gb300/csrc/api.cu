@@ -13,6 +13,8 @@
 #include "cycle.cuh"
 #include "internal.h"
 #include "setup.cuh"
+#include "fused.cuh"
+#include "tail.cuh"
 
 namespace {
 
@@ -40,6 +42,8 @@ struct Level {
   int* band = nullptr;
   int nbx = 0;
   int n_dof = 0;
+  int n_rtiles = 0;
+  int* rtiles = nullptr;        // tiles covering the coarse DOFs (fused restriction)
   // vectors
   double* u64[2] = {nullptr, nullptr};
   double* F64 = nullptr;
@@ -72,6 +76,11 @@ struct mg_ctx {
   double* stage[3] = {nullptr, nullptr, nullptr};
   std::vector<void*> allocs;
   double last_tol = 1e-10;
+  int tail_level = -1;           // first level run by the single-block tail kernel
+  size_t tail_smem[2] = {0, 0};  // [float, double]
+  bool tail_rows_smem[2] = {false, false};
+  bool fused[2] = {false, false};  // fused smoothing steps on the intermediate levels
+  size_t fused_smem[2] = {0, 0};
   float setup_ms = 0.f;
   float solve_ms = 0.f;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -316,9 +325,96 @@ void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine) {
 }
 
 template <class T>
+void tail_cycle(mg_ctx* c, int l, bool zero_init) {
+  const int nlev = (int)c->lev.size();
+  TailArgs<T> a;
+  a.nlev = nlev - l;
+  for (int k = 0; k < a.nlev; ++k) {
+    Level& w = c->lev[l + k];
+    a.n[k] = w.n;
+    a.L[k] = w.L;
+    a.code[k] = w.code;
+    a.tile_base[k] = w.tile_base;
+    a.rows[k] = P<T>::rows(w);
+    a.n_bnd[k] = w.n_bnd;
+  }
+  a.rows_in_smem = c->tail_rows_smem[sizeof(T) == 8 ? 1 : 0] ? 1 : 0;
+  Level& v = c->lev[l];
+  a.Ainv = c->Ainv;
+  a.F0 = P<T>::F(v);
+  a.u0 = P<T>::u(v, P<T>::cur(v));
+  a.load_u0 = zero_init ? 0 : 1;
+  a.eta = c->stab.eta;
+  a.nu1 = c->stab.nu1;
+  a.nu2 = c->stab.nu2;
+  Launch k(c, MG_PROF_COARSE, 1);
+  launch_tail<T>(a, c->tail_smem[sizeof(T) == 8 ? 1 : 0], c->st);
+}
+
+template <class T>
+void vcycle(mg_ctx* c, int l, bool zero_init);
+
+// One V-cycle level with fused smoothing steps: nu1 steps (the first from
+// u = 0, the last also restricting the residual), recursion, nu2 steps (the
+// first adding the prolongated correction).
+template <class T>
+void fused_cycle(mg_ctx* c, int l, bool zero_init) {
+  Level& v = c->lev[l];
+  Level& w = c->lev[l + 1];
+  const size_t smem = c->fused_smem[sizeof(T) == 8 ? 1 : 0];
+  int& cur = P<T>::cur(v);
+  FusedArgs<T> a;
+  a.L = v.L;
+  a.code = v.code;
+  a.tile_base = v.tile_base;
+  a.rows = P<T>::rows(v);
+  a.eta = c->stab.eta;
+  a.F = P<T>::F(v);
+  a.Lc = w.L;
+  a.Fc = P<T>::F(w);
+  a.ec = nullptr;
+  const int nu1 = c->stab.nu1, nu2 = c->stab.nu2;
+  for (int s = 0; s < nu1; ++s) {
+    const bool last = s == nu1 - 1;
+    a.uin = P<T>::u(v, cur);
+    a.uout = P<T>::u(v, cur ^ 1);
+    a.tiles = last ? v.rtiles : v.active;
+    Launch k(c, MG_PROF_COARSE, 1);
+    launch_smooth_step<T>(a, last ? v.n_rtiles : v.n_active, zero_init && s == 0, false, last,
+                          smem, c->st);
+    cur ^= 1;
+  }
+  if (nu1 == 0) {
+    if (zero_init) cudaMemsetAsync(P<T>::u(v, cur), 0, v.L.size() * sizeof(T), c->st);
+    Launch k(c, MG_PROF_COARSE, w.n_active > 0);
+    launch_resid_restrict<T>(op_of<T>(v), P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
+                             P<T>::F(w), nullptr, c->st);
+  }
+  vcycle<T>(c, l + 1, true);
+  a.ec = P<T>::u(w, P<T>::cur(w));
+  a.tiles = v.active;
+  for (int s = 0; s < nu2; ++s) {
+    a.uin = P<T>::u(v, cur);
+    a.uout = P<T>::u(v, cur ^ 1);
+    Launch k(c, MG_PROF_COARSE, 1);
+    launch_smooth_step<T>(a, v.n_active, false, s == 0, false, smem, c->st);
+    cur ^= 1;
+  }
+  if (nu2 == 0) {
+    Launch k(c, MG_PROF_COARSE, v.n_active > 0);
+    launch_prolong<T>(op_of<T>(v), v.active, v.n_active, P<T>::u(v, cur), w.L,
+                      P<T>::u(w, P<T>::cur(w)), c->st);
+  }
+}
+
+template <class T>
 void vcycle(mg_ctx* c, int l, bool zero_init) {
   Level& v = c->lev[l];
   const int nlev = (int)c->lev.size();
+  if (l == c->tail_level) {
+    tail_cycle<T>(c, l, zero_init);
+    return;
+  }
   if (l == nlev - 1) {
     Launch k(c, MG_PROF_COARSE, 1);
     launch_coarse_solve<T>(v.L, c->Ainv, P<T>::F(v), P<T>::u(v, 0), c->st);
@@ -327,6 +423,10 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
   }
   const bool fine = l == 0;
   int& cur = P<T>::cur(v);
+  if (!fine && c->fused[sizeof(T) == 8 ? 1 : 0]) {
+    fused_cycle<T>(c, l, zero_init);
+    return;
+  }
   if (zero_init && c->stab.nu1 == 0)
     cudaMemsetAsync(P<T>::u(v, cur), 0, v.L.size() * sizeof(T), c->st);
   for (int s = 0; s < c->stab.nu1; ++s) smooth<T>(c, v, zero_init && s == 0, fine);
@@ -394,10 +494,10 @@ void refinement_step(mg_ctx* c, double sigma) {
 int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info) {
   const bool mixed = c->stab.precision == MG_MIXED;
   double rmax;
-  int k = 0, grow = 0, status = MG_OK;
+  int k = 0, status = MG_OK;
   double sigma = mixed ? pow2_near_inverse(Fn) : 1.0;
   TRY(fine_residual(c, sigma, mixed, &rmax));
-  double rel = rmax / Fn, prev = rel;
+  double rel = rmax / Fn, best = rel;
   if (info) info->res_hist[0] = rel;
   while (rel > tol) {
     if (k >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
@@ -408,10 +508,10 @@ int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info) 
     TRY(fine_residual(c, sigma, mixed, &rmax));
     rel = rmax / Fn;
     if (info && k < 64) info->res_hist[k] = rel;
-    if (!std::isfinite(rel)) { status = MG_ERR_DIVERGED; break; }
-    grow = rel > prev ? grow + 1 : 0;
-    if (grow >= 3) { status = MG_ERR_DIVERGED; break; }
-    prev = rel;
+    // diverged: not finite, or grown far past the best residual seen (at the
+    // rounding floor the residual only jitters within a small factor)
+    if (!std::isfinite(rel) || rel > 1e3 * best) { status = MG_ERR_DIVERGED; break; }
+    best = std::min(best, rel);
   }
   if (info) {
     info->cycles = k;
@@ -567,6 +667,69 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
   }
   MG_CUDA_TRY(configure_kernels<double>(c->stab.eta));
   MG_CUDA_TRY(configure_kernels<float>(c->stab.eta));
+  {
+    // fused smoothing steps on the intermediate levels, if they fit
+    int dev = 0, optin = 0;
+    MG_CUDA_TRY(cudaGetDevice(&dev));
+    MG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    optin -= 1024;   // static shared memory of the kernel
+    // fp32 only: on GB300 the redundant halo arithmetic of the fused step is
+    // cheap in fp32 but fp64 arithmetic is a small fraction of the fp32 rate
+    for (int pi = 0; pi < 1; ++pi) {
+      size_t sm = fused_smem_bytes(c->stab.eta, pi ? sizeof(double) : sizeof(float));
+      if (sm <= (size_t)optin) {
+        c->fused[pi] = true;
+        c->fused_smem[pi] = sm;
+        MG_CUDA_TRY(pi ? configure_fused<double>(sm) : configure_fused<float>(sm));
+      }
+    }
+    const int nlev = (int)c->lev.size();
+    for (int l = 1; l + 1 < nlev; ++l) {
+      Level& v = c->lev[l];
+      Level& w = c->lev[l + 1];
+      const int nt = v.L.ntx * v.L.nty;
+      uint8_t* flag;
+      int *cnt, *tmp;
+      TRY(dalloc(c, &flag, (size_t)nt));
+      TRY(dalloc(c, &cnt, 1));
+      TRY(dalloc(c, &tmp, scan_tmp_ints((size_t)nt) + 8));
+      TRY(dalloc(c, &v.rtiles, (size_t)nt));
+      launch_restrict_tile_flags(v.L, w.L, w.code, flag, c->st);
+      compact_flags_u8(flag, v.rtiles, cnt, (size_t)nt, tmp, nullptr, c->st);
+      TRY(read_int(c, cnt, &v.n_rtiles));
+    }
+  }
+  {
+    // the levels with n <= MG_TAIL_MAX_N run inside one block
+    const int nlev = (int)c->lev.size();
+    int t = 0;
+    while (t < nlev && c->lev[t].n > MG_TAIL_MAX_N) ++t;
+    int dev = 0, optin = 0;
+    MG_CUDA_TRY(cudaGetDevice(&dev));
+    MG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    optin -= 1024;   // static shared memory of the kernel
+    if (t < nlev && nlev - t <= MG_TAIL_MAX_LEVELS) {
+      int n[MG_TAIL_MAX_LEVELS];
+      for (int k = 0; k < nlev - t; ++k) n[k] = c->lev[t + k].n;
+      int nb[MG_TAIL_MAX_LEVELS];
+      for (int k = 0; k < nlev - t; ++k) nb[k] = c->lev[t + k].n_bnd;
+      size_t s32 = tail_smem_bytes(n, nlev - t, sizeof(float));
+      size_t s64 = tail_smem_bytes(n, nlev - t, sizeof(double));
+      if (s64 + tail_list_bytes(nb, nlev - t) <= (size_t)optin) {
+        c->tail_level = t;
+        // stage the boundary rows in shared memory when they fit
+        size_t r32 = tail_rows_bytes(nb, nlev - t, sizeof(float));
+        size_t r64 = tail_rows_bytes(nb, nlev - t, sizeof(double));
+        size_t lb = tail_list_bytes(nb, nlev - t);
+        c->tail_rows_smem[0] = s32 + r32 + lb <= (size_t)optin;
+        c->tail_rows_smem[1] = s64 + r64 + lb <= (size_t)optin;
+        c->tail_smem[0] = s32 + (c->tail_rows_smem[0] ? r32 : 0) + lb;
+        c->tail_smem[1] = s64 + (c->tail_rows_smem[1] ? r64 : 0) + lb;
+        MG_CUDA_TRY(configure_tail<float>(c->tail_smem[0]));
+        MG_CUDA_TRY(configure_tail<double>(c->tail_smem[1]));
+      }
+    }
+  }
   TRY(sync_check(c));
   return MG_OK;
 }

@@ -48,24 +48,33 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
   const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
   const int ri0 = i0 - SW_H, rj0 = j0 - SW_H;
 
-  for (int it = threadIdx.x; it < SW_RY * SW_PX; it += blockDim.x) {
-    int rj = it / SW_PX, a = it - rj * SW_PX;
-    size_t g = op.L.idx(ri0 + 2 * a, rj0 + rj);
-    int pl = (rj & 1) * 2 * SW_PLANE + (rj >> 1) * SW_PX + a;
-    T2 f2 = *reinterpret_cast<const T2*>(F + g);
-    sF[pl] = f2.x;
-    sF[pl + SW_PLANE] = f2.y;
-    if (ZERO_IN) {
-      sU[pl] = T(0);
-      sU[pl + SW_PLANE] = T(0);
-    } else {
-      T2 u2 = *reinterpret_cast<const T2*>(uin + g);
-      sU[pl] = u2.x;
-      sU[pl + SW_PLANE] = u2.y;
+  constexpr int B = 3;
+  for (int it0 = threadIdx.x; it0 < SW_RY * SW_PX; it0 += B * blockDim.x) {
+    T2 f2[B], u2[B];
+    uint32_t c2[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      int it = it0 + b * blockDim.x;
+      int rj = it / SW_PX, a = it - rj * SW_PX;
+      bool ok = it < SW_RY * SW_PX;
+      size_t g = ok ? op.L.idx(ri0 + 2 * a, rj0 + rj) : op.L.idx(0, 0);
+      f2[b] = *reinterpret_cast<const T2*>(F + g);
+      if (!ZERO_IN) u2[b] = *reinterpret_cast<const T2*>(uin + g);
+      c2[b] = *reinterpret_cast<const uint32_t*>(op.code + g);
     }
-    uint32_t c2 = *reinterpret_cast<const uint32_t*>(op.code + g);
-    sC[pl] = (uint16_t)(c2 & 0xffffu);
-    sC[pl + SW_PLANE] = (uint16_t)(c2 >> 16);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      int it = it0 + b * blockDim.x;
+      if (it >= SW_RY * SW_PX) continue;
+      int rj = it / SW_PX, a = it - rj * SW_PX;
+      int pl = (rj & 1) * 2 * SW_PLANE + (rj >> 1) * SW_PX + a;
+      sF[pl] = f2[b].x;
+      sF[pl + SW_PLANE] = f2[b].y;
+      sU[pl] = ZERO_IN ? T(0) : u2[b].x;
+      sU[pl + SW_PLANE] = ZERO_IN ? T(0) : u2[b].y;
+      sC[pl] = (uint16_t)(c2[b] & 0xffffu);
+      sC[pl + SW_PLANE] = (uint16_t)(c2[b] >> 16);
+    }
   }
   __syncthreads();
 
@@ -129,7 +138,9 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
 // 4 eta colour phases redundantly on a halo of 4 eta + 1 nodes, so the owned
 // values equal those of the global sweep.  Boundary values are read from
 // bval (written by the preceding full sweep) and never from u, which other
-// blocks update concurrently.
+// blocks update concurrently.  The region is loaded with independent
+// coalesced loads, then each listed boundary node caches its row index and
+// F, so the colour phases touch only shared memory and L1-resident rows.
 template <class T>
 __global__ void __launch_bounds__(kThreads)
 k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __restrict__ u,
@@ -139,36 +150,53 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
   const int RB = 32 + 2 * H;
   const int cap = ((RB + 1) / 2) * ((RB + 1) / 2);
   T* sU = reinterpret_cast<T*>(smem_raw);
-  uint16_t* sC = reinterpret_cast<uint16_t*>(sU + RB * RB);
-  uint16_t* sL = sC + RB * RB;                      // [4][cap]
+  int* sRow = reinterpret_cast<int*>(sU + RB * RB);  // [4][cap] row index of listed nodes
+  uint16_t* sC = reinterpret_cast<uint16_t*>(sRow + 4 * cap);
+  uint16_t* sL = sC + RB * RB;                       // [4][cap] positions
   __shared__ int cnt[4];
   if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
   const int bt = btiles[blockIdx.x];
   const int bi0 = (bt % nbx) * 32 - H, bj0 = (bt / nbx) * 32 - H;
   const int n = op.L.n;
-  __syncthreads();
-  for (int p = threadIdx.x; p < RB * RB; p += blockDim.x) {
-    int y = p / RB, x = p - y * RB;
-    int gi = bi0 + x, gj = bj0 + y;
-    uint16_t cd = 0;
-    T v = T(0);
-    if (gi >= 0 && gj >= 0 && gi <= n && gj <= n) {
-      size_t g = op.L.idx(gi, gj);
-      cd = op.code[g];
-      if (cd >= 2) {
-        int r = op.tile_base[op.L.tile_of(gi, gj)] + cd - 2;
-        v = bval[r];
-        if (x > 0 && y > 0 && x < RB - 1 && y < RB - 1) {
-          int c = (gi & 1) + 2 * (gj & 1);
-          int pos = atomicAdd(&cnt[c], 1);
-          sL[c * cap + pos] = (uint16_t)p;
-        }
-      } else {
-        v = u[g];
+  // 1. codes and values of the region: independent loads, 4 per thread in flight
+  constexpr int B = 4;
+  for (int p0 = threadIdx.x; p0 < RB * RB; p0 += B * blockDim.x) {
+    uint16_t cdv[B];
+    T val[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      int p = p0 + b * blockDim.x;
+      int y = p / RB, x = p - y * RB;
+      int gi = bi0 + x, gj = bj0 + y;
+      bool in = p < RB * RB && gi >= 0 && gj >= 0 && gi <= n && gj <= n;
+      size_t g = in ? op.L.idx(gi, gj) : 0;
+      cdv[b] = in ? op.code[g] : (uint16_t)0;
+      val[b] = in ? u[g] : T(0);
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      int p = p0 + b * blockDim.x;
+      if (p < RB * RB) {
+        sC[p] = cdv[b];
+        sU[p] = val[b];
       }
     }
-    sU[p] = v;
-    sC[p] = cd;
+  }
+  __syncthreads();
+  // 2. boundary nodes: value from bval, row index and F cached, colour lists
+  for (int p = threadIdx.x; p < RB * RB; p += blockDim.x) {
+    uint16_t cd = sC[p];
+    if (cd < 2) continue;
+    int y = p / RB, x = p - y * RB;
+    int gi = bi0 + x, gj = bj0 + y;
+    int r = op.tile_base[op.L.tile_of(gi, gj)] + cd - 2;
+    sU[p] = bval[r];
+    if (x > 0 && y > 0 && x < RB - 1 && y < RB - 1) {
+      int c = (gi & 1) + 2 * (gj & 1);
+      int pos = atomicAdd(&cnt[c], 1);
+      sL[c * cap + pos] = (uint16_t)p;
+      sRow[c * cap + pos] = r;
+    }
   }
   __syncthreads();
   for (int ph = 0; ph < 4 * eta; ++ph) {
@@ -177,12 +205,11 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
     for (int e = threadIdx.x; e < m; e += blockDim.x) {
       int p = sL[c * cap + e];
       int y = p / RB, x = p - y * RB;
-      int gi = bi0 + x, gj = bj0 + y;
-      const T* R = row_of(op, gi, gj, sC[p]);
+      const T* R = op.rows + (size_t)sRow[c * cap + e] * MG_ROW;
+      T f = F[op.L.idx(bi0 + x, bj0 + y)];
       const T* Up = sU + p;
       T acc = R[0] * Up[-RB - 1] + R[1] * Up[-RB] + R[2] * Up[-RB + 1] + R[3] * Up[-1] +
               R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[RB - 1] + R[7] * Up[RB] + R[8] * Up[RB + 1];
-      T f = F[op.L.idx(gi, gj)];
       sU[p] = Up[0] + (f - acc) * R[9];
     }
     __syncthreads();
@@ -206,7 +233,7 @@ __device__ __forceinline__ T node_residual(const OpArgs<T>& op, const T* Up, uin
   if (cd == 1) {
     T s8 = ((Up[-1] + Up[1]) + (Up[-RS] + Up[RS])) +
            ((Up[-RS - 1] + Up[-RS + 1]) + (Up[RS - 1] + Up[RS + 1]));
-    return f - (T(8) * Up[0] - s8) / T(3);
+    return f - (T(8) * Up[0] - s8) * T(1.0 / 3.0);
   }
   const T* R = row_of(op, gi, gj, cd);
   T acc = R[0] * Up[-RS - 1] + R[1] * Up[-RS] + R[2] * Up[-RS + 1] + R[3] * Up[-1] +
@@ -229,15 +256,30 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
   const int J0 = (t / Lc.ntx) * MG_TY + (sub >> 1) * 16;
   if (I0 > Lc.n || J0 > Lc.n) return;
   const int fi0 = 2 * I0 - 2, fj0 = 2 * J0 - 2;
-  for (int it = threadIdx.x; it < RR_Y * (RR_X / 2); it += blockDim.x) {
-    int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
-    size_t g = op.L.idx(fi0 + 2 * a, fj0 + rj);
-    T2 u2 = *reinterpret_cast<const T2*>(u + g);
-    uint32_t c2 = *reinterpret_cast<const uint32_t*>(op.code + g);
-    sU[rj * RR_X + 2 * a] = u2.x;
-    sU[rj * RR_X + 2 * a + 1] = u2.y;
-    sC[rj * RR_X + 2 * a] = (uint16_t)(c2 & 0xffffu);
-    sC[rj * RR_X + 2 * a + 1] = (uint16_t)(c2 >> 16);
+  {
+    constexpr int B = 4;
+    for (int it0 = threadIdx.x; it0 < RR_Y * (RR_X / 2); it0 += B * blockDim.x) {
+      T2 u2[B];
+      uint32_t c2[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        int it = it0 + b * blockDim.x;
+        int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
+        size_t g = it < RR_Y * (RR_X / 2) ? op.L.idx(fi0 + 2 * a, fj0 + rj) : op.L.idx(0, 0);
+        u2[b] = *reinterpret_cast<const T2*>(u + g);
+        c2[b] = *reinterpret_cast<const uint32_t*>(op.code + g);
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        int it = it0 + b * blockDim.x;
+        if (it >= RR_Y * (RR_X / 2)) continue;
+        int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
+        sU[rj * RR_X + 2 * a] = u2[b].x;
+        sU[rj * RR_X + 2 * a + 1] = u2[b].y;
+        sC[rj * RR_X + 2 * a] = (uint16_t)(c2[b] & 0xffffu);
+        sC[rj * RR_X + 2 * a + 1] = (uint16_t)(c2[b] >> 16);
+      }
+    }
   }
   __syncthreads();
   double vmax = 0.0, vsum = 0.0;
@@ -280,15 +322,30 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
   const int t = tiles[blockIdx.x];
   const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
   const int fi0 = i0 - 2, fj0 = j0 - 2;
-  for (int it = threadIdx.x; it < RR_Y * (RR_X / 2); it += blockDim.x) {
-    int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
-    size_t g = op.L.idx(fi0 + 2 * a, fj0 + rj);
-    T2 u2 = *reinterpret_cast<const T2*>(u + g);
-    uint32_t c2 = *reinterpret_cast<const uint32_t*>(op.code + g);
-    sU[rj * RR_X + 2 * a] = u2.x;
-    sU[rj * RR_X + 2 * a + 1] = u2.y;
-    sC[rj * RR_X + 2 * a] = (uint16_t)(c2 & 0xffffu);
-    sC[rj * RR_X + 2 * a + 1] = (uint16_t)(c2 >> 16);
+  {
+    constexpr int B = 4;
+    for (int it0 = threadIdx.x; it0 < RR_Y * (RR_X / 2); it0 += B * blockDim.x) {
+      T2 u2[B];
+      uint32_t c2[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        int it = it0 + b * blockDim.x;
+        int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
+        size_t g = it < RR_Y * (RR_X / 2) ? op.L.idx(fi0 + 2 * a, fj0 + rj) : op.L.idx(0, 0);
+        u2[b] = *reinterpret_cast<const T2*>(u + g);
+        c2[b] = *reinterpret_cast<const uint32_t*>(op.code + g);
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        int it = it0 + b * blockDim.x;
+        if (it >= RR_Y * (RR_X / 2)) continue;
+        int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
+        sU[rj * RR_X + 2 * a] = u2[b].x;
+        sU[rj * RR_X + 2 * a + 1] = u2[b].y;
+        sC[rj * RR_X + 2 * a] = (uint16_t)(c2[b] & 0xffffu);
+        sC[rj * RR_X + 2 * a + 1] = (uint16_t)(c2[b] >> 16);
+      }
+    }
   }
   __syncthreads();
   double vmax = 0.0, vsum = 0.0;
@@ -313,19 +370,30 @@ k_prolong(OpArgs<T> op, const int* __restrict__ tiles, T* __restrict__ uf, Layou
           const T* __restrict__ ec) {
   const int t = tiles[blockIdx.x];
   const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
-  for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
+  constexpr int B = MG_TX * MG_TY / kThreads;     // 8 nodes per thread, loads batched
+  uint16_t cd[B];
+  T uu[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    int it = threadIdx.x + b * blockDim.x;
+    int rr = it / MG_TX, ii = it - rr * MG_TX;
+    size_t g = op.L.idx(i0 + ii, j0 + rr);
+    cd[b] = op.code[g];
+    uu[b] = uf[g];
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    if (cd[b] == 0) continue;
+    int it = threadIdx.x + b * blockDim.x;
     int rr = it / MG_TX, ii = it - rr * MG_TX;
     int i = i0 + ii, j = j0 + rr;
-    size_t g = op.L.idx(i, j);
-    if (op.code[g] == 0) continue;
-    int I = i >> 1, J = j >> 1;
-    const T* E = ec + Lc.idx(I, J);
+    const T* E = ec + Lc.idx(i >> 1, j >> 1);
     T e;
     if (!(i & 1) && !(j & 1)) e = E[0];
     else if (!(j & 1)) e = T(0.5) * (E[0] + E[1]);
     else if (!(i & 1)) e = T(0.5) * (E[0] + E[Lc.pitch]);
     else e = T(0.25) * ((E[0] + E[1]) + (E[Lc.pitch] + E[Lc.pitch + 1]));
-    uf[g] += e;
+    uf[op.L.idx(i, j)] = uu[b] + e;
   }
 }
 
@@ -467,7 +535,8 @@ size_t sweep_smem() { return 4 * SW_PLANE * (2 * sizeof(T) + sizeof(uint16_t)); 
 template <class T>
 size_t band_smem(int eta) {
   int H = 4 * eta + 1, RB = 32 + 2 * H, cap = ((RB + 1) / 2) * ((RB + 1) / 2);
-  return (size_t)RB * RB * (sizeof(T) + sizeof(uint16_t)) + 4 * (size_t)cap * sizeof(uint16_t);
+  return (size_t)RB * RB * (sizeof(T) + sizeof(uint16_t)) +
+         4 * (size_t)cap * (sizeof(int) + sizeof(uint16_t));
 }
 
 template <class T>

@@ -1,0 +1,25 @@
+// Fused smoothing step for the intermediate levels (see fused.cu).
+#pragma once
+
+#include "common.cuh"
+
+template <class T> struct FusedArgs {
+  Layout L;                 // this level
+  const uint16_t* code;
+  const int* tile_base;
+  const T* rows;
+  const int* tiles;         // tiles to process
+  int eta;
+  const T* uin;             // u before the step (unused when starting from 0)
+  T* uout;                  // u after the step
+  const T* F;
+  Layout Lc;                // next coarser level (prolongation source / restriction target)
+  const T* ec;              // coarse correction to prolongate
+  T* Fc;                    // restricted residual
+};
+
+size_t fused_smem_bytes(int eta, size_t elem);
+template <class T> cudaError_t configure_fused(size_t smem);
+template <class T>
+void launch_smooth_step(const FusedArgs<T>& a, int ntiles, bool zero_in, bool prolong,
+                        bool restrict_, size_t smem, cudaStream_t st);

@@ -91,7 +91,7 @@ k_residual_static(Layout L, const uint16_t* __restrict__ code, const int* __rest
       if (cd == 1) {
         double s8 = ((Up[-1] + Up[1]) + (Up[-kRX] + Up[kRX])) +
                     ((Up[-kRX - 1] + Up[-kRX + 1]) + (Up[kRX - 1] + Up[kRX + 1]));
-        res = f - (8.0 * Up[0] - s8) / 3.0;
+        res = f - (8.0 * Up[0] - s8) * (1.0 / 3.0);
       } else {
         const double* R = rows + (size_t)(tile_base[t] + cd - 2) * MG_ROW;
         double acc = R[0] * Up[-kRX - 1] + R[1] * Up[-kRX] + R[2] * Up[-kRX + 1] +

@@ -197,6 +197,23 @@ __global__ void k_tile_assemble(CellData cd, Layout L, const int* __restrict__ t
   }
 }
 
+// Flag the fine tiles whose 32 x 16 block of coarse nodes holds a coarse DOF
+// (a superset of the active fine tiles: a fine DOF at (i, j) makes the coarse
+// node (i/2, j/2) a DOF); the fused restriction runs on these tiles so that
+// every coarse DOF receives its restricted residual.
+__global__ void k_restrict_tile_flags(Layout Lf, Layout Lc, const uint16_t* __restrict__ code_c,
+                                      uint8_t* __restrict__ flag) {
+  int t = blockIdx.x;
+  int tx = t % Lf.ntx, ty = t / Lf.ntx;
+  int any = 0;
+  for (int k = threadIdx.x; k < (MG_TX / 2) * (MG_TY / 2); k += blockDim.x) {
+    int I = tx * (MG_TX / 2) + k % (MG_TX / 2), J = ty * (MG_TY / 2) + k / (MG_TX / 2);
+    if (I <= Lc.n && J <= Lc.n && code_c[Lc.idx(I, J)] != 0) any = 1;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) flag[t] = any ? 1 : 0;
+}
+
 // Flag the 32 x 32 band tiles containing boundary nodes.
 __global__ void k_band_flags(const int* __restrict__ bnode, int nb, int nbx, uint8_t* __restrict__ flag) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -400,6 +417,11 @@ void launch_tile_assemble(const CellData& cd, const Layout& L, const int* tile_b
 
 void launch_band_flags(const int* bnode, int nb, int nbx, uint8_t* flag, cudaStream_t st) {
   if (nb) k_band_flags<<<(nb + 255) / 256, 256, 0, st>>>(bnode, nb, nbx, flag);
+}
+
+void launch_restrict_tile_flags(const Layout& Lf, const Layout& Lc, const uint16_t* code_c,
+                                uint8_t* flag, cudaStream_t st) {
+  k_restrict_tile_flags<<<Lf.ntx * Lf.nty, 256, 0, st>>>(Lf, Lc, code_c, flag);
 }
 
 void launch_coarse_class(const uint8_t* fcls, int nf, uint8_t* ccls, uint8_t* cut_flag,

@@ -28,6 +28,8 @@ void launch_tile_assemble(const CellData& cd, const Layout& L, const int* tile_b
                           uint16_t* code, double* rows, int* bnode, unsigned* err,
                           cudaStream_t st);
 void launch_band_flags(const int* bnode, int nb, int nbx, uint8_t* flag, cudaStream_t st);
+void launch_restrict_tile_flags(const Layout& Lf, const Layout& Lc, const uint16_t* code_c,
+                                uint8_t* flag, cudaStream_t st);
 void launch_coarse_class(const uint8_t* fcls, int nf, uint8_t* ccls, uint8_t* cut_flag,
                          cudaStream_t st);
 void launch_coarse_cut(const CellData& fine, const int* clist, int ncut, int nc, double* Ke,

@@ -6,9 +6,12 @@ integrals and stencils in a different order, so entries agree to a few ulp):
 operator rows of every level to 1e-13 of the level's largest entry, cut-cell
 C, lambda, Ke, Mk, Gk to 1e-13 (relative / relative to the cell's largest
 entry), F to 1e-13; iterates of the 4-colour V(2,1)-cycle after k cycles to
-1e-10 of max|u|; solutions driven to ||F - Au||/||F|| <= 1e-13 to 1e-10 of
-the oracle's direct solution (refined to fp64 exactness).  Mixed precision
-(fp32 V-cycle inside fp64 refinement): driven to 1e-12, within 1e-9 max|u|;
+1e-10 max|u| + 64 k eps S_p at node p; solutions driven to
+||F - Au||/||F|| <= 1e-13 to 1e-10 max|u| + 64 eps S_p of the oracle's direct
+solution (refined to fp64 exactness), with S_p the rounding sensitivity of
+node p's equation (tests/parity_tol.py: it matters only at ghost nodes on
+tiny cut regions).  Mixed precision (fp32 V-cycle inside fp64 refinement):
+driven to 1e-12, within 1e-9 max|u| + 64 eps S_p;
 stopped at 1e-10, the oracle's own residual of the result is <= 1e-10 and
 the error is within 3x that of the fp64 V-cycle stopped at the same
 residual (the stopping test, not fp32, bounds the error there).
@@ -19,6 +22,8 @@ import pytest
 from oracle import ghostfem as gf
 from oracle import multigrid as mg
 from paper_2505_05105_gb300 import workloads as wl
+from parity_tol import (assert_nodewise, assert_solution, node_tolerance, residual,
+                        residual_term)
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +67,7 @@ PROBLEMS = {
     "hourglass64": lambda: wl.paper_hourglass(64),
     "discs256": lambda: wl.three_discs(256, seed=0),
     "batch3": lambda: wl.batch_geometry(3),
+    "flower512": lambda: wl.flower(512, k=7, phase=0.3),
 }
 
 
@@ -149,7 +155,8 @@ def test_residual(name, oracle_cache):
     assert nrm[1] == pytest.approx(np.linalg.norm(r_ref), rel=1e-10)
 
 
-@pytest.mark.parametrize("name", ["circle64", "flower128", "hourglass64", "discs256", "batch3"])
+@pytest.mark.parametrize("name", ["circle64", "flower128", "hourglass64", "discs256", "batch3",
+                                  "flower512"])
 def test_iterate_parity_vcycles(name, oracle_cache):
     p, s, lev = oracle_for(name, oracle_cache)
     F = s.rhs(p.f, p.g)
@@ -163,20 +170,30 @@ def test_iterate_parity_vcycles(name, oracle_cache):
             u_ref = mg.mg_cycle(lev, 0, u_ref, F, nu1=2, nu2=1, eta=4, order="color4")
             S.cycles(Fd, u, 1)
             got = host(u)
-            err = np.abs(got - u_ref).max() / np.abs(u_ref).max()
-            assert err <= 1e-10, (k, err)
+            assert_nodewise(got, u_ref, node_tolerance(s, F, u_ref, 1e-10, 64 * k), (name, k))
 
 
-@pytest.mark.parametrize("name", ["circle64", "flower128", "discs256"])
+@pytest.mark.parametrize("name", ["circle64", "flower128", "discs256", "flower512"])
 def test_solution_parity_fp64(name, oracle_cache):
+    # driven to the attainable fp64 residual: where ||F||_inf is dominated by
+    # the h-independent penalty terms of small cut cells, a relative residual
+    # of 1e-13 still allows interior errors of a few 1e-10
     p, s, lev = oracle_for(name, oracle_cache)
-    ud = gf.direct_solve(s, s.rhs(p.f, p.g))
-    with solver(p) as S:
+    F = s.rhs(p.f, p.g)
+    ud = gf.direct_solve(s, F)
+    # attainable relative residual: ~1e-16 |A| |u| / ||F||, larger when F is
+    # only the h^2-scaled source (g = 0)
+    tol = 1e-13 if name == "discs256" else 2e-15
+    with solver(p, max_cycles=200) as S:
         u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
-        info = S.solve(dev(p.f), dev(p.g), u, tol=1e-13)
+        info = S.solve(dev(p.f), dev(p.g), u, tol=tol)
         got = host(u)
-    assert info.rel_res <= 1e-13
-    assert np.abs(got - ud).max() <= 1e-10 * np.abs(ud).max()
+    assert info.rel_res <= tol
+    # the oracle's own residual of the GPU solution, then node-wise agreement
+    assert np.abs(residual(s, F, got)).max() <= 2 * tol * np.abs(F).max()
+    nweak, amax = assert_solution(got, ud, s, F, 1e-10, what=name)
+    print(f"{name}: {info.cycles} cycles, {nweak} weak ghost nodes "
+          f"(max amplification {amax:.3g})")
 
 
 @pytest.mark.parametrize("name", ["circle64", "flower128", "discs256"])
@@ -197,7 +214,7 @@ def test_solution_parity_mixed(name, oracle_cache):
         S.solve(dev(p.f), dev(p.g), u, tol=1e-10)
         fp64_10 = host(u)
     assert info.rel_res <= 1e-12
-    assert np.abs(tight - ud).max() <= 1e-9 * scale
+    assert_solution(tight, ud, s, F, 1e-9, what=name)
     # stopped at 1e-10: the oracle's residual of the result, and no less
     # accurate than the fp64 V-cycle at the same stopping residual
     r = F - s.A @ mixed10
