@@ -85,11 +85,15 @@ typedef struct {
  *   nu1 = 2, nu2 = 1  pre/post smoothing steps                 (Sec. 5.3), 0..8
  *   lambda_mode = MG_LAMBDA_LOCAL
  *   precision = MG_FP64 or MG_MIXED
- *   max_cycles = 100  cycles (MG_FP64) or refinement steps (MG_MIXED)      */
+ *   max_cycles = 100  cycles (MG_FP64) or refinement steps (MG_MIXED)
+ *   inner = 3     fp32 V-cycles per refinement step (MG_MIXED only), 1..8:
+ *                 each step computes the fp64 residual once, runs `inner`
+ *                 fp32 V-cycles on the correction equation, then updates u */
 typedef struct {
   double gamma, alpha;
   int eta, nu1, nu2;
   int lambda_mode, precision, max_cycles;
+  int inner;
 } mg_stab;
 
 /* Result summary of a solve. */

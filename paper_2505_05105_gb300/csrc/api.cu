@@ -40,10 +40,18 @@ struct Level {
   int* active = nullptr;
   int n_band = 0;
   int* band = nullptr;
+  int* band_off = nullptr;      // [5 n_band + 1] group offsets into band_ent
+  int2* band_ent = nullptr;     // boundary nodes of each band tile's region
+  BandMaps bmap[2]{};           // TMA maps of u32[0..1] (fp32) and u64[0..1] (fp64)
   int nbx = 0;
   int n_dof = 0;
   int n_rtiles = 0;
   int* rtiles = nullptr;        // tiles covering the coarse DOFs (fused restriction)
+  // fused smoothing steps (intermediate levels with few active tiles)
+  bool fused_ok = false;
+  FusedMaps fmap{};             // TMA maps of u32[0], u32[1], F32, code
+  int* foff = nullptr;          // [5 tile id ..] group offsets into fent
+  int2* fent = nullptr;         // boundary nodes of each tile's fused region
   // vectors
   double* u64[2] = {nullptr, nullptr};
   double* F64 = nullptr;
@@ -77,10 +85,11 @@ struct mg_ctx {
   std::vector<void*> allocs;
   double last_tol = 1e-10;
   int tail_level = -1;           // first level run by the single-block tail kernel
-  size_t tail_smem[2] = {0, 0};  // [float, double]
-  bool tail_rows_smem[2] = {false, false};
+  TailLayout tail_lay[2];          // [float, double] shared-memory layout of the tail block
+  unsigned char* tail_image[2] = {nullptr, nullptr};   // its static image
   bool fused[2] = {false, false};  // fused smoothing steps on the intermediate levels
   size_t fused_smem[2] = {0, 0};
+  int fused_max_tiles = 0;         // levels with more active tiles use the separate kernels
   float setup_ms = 0.f;
   float solve_ms = 0.f;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -147,6 +156,7 @@ int sync_check(mg_ctx* c) {
     cudaStreamSynchronize(c->st);
     if (err & DEV_ERR_NOT_SPD) return MG_ERR_NOT_SPD;
     if (err & (DEV_ERR_NAN | DEV_ERR_EDGE)) return MG_ERR_INVALID_ARG;
+    if (err & DEV_ERR_TIMEOUT) return MG_ERR_TIMEOUT;
     return MG_ERR_INTERNAL;
   }
   return MG_OK;
@@ -211,6 +221,27 @@ void harvest(mg_ctx* c) {
   c->pend.clear();
 }
 
+// Boundary-node lists (5 groups per tile, see launch_region_list) of the
+// regions of halo H around ntl tiles of tw x th nodes (tiles == nullptr: all
+// tiles, indexed by tile id).
+int build_region_lists(mg_ctx* c, Level& V, const int* tiles, int ntl, int tpr, int tw, int th,
+                       int H, int** off, int2** ent) {
+  const size_t ng = 5 * (size_t)ntl;
+  int *gcnt, *gtmp;
+  TRY(dalloc(c, &gcnt, ng));
+  TRY(dalloc(c, &gtmp, scan_tmp_ints(ng) + 8));
+  TRY(dalloc(c, off, ng + 1));
+  launch_region_list(V.L, V.code, V.tile_base, tiles, ntl, tpr, tw, th, H, gcnt, nullptr, nullptr,
+                     c->st);
+  exclusive_scan_int(gcnt, *off, *off + ng, ng, gtmp, c->st);
+  int nent = 0;
+  TRY(read_int(c, *off + ng, &nent));
+  TRY(dalloc(c, ent, (size_t)nent));
+  launch_region_list(V.L, V.code, V.tile_base, tiles, ntl, tpr, tw, th, H, nullptr, *off, *ent,
+                     c->st);
+  return MG_OK;
+}
+
 // Codes, boundary rows and tile lists of a level whose cells are ready.
 int build_nodes(mg_ctx* c, Level& V) {
   const Layout& L = V.L;
@@ -249,6 +280,9 @@ int build_nodes(mg_ctx* c, Level& V) {
   compact_flags_u8(bflag, V.band, d_cnt + 3, (size_t)nbx * nby, tmp, nullptr, c->st);
   TRY(read_int(c, d_cnt + 3, &V.n_band));
   V.nbx = nbx;
+  if (V.n_band > 0 && c->stab.eta > 0)
+    TRY(build_region_lists(c, V, V.band, V.n_band, nbx, 32, 32, 4 * c->stab.eta + 1, &V.band_off,
+                           &V.band_ent));
   size_t sz = L.size();
   TRY(dalloc(c, &V.u64[0], sz));
   TRY(dalloc(c, &V.u64[1], sz));
@@ -258,6 +292,13 @@ int build_nodes(mg_ctx* c, Level& V) {
   TRY(dalloc(c, &V.u32[1], sz));
   TRY(dalloc(c, &V.F32, sz));
   TRY(dalloc(c, &V.bval32, (size_t)V.n_bnd));
+  if (V.n_band > 0 && c->stab.eta > 0) {
+    const int bx = band_box_x(c->stab.eta), by = band_box_y(c->stab.eta);
+    for (int k = 0; k < 2; ++k) {
+      TRY(make_level_map(&V.bmap[0].u[k], V.u32[k], sizeof(float), L, bx, by));
+      TRY(make_level_map(&V.bmap[1].u[k], V.u64[k], sizeof(double), L, bx, by));
+    }
+  }
   return MG_OK;
 }
 
@@ -320,26 +361,19 @@ void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine) {
   if (eta > 0 && v.n_band > 0) {
     Launch k(c, fine ? MG_PROF_BAND : MG_PROF_COARSE, 1);
     launch_band<T>(op, v.band, v.n_band, v.nbx, eta, P<T>::u(v, cur), P<T>::F(v), P<T>::bval(v),
-                   c->st);
+                   v.band_off, v.band_ent, v.bmap[sizeof(T) == 8 ? 1 : 0], cur, c->d_err, c->st);
   }
 }
 
 template <class T>
 void tail_cycle(mg_ctx* c, int l, bool zero_init) {
-  const int nlev = (int)c->lev.size();
+  const int pi = sizeof(T) == 8 ? 1 : 0;
   TailArgs<T> a;
-  a.nlev = nlev - l;
-  for (int k = 0; k < a.nlev; ++k) {
-    Level& w = c->lev[l + k];
-    a.n[k] = w.n;
-    a.L[k] = w.L;
-    a.code[k] = w.code;
-    a.tile_base[k] = w.tile_base;
-    a.rows[k] = P<T>::rows(w);
-    a.n_bnd[k] = w.n_bnd;
-  }
-  a.rows_in_smem = c->tail_rows_smem[sizeof(T) == 8 ? 1 : 0] ? 1 : 0;
+  a.lay = c->tail_lay[pi];
+  for (int k = 0; k < a.lay.nlev; ++k) a.rows[k] = P<T>::rows(c->lev[l + k]);
   Level& v = c->lev[l];
+  a.L0 = v.L;
+  a.image = c->tail_image[pi];
   a.Ainv = c->Ainv;
   a.F0 = P<T>::F(v);
   a.u0 = P<T>::u(v, P<T>::cur(v));
@@ -347,8 +381,9 @@ void tail_cycle(mg_ctx* c, int l, bool zero_init) {
   a.eta = c->stab.eta;
   a.nu1 = c->stab.nu1;
   a.nu2 = c->stab.nu2;
+  a.err = c->d_err;
   Launch k(c, MG_PROF_COARSE, 1);
-  launch_tail<T>(a, c->tail_smem[sizeof(T) == 8 ? 1 : 0], c->st);
+  launch_tail<T>(a, c->st);
 }
 
 template <class T>
@@ -368,20 +403,23 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
   a.code = v.code;
   a.tile_base = v.tile_base;
   a.rows = P<T>::rows(v);
+  a.loff = v.foff;
+  a.lent = v.fent;
   a.eta = c->stab.eta;
   a.F = P<T>::F(v);
   a.Lc = w.L;
   a.Fc = P<T>::F(w);
   a.ec = nullptr;
+  a.err = c->d_err;
   const int nu1 = c->stab.nu1, nu2 = c->stab.nu2;
   for (int s = 0; s < nu1; ++s) {
     const bool last = s == nu1 - 1;
-    a.uin = P<T>::u(v, cur);
+    a.uin_map = cur;
     a.uout = P<T>::u(v, cur ^ 1);
     a.tiles = last ? v.rtiles : v.active;
     Launch k(c, MG_PROF_COARSE, 1);
-    launch_smooth_step<T>(a, last ? v.n_rtiles : v.n_active, zero_init && s == 0, false, last,
-                          smem, c->st);
+    launch_smooth_step<T>(a, v.fmap, last ? v.n_rtiles : v.n_active, zero_init && s == 0, false,
+                          last, smem, c->st);
     cur ^= 1;
   }
   if (nu1 == 0) {
@@ -394,10 +432,10 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
   a.ec = P<T>::u(w, P<T>::cur(w));
   a.tiles = v.active;
   for (int s = 0; s < nu2; ++s) {
-    a.uin = P<T>::u(v, cur);
+    a.uin_map = cur;
     a.uout = P<T>::u(v, cur ^ 1);
     Launch k(c, MG_PROF_COARSE, 1);
-    launch_smooth_step<T>(a, v.n_active, false, s == 0, false, smem, c->st);
+    launch_smooth_step<T>(a, v.fmap, v.n_active, false, s == 0, false, smem, c->st);
     cur ^= 1;
   }
   if (nu2 == 0) {
@@ -423,7 +461,7 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
   }
   const bool fine = l == 0;
   int& cur = P<T>::cur(v);
-  if (!fine && c->fused[sizeof(T) == 8 ? 1 : 0]) {
+  if (!fine && sizeof(T) == 4 && v.fused_ok) {
     fused_cycle<T>(c, l, zero_init);
     return;
   }
@@ -476,11 +514,12 @@ double pow2_near_inverse(double x) {
   return std::ldexp(1.0, -e);
 }
 
-// One refinement step: r = F - A u (fp64) -> sigma r in fp32, one fp32
-// V-cycle from e = 0, u += e / sigma.  rmax is ||F - A u||_inf before it.
-void refinement_step(mg_ctx* c, double sigma) {
+// One refinement step on sigma r (fp32, already in the fine level's fp32
+// right-hand side): `inner` fp32 V-cycles on A e = sigma r, the first from
+// e = 0, then u += e / sigma in fp64.
+void refinement_step(mg_ctx* c, double sigma, int inner) {
   Level& v = c->lev[0];
-  vcycle<float>(c, 0, true);
+  for (int s = 0; s < inner; ++s) vcycle<float>(c, 0, s == 0);
   Launch k(c, MG_PROF_UPDATE, v.n_active > 0);
   launch_update(v.L, v.active, v.n_active, v.code, v.u64[v.cur64], v.u32[v.cur32], 1.0 / sigma,
                 c->st);
@@ -501,7 +540,7 @@ int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info) 
   if (info) info->res_hist[0] = rel;
   while (rel > tol) {
     if (k >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
-    if (mixed) refinement_step(c, sigma);
+    if (mixed) refinement_step(c, sigma, c->stab.inner);
     else vcycle<double>(c, 0, false);
     ++k;
     if (mixed) sigma = pow2_near_inverse(rmax * 0.1);
@@ -578,6 +617,7 @@ int mg_default_stab(mg_stab* out) {
   out->lambda_mode = MG_LAMBDA_LOCAL;
   out->precision = MG_FP64;
   out->max_cycles = 100;
+  out->inner = 3;
   return MG_OK;
 }
 
@@ -673,6 +713,12 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     MG_CUDA_TRY(cudaGetDevice(&dev));
     MG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     optin -= 1024;   // static shared memory of the kernel
+    int nsm = 0;
+    MG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // the fused step recomputes a wide halo per tile: it pays while the level
+    // fits in about two waves of one block per SM; beyond that the separate
+    // sweep, band, restriction and prolongation kernels move less data
+    c->fused_max_tiles = 2 * nsm;
     // fp32 only: on GB300 the redundant halo arithmetic of the fused step is
     // cheap in fp32 but fp64 arithmetic is a small fraction of the fp32 rate
     for (int pi = 0; pi < 1; ++pi) {
@@ -709,25 +755,63 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     MG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     optin -= 1024;   // static shared memory of the kernel
     if (t < nlev && nlev - t <= MG_TAIL_MAX_LEVELS) {
-      int n[MG_TAIL_MAX_LEVELS];
-      for (int k = 0; k < nlev - t; ++k) n[k] = c->lev[t + k].n;
-      int nb[MG_TAIL_MAX_LEVELS];
-      for (int k = 0; k < nlev - t; ++k) nb[k] = c->lev[t + k].n_bnd;
-      size_t s32 = tail_smem_bytes(n, nlev - t, sizeof(float));
-      size_t s64 = tail_smem_bytes(n, nlev - t, sizeof(double));
-      if (s64 + tail_list_bytes(nb, nlev - t) <= (size_t)optin) {
-        c->tail_level = t;
-        // stage the boundary rows in shared memory when they fit
-        size_t r32 = tail_rows_bytes(nb, nlev - t, sizeof(float));
-        size_t r64 = tail_rows_bytes(nb, nlev - t, sizeof(double));
-        size_t lb = tail_list_bytes(nb, nlev - t);
-        c->tail_rows_smem[0] = s32 + r32 + lb <= (size_t)optin;
-        c->tail_rows_smem[1] = s64 + r64 + lb <= (size_t)optin;
-        c->tail_smem[0] = s32 + (c->tail_rows_smem[0] ? r32 : 0) + lb;
-        c->tail_smem[1] = s64 + (c->tail_rows_smem[1] ? r64 : 0) + lb;
-        MG_CUDA_TRY(configure_tail<float>(c->tail_smem[0]));
-        MG_CUDA_TRY(configure_tail<double>(c->tail_smem[1]));
+      const int nl = nlev - t;
+      int n[MG_TAIL_MAX_LEVELS], nb[MG_TAIL_MAX_LEVELS];
+      TailLevelSrc src[MG_TAIL_MAX_LEVELS];
+      for (int k = 0; k < nl; ++k) {
+        Level& w = c->lev[t + k];
+        n[k] = w.n;
+        nb[k] = w.n_bnd;
+        src[k] = TailLevelSrc{w.L, w.code, w.tile_base};
       }
+      const int m = (n[nl - 1] + 1) * (n[nl - 1] + 1);
+      TailLayout l32, l64;
+      if (tail_layout(n, nb, nl, m, sizeof(float), (size_t)optin, &l32) &&
+          tail_layout(n, nb, nl, m, sizeof(double), (size_t)optin, &l64)) {
+        c->tail_level = t;
+        const TailLayout* lay[2] = {&l32, &l64};
+        for (int pi = 0; pi < 2; ++pi) {
+          const TailLayout& y = *lay[pi];
+          c->tail_lay[pi] = y;
+          TRY(dalloc(c, &c->tail_image[pi], y.image_bytes));
+          launch_tail_image(y, src, c->tail_image[pi], c->st);
+          for (int k = 0; k < nl && y.rows_in_smem; ++k) {
+            Level& w = c->lev[t + k];
+            const size_t elem = pi ? sizeof(double) : sizeof(float);
+            const void* r = pi ? (const void*)w.rows64 : (const void*)w.rows32;
+            if (w.n_bnd)
+              MG_CUDA_TRY(cudaMemcpyAsync(c->tail_image[pi] + y.rows[k], r,
+                                          (size_t)w.n_bnd * MG_ROW * elem,
+                                          cudaMemcpyDeviceToDevice, c->st));
+          }
+          if (y.ainv_in_smem)
+            MG_CUDA_TRY(cudaMemcpyAsync(c->tail_image[pi] + y.Ainv, c->Ainv,
+                                        (size_t)m * m * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->st));
+        }
+        MG_CUDA_TRY(configure_tail<float>(l32.total));
+        MG_CUDA_TRY(configure_tail<double>(l64.total));
+      }
+    }
+  }
+  if (c->fused[0]) {
+    // TMA maps and boundary-node lists of the levels run by fused steps:
+    // between the fine level and the tail, with at most fused_max_tiles
+    // active tiles
+    const int nlev = (int)c->lev.size();
+    const int end = c->tail_level >= 0 ? c->tail_level : nlev - 1;
+    const int eta = c->stab.eta;
+    const int bx = fused_box_x(eta), by = fused_box_y(eta);
+    for (int l = 1; l < end; ++l) {
+      Level& v = c->lev[l];
+      if (v.n_active > c->fused_max_tiles) continue;
+      TRY(make_level_map(&v.fmap.u[0], v.u32[0], sizeof(float), v.L, bx, by));
+      TRY(make_level_map(&v.fmap.u[1], v.u32[1], sizeof(float), v.L, bx, by));
+      TRY(make_level_map(&v.fmap.F, v.F32, sizeof(float), v.L, bx, by));
+      TRY(make_level_map(&v.fmap.code, v.code, sizeof(uint16_t), v.L, bx, by));
+      TRY(build_region_lists(c, v, nullptr, v.L.ntx * v.L.nty, v.L.ntx, MG_TX, MG_TY,
+                             fused_halo(eta), &v.foff, &v.fent));
+      v.fused_ok = true;
     }
   }
   TRY(sync_check(c));
@@ -752,7 +836,8 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
   if (!(g.h > 0.0) || !std::isfinite(g.h) || !std::isfinite(g.x0) || !std::isfinite(g.y0))
     return MG_ERR_INVALID_ARG;
   if (!(s.gamma > 0.0) || !(s.alpha > 0.0) || s.eta < 0 || s.eta > 8 || s.nu1 < 0 || s.nu1 > 8 ||
-      s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0)
+      s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0 || s.inner < 1 ||
+      s.inner > 8)
     return MG_ERR_INVALID_ARG;
   if (s.lambda_mode != MG_LAMBDA_LOCAL) return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_FP64 && s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
@@ -811,10 +896,9 @@ int mg_solve(mg_handle c, const double* f, const double* g, double* u, double to
   MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
   {
     Launch k(c, MG_PROF_IO, 4);
-    launch_check_finite(sf.dev, m, c->d_err, c->st);
-    launch_check_finite(sg.dev, m, c->d_err, c->st);
+    launch_check_finite2(sf.dev, sg.dev, m, c->d_err, c->st);
     RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
-    launch_rhs(ra, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
+    launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
     v.cur64 = 0;
     launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st);
   }
@@ -856,7 +940,7 @@ int mg_rhs(mg_handle c, const double* f, const double* g, double* F) {
   TRY(stage_out(c, 2, F, &Fd, &Fh));
   MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
   RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
-  launch_rhs(ra, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
+  launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
   launch_unpack(v.L, v.code, v.F64, Fd, c->st);
   TRY(finish_out(c, F, Fd, Fh));
   return sync_check(c);
@@ -883,7 +967,7 @@ int mg_cycles(mg_handle c, const double* F, double* u, int k, int precision) {
       OpArgs<double> op = op_of<double>(v);
       launch_residual<double, float>(op, v.active, v.n_active, v.u64[v.cur64], v.F64, v.F32, sigma,
                                      (double*)nullptr, c->st);
-      refinement_step(c, sigma);
+      refinement_step(c, sigma, 1);
     }
   }
   double* ud = const_cast<double*>(su.dev);

@@ -32,6 +32,8 @@ enum : unsigned {
   DEV_ERR_NOT_SPD = 4u,      // coarsest Cholesky pivot <= 0
   DEV_ERR_TILE = 8u,         // more boundary nodes in a tile than codes allow
   DEV_ERR_GEOM = 16u,        // unexpected cut configuration
+  DEV_ERR_TIMEOUT = 32u,     // a bounded device wait ran out
+  DEV_ERR_ALIGN = 64u,       // a TMA / bulk copy operand failed its alignment check
 };
 
 struct Layout {
@@ -112,6 +114,40 @@ __device__ __forceinline__ void block_norms_to_global(double vmax, double vsum, 
       atomicAdd(out + 1, vsum);
     }
   }
+}
+
+// Programmatic dependent launch ---------------------------------------------
+//
+// The V-cycle kernels are launched with programmatic stream serialization:
+// a kernel's blocks may start while the previous kernel's last blocks are
+// still running.  Each kernel reads only static data (codes, lists, rows,
+// tensor maps) before griddep_wait(); every read of data another kernel
+// writes (u, F, bval, e, norms) and every global write comes after it.  The
+// wait returns once the previous kernel has completed and its writes are
+// visible (immediately when launched without the attribute).
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+// Lets the next kernel in the stream launch once every block of this one has
+// started (it still waits in griddep_wait for this kernel to complete).
+__device__ __forceinline__ void griddep_launch_next() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 // Host helpers ----------------------------------------------------------------

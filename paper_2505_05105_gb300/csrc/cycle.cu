@@ -17,6 +17,7 @@
 //   k_coarse_solve    u = A^{-1} F on the coarsest level (dense inverse)
 //   k_rhs             F = M f + G g (Eq. disc_rhs with Q1 interpolants)
 #include "cycle.cuh"
+#include "bandreg.cuh"
 
 namespace {
 
@@ -38,6 +39,8 @@ template <class T, bool ZERO_IN>
 __global__ void __launch_bounds__(kThreads)
 k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ uin,
            T* __restrict__ uout, const T* __restrict__ F, T* __restrict__ bval) {
+  griddep_launch_next();
+  griddep_wait();
   typedef typename Vec2<T>::type T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sU = reinterpret_cast<T*>(smem_raw);            // [4][PY][PX] parity planes
@@ -138,90 +141,164 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
 // 4 eta colour phases redundantly on a halo of 4 eta + 1 nodes, so the owned
 // values equal those of the global sweep.  Boundary values are read from
 // bval (written by the preceding full sweep) and never from u, which other
-// blocks update concurrently.  The region is loaded with independent
-// coalesced loads, then each listed boundary node caches its row index and
-// F, so the colour phases touch only shared memory and L1-resident rows.
+// blocks update concurrently.  The region's boundary nodes come from a list
+// built at setup (grouped by colour, rim last), so the block only
+//   1. loads u of the region with one TMA box copy and, meanwhile, stages
+//      row, F and bval of its first BandCap<T> listed nodes,
+//   2. overwrites the listed nodes with bval,
+//   3. runs the 4 eta colour phases on as many warps as the longest colour
+//      has 32-node groups (one warp syncs with __syncwarp, more with a
+//      named barrier),
+//   4. writes the owned listed nodes back.
+template <class T> struct BandCap;
+template <> struct BandCap<float> { static constexpr int value = 512; };
+template <> struct BandCap<double> { static constexpr int value = 256; };
+constexpr int kBandNS = MG_ROW + 2;    // staged per node: row, F, bval
+
+__host__ __device__ inline int band_halo(int eta) { return 4 * eta + 1; }
+__host__ __device__ inline int band_region(int eta) { return 32 + 2 * band_halo(eta); }
+__host__ __device__ inline size_t band_a128(size_t b) { return (b + 127) & ~(size_t)127; }
+
 template <class T>
 __global__ void __launch_bounds__(kThreads)
 k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __restrict__ u,
-       const T* __restrict__ F, const T* __restrict__ bval) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int H = 4 * eta + 1;
-  const int RB = 32 + 2 * H;
-  const int cap = ((RB + 1) / 2) * ((RB + 1) / 2);
-  T* sU = reinterpret_cast<T*>(smem_raw);
-  int* sRow = reinterpret_cast<int*>(sU + RB * RB);  // [4][cap] row index of listed nodes
-  uint16_t* sC = reinterpret_cast<uint16_t*>(sRow + 4 * cap);
-  uint16_t* sL = sC + RB * RB;                       // [4][cap] positions
-  __shared__ int cnt[4];
-  if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
-  const int bt = btiles[blockIdx.x];
+       const T* __restrict__ F, const T* __restrict__ bval, const int* __restrict__ boff,
+       const int2* __restrict__ bent, const __grid_constant__ BandMaps maps, int umap,
+       unsigned* err) {
+  griddep_launch_next();
+  constexpr int EC = BandCap<T>::value;
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem_raw = smem_align128(smem_dyn);
+  const int H = band_halo(eta);
+  const int RB = band_region(eta);
+  const int RS = tma_box_w(RB);                        // shared row stride (TMA box width)
+  T* sUb = reinterpret_cast<T*>(smem_raw);             // [RB][RS] TMA box
+  T* sS = reinterpret_cast<T*>(smem_raw + band_a128((size_t)RS * RB * sizeof(T)));  // [NS][EC]
+  int* sP = reinterpret_cast<int*>(sS + kBandNS * EC); // [EC] region positions
+  __shared__ uint64_t bar;
+  __shared__ int gs[6];
+  const int b = blockIdx.x;
+  const int bt = btiles[b];
   const int bi0 = (bt % nbx) * 32 - H, bj0 = (bt / nbx) * 32 - H;
-  const int n = op.L.n;
-  // 1. codes and values of the region: independent loads, 4 per thread in flight
-  constexpr int B = 4;
-  for (int p0 = threadIdx.x; p0 < RB * RB; p0 += B * blockDim.x) {
-    uint16_t cdv[B];
-    T val[B];
+  const int ax = tma_floor(bi0 + MG_G);
+  T* sU = sUb + (bi0 + MG_G - ax);                     // region (x, y) at sU[y RS + x]
+  __shared__ int bad;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    bad = !tma_box_ok(sUb, ax);
+  }
+  const int e0 = boff[5 * b];
+  if (threadIdx.x < 6) gs[threadIdx.x] = boff[5 * b + threadIdx.x] - e0;
+  const int m = boff[5 * b + 5] - e0;                  // all groups, rim included
+  const int nrim0 = boff[5 * b + 4] - e0;              // first rim entry
+  // 1a. static part of the listed nodes (rows, positions): before the wait
+  //     for the previous kernel
+  for (int e = threadIdx.x; e < m && e < EC; e += blockDim.x) {
+    const int2 en = bent[e0 + e];
+    const int x = en.x & 0xffff, y = en.x >> 16;
+    T v[MG_ROW];
+    if (e < nrim0) {
+      const T* R = op.rows + (size_t)en.y * MG_ROW;
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      int p = p0 + b * blockDim.x;
-      int y = p / RB, x = p - y * RB;
-      int gi = bi0 + x, gj = bj0 + y;
-      bool in = p < RB * RB && gi >= 0 && gj >= 0 && gi <= n && gj <= n;
-      size_t g = in ? op.L.idx(gi, gj) : 0;
-      cdv[b] = in ? op.code[g] : (uint16_t)0;
-      val[b] = in ? u[g] : T(0);
+      for (int k = 0; k < MG_ROW; ++k) v[k] = R[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < MG_ROW; ++k) v[k] = T(0);
     }
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      int p = p0 + b * blockDim.x;
-      if (p < RB * RB) {
-        sC[p] = cdv[b];
-        sU[p] = val[b];
-      }
-    }
+    for (int k = 0; k < MG_ROW; ++k) sS[k * EC + e] = v[k];
+    sP[e] = y * RS + x;
   }
   __syncthreads();
-  // 2. boundary nodes: value from bval, row index and F cached, colour lists
-  for (int p = threadIdx.x; p < RB * RB; p += blockDim.x) {
-    uint16_t cd = sC[p];
-    if (cd < 2) continue;
-    int y = p / RB, x = p - y * RB;
-    int gi = bi0 + x, gj = bj0 + y;
-    int r = op.tile_base[op.L.tile_of(gi, gj)] + cd - 2;
-    sU[p] = bval[r];
-    if (x > 0 && y > 0 && x < RB - 1 && y < RB - 1) {
-      int c = (gi & 1) + 2 * (gj & 1);
-      int pos = atomicAdd(&cnt[c], 1);
-      sL[c * cap + pos] = (uint16_t)p;
-      sRow[c * cap + pos] = r;
+  griddep_wait();
+  if (threadIdx.x == 0) {
+    if (!bad) {
+      mbar_arrive_expect_tx(&bar, (uint32_t)((size_t)RS * RB * sizeof(T)));
+      tma_load_2d(sUb, &maps.u[umap], ax, bj0 + MG_G, &bar);
+    } else {
+      atomicOr(err, DEV_ERR_ALIGN);
+      mbar_arrive_expect_tx(&bar, 0);
     }
   }
-  __syncthreads();
-  for (int ph = 0; ph < 4 * eta; ++ph) {
-    const int c = ph & 3;
-    const int m = cnt[c];
-    for (int e = threadIdx.x; e < m; e += blockDim.x) {
-      int p = sL[c * cap + e];
-      int y = p / RB, x = p - y * RB;
-      const T* R = op.rows + (size_t)sRow[c * cap + e] * MG_ROW;
-      T f = F[op.L.idx(bi0 + x, bj0 + y)];
-      const T* Up = sU + p;
-      T acc = R[0] * Up[-RB - 1] + R[1] * Up[-RB] + R[2] * Up[-RB + 1] + R[3] * Up[-1] +
-              R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[RB - 1] + R[7] * Up[RB] + R[8] * Up[RB + 1];
-      sU[p] = Up[0] + (f - acc) * R[9];
+  // 1b. F and bval of the listed nodes, while the TMA runs
+  for (int e = threadIdx.x; e < m && e < EC; e += blockDim.x) {
+    const int2 en = bent[e0 + e];
+    const int x = en.x & 0xffff, y = en.x >> 16;
+    const T f = e < nrim0 ? F[op.L.idx(bi0 + x, bj0 + y)] : T(0);
+    const T bv = bval[en.y];
+    sS[MG_ROW * EC + e] = f;
+    sS[(MG_ROW + 1) * EC + e] = bv;
+  }
+  const bool ok = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!ok || bad)) {
+    if (threadIdx.x == 0 && !ok) {
+      atomicOr(err, DEV_ERR_TIMEOUT);
+      mbar_wait(&bar, 0);        // bounded: let a copy still in flight land
     }
     __syncthreads();
+    return;
   }
-  for (int c = 0; c < 4; ++c) {
-    const int m = cnt[c];
-    for (int e = threadIdx.x; e < m; e += blockDim.x) {
-      int p = sL[c * cap + e];
-      int y = p / RB, x = p - y * RB;
-      if (x >= H && x < H + 32 && y >= H && y < H + 32)
-        u[op.L.idx(bi0 + x, bj0 + y)] = sU[p];
+  // 2. boundary values from bval
+  for (int e = threadIdx.x; e < m; e += blockDim.x) {
+    if (e < EC) {
+      sU[sP[e]] = sS[(MG_ROW + 1) * EC + e];
+    } else {
+      const int2 en = bent[e0 + e];
+      sU[(en.x >> 16) * RS + (en.x & 0xffff)] = bval[en.y];
     }
+  }
+  __syncthreads();
+  // 3. 4 eta colour phases on nw warps, each thread's nodes in registers
+  int g[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) g[c] = gs[c];
+  int mc = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) mc = max(mc, g[c + 1] - g[c]);
+  const int nw = min((int)(blockDim.x >> 5), max(1, (mc + 31) / 32));
+  if ((int)(threadIdx.x >> 5) < nw) {
+    auto fetch = [&](int e, T* w, int& p) {
+      if (e < EC) {
+        p = sP[e];
+#pragma unroll
+        for (int k = 0; k <= MG_ROW; ++k) w[k] = sS[k * EC + e];
+      } else {
+        const int2 en = bent[e0 + e];
+        const int x = en.x & 0xffff, y = en.x >> 16;
+        p = y * RS + x;
+        const T* R = op.rows + (size_t)en.y * MG_ROW;
+#pragma unroll
+        for (int k = 0; k < MG_ROW; ++k) w[k] = R[k];
+        w[MG_ROW] = F[op.L.idx(bi0 + x, bj0 + y)];
+      }
+    };
+    auto extra = [&](int e) {
+      T w[MG_ROW + 1];
+      int p;
+      fetch(e, w, p);
+      const T* Up = sU + p;
+      T acc = w[0] * Up[-RS - 1] + w[1] * Up[-RS] + w[2] * Up[-RS + 1] + w[3] * Up[-1] +
+              w[4] * Up[0] + w[5] * Up[1] + w[6] * Up[RS - 1] + w[7] * Up[RS] +
+              w[8] * Up[RS + 1];
+      sU[p] = Up[0] + (w[MG_ROW] - acc) * w[9];
+    };
+    band_phases_reg<T>(sU, RS, g, eta, 32 * nw, fetch, extra);
+  }
+  __syncthreads();
+  // 4. owned listed nodes back to u
+  for (int e = threadIdx.x; e < nrim0; e += blockDim.x) {
+    int x, y;
+    if (e < EC) {
+      const int p = sP[e];
+      y = p / RS;
+      x = p - y * RS;
+    } else {
+      const int2 en = bent[e0 + e];
+      x = en.x & 0xffff;
+      y = en.x >> 16;
+    }
+    if (x >= H && x < H + 32 && y >= H && y < H + 32)
+      u[op.L.idx(bi0 + x, bj0 + y)] = sU[y * RS + x];
   }
 }
 
@@ -247,6 +324,8 @@ template <class T, bool NORM>
 __global__ void __launch_bounds__(kThreads)
 k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F, Layout Lc,
                  const int* __restrict__ ctiles, T* __restrict__ Fc, double* __restrict__ norms) {
+  griddep_launch_next();
+  griddep_wait();
   typedef typename Vec2<T>::type T2;
   __shared__ __align__(16) T sU[RR_Y * RR_X];
   __shared__ __align__(16) T sR[RR_Y * RR_X];
@@ -316,6 +395,8 @@ template <class T, class TR>
 __global__ void __launch_bounds__(kThreads)
 k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
            const T* __restrict__ F, TR* __restrict__ rout, T scale, double* __restrict__ norms) {
+  griddep_launch_next();
+  griddep_wait();
   typedef typename Vec2<T>::type T2;
   __shared__ __align__(16) T sU[RR_Y * RR_X];
   __shared__ uint16_t sC[RR_Y * RR_X];
@@ -368,6 +449,8 @@ template <class T>
 __global__ void __launch_bounds__(kThreads)
 k_prolong(OpArgs<T> op, const int* __restrict__ tiles, T* __restrict__ uf, Layout Lc,
           const T* __restrict__ ec) {
+  griddep_launch_next();
+  griddep_wait();
   const int t = tiles[blockIdx.x];
   const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
   constexpr int B = MG_TX * MG_TY / kThreads;     // 8 nodes per thread, loads batched
@@ -400,6 +483,8 @@ k_prolong(OpArgs<T> op, const int* __restrict__ tiles, T* __restrict__ uf, Layou
 template <class T>
 __global__ void k_coarse_solve(Layout Lc, const double* __restrict__ Ainv, const T* __restrict__ Fc,
                                T* __restrict__ uc) {
+  griddep_launch_next();
+  griddep_wait();
   extern __shared__ double sF[];
   const int n = Lc.n, m = (n + 1) * (n + 1);
   for (int p = threadIdx.x; p < m; p += blockDim.x)
@@ -412,39 +497,81 @@ __global__ void k_coarse_solve(Layout Lc, const double* __restrict__ Ainv, const
   }
 }
 
-__global__ void k_rhs(RhsArgs a, const double* __restrict__ f, const double* __restrict__ g,
-                      double* __restrict__ F, double* __restrict__ norms) {
+// F = M f + G g on one active tile (64 x 32 nodes).  Interior nodes (all
+// four cells inside) take the whole-cell Q1 mass, whose sum over the four
+// cells is the separable 9-point stencil h^2/36 [1 4 1] x [1 4 1]: a row pass
+// and a column pass over f staged in shared memory (5 fp64 operations per
+// node instead of 16).  Vertices of cut cells sum the cells one by one, with
+// the cut cells' Mk and Gk (Eq. disc_rhs with Q1 interpolants).
+constexpr int RHS_X = MG_TX + 2, RHS_Y = MG_TY + 2;
+__global__ void __launch_bounds__(kThreads)
+k_rhs(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ f,
+      const double* __restrict__ g, double* __restrict__ F, double* __restrict__ norms) {
+  __shared__ double sf[RHS_Y * RHS_X];       // f on the tile plus one ring
+  __shared__ double st[RHS_Y * MG_TX];       // row pass f(i-1) + 4 f(i) + f(i+1)
   const int n = a.L.n;
-  const size_t m = (size_t)(n + 1) * (n + 1);
+  const size_t W = (size_t)n + 1;
+  const int t = tiles[blockIdx.x];
+  const int i0 = (t % a.L.ntx) * MG_TX, j0 = (t / a.L.ntx) * MG_TY;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int y = warp; y < RHS_Y; y += nw) {
+    const int j = j0 - 1 + y;
+    double v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int x = lane + 32 * k, i = i0 - 1 + x;
+      const bool in = x < RHS_X && i >= 0 && j >= 0 && i <= n && j <= n;
+      v[k] = in ? f[(size_t)j * W + i] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int x = lane + 32 * k;
+      if (x < RHS_X) sf[y * RHS_X + x] = v[k];
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < RHS_Y * MG_TX; q += blockDim.x) {
+    const int y = q / MG_TX, x = q - y * MG_TX;
+    const double* r = sf + y * RHS_X + x;
+    st[q] = fma(4.0, r[1], r[0] + r[2]);
+  }
+  __syncthreads();
   const double h2 = a.h * a.h / 36.0;
   double vmax = 0.0;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
-       k += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(k % (n + 1)), j = (int)(k / (n + 1));
-    size_t gk = a.L.idx(i, j);
+  for (int q = threadIdx.x; q < MG_TY * MG_TX; q += blockDim.x) {
+    const int y = q / MG_TX, x = q - y * MG_TX;
+    const int i = i0 + x, j = j0 + y;
+    const size_t gk = a.L.idx(i, j);
+    const uint16_t cd = a.code[gk];
     double s = 0.0;
-    if (a.code[gk]) {
-      for (int q = 0; q < 4; ++q) {
-        int dx = q & 1, dy = q >> 1;
-        int ic = i - 1 + dx, jc = j - 1 + dy;
+    if (cd == 1) {
+      const double* c = st + y * MG_TX + x;
+      s = h2 * fma(4.0, c[MG_TX], c[0] + c[2 * MG_TX]);
+    } else if (cd) {
+      for (int k = 0; k < 4; ++k) {
+        const int dx = k & 1, dy = k >> 1;
+        const int ic = i - 1 + dx, jc = j - 1 + dy;
         if (ic < 0 || jc < 0 || ic >= n || jc >= n) continue;
-        size_t c = (size_t)jc * n + ic;
-        uint8_t cl = a.cls[c];
+        const size_t c = (size_t)jc * n + ic;
+        const uint8_t cl = a.cls[c];
         if (cl == CELL_EXT) continue;
-        int av = (1 - dx) + 2 * (1 - dy);
-        size_t k0 = (size_t)jc * (n + 1) + ic;
-        size_t vk[4] = {k0, k0 + 1, k0 + n + 1, k0 + n + 2};
+        const int av = (1 - dx) + 2 * (1 - dy);
+        // the cell's vertices (0,0),(1,0),(0,1),(1,1) in sf
+        const double* fv = sf + (y + dy) * RHS_X + (x + dx);
+        const double fb[4] = {fv[0], fv[1], fv[RHS_X], fv[RHS_X + 1]};
         if (cl == CELL_INT) {
           // whole-cell Q1 mass h^2/36 [[4,2,2,1],...]: 4 on the diagonal,
           // 2 along edges, 1 across the diagonal
           for (int b = 0; b < 4; ++b) {
             int wgt = (b == av) ? 4 : ((b ^ av) == 3 ? 1 : 2);
-            s += h2 * wgt * f[vk[b]];
+            s += h2 * wgt * fb[b];
           }
         } else {
           const double* Mk = a.Mk + (size_t)a.cell_cut[c] * 16 + av * 4;
           const double* Gk = a.Gk + (size_t)a.cell_cut[c] * 16 + av * 4;
-          for (int b = 0; b < 4; ++b) s += Mk[b] * f[vk[b]] + Gk[b] * g[vk[b]];
+          const size_t k0 = (size_t)jc * W + ic;
+          const size_t vk[4] = {k0, k0 + 1, k0 + W, k0 + W + 1};
+          for (int b = 0; b < 4; ++b) s += Mk[b] * fb[b] + Gk[b] * g[vk[b]];
         }
       }
     }
@@ -452,6 +579,27 @@ __global__ void k_rhs(RhsArgs a, const double* __restrict__ f, const double* __r
     vmax = fmax(vmax, fabs(s));
   }
   block_norms_to_global(vmax, 0.0, norms);
+}
+
+// Any NaN or Inf in two arrays of m doubles (vectorised reads).
+__global__ void k_check_finite2(const double* __restrict__ p, const double* __restrict__ q,
+                                size_t m, unsigned* err) {
+  bool bad = false;
+  const size_t m2 = m / 2;
+  const bool al = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0;
+  if (al) {
+    const double2* p2 = reinterpret_cast<const double2*>(p);
+    const double2* q2 = reinterpret_cast<const double2*>(q);
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m2;
+         k += (size_t)gridDim.x * blockDim.x) {
+      double2 a = p2[k], b = q2[k];
+      bad |= !isfinite(a.x) || !isfinite(a.y) || !isfinite(b.x) || !isfinite(b.y);
+    }
+  }
+  for (size_t k = (al ? 2 * m2 : 0) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(p[k]) || !isfinite(q[k]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEV_ERR_NAN);
 }
 
 template <class T>
@@ -481,14 +629,11 @@ __global__ void k_unpack(Layout L, const uint16_t* __restrict__ code, const doub
   }
 }
 
-__global__ void k_check_finite(const double* __restrict__ p, size_t m, unsigned* err) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
-       k += (size_t)gridDim.x * blockDim.x)
-    if (!isfinite(p[k])) atomicOr(err, DEV_ERR_NAN);
-}
 
 __global__ void k_update(Layout L, const int* __restrict__ tiles, const uint16_t* __restrict__ code,
                          double* __restrict__ u, const float* __restrict__ e, double inv_scale) {
+  griddep_launch_next();
+  griddep_wait();
   const int t = tiles[blockIdx.x];
   const int i0 = (t % L.ntx) * MG_TX, j0 = (t / L.ntx) * MG_TY;
   for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
@@ -534,10 +679,13 @@ size_t sweep_smem() { return 4 * SW_PLANE * (2 * sizeof(T) + sizeof(uint16_t)); 
 
 template <class T>
 size_t band_smem(int eta) {
-  int H = 4 * eta + 1, RB = 32 + 2 * H, cap = ((RB + 1) / 2) * ((RB + 1) / 2);
-  return (size_t)RB * RB * (sizeof(T) + sizeof(uint16_t)) +
-         4 * (size_t)cap * (sizeof(int) + sizeof(uint16_t));
+  const int RB = band_region(eta), RS = tma_box_w(RB), EC = BandCap<T>::value;
+  return kSmemSlack + band_a128((size_t)RS * RB * sizeof(T)) + (size_t)kBandNS * EC * sizeof(T) +
+         (size_t)EC * sizeof(int);
 }
+
+int band_box_x(int eta) { return tma_box_w(band_region(eta)); }
+int band_box_y(int eta) { return band_region(eta); }
 
 template <class T>
 cudaError_t configure_kernels(int eta) {
@@ -560,16 +708,20 @@ void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T*
                      const T* F, T* bval, bool zero_in, cudaStream_t st) {
   if (!ntiles) return;
   if (zero_in)
-    k_gs_sweep<T, true><<<ntiles, kThreads, sweep_smem<T>(), st>>>(op, tiles, uin, uout, F, bval);
+    launch_pdl(k_gs_sweep<T, true>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin, uout, F,
+               bval);
   else
-    k_gs_sweep<T, false><<<ntiles, kThreads, sweep_smem<T>(), st>>>(op, tiles, uin, uout, F, bval);
+    launch_pdl(k_gs_sweep<T, false>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin, uout,
+               F, bval);
 }
 
 template <class T>
 void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
-                 const T* F, const T* bval, cudaStream_t st) {
+                 const T* F, const T* bval, const int* boff, const int2* bent,
+                 const BandMaps& maps, int umap, unsigned* err, cudaStream_t st) {
   if (!nbt || eta <= 0) return;
-  k_band<T><<<nbt, kThreads, band_smem<T>(eta), st>>>(op, btiles, nbx, eta, u, F, bval);
+  launch_pdl(k_band<T>, nbt, kThreads, band_smem<T>(eta), st, op, btiles, nbx, eta, u, F, bval,
+             boff, bent, maps, umap, err);
 }
 
 template <class T>
@@ -577,35 +729,36 @@ void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const La
                            const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st) {
   if (!nct) return;
   if (norms)
-    k_resid_restrict<T, true><<<nct * 4, kThreads, 0, st>>>(op, u, F, Lc, ctiles, Fc, norms);
+    launch_pdl(k_resid_restrict<T, true>, nct * 4, kThreads, 0, st, op, u, F, Lc, ctiles, Fc, norms);
   else
-    k_resid_restrict<T, false><<<nct * 4, kThreads, 0, st>>>(op, u, F, Lc, ctiles, Fc, norms);
+    launch_pdl(k_resid_restrict<T, false>, nct * 4, kThreads, 0, st, op, u, F, Lc, ctiles, Fc,
+               norms);
 }
 
 template <class T, class TR>
 void launch_residual(const OpArgs<T>& op, const int* tiles, int ntiles, const T* u, const T* F,
                      TR* rout, T scale, double* norms, cudaStream_t st) {
   if (!ntiles) return;
-  k_residual<T, TR><<<ntiles, kThreads, 0, st>>>(op, tiles, u, F, rout, scale, norms);
+  launch_pdl(k_residual<T, TR>, ntiles, kThreads, 0, st, op, tiles, u, F, rout, scale, norms);
 }
 
 template <class T>
 void launch_prolong(const OpArgs<T>& op, const int* tiles, int ntiles, T* uf, const Layout& Lc,
                     const T* ec, cudaStream_t st) {
   if (!ntiles) return;
-  k_prolong<T><<<ntiles, kThreads, 0, st>>>(op, tiles, uf, Lc, ec);
+  launch_pdl(k_prolong<T>, ntiles, kThreads, 0, st, op, tiles, uf, Lc, ec);
 }
 
 template <class T>
 void launch_coarse_solve(const Layout& Lc, const double* Ainv, const T* Fc, T* uc, cudaStream_t st) {
   int m = (Lc.n + 1) * (Lc.n + 1);
-  k_coarse_solve<T><<<1, kThreads, m * sizeof(double), st>>>(Lc, Ainv, Fc, uc);
+  launch_pdl(k_coarse_solve<T>, 1, kThreads, m * sizeof(double), st, Lc, Ainv, Fc, uc);
 }
 
-void launch_rhs(const RhsArgs& a, const double* f, const double* g, double* F, double* norms,
-                cudaStream_t st) {
-  size_t m = (size_t)(a.L.n + 1) * (a.L.n + 1);
-  k_rhs<<<grid_for(m), kThreads, 0, st>>>(a, f, g, F, norms);
+void launch_rhs(const RhsArgs& a, const int* tiles, int ntiles, const double* f, const double* g,
+                double* F, double* norms, cudaStream_t st) {
+  if (!ntiles) return;
+  k_rhs<<<ntiles, kThreads, 0, st>>>(a, tiles, f, g, F, norms);
 }
 
 template <class T>
@@ -621,14 +774,15 @@ void launch_unpack(const Layout& L, const uint16_t* code, const double* src, dou
   k_unpack<<<grid_for(m), kThreads, 0, st>>>(L, code, src, dst);
 }
 
-void launch_check_finite(const double* p, size_t m, unsigned* err, cudaStream_t st) {
-  k_check_finite<<<grid_for(m), kThreads, 0, st>>>(p, m, err);
+void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,
+                          cudaStream_t st) {
+  k_check_finite2<<<grid_for(m / 2 + 1), kThreads, 0, st>>>(p, q, m, err);
 }
 
 void launch_update(const Layout& L, const int* tiles, int ntiles, const uint16_t* code, double* u,
                    const float* e, double inv_scale, cudaStream_t st) {
   if (!ntiles) return;
-  k_update<<<ntiles, kThreads, 0, st>>>(L, tiles, code, u, e, inv_scale);
+  launch_pdl(k_update, ntiles, kThreads, 0, st, L, tiles, code, u, e, inv_scale);
 }
 
 template <class T>
@@ -644,7 +798,8 @@ void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st) {
   template void launch_gs_sweep<T>(const OpArgs<T>&, const int*, int, const T*, T*, const T*, T*, \
                                    bool, cudaStream_t);                                          \
   template void launch_band<T>(const OpArgs<T>&, const int*, int, int, int, T*, const T*,        \
-                               const T*, cudaStream_t);                                          \
+                               const T*, const int*, const int2*, const BandMaps&, int,          \
+                               unsigned*, cudaStream_t);                                         \
   template void launch_resid_restrict<T>(const OpArgs<T>&, const T*, const T*, const Layout&,    \
                                          const int*, int, T*, double*, cudaStream_t);            \
   template void launch_prolong<T>(const OpArgs<T>&, const int*, int, T*, const Layout&, const T*, \

@@ -1,7 +1,7 @@
 // V-cycle kernel launchers (see cycle.cu).
 #pragma once
 
-#include "common.cuh"
+#include "tma.cuh"
 
 // Operator of one level for kernels in arithmetic type T.
 template <class T> struct OpArgs {
@@ -22,6 +22,13 @@ struct RhsArgs {
   const double* Gk;          // 16 per cut cell, boundary load
 };
 
+// TMA descriptors of a level's two u buffers in one precision (band kernel box)
+struct BandMaps {
+  CUtensorMap u[2];
+};
+int band_box_x(int eta);
+int band_box_y(int eta);
+
 template <class T> size_t sweep_smem();
 template <class T> size_t band_smem(int eta);
 template <class T> cudaError_t configure_kernels(int eta);
@@ -31,7 +38,8 @@ void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T*
                      const T* F, T* bval, bool zero_in, cudaStream_t st);
 template <class T>
 void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
-                 const T* F, const T* bval, cudaStream_t st);
+                 const T* F, const T* bval, const int* boff, const int2* bent,
+                 const BandMaps& maps, int umap, unsigned* err, cudaStream_t st);
 template <class T>
 void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const Layout& Lc,
                            const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st);
@@ -43,14 +51,15 @@ void launch_prolong(const OpArgs<T>& op, const int* tiles, int ntiles, T* uf, co
                     const T* ec, cudaStream_t st);
 template <class T>
 void launch_coarse_solve(const Layout& Lc, const double* Ainv, const T* Fc, T* uc, cudaStream_t st);
-void launch_rhs(const RhsArgs& a, const double* f, const double* g, double* F, double* norms,
-                cudaStream_t st);
+void launch_rhs(const RhsArgs& a, const int* tiles, int ntiles, const double* f, const double* g,
+                double* F, double* norms, cudaStream_t st);
 template <class T>
 void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* dst, unsigned* err,
                  cudaStream_t st);
 void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
                    cudaStream_t st);
-void launch_check_finite(const double* p, size_t m, unsigned* err, cudaStream_t st);
+void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,
+                          cudaStream_t st);
 void launch_update(const Layout& L, const int* tiles, int ntiles, const uint16_t* code, double* u,
                    const float* e, double inv_scale, cudaStream_t st);
 template <class T>

@@ -223,6 +223,40 @@ __global__ void k_band_flags(const int* __restrict__ bnode, int nb, int nbx, uin
   flag[(j >> 5) * nbx + (i >> 5)] = 1;
 }
 
+// Boundary-node lists of tile regions.  For tile b (tw x th nodes, tpr tiles
+// per row; tiles[b] or, if tiles is null, b itself) and its region of halo
+// H, every vertex of a cut cell in the region is listed once, grouped: the
+// four colours (i mod 2) + 2 (j mod 2) off the region's rim, then the rim
+// nodes (read by the sweeps, never updated).  Entry: {x | y << 16 (region
+// coordinates), boundary row index}.  First pass (ent == nullptr): counts
+// per group into cnt[5 b ..]; second pass: fills from the offsets
+// off[5 b ..] (exclusive scan of the counts).  The order inside a group is
+// immaterial: nodes of one colour never interact.
+__global__ void k_region_list(Layout L, const uint16_t* __restrict__ code,
+                              const int* __restrict__ tile_base, const int* __restrict__ tiles,
+                              int tpr, int tw, int th, int H, int* __restrict__ cnt,
+                              const int* __restrict__ off, int2* __restrict__ ent) {
+  __shared__ int c5[5];
+  const int b = blockIdx.x, t = tiles ? tiles[b] : b;
+  const int ri0 = (t % tpr) * tw - H, rj0 = (t / tpr) * th - H;
+  const int RX = tw + 2 * H, RY = th + 2 * H;
+  if (threadIdx.x < 5) c5[threadIdx.x] = ent ? off[5 * b + threadIdx.x] : 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < RX * RY; p += blockDim.x) {
+    const int y = p / RX, x = p - y * RX;
+    const int gi = ri0 + x, gj = rj0 + y;
+    if (gi < 0 || gj < 0 || gi > L.n || gj > L.n) continue;
+    const uint16_t cd = code[L.idx(gi, gj)];
+    if (cd < 2) continue;
+    const bool rim = x == 0 || y == 0 || x == RX - 1 || y == RY - 1;
+    const int g = rim ? 4 : (gi & 1) + 2 * (gj & 1);
+    const int pos = atomicAdd(&c5[g], 1);
+    if (ent) ent[pos] = make_int2(x | (y << 16), tile_base[L.tile_of(gi, gj)] + cd - 2);
+  }
+  __syncthreads();
+  if (!ent && threadIdx.x < 5) cnt[5 * b + threadIdx.x] = c5[threadIdx.x];
+}
+
 // Coarse cell classes from the four children (Sec. 5.1 hierarchy).
 __global__ void k_coarse_class(const uint8_t* __restrict__ fcls, int nf, uint8_t* __restrict__ ccls,
                                uint8_t* __restrict__ cut_flag) {
@@ -417,6 +451,13 @@ void launch_tile_assemble(const CellData& cd, const Layout& L, const int* tile_b
 
 void launch_band_flags(const int* bnode, int nb, int nbx, uint8_t* flag, cudaStream_t st) {
   if (nb) k_band_flags<<<(nb + 255) / 256, 256, 0, st>>>(bnode, nb, nbx, flag);
+}
+
+void launch_region_list(const Layout& L, const uint16_t* code, const int* tile_base,
+                        const int* tiles, int ntl, int tpr, int tw, int th, int H, int* cnt,
+                        const int* off, int2* ent, cudaStream_t st) {
+  if (ntl)
+    k_region_list<<<ntl, 256, 0, st>>>(L, code, tile_base, tiles, tpr, tw, th, H, cnt, off, ent);
 }
 
 void launch_restrict_tile_flags(const Layout& Lf, const Layout& Lc, const uint16_t* code_c,

@@ -28,6 +28,11 @@ void launch_tile_assemble(const CellData& cd, const Layout& L, const int* tile_b
                           uint16_t* code, double* rows, int* bnode, unsigned* err,
                           cudaStream_t st);
 void launch_band_flags(const int* bnode, int nb, int nbx, uint8_t* flag, cudaStream_t st);
+// Boundary-node lists of tile regions (see k_region_list): 5 groups per
+// tile (colours 0..3 off the rim, then the rim), entries {x | y << 16, row}.
+void launch_region_list(const Layout& L, const uint16_t* code, const int* tile_base,
+                        const int* tiles, int ntl, int tpr, int tw, int th, int H, int* cnt,
+                        const int* off, int2* ent, cudaStream_t st);
 void launch_restrict_tile_flags(const Layout& Lf, const Layout& Lc, const uint16_t* code_c,
                                 uint8_t* flag, cudaStream_t st);
 void launch_coarse_class(const uint8_t* fcls, int nf, uint8_t* ccls, uint8_t* cut_flag,

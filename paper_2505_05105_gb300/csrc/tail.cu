@@ -12,123 +12,153 @@
 // level in that level's padded global layout, so it slots in where the
 // multi-block kernels leave off.  The arithmetic and the colour order are
 // those of the multi-block kernels.
+//
+// Everything that does not change between launches -- node tags, the
+// colour-sorted boundary lists, the boundary rows and the coarsest inverse
+// -- is a static image built at setup and copied into shared memory with
+// one bulk copy, while the threads load F and u of the top level.
 #include "tail.cuh"
+#include "bandreg.cuh"
 
 namespace {
 
 constexpr int kThreads = 1024;
 
-struct Grid {
-  int n, S;             // cells per side, bordered side n + 3
-};
-
-template <class T>
-struct Smem {
-  T* U[MG_TAIL_MAX_LEVELS];
-  T* F[MG_TAIL_MAX_LEVELS];
-  int16_t* G[MG_TAIL_MAX_LEVELS];   // -2 not a DOF, -1 interior, >= 0 boundary row
-  const T* rows[MG_TAIL_MAX_LEVELS];  // boundary rows (shared or global memory)
-  uint16_t* BL[MG_TAIL_MAX_LEVELS];   // boundary nodes' bordered positions, by colour
-  int* off;                           // [level][5]: colour offsets into BL
-  T* R;                             // residual of the level being restricted
-};
-
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Per-level pointers and sizes, kept in shared memory: indexing the kernel
+// parameters or a local array by a runtime level would go through the stack.
 template <class T>
-__device__ void carve(const TailArgs<T>& a, unsigned char* base, Smem<T>& s) {
-  size_t off = 0;
-  for (int k = 0; k < a.nlev; ++k) {
-    int S = a.n[k] + 3;
-    s.U[k] = reinterpret_cast<T*>(base + off); off = align16(off + (size_t)S * S * sizeof(T));
-    s.F[k] = reinterpret_cast<T*>(base + off); off = align16(off + (size_t)S * S * sizeof(T));
-    s.G[k] = reinterpret_cast<int16_t*>(base + off); off = align16(off + (size_t)S * S * 2);
-  }
-  s.R = reinterpret_cast<T*>(base + off);
-  off = align16(off + (size_t)(a.n[0] + 3) * (a.n[0] + 3) * sizeof(T));
-  for (int k = 0; k < a.nlev; ++k) {
-    if (a.rows_in_smem) {
-      s.rows[k] = reinterpret_cast<const T*>(base + off);
-      off = align16(off + (size_t)a.n_bnd[k] * MG_ROW * sizeof(T));
-    } else {
-      s.rows[k] = a.rows[k];
-    }
-  }
-  for (int k = 0; k < a.nlev; ++k) {
-    s.BL[k] = reinterpret_cast<uint16_t*>(base + off);
-    off = align16(off + (size_t)a.n_bnd[k] * sizeof(uint16_t));
-  }
+struct Smem {
+  int n[MG_TAIL_MAX_LEVELS];
+  T* U[MG_TAIL_MAX_LEVELS];
+  T* F[MG_TAIL_MAX_LEVELS];
+  const int16_t* G[MG_TAIL_MAX_LEVELS];   // -2 not a DOF, -1 interior, >= 0 boundary row
+  const T* rows[MG_TAIL_MAX_LEVELS];      // boundary rows (shared or global memory)
+  const uint16_t* BL[MG_TAIL_MAX_LEVELS]; // boundary nodes' bordered positions, by colour
+  const int* off;                         // [level][5]: colour offsets into BL
+  const double* Ainv;                     // coarsest inverse (shared or global memory)
+  T* R;                                   // residual of the level being restricted
+};
+
+// Level data used by the phases of one level, loaded once per smoothing step.
+template <class T>
+struct Lvl {
+  int n, S;
+  T* U;
+  const T* F;
+  const int16_t* G;
+  const T* rows;
+  const uint16_t* BL;
+  int o[5];
+};
+
+template <class T>
+__device__ __forceinline__ Lvl<T> level(const Smem<T>& s, int k) {
+  Lvl<T> v;
+  v.n = s.n[k];
+  v.S = v.n + 3;
+  v.U = s.U[k];
+  v.F = s.F[k];
+  v.G = s.G[k];
+  v.rows = s.rows[k];
+  v.BL = s.BL[k];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) v.o[c] = s.off[k * 5 + c];
+  return v;
 }
 
-// one colour phase; boundary_only restricts it to the cut-cell vertices.
-// Interior nodes of the colour are found by scanning the colour's lattice,
-// boundary nodes come from the level's colour-sorted list.
+// one colour phase of the full sweep: interior nodes of the colour by
+// scanning the colour's lattice (a warp per lattice row), boundary nodes from
+// the level's colour-sorted list.
 template <class T>
-__device__ __forceinline__ void colour_phase(const TailArgs<T>& a, const Smem<T>& s, int k, int c,
-                                             bool boundary_only) {
-  const int n = a.n[k], S = n + 3;
-  T* U = s.U[k];
-  const T* F = s.F[k];
+__device__ __forceinline__ void colour_phase(const Lvl<T>& v, int c, bool boundary_only) {
+  const int n = v.n, S = v.S;
+  T* U = v.U;
   if (!boundary_only) {
     const int ci = c & 1, cj = c >> 1;
-    const int wa = (n + 1 - ci + 1) / 2, wb = (n + 1 - cj + 1) / 2;
-    const int16_t* G = s.G[k];
-    for (int it = threadIdx.x; it < wa * wb; it += blockDim.x) {
-      int b = it / wa, aa = it - b * wa;
-      int q = (2 * b + cj + 1) * S + (2 * aa + ci + 1);
-      if (G[q] != -1) continue;
-      const T* Up = U + q;
-      T sum = ((Up[-1] + Up[1]) + (Up[-S] + Up[S])) +
-              ((Up[-S - 1] + Up[-S + 1]) + (Up[S - 1] + Up[S + 1]));
-      U[q] = (T(3) * F[q] + sum) * T(0.125);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = cj + 2 * warp; j <= n; j += 2 * nw) {
+      for (int i = ci + 2 * lane; i <= n; i += 64) {
+        const int q = (j + 1) * S + (i + 1);
+        if (v.G[q] != -1) continue;
+        const T* Up = U + q;
+        T sum = ((Up[-1] + Up[1]) + (Up[-S] + Up[S])) +
+                ((Up[-S - 1] + Up[-S + 1]) + (Up[S - 1] + Up[S + 1]));
+        U[q] = (T(3) * v.F[q] + sum) * T(0.125);
+      }
     }
   }
-  const int e0 = s.off[k * 5 + c], e1 = s.off[k * 5 + c + 1];
-  const uint16_t* BL = s.BL[k];
+  const int e0 = c == 0 ? v.o[0] : c == 1 ? v.o[1] : c == 2 ? v.o[2] : v.o[3];
+  const int e1 = c == 0 ? v.o[1] : c == 1 ? v.o[2] : c == 2 ? v.o[3] : v.o[4];
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    int q = BL[e];
-    const T* R = s.rows[k] + (size_t)s.G[k][q] * MG_ROW;
+    const int q = v.BL[e];
+    const T* R = v.rows + (size_t)v.G[q] * MG_ROW;
     const T* Up = U + q;
     T acc = R[0] * Up[-S - 1] + R[1] * Up[-S] + R[2] * Up[-S + 1] + R[3] * Up[-1] +
             R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[S - 1] + R[7] * Up[S] + R[8] * Up[S + 1];
-    U[q] = Up[0] + (F[q] - acc) * R[9];
+    U[q] = Up[0] + (v.F[q] - acc) * R[9];
+  }
+  __syncthreads();
+}
+
+// one smoothing step: the full 4-colour sweep, then the eta sweeps over the
+// cut-cell vertices on as many warps as the longest colour list needs, each
+// thread's nodes in registers
+template <class T>
+__device__ void smooth(const TailArgs<T>& a, const Smem<T>& s, int k) {
+  const Lvl<T> v = level(s, k);
+  for (int c = 0; c < 4; ++c) colour_phase(v, c, false);
+  if (a.eta <= 0) return;
+  int mc = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) mc = max(mc, v.o[c + 1] - v.o[c]);
+  const int nw = min((int)(blockDim.x >> 5), max(1, (mc + 31) / 32));
+  if ((int)(threadIdx.x >> 5) < nw) {
+    auto fetch = [&](int e, int& r, T& f, int& p) {
+      const int q = v.BL[e];
+      r = v.G[q];
+      f = v.F[q];
+      p = q;
+    };
+    auto extra = [&](int e) {
+      const int q = v.BL[e];
+      const T* w = v.rows + (size_t)v.G[q] * MG_ROW;
+      const T* Up = v.U + q;
+      const int S = v.S;
+      T acc = w[0] * Up[-S - 1] + w[1] * Up[-S] + w[2] * Up[-S + 1] + w[3] * Up[-1] +
+              w[4] * Up[0] + w[5] * Up[1] + w[6] * Up[S - 1] + w[7] * Up[S] + w[8] * Up[S + 1];
+      v.U[q] = Up[0] + (v.F[q] - acc) * w[9];
+    };
+    band_phases_idx<T>(v.U, v.S, v.rows, v.o, a.eta, 32 * nw, fetch, extra);
   }
   __syncthreads();
 }
 
 template <class T>
-__device__ void smooth(const TailArgs<T>& a, const Smem<T>& s, int k) {
-  for (int c = 0; c < 4; ++c) colour_phase(a, s, k, c, false);
-  for (int e = 0; e < a.eta; ++e)
-    for (int c = 0; c < 4; ++c) colour_phase(a, s, k, c, true);
-}
-
-template <class T>
-__device__ void residual_restrict(const TailArgs<T>& a, const Smem<T>& s, int k) {
-  const int n = a.n[k], S = n + 3;
-  const T* U = s.U[k];
-  const T* F = s.F[k];
-  const int16_t* G = s.G[k];
+__device__ void residual_restrict(const Smem<T>& s, int k) {
+  const Lvl<T> v = level(s, k);
+  const int S = v.S;
   for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
-    int tag = G[q];
+    const int tag = v.G[q];
     T r = T(0);
     if (tag != -2) {
-      const T* Up = U + q;
+      const T* Up = v.U + q;
       if (tag == -1) {
         T s8 = ((Up[-1] + Up[1]) + (Up[-S] + Up[S])) +
                ((Up[-S - 1] + Up[-S + 1]) + (Up[S - 1] + Up[S + 1]));
-        r = F[q] - (T(8) * Up[0] - s8) * T(1.0 / 3.0);
+        r = v.F[q] - (T(8) * Up[0] - s8) * T(1.0 / 3.0);
       } else {
-        const T* R = s.rows[k] + (size_t)tag * MG_ROW;
+        const T* R = v.rows + (size_t)tag * MG_ROW;
         T acc = R[0] * Up[-S - 1] + R[1] * Up[-S] + R[2] * Up[-S + 1] + R[3] * Up[-1] +
                 R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[S - 1] + R[7] * Up[S] + R[8] * Up[S + 1];
-        r = F[q] - acc;
+        r = v.F[q] - acc;
       }
     }
     s.R[q] = r;
   }
   __syncthreads();
-  const int nc = a.n[k + 1], Sc = nc + 3;
+  const int nc = s.n[k + 1], Sc = nc + 3;
   T* Fc = s.F[k + 1];
   for (int p = threadIdx.x; p < (nc + 1) * (nc + 1); p += blockDim.x) {
     int J = p / (nc + 1), I = p - J * (nc + 1);
@@ -141,8 +171,8 @@ __device__ void residual_restrict(const TailArgs<T>& a, const Smem<T>& s, int k)
 }
 
 template <class T>
-__device__ void prolong(const TailArgs<T>& a, const Smem<T>& s, int k) {
-  const int n = a.n[k], S = n + 3, Sc = a.n[k + 1] + 3;
+__device__ void prolong(const Smem<T>& s, int k) {
+  const int n = s.n[k], S = n + 3, Sc = s.n[k + 1] + 3;
   T* U = s.U[k];
   const T* E = s.U[k + 1];
   const int16_t* G = s.G[k];
@@ -161,146 +191,232 @@ __device__ void prolong(const TailArgs<T>& a, const Smem<T>& s, int k) {
   __syncthreads();
 }
 
-// u = A^{-1} F on the coarsest level: one warp per row group, lanes split
-// the columns, warp-shuffle sums (fp64 accumulation)
+// u = A^{-1} F on the coarsest level in fp64: one row per thread (the
+// inverse is stored by columns, so a warp's rows read consecutive entries)
 template <class T>
-__device__ void coarsest(const TailArgs<T>& a, const Smem<T>& s, int k) {
-  const int n = a.n[k], S = n + 3, m = (n + 1) * (n + 1);
+__device__ void coarsest(const Smem<T>& s, int k) {
+  const int n = s.n[k], S = n + 3, m = (n + 1) * (n + 1);
   const T* F = s.F[k];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int p = warp; p < m; p += nwarp) {
+  const double* Ainv = s.Ainv;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
     double x = 0.0;
-    for (int c = lane; c < m; c += 32) {
-      int cj = c / (n + 1), ci = c - cj * (n + 1);
-      x += a.Ainv[(size_t)c * m + p] * (double)F[(cj + 1) * S + (ci + 1)];
+    for (int cj = 0; cj <= n; ++cj) {
+      const T* Fr = F + (cj + 1) * S + 1;
+      const double* A = Ainv + (size_t)cj * (n + 1) * m + p;
+      for (int ci = 0; ci <= n; ++ci) x += A[(size_t)ci * m] * (double)Fr[ci];
     }
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) {
-      int j = p / (n + 1), i = p - j * (n + 1);
-      s.U[k][(j + 1) * S + (i + 1)] = (T)x;
-    }
+    const int j = p / (n + 1), i = p - j * (n + 1);
+    s.U[k][(j + 1) * S + (i + 1)] = (T)x;
   }
   __syncthreads();
 }
 
 template <class T>
 __global__ void __launch_bounds__(kThreads, 1) k_tail(TailArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T> s;
-  carve(a, smem_raw, s);
-  // tags, F of the top level, u of the top level (or 0), zero everywhere else;
-  // loads are issued in batches of 4 per thread before any shared store
-  for (int k = 0; k < a.nlev; ++k) {
-    const int n = a.n[k], S = n + 3;
-    const Layout& L = a.L[k];
-    constexpr int B = 4;
-    for (int q0 = threadIdx.x; q0 < S * S; q0 += B * blockDim.x) {
-      uint16_t cd[B];
-      T u[B], f[B];
+  griddep_launch_next();
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem_raw = smem_align128(smem_dyn);
+  __shared__ Smem<T> s;
+  __shared__ uint64_t bar;
+  __shared__ int bad;
+  const TailLayout& lay = a.lay;
+  const int K = lay.nlev;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < K; ++k) {
+      s.n[k] = lay.n[k];
+      s.U[k] = reinterpret_cast<T*>(smem_raw + lay.U[k]);
+      s.F[k] = reinterpret_cast<T*>(smem_raw + lay.F[k]);
+      s.G[k] = reinterpret_cast<const int16_t*>(smem_raw + lay.G[k]);
+      s.BL[k] = reinterpret_cast<const uint16_t*>(smem_raw + lay.BL[k]);
+      s.rows[k] = lay.rows_in_smem ? reinterpret_cast<const T*>(smem_raw + lay.rows[k])
+                                   : a.rows[k];
+    }
+    s.off = reinterpret_cast<const int*>(smem_raw + lay.off);
+    s.Ainv = lay.ainv_in_smem ? reinterpret_cast<const double*>(smem_raw + lay.Ainv) : a.Ainv;
+    s.R = reinterpret_cast<T*>(smem_raw + lay.R);
+    mbar_init(&bar, 1);
+    bad = !bulk_ok(smem_raw, a.image, lay.image_bytes);
+  }
+  __syncthreads();
+  // the static image: one bulk copy (in pieces of at most 64 KB)
+  if (threadIdx.x == 0) {
+    if (!bad) {
+      mbar_arrive_expect_tx(&bar, (uint32_t)lay.image_bytes);
+      for (size_t o = 0; o < lay.image_bytes; o += 65536) {
+        const size_t nb = lay.image_bytes - o < 65536 ? lay.image_bytes - o : 65536;
+        bulk_load(smem_raw + o, a.image + o, (uint32_t)nb, &bar);
+      }
+    } else {
+      atomicOr(a.err, DEV_ERR_ALIGN);
+      mbar_arrive_expect_tx(&bar, 0);
+    }
+  }
+  // meanwhile: u and F of every level start at zero, then (once the
+  // previous kernel is done) the top level's F and u from global memory, all
+  // loads of a thread in flight at once
+  {
+    T* dyn = reinterpret_cast<T*>(smem_raw + lay.U[0]);
+    const size_t nd = (lay.R - lay.U[0]) / sizeof(T);
+    for (size_t q = threadIdx.x; q < nd; q += blockDim.x) dyn[q] = T(0);
+  }
+  __syncthreads();
+  griddep_wait();
+  {
+    const int n = lay.n[0], S = n + 3, W = n + 1;
+    constexpr int B = 6;
+    for (int p0 = threadIdx.x; p0 < W * W; p0 += B * blockDim.x) {
+      T f[B], u[B];
 #pragma unroll
       for (int b = 0; b < B; ++b) {
-        int q = q0 + b * blockDim.x;
-        int j = q / S - 1, i = q % S - 1;
-        bool in = q < S * S && i >= 0 && j >= 0 && i <= n && j <= n;
-        size_t g = in ? L.idx(i, j) : 0;
-        cd[b] = in ? a.code[k][g] : (uint16_t)0;
-        f[b] = (in && k == 0) ? a.F0[g] : T(0);
-        u[b] = (in && k == 0 && a.load_u0) ? a.u0[g] : T(0);
+        const int p = p0 + b * blockDim.x;
+        const int j = p / W, i = p - j * W;
+        const bool in = p < W * W;
+        const size_t g = in ? a.L0.idx(i, j) : 0;
+        f[b] = in ? a.F0[g] : T(0);
+        u[b] = (in && a.load_u0) ? a.u0[g] : T(0);
       }
 #pragma unroll
       for (int b = 0; b < B; ++b) {
-        int q = q0 + b * blockDim.x;
-        if (q >= S * S) continue;
-        int j = q / S - 1, i = q % S - 1;
-        int tag = -2;
-        if (cd[b] == 1) tag = -1;
-        else if (cd[b] >= 2) tag = a.tile_base[k][L.tile_of(i, j)] + cd[b] - 2;
-        s.G[k][q] = (int16_t)tag;
-        s.U[k][q] = cd[b] ? u[b] : T(0);
-        s.F[k][q] = f[b];
+        const int p = p0 + b * blockDim.x;
+        if (p >= W * W) continue;
+        const int j = p / W, i = p - j * W;
+        s.F[0][(j + 1) * S + (i + 1)] = f[b];
+        s.U[0][(j + 1) * S + (i + 1)] = u[b];
       }
     }
-    if (a.rows_in_smem) {
-      T* dst = const_cast<T*>(s.rows[k]);
-      for (int e = threadIdx.x; e < a.n_bnd[k] * MG_ROW; e += blockDim.x) dst[e] = a.rows[k][e];
-    }
   }
-  // colour-sorted boundary lists: count, offsets, fill
-  __shared__ int s_cnt[MG_TAIL_MAX_LEVELS * 4];
-  __shared__ int s_off[MG_TAIL_MAX_LEVELS * 5];
-  s.off = s_off;
-  if (threadIdx.x < MG_TAIL_MAX_LEVELS * 4) s_cnt[threadIdx.x] = 0;
-  __syncthreads();
-  for (int k = 0; k < a.nlev; ++k) {
-    const int n = a.n[k], S = n + 3;
-    for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
-      if (s.G[k][q] < 0) continue;
-      int j = q / S - 1, i = q % S - 1;
-      atomicAdd(&s_cnt[k * 4 + (i & 1) + 2 * (j & 1)], 1);
+  const bool ok = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!ok || bad)) {
+    if (threadIdx.x == 0 && !ok) {
+      atomicOr(a.err, DEV_ERR_TIMEOUT);
+      mbar_wait(&bar, 0);        // bounded: let copies still in flight land
     }
+    __syncthreads();
+    return;
   }
-  __syncthreads();
-  if (threadIdx.x < a.nlev) {
-    int k = threadIdx.x, acc = 0;
-    for (int c = 0; c < 4; ++c) {
-      s_off[k * 5 + c] = acc;
-      acc += s_cnt[k * 4 + c];
-      s_cnt[k * 4 + c] = s_off[k * 5 + c];      // fill cursor
-    }
-    s_off[k * 5 + 4] = acc;
-  }
-  __syncthreads();
-  for (int k = 0; k < a.nlev; ++k) {
-    const int n = a.n[k], S = n + 3;
-    for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
-      if (s.G[k][q] < 0) continue;
-      int j = q / S - 1, i = q % S - 1;
-      int e = atomicAdd(&s_cnt[k * 4 + (i & 1) + 2 * (j & 1)], 1);
-      s.BL[k][e] = (uint16_t)q;
-    }
-  }
-  __syncthreads();
-  const int K = a.nlev;
   for (int k = 0; k + 1 < K; ++k) {
     for (int r = 0; r < a.nu1; ++r) smooth(a, s, k);
-    residual_restrict(a, s, k);
+    residual_restrict(s, k);
   }
-  coarsest(a, s, K - 1);
+  coarsest(s, K - 1);
   for (int k = K - 2; k >= 0; --k) {
-    prolong(a, s, k);
+    prolong(s, k);
     for (int r = 0; r < a.nu2; ++r) smooth(a, s, k);
   }
-  const int n = a.n[0], S = n + 3;
+  const int n = lay.n[0], S = n + 3;
   for (int p = threadIdx.x; p < (n + 1) * (n + 1); p += blockDim.x) {
     int j = p / (n + 1), i = p - j * (n + 1);
-    a.u0[a.L[0].idx(i, j)] = s.U[0][(j + 1) * S + (i + 1)];
+    a.u0[a.L0.idx(i, j)] = s.U[0][(j + 1) * S + (i + 1)];
+  }
+}
+
+// Setup: tags, colour-sorted boundary lists and their offsets of the image.
+__global__ void k_tail_image(TailLayout lay, TailLevelSrc l0, TailLevelSrc l1, TailLevelSrc l2,
+                             TailLevelSrc l3, TailLevelSrc l4, TailLevelSrc l5,
+                             unsigned char* image) {
+  __shared__ int cnt[MG_TAIL_MAX_LEVELS * 4];
+  __shared__ int cur[MG_TAIL_MAX_LEVELS * 4];
+  const TailLevelSrc lv[MG_TAIL_MAX_LEVELS] = {l0, l1, l2, l3, l4, l5};
+  int* off = reinterpret_cast<int*>(image + lay.off);
+  if (threadIdx.x < MG_TAIL_MAX_LEVELS * 4) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int k = 0; k < lay.nlev; ++k) {
+    const int n = lay.n[k], S = n + 3;
+    int16_t* G = reinterpret_cast<int16_t*>(image + lay.G[k]);
+    for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
+      const int j = q / S - 1, i = q % S - 1;
+      const bool in = i >= 0 && j >= 0 && i <= n && j <= n;
+      const uint16_t cd = in ? lv[k].code[lv[k].L.idx(i, j)] : (uint16_t)0;
+      int tag = -2;
+      if (cd == 1) tag = -1;
+      else if (cd >= 2) tag = lv[k].tile_base[lv[k].L.tile_of(i, j)] + cd - 2;
+      G[q] = (int16_t)tag;
+      if (tag >= 0) atomicAdd(&cnt[k * 4 + (i & 1) + 2 * (j & 1)], 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < lay.nlev) {
+    const int k = threadIdx.x;
+    int acc = 0;
+    for (int c = 0; c < 4; ++c) {
+      off[k * 5 + c] = acc;
+      cur[k * 4 + c] = acc;
+      acc += cnt[k * 4 + c];
+    }
+    off[k * 5 + 4] = acc;
+  }
+  __syncthreads();
+  for (int k = 0; k < lay.nlev; ++k) {
+    const int n = lay.n[k], S = n + 3;
+    const int16_t* G = reinterpret_cast<const int16_t*>(image + lay.G[k]);
+    uint16_t* BL = reinterpret_cast<uint16_t*>(image + lay.BL[k]);
+    for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
+      if (G[q] < 0) continue;
+      const int j = q / S - 1, i = q % S - 1;
+      BL[atomicAdd(&cur[k * 4 + (i & 1) + 2 * (j & 1)], 1)] = (uint16_t)q;
+    }
   }
 }
 
 }  // namespace
 
-size_t tail_smem_bytes(const int* n, int nlev, size_t elem) {
-  size_t off = 0;
-  for (int k = 0; k < nlev; ++k) {
-    size_t S = (size_t)n[k] + 3;
-    off = align16(off + S * S * elem);
-    off = align16(off + S * S * elem);
-    off = align16(off + S * S * 2);
+bool tail_layout(const int* n, const int* n_bnd, int nlev, int m, size_t elem, size_t max_bytes,
+                 TailLayout* out) {
+  if (nlev < 1 || nlev > MG_TAIL_MAX_LEVELS) return false;
+  for (int rows = 1; rows >= 0; --rows) {
+    for (int ainv = 1; ainv >= 0; --ainv) {
+      TailLayout t;
+      t.nlev = nlev;
+      size_t o = 0;
+      for (int k = 0; k < nlev; ++k) {
+        t.n[k] = n[k];
+        t.n_bnd[k] = n_bnd[k];
+        const size_t S = (size_t)n[k] + 3;
+        t.G[k] = o;
+        o = align16(o + S * S * sizeof(int16_t));
+      }
+      for (int k = 0; k < nlev; ++k) {
+        t.BL[k] = o;
+        o = align16(o + (size_t)n_bnd[k] * sizeof(uint16_t));
+      }
+      t.off = o;
+      o = align16(o + (size_t)nlev * 5 * sizeof(int));
+      t.rows_in_smem = rows != 0;
+      for (int k = 0; k < nlev && rows; ++k) {
+        t.rows[k] = o;
+        o = align16(o + (size_t)n_bnd[k] * MG_ROW * elem);
+      }
+      t.ainv_in_smem = ainv != 0;
+      if (ainv) {
+        t.Ainv = o;
+        o = align16(o + (size_t)m * m * sizeof(double));
+      }
+      t.image_bytes = o;
+      for (int k = 0; k < nlev; ++k) {
+        const size_t S = (size_t)n[k] + 3;
+        t.U[k] = o;
+        o = align16(o + S * S * elem);
+        t.F[k] = o;
+        o = align16(o + S * S * elem);
+      }
+      t.R = o;
+      const size_t S0 = (size_t)n[0] + 3;
+      o = align16(o + S0 * S0 * elem);
+      t.total = o + kSmemSlack;
+      if (t.total <= max_bytes) {
+        *out = t;
+        return true;
+      }
+    }
   }
-  size_t S0 = (size_t)n[0] + 3;
-  return align16(off + S0 * S0 * elem);
+  return false;
 }
 
-size_t tail_rows_bytes(const int* n_bnd, int nlev, size_t elem) {
-  size_t off = 0;
-  for (int k = 0; k < nlev; ++k) off = align16(off + (size_t)n_bnd[k] * MG_ROW * elem);
-  return off;
-}
-
-size_t tail_list_bytes(const int* n_bnd, int nlev) {
-  size_t off = 0;
-  for (int k = 0; k < nlev; ++k) off = align16(off + (size_t)n_bnd[k] * sizeof(uint16_t));
-  return off;
+void launch_tail_image(const TailLayout& lay, const TailLevelSrc* lv, unsigned char* image,
+                       cudaStream_t st) {
+  TailLevelSrc l[MG_TAIL_MAX_LEVELS] = {};
+  for (int k = 0; k < lay.nlev; ++k) l[k] = lv[k];
+  k_tail_image<<<1, kThreads, 0, st>>>(lay, l[0], l[1], l[2], l[3], l[4], l[5], image);
 }
 
 template <class T>
@@ -309,11 +425,11 @@ cudaError_t configure_tail(size_t smem) {
 }
 
 template <class T>
-void launch_tail(const TailArgs<T>& a, size_t smem, cudaStream_t st) {
-  k_tail<T><<<1, kThreads, smem, st>>>(a);
+void launch_tail(const TailArgs<T>& a, cudaStream_t st) {
+  launch_pdl(k_tail<T>, 1, kThreads, a.lay.total, st, a);
 }
 
 template cudaError_t configure_tail<float>(size_t);
 template cudaError_t configure_tail<double>(size_t);
-template void launch_tail<float>(const TailArgs<float>&, size_t, cudaStream_t);
-template void launch_tail<double>(const TailArgs<double>&, size_t, cudaStream_t);
+template void launch_tail<float>(const TailArgs<float>&, cudaStream_t);
+template void launch_tail<double>(const TailArgs<double>&, cudaStream_t);

@@ -44,7 +44,8 @@ class mg_bc(ctypes.Structure):
 class mg_stab(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("alpha", ctypes.c_double), ("eta", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("lambda_mode", ctypes.c_int),
-                ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
+                ("inner", ctypes.c_int)]
 
 
 class mg_info(ctypes.Structure):
@@ -242,11 +243,11 @@ class Solver:
     def __init__(self, psi, n_cells: int, x0: float, y0: float, h: float, *,
                  coarsest: int = 8, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
                  nu1: int = 2, nu2: int = 1, precision: str = "fp64", max_cycles: int = 100,
-                 stream: int = 0):
+                 inner: int = 3, stream: int = 0):
         self.N = n_cells
         stab = mg_default_stab()
         stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta
-        stab.nu1, stab.nu2, stab.max_cycles = nu1, nu2, max_cycles
+        stab.nu1, stab.nu2, stab.max_cycles, stab.inner = nu1, nu2, max_cycles, inner
         stab.precision = {"fp64": MG_FP64, "mixed": MG_MIXED}[precision]
         grid = mg_grid(n_cells, x0, y0, h, coarsest)
         self.handle = mg_setup(psi, grid, mg_bc(MG_BC_DIRICHLET, None), stab, stream)
