@@ -59,8 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--N", type=int, default=4096)
-    ap.add_argument("--inner", type=int, default=3,
-                    help="fp32 V-cycles per fp64 refinement step (mixed)")
+    ap.add_argument("--inner", type=int, default=0,
+                    help="V-cycles between fp64 residual checks (0: adaptive)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -362,7 +362,8 @@ def run_ours(args):
             "config": {"workload": workload_name(N), "N": N, "n_dof": ndof, "n_cut": ncut,
                        "n_levels": n_levels, "tol": TOL, "precision": "mixed",
                        "cycles_per_solve": cyc_mx[-1], "V": "V(2,1), eta=4, gamma=2",
-                       "fp32_cycles_per_refinement": args.inner,
+                       "cycles_between_fp64_checks": args.inner or "adaptive",
+                       "fp64_checks_per_solve": info_mx.checks,
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{world}"},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": total_64 / args.steps,

@@ -85,10 +85,13 @@ typedef struct {
  *   nu1 = 2, nu2 = 1  pre/post smoothing steps                 (Sec. 5.3), 0..8
  *   lambda_mode = MG_LAMBDA_LOCAL
  *   precision = MG_FP64 or MG_MIXED
- *   max_cycles = 100  cycles (MG_FP64) or refinement steps (MG_MIXED)
- *   inner = 3     fp32 V-cycles per refinement step (MG_MIXED only), 1..8:
- *                 each step computes the fp64 residual once, runs `inner`
- *                 fp32 V-cycles on the correction equation, then updates u */
+ *   max_cycles = 100  V-cycles in total (both precisions)
+ *   inner = 0     V-cycles between two fp64 residual checks, 0..8:
+ *                 0 = chosen after each check from the contraction seen so
+ *                 far, as the number predicted to reach tol (first group 4,
+ *                 at most 8); k > 0 = always k.  In MG_MIXED each group is
+ *                 one refinement step: fp64 residual, `k` fp32 V-cycles on
+ *                 the correction equation (the first from e = 0), u += e. */
 typedef struct {
   double gamma, alpha;
   int eta, nu1, nu2;
@@ -98,14 +101,15 @@ typedef struct {
 
 /* Result summary of a solve. */
 typedef struct {
-  int cycles;             /* V-cycles (MG_FP64) or refinement steps (MG_MIXED) */
+  int cycles;             /* V-cycles run (both precisions) */
   double rel_res;         /* final ||F - A u||_inf / ||F||_inf, in fp64 */
-  double res_hist[64];    /* rel_res before cycle 1, after cycle 1, ... */
+  double res_hist[64];    /* rel_res at check 0 (before cycle 1), 1, 2, ... */
   int n_dof;              /* fine-level DOFs (vertices of active cells) */
   int n_cut;              /* fine-level cut cells */
   int n_levels;           /* levels including the coarsest */
   float setup_ms;         /* wall time of mg_setup */
   float solve_ms;         /* wall time of the last mg_solve (device events) */
+  int checks;             /* fp64 residual checks after the initial one */
 } mg_info;
 
 /* Fills *out with the defaults above.  Returns MG_ERR_INVALID_ARG if out is

@@ -347,15 +347,19 @@ OpArgs<T> op_of(Level& v) {
   return o;
 }
 
+// One smoothing step (full sweep, then the eta band sweeps).  With `coarse`
+// the sweep first adds the prolongated correction of that level to u.
 template <class T>
-void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine) {
+void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine, Level* coarse = nullptr) {
   OpArgs<T> op = op_of<T>(v);
   int& cur = P<T>::cur(v);
   const int eta = c->stab.eta;
   {
     Launch k(c, fine ? MG_PROF_SWEEP : MG_PROF_COARSE, v.n_active > 0);
     launch_gs_sweep<T>(op, v.active, v.n_active, P<T>::u(v, cur), P<T>::u(v, cur ^ 1), P<T>::F(v),
-                       eta > 0 ? P<T>::bval(v) : (T*)nullptr, zero_in, c->st);
+                       eta > 0 ? P<T>::bval(v) : (T*)nullptr, zero_in,
+                       coarse ? &coarse->L : nullptr,
+                       coarse ? P<T>::u(*coarse, P<T>::cur(*coarse)) : (const T*)nullptr, c->st);
   }
   cur ^= 1;
   if (eta > 0 && v.n_band > 0) {
@@ -476,12 +480,13 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
                              P<T>::F(w), nullptr, c->st);
   }
   vcycle<T>(c, l + 1, true);
-  {
+  if (c->stab.nu2 == 0) {
     Launch k(c, fine ? MG_PROF_PROLONG : MG_PROF_COARSE, v.n_active > 0);
     launch_prolong<T>(op, v.active, v.n_active, P<T>::u(v, cur), w.L, P<T>::u(w, P<T>::cur(w)),
                       c->st);
   }
-  for (int s = 0; s < c->stab.nu2; ++s) smooth<T>(c, v, false, fine);
+  // the first post-smoothing sweep adds the prolongated correction itself
+  for (int s = 0; s < c->stab.nu2; ++s) smooth<T>(c, v, false, fine, s == 0 ? &w : nullptr);
 }
 
 // ||F - A u||_inf of the fine level in fp64 (host value); optionally writes
@@ -526,34 +531,62 @@ void refinement_step(mg_ctx* c, double sigma, int inner) {
 }
 
 // Cycles from the current fine-level u64 with F64 set; Fn = ||F||_inf.
-// In MG_MIXED the fp32 residual is scaled by a power of two sigma chosen
-// from the previous residual norm (times an expected reduction of 0.1), so
-// the fp32 V-cycle works on O(1) values; the update divides by the same
-// sigma exactly.
-int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info) {
+// The fp64 residual is checked after groups of V-cycles: a fixed group size
+// (stab.inner > 0) or, by default, the size predicted to reach tol from the
+// contraction per cycle seen in the previous group, plus half a cycle (first
+// group 4, at most 8).  In MG_MIXED a group is one refinement step whose fp32 right-hand side
+// sigma r is scaled by a power of two sigma chosen from the predicted
+// residual, so the fp32 V-cycles work on O(1) values; the update divides by
+// the same sigma exactly.
+int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info, bool u_zero) {
   const bool mixed = c->stab.precision == MG_MIXED;
+  const bool adaptive = c->stab.inner == 0;
   double rmax;
-  int k = 0, status = MG_OK;
+  int cycles = 0, checks = 0, status = MG_OK;
   double sigma = mixed ? pow2_near_inverse(Fn) : 1.0;
-  TRY(fine_residual(c, sigma, mixed, &rmax));
-  double rel = rmax / Fn, best = rel;
-  if (info) info->res_hist[0] = rel;
-  while (rel > tol) {
-    if (k >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
-    if (mixed) refinement_step(c, sigma, c->stab.inner);
-    else vcycle<double>(c, 0, false);
-    ++k;
-    if (mixed) sigma = pow2_near_inverse(rmax * 0.1);
+  if (u_zero) {
+    // u = 0: the residual is F itself (bit for bit what fine_residual gives)
+    Level& v = c->lev[0];
+    rmax = Fn;
+    if (mixed) {
+      Launch kk(c, MG_PROF_RESIDUAL, v.n_active > 0);
+      launch_scale_to_f32(v.L, v.active, v.n_active, v.F64, v.F32, sigma, c->st);
+    }
+  } else {
     TRY(fine_residual(c, sigma, mixed, &rmax));
-    rel = rmax / Fn;
-    if (info && k < 64) info->res_hist[k] = rel;
+  }
+  double rel = rmax / Fn, best = rel, rho = 0.1;
+  if (info) info->res_hist[0] = rel;
+  int k = adaptive ? 4 : c->stab.inner;
+  while (rel > tol) {
+    if (cycles >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
+    k = std::min(k, max_cycles - cycles);
+    if (mixed) refinement_step(c, sigma, k);
+    else
+      for (int s = 0; s < k; ++s) vcycle<double>(c, 0, false);
+    cycles += k;
+    if (mixed) sigma = pow2_near_inverse(rmax * std::pow(rho, k));
+    double rnew;
+    TRY(fine_residual(c, sigma, mixed, &rnew));
+    ++checks;
+    rel = rnew / Fn;
+    if (info && checks < 64) info->res_hist[checks] = rel;
     // diverged: not finite, or grown far past the best residual seen (at the
     // rounding floor the residual only jitters within a small factor)
     if (!std::isfinite(rel) || rel > 1e3 * best) { status = MG_ERR_DIVERGED; break; }
     best = std::min(best, rel);
+    rho = std::min(0.9, std::max(0.01, std::pow(rnew / rmax, 1.0 / k)));
+    rmax = rnew;
+    if (adaptive && rel > tol) {
+      // half a cycle of margin: a V-cycle too many costs less than a check
+      // plus another group
+      const double need = std::log(tol / rel) / std::log(rho);
+      k = std::max(1, std::min(8, (int)std::ceil(need + 0.5)));
+    }
   }
   if (info) {
-    info->cycles = k;
+    info->cycles = cycles;
+    info->checks = checks;
     info->rel_res = rel;
   }
   return status;
@@ -617,7 +650,7 @@ int mg_default_stab(mg_stab* out) {
   out->lambda_mode = MG_LAMBDA_LOCAL;
   out->precision = MG_FP64;
   out->max_cycles = 100;
-  out->inner = 3;
+  out->inner = 0;
   return MG_OK;
 }
 
@@ -836,7 +869,7 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
   if (!(g.h > 0.0) || !std::isfinite(g.h) || !std::isfinite(g.x0) || !std::isfinite(g.y0))
     return MG_ERR_INVALID_ARG;
   if (!(s.gamma > 0.0) || !(s.alpha > 0.0) || s.eta < 0 || s.eta > 8 || s.nu1 < 0 || s.nu1 > 8 ||
-      s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0 || s.inner < 1 ||
+      s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0 || s.inner < 0 ||
       s.inner > 8)
     return MG_ERR_INVALID_ARG;
   if (s.lambda_mode != MG_LAMBDA_LOCAL) return MG_ERR_UNIMPLEMENTED;
@@ -893,26 +926,30 @@ int mg_solve(mg_handle c, const double* f, const double* g, double* u, double to
   TRY(stage_in(c, 1, g, sg));
   TRY(stage_in(c, 2, u, su));
   size_t m = (size_t)(c->N + 1) * (c->N + 1);
-  MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
+  // d_norms[0..1]: ||F||; the word at d_norms[2]: u has a nonzero DOF value
+  unsigned* d_nz = reinterpret_cast<unsigned*>(c->d_norms + 2);
+  MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 3 * sizeof(double), c->st));
   {
-    Launch k(c, MG_PROF_IO, 4);
+    Launch k(c, MG_PROF_IO, 3);
     launch_check_finite2(sf.dev, sg.dev, m, c->d_err, c->st);
     RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
     launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
     v.cur64 = 0;
-    launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st);
+    launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st, d_nz);
   }
-  MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+  MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                               c->st));
   TRY(sync_check(c));
   double Fn = c->h_norms[0];
+  unsigned nz = 0;
+  memcpy(&nz, c->h_norms + 2, sizeof(unsigned));
   int status = MG_OK;
   if (Fn == 0.0) {
     // F = 0: the solution is u = 0
     MG_CUDA_TRY(cudaMemsetAsync(v.u64[0], 0, v.L.size() * sizeof(double), c->st));
     if (info) info->rel_res = 0.0;
   } else {
-    status = solve_loop(c, Fn, tol, c->stab.max_cycles, info);
+    status = solve_loop(c, Fn, tol, c->stab.max_cycles, info, nz == 0);
     if (status == MG_ERR_CUDA) return status;
   }
   double* ud = const_cast<double*>(su.dev);

@@ -35,10 +35,16 @@ __device__ __forceinline__ const T* row_of(const OpArgs<T>& op, int i, int j, in
   return op.rows + (size_t)r * MG_ROW;
 }
 
-template <class T, bool ZERO_IN>
+// MODE: kSweepPlain (u from uin), kSweepZero (u = 0: first pre-smoothing
+// step), kSweepProlong (u = uin + P e_2h: the prolongation of Sec. 5.1,
+// added while loading, with the same arithmetic as k_prolong).
+enum : int { kSweepPlain = 0, kSweepZero = 1, kSweepProlong = 2 };
+
+template <class T, int MODE>
 __global__ void __launch_bounds__(kThreads)
 k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ uin,
-           T* __restrict__ uout, const T* __restrict__ F, T* __restrict__ bval) {
+           T* __restrict__ uout, const T* __restrict__ F, T* __restrict__ bval, Layout Lc,
+           const T* __restrict__ ec) {
   griddep_launch_next();
   griddep_wait();
   typedef typename Vec2<T>::type T2;
@@ -49,12 +55,13 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
 
   const int t = tiles[blockIdx.x];
   const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
-  const int ri0 = i0 - SW_H, rj0 = j0 - SW_H;
+  const int ri0 = i0 - SW_H, rj0 = j0 - SW_H;        // both even
 
   constexpr int B = 3;
   for (int it0 = threadIdx.x; it0 < SW_RY * SW_PX; it0 += B * blockDim.x) {
     T2 f2[B], u2[B];
     uint32_t c2[B];
+    T e00[B], e10[B], e01[B], e11[B];   // coarse values around the node pair
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       int it = it0 + b * blockDim.x;
@@ -62,8 +69,19 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
       bool ok = it < SW_RY * SW_PX;
       size_t g = ok ? op.L.idx(ri0 + 2 * a, rj0 + rj) : op.L.idx(0, 0);
       f2[b] = *reinterpret_cast<const T2*>(F + g);
-      if (!ZERO_IN) u2[b] = *reinterpret_cast<const T2*>(uin + g);
+      if (MODE != kSweepZero) u2[b] = *reinterpret_cast<const T2*>(uin + g);
       c2[b] = *reinterpret_cast<const uint32_t*>(op.code + g);
+      if (MODE == kSweepProlong) {
+        // fine nodes (2I, j) and (2I+1, j), I = (ri0 + 2a) / 2, J = j / 2:
+        // E(I, J), E(I+1, J) and, for odd j, the row J+1
+        const int gi = ri0 + 2 * a, gj = rj0 + rj;
+        const bool in = ok && gi >= 0 && gj >= 0 && gi <= op.L.n && gj <= op.L.n;
+        const T* E = ec + (in ? Lc.idx(gi >> 1, gj >> 1) : Lc.idx(0, 0));
+        e00[b] = E[0];
+        e10[b] = E[1];
+        e01[b] = (gj & 1) ? E[Lc.pitch] : T(0);
+        e11[b] = (gj & 1) ? E[Lc.pitch + 1] : T(0);
+      }
     }
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -71,12 +89,25 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
       if (it >= SW_RY * SW_PX) continue;
       int rj = it / SW_PX, a = it - rj * SW_PX;
       int pl = (rj & 1) * 2 * SW_PLANE + (rj >> 1) * SW_PX + a;
+      const uint16_t c0 = (uint16_t)(c2[b] & 0xffffu), c1 = (uint16_t)(c2[b] >> 16);
+      T u0 = MODE == kSweepZero ? T(0) : u2[b].x;
+      T u1 = MODE == kSweepZero ? T(0) : u2[b].y;
+      if (MODE == kSweepProlong) {
+        // same association as k_prolong: u + e with e the bilinear average
+        if ((rj0 + rj) & 1) {
+          if (c0) u0 = u0 + T(0.5) * (e00[b] + e01[b]);
+          if (c1) u1 = u1 + T(0.25) * ((e00[b] + e10[b]) + (e01[b] + e11[b]));
+        } else {
+          if (c0) u0 = u0 + e00[b];
+          if (c1) u1 = u1 + T(0.5) * (e00[b] + e10[b]);
+        }
+      }
       sF[pl] = f2[b].x;
       sF[pl + SW_PLANE] = f2[b].y;
-      sU[pl] = ZERO_IN ? T(0) : u2[b].x;
-      sU[pl + SW_PLANE] = ZERO_IN ? T(0) : u2[b].y;
-      sC[pl] = (uint16_t)(c2[b] & 0xffffu);
-      sC[pl + SW_PLANE] = (uint16_t)(c2[b] >> 16);
+      sU[pl] = u0;
+      sU[pl + SW_PLANE] = u1;
+      sC[pl] = c0;
+      sC[pl + SW_PLANE] = c1;
     }
   }
   __syncthreads();
@@ -602,33 +633,56 @@ __global__ void k_check_finite2(const double* __restrict__ p, const double* __re
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEV_ERR_NAN);
 }
 
+// User layout (row-major (n+1)^2) -> padded layout, zero on nodes that are
+// not DOFs; flags NaN/Inf (err) and any nonzero DOF value (nz).  One block
+// row per node row: blockIdx.y = j.
 template <class T>
 __global__ void k_pack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
-                       T* __restrict__ dst, unsigned* err) {
-  const int n = L.n;
-  const size_t m = (size_t)(n + 1) * (n + 1);
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
-       k += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(k % (n + 1)), j = (int)(k / (n + 1));
-    size_t g = L.idx(i, j);
-    double v = src[k];
-    if (err && !isfinite(v)) atomicOr(err, DEV_ERR_NAN);
-    dst[g] = code[g] ? (T)v : T(0);
+                       T* __restrict__ dst, unsigned* err, unsigned* nz) {
+  const int n = L.n, j = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false, any = false;
+  if (i <= n) {
+    const size_t g = L.idx(i, j);
+    const double v = src[(size_t)j * (n + 1) + i];
+    bad = !isfinite(v);
+    const bool dof = code[g] != 0;
+    any = dof && v != 0.0;
+    dst[g] = dof ? (T)v : T(0);
   }
+  if (err && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, DEV_ERR_NAN);
+  if (nz && __any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(nz, 1u);
 }
 
+// Padded layout -> user layout, zero on nodes that are not DOFs.
 __global__ void k_unpack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
                          double* __restrict__ dst) {
-  const int n = L.n;
-  const size_t m = (size_t)(n + 1) * (n + 1);
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
-       k += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(k % (n + 1)), j = (int)(k / (n + 1));
-    size_t g = L.idx(i, j);
-    dst[k] = code[g] ? src[g] : 0.0;
-  }
+  const int n = L.n, j = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  const size_t g = L.idx(i, j);
+  dst[(size_t)j * (n + 1) + i] = code[g] ? src[g] : 0.0;
 }
 
+
+// dst = (float)(src * scale) over the tiles (both padded layouts)
+__global__ void k_scale_to_f32(Layout L, const int* __restrict__ tiles,
+                               const double* __restrict__ src, float* __restrict__ dst,
+                               double scale) {
+  griddep_launch_next();
+  griddep_wait();
+  const int t = tiles[blockIdx.x];
+  const int i0 = (t % L.ntx) * MG_TX, j0 = (t / L.ntx) * MG_TY;
+  for (int rr = threadIdx.x >> 5; rr < MG_TY; rr += blockDim.x >> 5) {
+    const size_t g = L.idx(i0, j0 + rr);
+    const int ii = 2 * (threadIdx.x & 31);
+    const double2 v = *reinterpret_cast<const double2*>(src + g + ii);
+    float2 o;
+    o.x = (float)(v.x * scale);
+    o.y = (float)(v.y * scale);
+    *reinterpret_cast<float2*>(dst + g + ii) = o;
+  }
+}
 
 __global__ void k_update(Layout L, const int* __restrict__ tiles, const uint16_t* __restrict__ code,
                          double* __restrict__ u, const float* __restrict__ e, double inv_scale) {
@@ -690,11 +744,14 @@ int band_box_y(int eta) { return band_region(eta); }
 template <class T>
 cudaError_t configure_kernels(int eta) {
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_gs_sweep<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_gs_sweep<T, kSweepPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sweep_smem<T>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gs_sweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_gs_sweep<T, kSweepZero>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sweep_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gs_sweep<T, kSweepProlong>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<T>());
   if (e != cudaSuccess) return e;
   // the largest eta allowed by the ABI, so handles with different eta coexist
   (void)eta;
@@ -705,14 +762,19 @@ cudaError_t configure_kernels(int eta) {
 
 template <class T>
 void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T* uin, T* uout,
-                     const T* F, T* bval, bool zero_in, cudaStream_t st) {
+                     const T* F, T* bval, bool zero_in, const Layout* Lc, const T* ec,
+                     cudaStream_t st) {
   if (!ntiles) return;
-  if (zero_in)
-    launch_pdl(k_gs_sweep<T, true>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin, uout, F,
-               bval);
+  const Layout L0 = Lc ? *Lc : op.L;
+  if (ec)
+    launch_pdl(k_gs_sweep<T, kSweepProlong>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin,
+               uout, F, bval, L0, ec);
+  else if (zero_in)
+    launch_pdl(k_gs_sweep<T, kSweepZero>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin,
+               uout, F, bval, L0, ec);
   else
-    launch_pdl(k_gs_sweep<T, false>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin, uout,
-               F, bval);
+    launch_pdl(k_gs_sweep<T, kSweepPlain>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin,
+               uout, F, bval, L0, ec);
 }
 
 template <class T>
@@ -763,15 +825,15 @@ void launch_rhs(const RhsArgs& a, const int* tiles, int ntiles, const double* f,
 
 template <class T>
 void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* dst, unsigned* err,
-                 cudaStream_t st) {
-  size_t m = (size_t)(L.n + 1) * (L.n + 1);
-  k_pack<T><<<grid_for(m), kThreads, 0, st>>>(L, code, src, dst, err);
+                 cudaStream_t st, unsigned* nz) {
+  dim3 grid((L.n + 1 + kThreads - 1) / kThreads, L.n + 1);
+  k_pack<T><<<grid, kThreads, 0, st>>>(L, code, src, dst, err, nz);
 }
 
 void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
                    cudaStream_t st) {
-  size_t m = (size_t)(L.n + 1) * (L.n + 1);
-  k_unpack<<<grid_for(m), kThreads, 0, st>>>(L, code, src, dst);
+  dim3 grid((L.n + 1 + kThreads - 1) / kThreads, L.n + 1);
+  k_unpack<<<grid, kThreads, 0, st>>>(L, code, src, dst);
 }
 
 void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,
@@ -785,6 +847,12 @@ void launch_update(const Layout& L, const int* tiles, int ntiles, const uint16_t
   launch_pdl(k_update, ntiles, kThreads, 0, st, L, tiles, code, u, e, inv_scale);
 }
 
+void launch_scale_to_f32(const Layout& L, const int* tiles, int ntiles, const double* src,
+                         float* dst, double scale, cudaStream_t st) {
+  if (!ntiles) return;
+  launch_pdl(k_scale_to_f32, ntiles, kThreads, 0, st, L, tiles, src, dst, scale);
+}
+
 template <class T>
 void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st) {
   size_t m = (size_t)(op.L.n + 1) * (op.L.n + 1);
@@ -796,7 +864,7 @@ void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st) {
   template size_t band_smem<T>(int);                                                             \
   template cudaError_t configure_kernels<T>(int);                                                \
   template void launch_gs_sweep<T>(const OpArgs<T>&, const int*, int, const T*, T*, const T*, T*, \
-                                   bool, cudaStream_t);                                          \
+                                   bool, const Layout*, const T*, cudaStream_t);                 \
   template void launch_band<T>(const OpArgs<T>&, const int*, int, int, int, T*, const T*,        \
                                const T*, const int*, const int2*, const BandMaps&, int,          \
                                unsigned*, cudaStream_t);                                         \
@@ -806,7 +874,7 @@ void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st) {
                                   cudaStream_t);                                                 \
   template void launch_coarse_solve<T>(const Layout&, const double*, const T*, T*, cudaStream_t); \
   template void launch_pack<T>(const Layout&, const uint16_t*, const double*, T*, unsigned*,     \
-                               cudaStream_t);                                                    \
+                               cudaStream_t, unsigned*);                                         \
   template void launch_export_stencil<T>(const OpArgs<T>&, double*, cudaStream_t);
 
 MG_INSTANTIATE(double)

@@ -34,8 +34,11 @@ template <class T> size_t band_smem(int eta);
 template <class T> cudaError_t configure_kernels(int eta);
 
 template <class T>
+// One 4-colour sweep; ec != nullptr adds the prolongated coarse correction
+// P ec (coarse layout *Lc) to uin while loading.
 void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T* uin, T* uout,
-                     const T* F, T* bval, bool zero_in, cudaStream_t st);
+                     const T* F, T* bval, bool zero_in, const Layout* Lc, const T* ec,
+                     cudaStream_t st);
 template <class T>
 void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
                  const T* F, const T* bval, const int* boff, const int2* bent,
@@ -55,11 +58,15 @@ void launch_rhs(const RhsArgs& a, const int* tiles, int ntiles, const double* f,
                 double* F, double* norms, cudaStream_t st);
 template <class T>
 void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* dst, unsigned* err,
-                 cudaStream_t st);
+                 cudaStream_t st, unsigned* nz = nullptr);
 void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
                    cudaStream_t st);
 void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,
                           cudaStream_t st);
+// dst = (float)(src * scale) on the DOFs of the tiles (the refinement
+// residual when u = 0: r = F)
+void launch_scale_to_f32(const Layout& L, const int* tiles, int ntiles, const double* src,
+                         float* dst, double scale, cudaStream_t st);
 void launch_update(const Layout& L, const int* tiles, int ntiles, const uint16_t* code, double* u,
                    const float* e, double inv_scale, cudaStream_t st);
 template <class T>

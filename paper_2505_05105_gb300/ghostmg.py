@@ -52,10 +52,11 @@ class mg_info(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("res_hist", ctypes.c_double * 64), ("n_dof", ctypes.c_int),
                 ("n_cut", ctypes.c_int), ("n_levels", ctypes.c_int),
-                ("setup_ms", ctypes.c_float), ("solve_ms", ctypes.c_float)]
+                ("setup_ms", ctypes.c_float), ("solve_ms", ctypes.c_float),
+                ("checks", ctypes.c_int)]
 
     def history(self):
-        return [self.res_hist[k] for k in range(min(self.cycles + 1, 64))]
+        return [self.res_hist[k] for k in range(min(self.checks + 1, 64))]
 
 
 _P = ctypes.c_void_p
@@ -243,7 +244,7 @@ class Solver:
     def __init__(self, psi, n_cells: int, x0: float, y0: float, h: float, *,
                  coarsest: int = 8, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
                  nu1: int = 2, nu2: int = 1, precision: str = "fp64", max_cycles: int = 100,
-                 inner: int = 3, stream: int = 0):
+                 inner: int = 0, stream: int = 0):
         self.N = n_cells
         stab = mg_default_stab()
         stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta

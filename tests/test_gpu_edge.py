@@ -139,3 +139,26 @@ def test_tiny_domain_and_saddle_cells():
         F = s.rhs(p.f, p.g)
         assert_solution(u.cpu().numpy(), ud, s, F, 1e-10)
         S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_check_schedule(precision):
+    """Residual checks after groups of V-cycles: the adaptive schedule reaches
+    the same tolerance as checking after every cycle, with at most one extra
+    cycle and fewer fp64 residual evaluations."""
+    from paper_2505_05105_gb300 import ghostmg as G
+    p = wl.flower(256)
+    out = {}
+    for inner in (1, 0, 5):
+        S = G.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h, precision=precision, inner=inner)
+        u = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
+        info = S.solve(dev(p.f), dev(p.g), u, tol=1e-10)
+        assert info.rel_res <= 1e-10
+        hist = info.history()
+        assert len(hist) == info.checks + 1 and hist[-1] == pytest.approx(info.rel_res)
+        out[inner] = (info.cycles, info.checks)
+        S.close()
+    every = out[1]
+    assert every[1] == every[0]                       # one check per cycle
+    assert out[0][0] <= every[0] + 1 and out[0][1] < every[1]
+    assert out[5][0] % 5 == 0 and out[5][1] == out[5][0] // 5
