@@ -49,7 +49,6 @@ struct Level {
   int* rtiles = nullptr;        // tiles covering the coarse DOFs (fused restriction)
   // fused smoothing steps (intermediate levels with few active tiles)
   bool fused_ok = false;
-  FusedMaps fmap{};             // TMA maps of u32[0], u32[1], F32, code
   int* foff = nullptr;          // [5 tile id ..] group offsets into fent
   int2* fent = nullptr;         // boundary nodes of each tile's fused region
   // vectors
@@ -414,16 +413,15 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
   a.Lc = w.L;
   a.Fc = P<T>::F(w);
   a.ec = nullptr;
-  a.err = c->d_err;
   const int nu1 = c->stab.nu1, nu2 = c->stab.nu2;
   for (int s = 0; s < nu1; ++s) {
     const bool last = s == nu1 - 1;
-    a.uin_map = cur;
+    a.uin = P<T>::u(v, cur);
     a.uout = P<T>::u(v, cur ^ 1);
     a.tiles = last ? v.rtiles : v.active;
     Launch k(c, MG_PROF_COARSE, 1);
-    launch_smooth_step<T>(a, v.fmap, last ? v.n_rtiles : v.n_active, zero_init && s == 0, false,
-                          last, smem, c->st);
+    launch_smooth_step<T>(a, last ? v.n_rtiles : v.n_active, zero_init && s == 0, false, last,
+                          smem, c->st);
     cur ^= 1;
   }
   if (nu1 == 0) {
@@ -436,10 +434,10 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
   a.ec = P<T>::u(w, P<T>::cur(w));
   a.tiles = v.active;
   for (int s = 0; s < nu2; ++s) {
-    a.uin_map = cur;
+    a.uin = P<T>::u(v, cur);
     a.uout = P<T>::u(v, cur ^ 1);
     Launch k(c, MG_PROF_COARSE, 1);
-    launch_smooth_step<T>(a, v.fmap, v.n_active, false, s == 0, false, smem, c->st);
+    launch_smooth_step<T>(a, v.n_active, false, s == 0, false, smem, c->st);
     cur ^= 1;
   }
   if (nu2 == 0) {
@@ -828,20 +826,15 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     }
   }
   if (c->fused[0]) {
-    // TMA maps and boundary-node lists of the levels run by fused steps:
+    // boundary-node lists of the levels run by fused steps:
     // between the fine level and the tail, with at most fused_max_tiles
     // active tiles
     const int nlev = (int)c->lev.size();
     const int end = c->tail_level >= 0 ? c->tail_level : nlev - 1;
     const int eta = c->stab.eta;
-    const int bx = fused_box_x(eta), by = fused_box_y(eta);
     for (int l = 1; l < end; ++l) {
       Level& v = c->lev[l];
       if (v.n_active > c->fused_max_tiles) continue;
-      TRY(make_level_map(&v.fmap.u[0], v.u32[0], sizeof(float), v.L, bx, by));
-      TRY(make_level_map(&v.fmap.u[1], v.u32[1], sizeof(float), v.L, bx, by));
-      TRY(make_level_map(&v.fmap.F, v.F32, sizeof(float), v.L, bx, by));
-      TRY(make_level_map(&v.fmap.code, v.code, sizeof(uint16_t), v.L, bx, by));
       TRY(build_region_lists(c, v, nullptr, v.L.ntx * v.L.nty, v.L.ntx, MG_TX, MG_TY,
                              fused_halo(eta), &v.foff, &v.fent));
       v.fused_ok = true;

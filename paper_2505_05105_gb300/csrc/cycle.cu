@@ -765,6 +765,10 @@ void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T*
                      const T* F, T* bval, bool zero_in, const Layout* Lc, const T* ec,
                      cudaStream_t st) {
   if (!ntiles) return;
+  if constexpr (sizeof(T) == 4) {
+    launch_gs_sweep_f32(op, tiles, ntiles, uin, uout, F, bval, zero_in, Lc, ec, st);
+    return;
+  }
   const Layout L0 = Lc ? *Lc : op.L;
   if (ec)
     launch_pdl(k_gs_sweep<T, kSweepProlong>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin,

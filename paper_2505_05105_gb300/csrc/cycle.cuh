@@ -39,6 +39,10 @@ template <class T>
 void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T* uin, T* uout,
                      const T* F, T* bval, bool zero_in, const Layout* Lc, const T* ec,
                      cudaStream_t st);
+// the fp32 instance of launch_gs_sweep (sweep32.cu)
+void launch_gs_sweep_f32(const OpArgs<float>& op, const int* tiles, int ntiles, const float* uin,
+                         float* uout, const float* F, float* bval, bool zero_in,
+                         const Layout* Lc, const float* ec, cudaStream_t st);
 template <class T>
 void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
                  const T* F, const T* bval, const int* boff, const int2* bent,

@@ -5,36 +5,37 @@
 // dominate.  k_smooth_step does one smoothing step -- a 4-colour Gauss-Seidel
 // sweep (Sec. 4.1) followed by eta colour sweeps over the cut-cell vertices
 // (Sec. 5.3) -- for one 64 x 32 tile, redundantly on a halo of
-// HS = 4 eta + 7 nodes: after 4 + 4 eta colour phases a stale halo value can
-// have spread at most 4 + 4 eta nodes inwards, so the owned tile and two more
-// rings are exact.  Optionally it
+// HS = 4 (eta + 2) >= 4 eta + 7 nodes: after 4 + 4 eta colour phases a stale
+// halo value can have spread at most 4 + 4 eta nodes inwards, so the owned
+// tile and two more rings are exact (the extra node keeps the region 16-byte
+// aligned).  Optionally it
 //   * starts from u = 0 (first smoothing step on a coarse level),
-//   * adds the prolongated correction P e_2h after loading u (Sec. 5.1), and
+//   * adds the prolongated correction P e_2h while loading u (Sec. 5.1), and
 //   * computes r = F - A u on the owned nodes plus one ring and restricts it,
 //     F_2h = P^T r, for the 32 x 16 coarse block the tile covers.
 // This replaces 8 launches per level (3 sweeps, 3 band sweeps, restriction,
 // prolongation) by 3.
 //
-// Latency is what counts here, so: u, F and the codes of the region arrive
-// by three TMA box copies on one mbarrier; meanwhile the block stages the
-// matrix row and F of the region's boundary nodes (cut-cell vertices, from a
-// list built at setup, grouped by colour) in shared memory.  The colour
-// phases then run from shared memory only, the full phases with several
-// lattice nodes in flight per thread, the band phases on as few warps as
-// cover the longest colour list.
+// The region is held as four parity planes, one per colour, so a colour's
+// nodes and each class of their neighbours are contiguous: the full phases
+// update two neighbouring nodes per thread with 8-byte shared loads and
+// paired fp32 arithmetic (each lane an ordinary IEEE fp32 operation), and a
+// band node's 9 stencil neighbours sit at offsets fixed per colour.  The
+// region arrives with 16-byte loads straight into the planes (prolongation
+// applied on the way); the boundary nodes (cut-cell vertices) of the region
+// come from a list built at setup, grouped by colour, with their rows staged
+// in shared memory before the wait for the previous kernel.
 #include "fused.cuh"
-#include "bandreg.cuh"
 
 namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kXL = 3;               // 32-node lattice chunks per region row (RX <= 190)
+constexpr size_t kSlack = 128;        // the dynamic shared base is rounded up to 128 bytes
 
-__host__ __device__ inline int halo_of(int eta) { return 4 * eta + 7; }
+__host__ __device__ inline int halo_of(int eta) { return 4 * (eta + 2); }
 __host__ __device__ inline int region_x(int eta) { return MG_TX + 2 * halo_of(eta); }
 __host__ __device__ inline int region_y(int eta) { return MG_TY + 2 * halo_of(eta); }
-__host__ __device__ inline int box_x(int eta) { return tma_box_w(region_x(eta)); }
 __host__ __device__ inline size_t a128(size_t b) { return (b + 127) & ~(size_t)127; }
 
 // elements of the shared area used for the coarse correction (prolongation)
@@ -44,250 +45,302 @@ __host__ __device__ inline int e_size(int RX, int RY) {
   return a > b ? a : b;
 }
 
-// listed boundary nodes whose row and F are staged in shared memory
-template <class T> struct FusedCap;
-template <> struct FusedCap<float> { static constexpr int value = 512; };
-template <> struct FusedCap<double> { static constexpr int value = 256; };
-constexpr int kNS = MG_ROW;          // staged values per node: the row
+// listed boundary nodes whose rows are staged in shared memory (stride kRS)
+constexpr int kRC = 1024;
+constexpr int kRS = MG_ROW + 1;       // odd stride: conflict-free row reads
 // tiles around the owned one whose boundary-row bases a region can need:
 // x offsets -1..1 (HS < MG_TX), y offsets -2..2 (HS < 2 MG_TY)
 constexpr int kTBX = 3, kTBY = 5;
 
-template <class T>
 struct Carve {
-  T *sUb, *sFb, *sE, *sS;
-  uint16_t* sCb;
+  float *sU, *sF, *sE, *sS;
+  uint16_t* sC;
   int* sP;
 };
 
-template <class T>
-__host__ __device__ inline size_t carve(unsigned char* base, int eta, Carve<T>* c) {
-  const int BX = box_x(eta), BY = region_y(eta);
-  const int RC = FusedCap<T>::value;
+__host__ __device__ inline size_t carve(unsigned char* base, int eta, Carve* c) {
+  const int n4 = region_x(eta) * region_y(eta);          // 4 planes
   size_t off = 0;
   auto take = [&](size_t bytes) { unsigned char* p = base + off; off += a128(bytes); return p; };
-  unsigned char* u = take((size_t)BX * BY * sizeof(T));
-  unsigned char* f = take((size_t)BX * BY * sizeof(T));
-  unsigned char* cd = take((size_t)BX * BY * sizeof(uint16_t));
-  unsigned char* e = take((size_t)e_size(region_x(eta), BY) * sizeof(T));
-  unsigned char* s = take((size_t)kNS * RC * sizeof(T));
-  unsigned char* pp = take((size_t)RC * sizeof(int));
+  unsigned char* u = take((size_t)n4 * sizeof(float));
+  unsigned char* f = take((size_t)n4 * sizeof(float));
+  unsigned char* cd = take((size_t)n4 * sizeof(uint16_t));
+  unsigned char* e = take((size_t)e_size(region_x(eta), region_y(eta)) * sizeof(float));
+  unsigned char* s = take((size_t)kRC * kRS * sizeof(float));
+  unsigned char* pp = take((size_t)kRC * sizeof(int));
   if (c) {
-    c->sUb = reinterpret_cast<T*>(u);
-    c->sFb = reinterpret_cast<T*>(f);
-    c->sCb = reinterpret_cast<uint16_t*>(cd);
-    c->sE = reinterpret_cast<T*>(e);
-    c->sS = reinterpret_cast<T*>(s);
+    c->sU = reinterpret_cast<float*>(u);
+    c->sF = reinterpret_cast<float*>(f);
+    c->sC = reinterpret_cast<uint16_t*>(cd);
+    c->sE = reinterpret_cast<float*>(e);
+    c->sS = reinterpret_cast<float*>(s);
     c->sP = reinterpret_cast<int*>(pp);
   }
   return off;
 }
 
-template <class T>
-__device__ __forceinline__ T row_update(const T* w, const T* Up, T f, int RS) {
-  T acc = w[0] * Up[-RS - 1] + w[1] * Up[-RS] + w[2] * Up[-RS + 1] + w[3] * Up[-1] +
-          w[4] * Up[0] + w[5] * Up[1] + w[6] * Up[RS - 1] + w[7] * Up[RS] + w[8] * Up[RS + 1];
-  return Up[0] + (f - acc) * w[9];
+__device__ __forceinline__ unsigned long long as_u64(float2 v) {
+  return *reinterpret_cast<unsigned long long*>(&v);
+}
+__device__ __forceinline__ float2 as_f2(unsigned long long v) {
+  return *reinterpret_cast<float2*>(&v);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(as_u64(a)), "l"(as_u64(b)));
+  return as_f2(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(as_u64(a)), "l"(as_u64(b)));
+  return as_f2(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(as_u64(a)), "l"(as_u64(b)), "l"(as_u64(c)));
+  return as_f2(r);
 }
 
-template <class T, bool ZERO_IN, bool PROLONG, bool RESTRICT>
+// boundary-row update u_p + (F_p - sum_s w_s u_s) w_9 of a node whose 9
+// stencil values are U[off[s]]
+__device__ __forceinline__ float row_update(const float* w, const float* U, const int* off,
+                                            float f) {
+  float acc = w[0] * U[off[0]] + w[1] * U[off[1]] + w[2] * U[off[2]] + w[3] * U[off[3]] +
+              w[4] * U[off[4]] + w[5] * U[off[5]] + w[6] * U[off[6]] + w[7] * U[off[7]] +
+              w[8] * U[off[8]];
+  return U[off[4]] + (f - acc) * w[9];
+}
+
+template <bool ZERO_IN, bool PROLONG, bool RESTRICT>
 __global__ void __launch_bounds__(kThreads)
-k_smooth_step(FusedArgs<T> a, const __grid_constant__ FusedMaps maps) {
+k_smooth_step(FusedArgs<float> a) {
   griddep_launch_next();
-  constexpr int RC = FusedCap<T>::value;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
-  unsigned char* smem_raw = smem_align128(smem_dyn);
+  unsigned char* smem_raw =
+      smem_dyn + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_dyn) & 127u)) & 127u);
   const int HS = halo_of(a.eta);
   const int RX = region_x(a.eta), RY = region_y(a.eta);
-  const int RS = box_x(a.eta);                 // shared row stride (TMA box width)
-  Carve<T> cv;
-  carve<T>(smem_raw, a.eta, &cv);
-  __shared__ uint64_t bar;
+  const int PX = RX / 2, PY = RY / 2, PL = PX * PY;
+  Carve cv;
+  carve(smem_raw, a.eta, &cv);
+  float* sU = cv.sU;
+  float* sF = cv.sF;
+  uint16_t* sC = cv.sC;
+  float* sE = cv.sE;
+  float* sS = cv.sS;
+  int* sP = cv.sP;
   __shared__ int sTB[kTBX * kTBY];
   __shared__ int gs[6];
+  __shared__ int soff[4][9];            // stencil offsets (plane base + shift) per colour
   const Layout& L = a.L;
+  const int n = L.n;
   const int t = a.tiles[blockIdx.x];
   const int tx = t % L.ntx, ty = t / L.ntx;
   const int i0 = tx * MG_TX, j0 = ty * MG_TY;
-  const int ri0 = i0 - HS, rj0 = j0 - HS;
-  const int ax = tma_floor(ri0 + MG_G), ay = rj0 + MG_G;   // box origin, padded coordinates
-  const int ox = ri0 + MG_G - ax;                          // region column 0 inside the box
-  T* sU = cv.sUb + ox;
-  T* sF = cv.sFb + ox;
-  const uint16_t* sC = cv.sCb + ox;
-  T* sE = cv.sE;
-  T* sS = cv.sS;
-  int* sP = cv.sP;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ri0 = i0 - HS, rj0 = j0 - HS;          // multiples of 4
+  const int warp = threadIdx.x >> 5;
   auto row_base = [&](int gi, int gj) {
     return sTB[((gj / MG_TY) - ty + 2) * kTBX + (gi / MG_TX) - tx + 1];
   };
 
-  __shared__ int bad;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    bad = !(tma_box_ok(cv.sFb, ax) && tma_box_ok(cv.sCb, ax) && tma_box_ok(cv.sUb, ax));
-  }
-  __syncthreads();
-  // static data first (codes, row bases, lists, rows): it may overlap the
+  // static data first (row bases, lists, rows, offsets): it may overlap the
   // end of the previous kernel
-  if (threadIdx.x == 0) {
-    if (!bad) {
-      const uint32_t bytes =
-          (uint32_t)((size_t)RS * RY * ((ZERO_IN ? 1 : 2) * sizeof(T) + sizeof(uint16_t)));
-      mbar_arrive_expect_tx(&bar, bytes);
-      tma_load_2d(cv.sCb, &maps.code, ax, ay, &bar);
-    } else {
-      atomicOr(a.err, DEV_ERR_ALIGN);
-      mbar_arrive_expect_tx(&bar, 0);
-    }
-  }
   if (threadIdx.x < kTBX * kTBY) {
     int ux = tx + threadIdx.x % kTBX - 1, uy = ty + threadIdx.x / kTBX - 2;
     sTB[threadIdx.x] =
         (ux >= 0 && uy >= 0 && ux < L.ntx && uy < L.nty) ? a.tile_base[uy * L.ntx + ux] : 0;
   }
+  if (threadIdx.x < 36) {
+    // neighbour (dx, dy) of a node of colour c = px + 2 py: plane
+    // ((py + dy) & 1) * 2 + ((px + dx) & 1), row shift (py + dy) >> 1,
+    // column shift (px + dx) >> 1 (floor); s = (dx + 1) + 3 (dy + 1)
+    const int c = threadIdx.x / 9, s = threadIdx.x - 9 * (threadIdx.x / 9);
+    const int nx = (c & 1) + (s % 3) - 1, ny = (c >> 1) + (s / 3) - 1;
+    soff[c][s] = ((ny & 1) * 2 + (nx & 1)) * PL + (ny >> 1) * PX + (nx >> 1);
+  }
   const int e0 = a.loff[5 * t];
   if (threadIdx.x < 6) gs[threadIdx.x] = a.loff[5 * t + threadIdx.x] - e0;
   const int m = a.loff[5 * t + 4] - e0;        // colour groups only: the rim is never updated
-  // rows of the first RC listed nodes
-  for (int e = threadIdx.x; e < m && e < RC; e += blockDim.x) {
+  for (int e = threadIdx.x; e < m && e < kRC; e += blockDim.x) {
     const int2 en = a.lent[e0 + e];
     const int x = en.x & 0xffff, y = en.x >> 16;
-    const T* R = a.rows + (size_t)en.y * MG_ROW;
-    T v[MG_ROW];
+    const float* R = a.rows + (size_t)en.y * MG_ROW;
+    float v[MG_ROW];
 #pragma unroll
     for (int k = 0; k < MG_ROW; ++k) v[k] = R[k];
 #pragma unroll
-    for (int k = 0; k < MG_ROW; ++k) sS[k * RC + e] = v[k];
-    sP[e] = y * RS + x;
-  }
-  // then the data of the previous kernels: F, u, the coarse correction
-  griddep_wait();
-  if (threadIdx.x == 0 && !bad) {
-    tma_load_2d(cv.sFb, &maps.F, ax, ay, &bar);
-    if (!ZERO_IN) tma_load_2d(cv.sUb, &maps.u[a.uin_map], ax, ay, &bar);
-  }
-  const int ci0 = (ri0 >> 1) - 1, cj0 = (rj0 >> 1) - 1;
-  const int EX = RX / 2 + 3, EY = RY / 2 + 3;
-  if (PROLONG) {
-    // coarse nodes (I, J) covering the region, all loads of a thread in flight
-    const int nc = a.Lc.n;
-    constexpr int B = 8;
-    for (int q0 = threadIdx.x; q0 < EX * EY; q0 += B * kThreads) {
-      T v[B];
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        const int q = q0 + b * kThreads;
-        const int y = q / EX, x = q - y * EX;
-        const int I = ci0 + x, J = cj0 + y;
-        const bool in = q < EX * EY && I >= 0 && J >= 0 && I <= nc && J <= nc;
-        v[b] = in ? a.ec[a.Lc.idx(I, J)] : T(0);
-      }
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        const int q = q0 + b * kThreads;
-        if (q < EX * EY) sE[q] = v[b];
-      }
-    }
-  }
-  if (ZERO_IN)
-    for (int q = threadIdx.x; q < RS * RY; q += blockDim.x) cv.sUb[q] = T(0);
-  const bool ok = mbar_wait(&bar, 0);
-  if (__syncthreads_or(!ok || bad)) {
-    if (threadIdx.x == 0 && !ok) {
-      atomicOr(a.err, DEV_ERR_TIMEOUT);
-      mbar_wait(&bar, 0);        // bounded: let copies still in flight land
-    }
-    __syncthreads();
-    return;
+    for (int k = 0; k < MG_ROW; ++k) sS[e * kRS + k] = v[k];
+    sP[e] = (y >> 1) * PX + (x >> 1);
   }
 
-  if (PROLONG) {
-    // u += P e_2h on the region's DOFs: per region row all corrections are
-    // computed before any is added (several nodes in flight per thread)
-    constexpr int kXB = 5;           // 32-column chunks per region row (RX <= 160)
-    for (int y = warp; y < RY; y += kWarps) {
-      const int gj = rj0 + y;
-      T v[kXB];
+  // then the data of the previous kernels: u, F (and codes) of the region,
+  // 4 nodes per 16-byte load straight into the planes, the coarse correction
+  // added on the way.  A group of 4 nodes starts at a multiple of 4, so it
+  // lies either wholly left of column 0 or starts inside the row (the
+  // padded row holds zeros past n).
+  griddep_wait();
+  {
+    const int QX = RX / 4, NI = RY * QX;
+    constexpr int B = 5;
+    for (int it0 = threadIdx.x; it0 < NI; it0 += B * kThreads) {
+      float4 f4[B], u4[B];
+      uint2 c4[B];
+      float e0v[B], e1v[B], e2v[B], g0v[B], g1v[B], g2v[B];
 #pragma unroll
-      for (int k = 0; k < kXB; ++k) {
-        const int x = lane + 32 * k;
-        v[k] = T(0);
-        if (x < RX && sC[y * RS + x]) {
-          const int gi = ri0 + x;
-          const T* e = sE + ((gj >> 1) - cj0) * EX + ((gi >> 1) - ci0);
-          if (!(gi & 1) && !(gj & 1)) v[k] = e[0];
-          else if (!(gj & 1)) v[k] = T(0.5) * (e[0] + e[1]);
-          else if (!(gi & 1)) v[k] = T(0.5) * (e[0] + e[EX]);
-          else v[k] = T(0.25) * ((e[0] + e[1]) + (e[EX] + e[EX + 1]));
+      for (int k = 0; k < B; ++k) {
+        const int it = it0 + k * kThreads;
+        const int y = it / QX, q = it - y * QX;
+        const int gi = ri0 + 4 * q, gj = rj0 + y;
+        const bool in = it < NI && gi >= 0 && gj >= 0 && gi <= n && gj <= n;
+        const size_t g = in ? L.idx(gi, gj) : 0;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        f4[k] = in ? *reinterpret_cast<const float4*>(a.F + g) : z;
+        u4[k] = (in && !ZERO_IN) ? *reinterpret_cast<const float4*>(a.uin + g) : z;
+        c4[k] = in ? *reinterpret_cast<const uint2*>(a.code + g) : make_uint2(0u, 0u);
+        if (PROLONG) {
+          // coarse nodes I .. I+2 of row J (and J+1 for odd j), I = gi / 2
+          const float* E = a.ec + (in ? a.Lc.idx(gi >> 1, gj >> 1) : a.Lc.idx(0, 0));
+          e0v[k] = E[0];
+          e1v[k] = E[1];
+          e2v[k] = E[2];
+          const bool odd = gj & 1;
+          g0v[k] = odd ? E[a.Lc.pitch] : 0.f;
+          g1v[k] = odd ? E[a.Lc.pitch + 1] : 0.f;
+          g2v[k] = odd ? E[a.Lc.pitch + 2] : 0.f;
         }
       }
 #pragma unroll
-      for (int k = 0; k < kXB; ++k) {
-        const int x = lane + 32 * k;
-        if (x < RX) sU[y * RS + x] += v[k];
+      for (int k = 0; k < B; ++k) {
+        const int it = it0 + k * kThreads;
+        if (it >= NI) continue;
+        const int y = it / QX, q = it - y * QX;
+        const uint32_t c0 = c4[k].x & 0xffffu, c1 = c4[k].x >> 16;
+        const uint32_t c2 = c4[k].y & 0xffffu, c3 = c4[k].y >> 16;
+        float u0 = u4[k].x, u1 = u4[k].y, u2 = u4[k].z, u3 = u4[k].w;
+        if (PROLONG) {
+          // same association as k_prolong
+          if ((rj0 + y) & 1) {
+            if (c0) u0 = u0 + 0.5f * (e0v[k] + g0v[k]);
+            if (c1) u1 = u1 + 0.25f * ((e0v[k] + e1v[k]) + (g0v[k] + g1v[k]));
+            if (c2) u2 = u2 + 0.5f * (e1v[k] + g1v[k]);
+            if (c3) u3 = u3 + 0.25f * ((e1v[k] + e2v[k]) + (g1v[k] + g2v[k]));
+          } else {
+            if (c0) u0 = u0 + e0v[k];
+            if (c1) u1 = u1 + 0.5f * (e0v[k] + e1v[k]);
+            if (c2) u2 = u2 + e1v[k];
+            if (c3) u3 = u3 + 0.5f * (e1v[k] + e2v[k]);
+          }
+        }
+        const int pe = (y & 1) * 2 * PL + (y >> 1) * PX + 2 * q;   // even-x plane
+        const int po = pe + PL;                                     // odd-x plane
+        *reinterpret_cast<float2*>(sU + pe) = make_float2(u0, u2);
+        *reinterpret_cast<float2*>(sU + po) = make_float2(u1, u3);
+        *reinterpret_cast<float2*>(sF + pe) = make_float2(f4[k].x, f4[k].z);
+        *reinterpret_cast<float2*>(sF + po) = make_float2(f4[k].y, f4[k].w);
+        *reinterpret_cast<uint32_t*>(sC + pe) = c0 | (c2 << 16);
+        *reinterpret_cast<uint32_t*>(sC + po) = c1 | (c3 << 16);
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
 
-  // one listed node of colour c, entry e
-  auto listed = [&](int e) {
-    T w[MG_ROW + 1];
-    int p;
-    if (e < RC) {
-      p = sP[e];
+  // one listed node (entry e, colour c), from shared memory when staged
+  auto listed = [&](int c, int e) {
+    int off[9];
 #pragma unroll
-      for (int k = 0; k < MG_ROW; ++k) w[k] = sS[k * RC + e];
+    for (int s = 0; s < 9; ++s) off[s] = soff[c][s];
+    int q;
+    float w[MG_ROW];
+    if (e < kRC) {
+      q = sP[e];
+#pragma unroll
+      for (int k = 0; k < MG_ROW; ++k) w[k] = sS[e * kRS + k];
     } else {
       const int2 en = a.lent[e0 + e];
-      p = (en.x >> 16) * RS + (en.x & 0xffff);
-      const T* R = a.rows + (size_t)en.y * MG_ROW;
+      q = ((en.x >> 16) >> 1) * PX + ((en.x & 0xffff) >> 1);
+      const float* R = a.rows + (size_t)en.y * MG_ROW;
 #pragma unroll
       for (int k = 0; k < MG_ROW; ++k) w[k] = R[k];
     }
-    w[MG_ROW] = sF[p];
-    sU[p] = row_update(w, sU + p, w[MG_ROW], RS);
+    float* U = sU + q;
+    U[off[4]] = row_update(w, U, off, sF[c * PL + q]);
   };
 
-  // 4 full colour phases over the region interior: interior nodes by
-  // scanning the colour's lattice (a warp per lattice row, kXL nodes in
-  // flight per thread), boundary nodes from the list (same-colour nodes
-  // never interact)
-  for (int c = 0; c < 4; ++c) {
-    // first x >= 1 with (ri0 + x) of the colour's parity, then every other one
-    const int x0 = 2 - (((c & 1) - ri0) & 1), y0 = 2 - (((c >> 1) - rj0) & 1);
-    const int nxl = (RX - x0) / 2, nyl = (RY - y0) / 2;   // lattice nodes with x, y <= R - 2
-    for (int yl0 = warp; yl0 < nyl; yl0 += 2 * kWarps) {
-      // two lattice rows, kXL nodes each, all loads before any store
-      T val[2 * kXL];
-      int pp[2 * kXL];
-      bool dd[2 * kXL];
-#pragma unroll
-      for (int k = 0; k < 2 * kXL; ++k) {
-        const int yl = yl0 + (k / kXL) * kWarps, xl = lane + 32 * (k % kXL);
-        const int p = (y0 + 2 * yl) * RS + x0 + 2 * xl;
-        pp[k] = p;
-        dd[k] = yl < nyl && xl < nxl && sC[p] == 1;
-        val[k] = T(0);
-        if (dd[k]) {
-          const T* Up = sU + p;
-          T s8 = ((Up[-1] + Up[1]) + (Up[-RS] + Up[RS])) +
-                 ((Up[-RS - 1] + Up[-RS + 1]) + (Up[RS - 1] + Up[RS + 1]));
-          val[k] = (T(3) * sF[p] + s8) * T(0.125);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 2 * kXL; ++k)
-        if (dd[k]) sU[pp[k]] = val[k];
-    }
-    for (int e = gs[c] + threadIdx.x; e < gs[c + 1]; e += blockDim.x) listed(e);
-    __syncthreads();
-  }
-  // 4 eta phases on the cut-cell vertices only, on nw warps, each thread's
-  // nodes in registers
+  // 4 full colour phases; a thread updates plane nodes (a, b) and (a + 1, b)
+  // of the colour's plane: interior nodes by the constant stencil, the
+  // colour's listed boundary nodes from their rows (same-colour nodes never
+  // interact).  Every node off the region's rim is updated in every phase:
+  // a node near the rim computed from stale neighbours is itself stale, and
+  // staleness moves inward by one node per phase.
   {
+    const int pairs = PX / 2;
+    const int step = kThreads / pairs;
+    const int tb = threadIdx.x / pairs, ta = 2 * (threadIdx.x - tb * pairs);
+    const bool on = tb < step;
+    for (int c = 0; c < 4; ++c) {
+      const int ci = c & 1, cj = c >> 1;
+      float* P = sU + c * PL;
+      const float* PXn = sU + (c ^ 1) * PL;
+      const float* PYn = sU + (c ^ 2) * PL;
+      const float* PDn = sU + (c ^ 3) * PL;
+      const float* PF = sF + c * PL;
+      const uint16_t* PC = sC + c * PL;
+      const int b0 = cj ? 0 : 1, b1 = cj ? PY - 2 : PY - 1;
+      const uint32_t mask = (ta == 0 && ci == 0) ? 0xffff0000u
+                            : (ta == PX - 2 && ci == 1) ? 0x0000ffffu : 0xffffffffu;
+      for (int b = b0 + tb; on && b <= b1; b += step) {
+        const int a2 = ta;
+        const uint32_t cc = *reinterpret_cast<const uint32_t*>(PC + b * PX + a2) & mask;
+        const bool in0 = (cc & 0xffffu) == 1u, in1 = (cc >> 16) == 1u;
+        if (!in0 && !in1) continue;
+        const int ym = b + cj - 1, yp = b + cj;
+        float2 W, E, SW, SE, NW, NE;
+        if (ci) {
+          const float2 mm = *reinterpret_cast<const float2*>(PXn + b * PX + a2);
+          const float r = PXn[b * PX + a2 + 2];
+          W = mm;
+          E = make_float2(mm.y, r);
+          const float2 dm = *reinterpret_cast<const float2*>(PDn + ym * PX + a2);
+          const float dr = PDn[ym * PX + a2 + 2];
+          SW = dm;
+          SE = make_float2(dm.y, dr);
+          const float2 um = *reinterpret_cast<const float2*>(PDn + yp * PX + a2);
+          const float ur = PDn[yp * PX + a2 + 2];
+          NW = um;
+          NE = make_float2(um.y, ur);
+        } else {
+          const float l = PXn[b * PX + a2 - 1];
+          const float2 mm = *reinterpret_cast<const float2*>(PXn + b * PX + a2);
+          W = make_float2(l, mm.x);
+          E = mm;
+          const float dl = PDn[ym * PX + a2 - 1];
+          const float2 dm = *reinterpret_cast<const float2*>(PDn + ym * PX + a2);
+          SW = make_float2(dl, dm.x);
+          SE = dm;
+          const float ul = PDn[yp * PX + a2 - 1];
+          const float2 um = *reinterpret_cast<const float2*>(PDn + yp * PX + a2);
+          NW = make_float2(ul, um.x);
+          NE = um;
+        }
+        const float2 S = *reinterpret_cast<const float2*>(PYn + ym * PX + a2);
+        const float2 N = *reinterpret_cast<const float2*>(PYn + yp * PX + a2);
+        const float2 f = *reinterpret_cast<const float2*>(PF + b * PX + a2);
+        // u_p = (3 F_p + sum of the 8 neighbours) / 8, the sum as
+        // ((W + E) + (S + N)) + ((SW + SE) + (NW + NE))
+        const float2 s8 = add2(add2(add2(W, E), add2(S, N)), add2(add2(SW, SE), add2(NW, NE)));
+        const float2 v = mul2(fma2(make_float2(3.f, 3.f), f, s8), make_float2(0.125f, 0.125f));
+        if (in0 && in1) *reinterpret_cast<float2*>(P + b * PX + a2) = v;
+        else if (in0) P[b * PX + a2] = v.x;
+        else P[b * PX + a2 + 1] = v.y;
+      }
+      for (int e = gs[c] + threadIdx.x; e < gs[c + 1]; e += blockDim.x) listed(c, e);
+      __syncthreads();
+    }
+  }
+
+  // 4 eta phases on the cut-cell vertices only, on nw warps; each thread's
+  // node of every colour (position, F, staged row) stays in registers
+  if (a.eta > 0) {
     int g[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) g[c] = gs[c];
@@ -295,56 +348,85 @@ k_smooth_step(FusedArgs<T> a, const __grid_constant__ FusedMaps maps) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) mc = max(mc, g[c + 1] - g[c]);
     const int nw = min(kWarps, max(1, (mc + 31) / 32));
-    if (warp < nw && a.eta > 0) {
-      auto stage = [&](int e, T* w, int& p) {
-        if (e < RC) {
-          p = sP[e];
+    if (warp < nw) {
+      const int nt = 32 * nw;
+      int q[4], r[4];
+      float fv[4];
+      bool more = false;
 #pragma unroll
-          for (int k = 0; k < MG_ROW; ++k) w[k] = sS[k * RC + e];
-        } else {
-          const int2 en = a.lent[e0 + e];
-          p = (en.x >> 16) * RS + (en.x & 0xffff);
-          const T* R = a.rows + (size_t)en.y * MG_ROW;
-#pragma unroll
-          for (int k = 0; k < MG_ROW; ++k) w[k] = R[k];
+      for (int c = 0; c < 4; ++c) {
+        const int e = g[c] + threadIdx.x;
+        q[c] = -1;
+        r[c] = 0;
+        fv[c] = 0.f;
+        if (e < g[c + 1] && e < kRC) {
+          q[c] = sP[e];
+          r[c] = e;
+          fv[c] = sF[c * PL + q[c]];
         }
-        w[MG_ROW] = sF[p];
-      };
-      band_phases_reg<T>(sU, RS, g, a.eta, 32 * nw, stage, listed);
+        more |= g[c + 1] - g[c] > nt || g[c + 1] > kRC;
+      }
+      for (int it = 0; it < a.eta; ++it) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (q[c] >= 0) {
+            int off[9];
+#pragma unroll
+            for (int s = 0; s < 9; ++s) off[s] = soff[c][s];
+            float* U = sU + q[c];
+            U[off[4]] = row_update(sS + r[c] * kRS, U, off, fv[c]);
+          }
+          if (more)
+            for (int e = g[c] + threadIdx.x; e < g[c + 1]; e += nt)
+              if (e - g[c] >= nt || e >= kRC) listed(c, e);
+          if (nt == 32) __syncwarp();
+          else asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+        }
+      }
     }
     __syncthreads();
   }
 
-  // owned tile out
-  for (int rr = warp; rr < MG_TY; rr += kWarps)
-    for (int ii = lane; ii < MG_TX; ii += 32)
-      a.uout[L.idx(i0 + ii, j0 + rr)] = sU[(HS + rr) * RS + HS + ii];
+  // owned tile out: 4 nodes per 16-byte store
+  for (int it = threadIdx.x; it < MG_TY * (MG_TX / 4); it += blockDim.x) {
+    const int rr = it / (MG_TX / 4), q4 = it - rr * (MG_TX / 4);
+    const int y = HS + rr;
+    const int pe = (y & 1) * 2 * PL + (y >> 1) * PX + HS / 2 + 2 * q4, po = pe + PL;
+    const float2 ve = *reinterpret_cast<const float2*>(sU + pe);
+    const float2 vo = *reinterpret_cast<const float2*>(sU + po);
+    *reinterpret_cast<float4*>(a.uout + L.idx(i0 + 4 * q4, j0 + rr)) =
+        make_float4(ve.x, vo.x, ve.y, vo.y);
+  }
 
   if (RESTRICT) {
-    // residual on the owned nodes plus one ring, staged in sE
+    // residual on the owned nodes plus one ring, staged in sE (natural layout)
     constexpr int SX = MG_TX + 2;
-    for (int rr = warp; rr < MG_TY + 2; rr += kWarps) {
-      for (int ii = lane; ii < SX; ii += 32) {
-        const int x = HS - 1 + ii, y = HS - 1 + rr;
-        const int p = y * RS + x;
-        const uint16_t cd = sC[p];
-        T r = T(0);
-        if (cd) {
-          const T* Up = sU + p;
-          if (cd == 1) {
-            T s8 = ((Up[-1] + Up[1]) + (Up[-RS] + Up[RS])) +
-                   ((Up[-RS - 1] + Up[-RS + 1]) + (Up[RS - 1] + Up[RS + 1]));
-            r = sF[p] - (T(8) * Up[0] - s8) * T(1.0 / 3.0);
-          } else {
-            const T* R = a.rows + (size_t)(row_base(ri0 + x, rj0 + y) + cd - 2) * MG_ROW;
-            T acc = R[0] * Up[-RS - 1] + R[1] * Up[-RS] + R[2] * Up[-RS + 1] + R[3] * Up[-1] +
-                    R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[RS - 1] + R[7] * Up[RS] +
-                    R[8] * Up[RS + 1];
-            r = sF[p] - acc;
-          }
+    for (int it = threadIdx.x; it < (MG_TX + 2) * (MG_TY + 2); it += blockDim.x) {
+      const int rr = it / SX, ii = it - rr * SX;
+      const int x = HS - 1 + ii, y = HS - 1 + rr;
+      const int c = (x & 1) + 2 * (y & 1);
+      const int q = (y >> 1) * PX + (x >> 1);
+      const uint16_t cd = sC[c * PL + q];
+      float r = 0.f;
+      if (cd) {
+        int off[9];
+#pragma unroll
+        for (int s = 0; s < 9; ++s) off[s] = soff[c][s];
+        const float* U = sU + q;
+        const float f = sF[c * PL + q];
+        if (cd == 1) {
+          float s8 = ((U[off[3]] + U[off[5]]) + (U[off[1]] + U[off[7]])) +
+                     ((U[off[0]] + U[off[2]]) + (U[off[6]] + U[off[8]]));
+          r = f - (8.f * U[off[4]] - s8) * (1.f / 3.f);
+        } else {
+          const float* R = a.rows + (size_t)(row_base(ri0 + x, rj0 + y) + cd - 2) * MG_ROW;
+          float acc = R[0] * U[off[0]] + R[1] * U[off[1]] + R[2] * U[off[2]] +
+                      R[3] * U[off[3]] + R[4] * U[off[4]] + R[5] * U[off[5]] +
+                      R[6] * U[off[6]] + R[7] * U[off[7]] + R[8] * U[off[8]];
+          r = f - acc;
         }
-        sE[rr * SX + ii] = r;
       }
+      sE[it] = r;
     }
     __syncthreads();
     const Layout& Lc = a.Lc;
@@ -353,9 +435,9 @@ k_smooth_step(FusedArgs<T> a, const __grid_constant__ FusedMaps maps) {
       const int cy = it / (MG_TX / 2), cx = it - cy * (MG_TX / 2);
       const int I = I0 + cx, J = J0 + cy;
       if (I > Lc.n || J > Lc.n) continue;
-      const T* R = sE + (2 * cy + 1) * SX + (2 * cx + 1);
-      T rc = R[0] + T(0.5) * ((R[-1] + R[1]) + (R[-SX] + R[SX])) +
-             T(0.25) * ((R[-SX - 1] + R[-SX + 1]) + (R[SX - 1] + R[SX + 1]));
+      const float* R = sE + (2 * cy + 1) * SX + (2 * cx + 1);
+      float rc = R[0] + 0.5f * ((R[-1] + R[1]) + (R[-SX] + R[SX])) +
+                 0.25f * ((R[-SX - 1] + R[-SX + 1]) + (R[SX - 1] + R[SX + 1]));
       a.Fc[Lc.idx(I, J)] = rc;
     }
   }
@@ -363,21 +445,20 @@ k_smooth_step(FusedArgs<T> a, const __grid_constant__ FusedMaps maps) {
 
 }  // namespace
 
-int fused_box_x(int eta) { return box_x(eta); }
-int fused_box_y(int eta) { return region_y(eta); }
 int fused_halo(int eta) { return halo_of(eta); }
 
+// fp32 only (the fp64 cycle uses the separate kernels)
 size_t fused_smem_bytes(int eta, size_t elem) {
-  return kSmemSlack +
-         (elem == 8 ? carve<double>(nullptr, eta, nullptr) : carve<float>(nullptr, eta, nullptr));
+  return elem == sizeof(float) ? kSlack + carve(nullptr, eta, nullptr) : ~(size_t)0;
 }
 
 template <class T>
 cudaError_t configure_fused(size_t smem) {
+  if (sizeof(T) != sizeof(float)) return cudaSuccess;
   cudaError_t e;
-#define MG_CFG(Z, P, R)                                                                       \
-  e = cudaFuncSetAttribute(k_smooth_step<T, Z, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           (int)smem);                                                        \
+#define MG_CFG(Z, P, R)                                                                     \
+  e = cudaFuncSetAttribute(k_smooth_step<Z, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           (int)smem);                                                      \
   if (e != cudaSuccess) return e;
   MG_CFG(true, false, false)
   MG_CFG(false, false, false)
@@ -390,26 +471,30 @@ cudaError_t configure_fused(size_t smem) {
 }
 
 template <class T>
-void launch_smooth_step(const FusedArgs<T>& a, const FusedMaps& maps, int ntiles, bool zero_in,
-                        bool prolong, bool restrict_, size_t smem, cudaStream_t st) {
-  if (!ntiles) return;
-  if (zero_in && !prolong && !restrict_)
-    launch_pdl(k_smooth_step<T, true, false, false>, ntiles, kThreads, smem, st, a, maps);
-  else if (zero_in && !prolong && restrict_)
-    launch_pdl(k_smooth_step<T, true, false, true>, ntiles, kThreads, smem, st, a, maps);
-  else if (!zero_in && !prolong && !restrict_)
-    launch_pdl(k_smooth_step<T, false, false, false>, ntiles, kThreads, smem, st, a, maps);
-  else if (!zero_in && !prolong && restrict_)
-    launch_pdl(k_smooth_step<T, false, false, true>, ntiles, kThreads, smem, st, a, maps);
-  else if (!zero_in && prolong && !restrict_)
-    launch_pdl(k_smooth_step<T, false, true, false>, ntiles, kThreads, smem, st, a, maps);
-  else
-    launch_pdl(k_smooth_step<T, false, true, true>, ntiles, kThreads, smem, st, a, maps);
+void launch_smooth_step(const FusedArgs<T>& a, int ntiles, bool zero_in, bool prolong,
+                        bool restrict_, size_t smem, cudaStream_t st) {
+  if constexpr (sizeof(T) != sizeof(float)) {
+    (void)a; (void)ntiles; (void)zero_in; (void)prolong; (void)restrict_; (void)smem; (void)st;
+  } else {
+    if (!ntiles) return;
+    if (zero_in && !prolong && !restrict_)
+      launch_pdl(k_smooth_step<true, false, false>, ntiles, kThreads, smem, st, a);
+    else if (zero_in && !prolong && restrict_)
+      launch_pdl(k_smooth_step<true, false, true>, ntiles, kThreads, smem, st, a);
+    else if (!zero_in && !prolong && !restrict_)
+      launch_pdl(k_smooth_step<false, false, false>, ntiles, kThreads, smem, st, a);
+    else if (!zero_in && !prolong && restrict_)
+      launch_pdl(k_smooth_step<false, false, true>, ntiles, kThreads, smem, st, a);
+    else if (!zero_in && prolong && !restrict_)
+      launch_pdl(k_smooth_step<false, true, false>, ntiles, kThreads, smem, st, a);
+    else
+      launch_pdl(k_smooth_step<false, true, true>, ntiles, kThreads, smem, st, a);
+  }
 }
 
 template cudaError_t configure_fused<float>(size_t);
 template cudaError_t configure_fused<double>(size_t);
-template void launch_smooth_step<float>(const FusedArgs<float>&, const FusedMaps&, int, bool, bool,
-                                        bool, size_t, cudaStream_t);
-template void launch_smooth_step<double>(const FusedArgs<double>&, const FusedMaps&, int, bool,
-                                         bool, bool, size_t, cudaStream_t);
+template void launch_smooth_step<float>(const FusedArgs<float>&, int, bool, bool, bool, size_t,
+                                        cudaStream_t);
+template void launch_smooth_step<double>(const FusedArgs<double>&, int, bool, bool, bool, size_t,
+                                         cudaStream_t);
