@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--inner", type=int, default=0,
                     help="V-cycles between fp64 residual checks (0: adaptive)")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="setup and one untimed mixed solve (for single-kernel profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -80,11 +82,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(kernel_tag):
+# source file of each fine-level kernel class
+KERNEL_SOURCE = {"sweep": "sweep32.cu", "restrict": "cycle.cu", "prolong": "cycle.cu",
+                 "residual": "cycle.cu", "update": "cycle.cu"}
+
+
+def profile_traffic(kernel_tag, kind):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
     source has not changed since it was captured."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    src = os.path.join(ROOT, "paper_2505_05105_gb300", "csrc", "cycle.cu")
+    src = os.path.join(ROOT, "paper_2505_05105_gb300", "csrc", KERNEL_SOURCE.get(kind, "cycle.cu"))
     try:
         txt = open(path).read()
         want = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -305,10 +312,10 @@ def run_ours(args):
     algo = ALGO_BYTES[(dom, kinds[dom])] * ndof
     peak, peak_src = measured_peaks()
     achieved = algo / per_launch_s / 1e9
-    traffic = profile_traffic(f"{dom}_f32_flower{N}")
+    traffic = profile_traffic(f"{dom}_f32_flower{N}", dom)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"k_gs_sweep<float> (fine level)" if dom == "sweep" else dom,
+                "kernel": "k_gs_sweep_f32 (fine level)" if dom == "sweep" else dom,
                 "algorithmic_bytes_per_launch": algo, "launches": n_launch,
                 "avg_launch_us": per_launch_s * 1e6, "peak_source": f"{peak_src} hbm_gbs",
                 "timing": f"CUDA events around each launch on the solver stream, over {args.steps} "
@@ -383,9 +390,28 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def profile_solve(args):
+    """Setup and one mixed solve of the flower workload, untimed: the program
+    that single-kernel profiler captures run (no flush buffer, no oracle)."""
+    import numpy as np
+    import torch
+    from paper_2505_05105_gb300 import ghostmg, workloads as wl
+    ghostmg.load()
+    p = wl.flower(args.N)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+    S = ghostmg.Solver(t(p.psi), p.N, p.x0, p.y0, p.h, precision="mixed")
+    u = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
+    info = S.solve(t(p.f), t(p.g), u, tol=TOL)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": args.N, "cycles": info.cycles, "rel_res": info.rel_res}))
+    S.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_solve:
+        profile_solve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
