@@ -149,7 +149,11 @@ int mg_solve(mg_handle h, const double* f, const double* g, double* u, double to
  * Sec. 4.1) to the tolerance of the last mg_solve (1e-10 if none), then
  * dL/df = M^T w and dL/dg = G^T w (F is linear in f and g, Eq. disc_rhs).
  * dLdu, dLdf, dLdg: (N+1)^2 doubles, device or host; dLdf or dLdg may be
- * NULL to skip it.  Errors as mg_solve. */
+ * NULL to skip it (not both).  dL/du off the DOFs is ignored; both outputs
+ * are 0 off the DOFs, dL/dg also away from cut cells.  The right-hand side
+ * dL/du has no h^2 mass factor, so the fp64 rounding floor of this solve
+ * relative to ||dL/du||_inf is about eps / h^2: ask for a tolerance above it.
+ * Errors as mg_solve (MG_ERR_NOT_CONVERGED: outputs still written). */
 int mg_adjoint(mg_handle h, const double* dLdu, double* dLdf, double* dLdg);
 
 /* Releases the handle and its device memory (NULL is ignored). */

@@ -30,7 +30,9 @@ the 1D matrices of Eq. ls1dA / ls1dF on a straight cut; Eq. c_triangle vs the
 eigen definition; quad theta1 = theta2 => C = 1/(theta h) (Sec. 5.3);
 polygon areas against closed forms and pi r^2; symmetry and positive
 definiteness by dense eigenvalues; second-order convergence on manufactured
-solutions.
+solutions; the adjoint gradients against central differences of the forward
+solve (exact up to rounding for the quadratic losses used) and their support
+(zero off the DOFs, dL/dg zero away from cut cells).
 """
 from __future__ import annotations
 
@@ -481,3 +483,19 @@ def direct_solve(system: System, F: np.ndarray, refine: int = 4) -> np.ndarray:
             break
     u[d] = x
     return u
+
+
+# ----------------------------------------------------------------------------
+# Adjoint of the solve: gradients of a loss L(u) with respect to f and g
+# ----------------------------------------------------------------------------
+
+def adjoint(system: System, dLdu: np.ndarray):
+    """dL/df and dL/dg (nodal vectors) of a loss L(u) where u solves
+    A u = M f + G g on the DOFs (Eq. disc_bil_form, Eq. disc_rhs with the
+    Q1 interpolants of nodal f and g).  A is symmetric (Sec. 4.1), so with w
+    the solution of A w = dL/du on the DOFs, dL/df = M^T w and dL/dg = G^T w
+    (F depends linearly on f and g).  Values of dL/du off the DOFs do not
+    matter: u is 0 there whatever f and g are."""
+    d = np.ravel(dLdu).astype(np.float64) * system.dof
+    w = direct_solve(system, d)
+    return system.M.T @ w, system.G.T @ w

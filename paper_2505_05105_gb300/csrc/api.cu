@@ -1136,9 +1136,46 @@ int mg_get_profile(mg_handle c, long long* launches, long long* counts, double* 
   return MG_OK;
 }
 
+// A is symmetric (Sec. 4.1): w solves A w = dL/du with the handle's own
+// cycle and precision, to the tolerance of the last solve; F = M f + G g is
+// linear in f and g (Eq. disc_rhs), so dL/df = M^T w and dL/dg = G^T w.
 int mg_adjoint(mg_handle c, const double* dLdu, double* dLdf, double* dLdg) {
-  if (!c || !dLdu) return MG_ERR_INVALID_ARG;
-  return MG_ERR_UNIMPLEMENTED;
+  if (!c || !dLdu || (!dLdf && !dLdg)) return MG_ERR_INVALID_ARG;
+  Level& v = c->lev[0];
+  const double tol = c->last_tol > 0.0 ? c->last_tol : 1e-10;
+  Staged sd;
+  TRY(stage_in(c, 0, dLdu, sd));
+  double *fd = nullptr, *gd = nullptr;
+  bool fh = false, gh = false;
+  if (dLdf) TRY(stage_out(c, 1, dLdf, &fd, &fh));
+  if (dLdg) TRY(stage_out(c, 2, dLdg, &gd, &gh));
+  // right-hand side dL/du on the DOFs (NaN / Inf rejected), w from 0
+  launch_pack<double>(v.L, v.code, sd.dev, v.F64, c->d_err, c->st);
+  v.cur64 = 0;
+  MG_CUDA_TRY(cudaMemsetAsync(v.u64[0], 0, v.L.size() * sizeof(double), c->st));
+  TRY(sync_check(c));
+  double Fn = 0.0;
+  TRY(fine_residual(c, 1.0, false, &Fn));     // ||dL/du||_inf on the DOFs (w = 0)
+  int status = MG_OK;
+  if (Fn > 0.0) {
+    status = solve_loop(c, Fn, tol, c->stab.max_cycles, nullptr, true);
+    if (status == MG_ERR_CUDA) return status;
+  }
+  const double* w = v.u64[v.cur64];
+  double* tf = v.F64;                          // dL/du is no longer needed
+  double* tg = v.u64[v.cur64 ^ 1];
+  RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
+  launch_rhs_adj(ra, v.active, v.n_active, w, dLdf ? tf : nullptr, dLdg ? tg : nullptr, c->st);
+  if (dLdf) {
+    launch_unpack(v.L, v.code, tf, fd, c->st);
+    TRY(finish_out(c, dLdf, fd, fh));
+  }
+  if (dLdg) {
+    launch_unpack(v.L, v.code, tg, gd, c->st);
+    TRY(finish_out(c, dLdg, gd, gh));
+  }
+  TRY(sync_check(c));
+  return status;
 }
 
 }  // extern "C"

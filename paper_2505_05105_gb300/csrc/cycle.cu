@@ -612,6 +612,71 @@ k_rhs(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ f,
   block_norms_to_global(vmax, 0.0, norms);
 }
 
+// Adjoint of the right-hand side map (f, g) -> F = M f + G g (Eq. disc_rhs):
+// for w on the DOFs (padded layout, zero elsewhere) dLdf = M^T w = M w (the
+// mass matrices are symmetric) and dLdg = G^T w, on one active tile.
+// Interior nodes take the separable mass stencil of k_rhs and no G term;
+// vertices of cut cells sum the cells one by one with column `av` of Mk, Gk.
+__global__ void __launch_bounds__(kThreads)
+k_rhs_adj(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ w,
+          double* __restrict__ dLdf, double* __restrict__ dLdg) {
+  __shared__ double sw[RHS_Y * RHS_X];       // w on the tile plus one ring
+  __shared__ double st[RHS_Y * MG_TX];       // row pass w(i-1) + 4 w(i) + w(i+1)
+  const int n = a.L.n;
+  const int t = tiles[blockIdx.x];
+  const int i0 = (t % a.L.ntx) * MG_TX, j0 = (t / a.L.ntx) * MG_TY;
+  for (int q = threadIdx.x; q < RHS_Y * RHS_X; q += blockDim.x) {
+    const int y = q / RHS_X, x = q - y * RHS_X;
+    sw[q] = w[a.L.idx(i0 - 1 + x, j0 - 1 + y)];        // zero margin: no checks needed
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < RHS_Y * MG_TX; q += blockDim.x) {
+    const int y = q / MG_TX, x = q - y * MG_TX;
+    const double* r = sw + y * RHS_X + x;
+    st[q] = fma(4.0, r[1], r[0] + r[2]);
+  }
+  __syncthreads();
+  const double h2 = a.h * a.h / 36.0;
+  for (int q = threadIdx.x; q < MG_TY * MG_TX; q += blockDim.x) {
+    const int y = q / MG_TX, x = q - y * MG_TX;
+    const int i = i0 + x, j = j0 + y;
+    const size_t gk = a.L.idx(i, j);
+    const uint16_t cd = a.code[gk];
+    double sf = 0.0, sg = 0.0;
+    if (cd == 1) {
+      const double* c = st + y * MG_TX + x;
+      sf = h2 * fma(4.0, c[MG_TX], c[0] + c[2 * MG_TX]);
+    } else if (cd) {
+      for (int k = 0; k < 4; ++k) {
+        const int dx = k & 1, dy = k >> 1;
+        const int ic = i - 1 + dx, jc = j - 1 + dy;
+        if (ic < 0 || jc < 0 || ic >= n || jc >= n) continue;
+        const size_t c = (size_t)jc * n + ic;
+        const uint8_t cl = a.cls[c];
+        if (cl == CELL_EXT) continue;
+        const int av = (1 - dx) + 2 * (1 - dy);
+        const double* wv = sw + (y + dy) * RHS_X + (x + dx);
+        const double wb[4] = {wv[0], wv[1], wv[RHS_X], wv[RHS_X + 1]};
+        if (cl == CELL_INT) {
+          for (int b = 0; b < 4; ++b) {
+            int wgt = (b == av) ? 4 : ((b ^ av) == 3 ? 1 : 2);
+            sf += h2 * wgt * wb[b];
+          }
+        } else {
+          const double* Mk = a.Mk + (size_t)a.cell_cut[c] * 16;
+          const double* Gk = a.Gk + (size_t)a.cell_cut[c] * 16;
+          for (int b = 0; b < 4; ++b) {
+            sf += Mk[b * 4 + av] * wb[b];
+            sg += Gk[b * 4 + av] * wb[b];
+          }
+        }
+      }
+    }
+    if (dLdf) dLdf[gk] = sf;
+    if (dLdg) dLdg[gk] = sg;
+  }
+}
+
 // Any NaN or Inf in two arrays of m doubles (vectorised reads).
 __global__ void k_check_finite2(const double* __restrict__ p, const double* __restrict__ q,
                                 size_t m, unsigned* err) {
@@ -825,6 +890,12 @@ void launch_rhs(const RhsArgs& a, const int* tiles, int ntiles, const double* f,
                 double* F, double* norms, cudaStream_t st) {
   if (!ntiles) return;
   k_rhs<<<ntiles, kThreads, 0, st>>>(a, tiles, f, g, F, norms);
+}
+
+void launch_rhs_adj(const RhsArgs& a, const int* tiles, int ntiles, const double* w,
+                    double* dLdf, double* dLdg, cudaStream_t st) {
+  if (!ntiles) return;
+  k_rhs_adj<<<ntiles, kThreads, 0, st>>>(a, tiles, w, dLdf, dLdg);
 }
 
 template <class T>

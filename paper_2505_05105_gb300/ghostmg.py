@@ -162,9 +162,9 @@ def mg_solve(handle: int, f, g, u, tol: float, info: Optional[mg_info] = None,
                   "mg_solve", ok)
 
 
-def mg_adjoint(handle: int, dLdu, dLdf=None, dLdg=None) -> int:
+def mg_adjoint(handle: int, dLdu, dLdf=None, dLdg=None, ok=(MG_OK,)) -> int:
     return _check(load().mg_adjoint(handle, _addr(dLdu), _addr(dLdf, True), _addr(dLdg, True)),
-                  "mg_adjoint")
+                  "mg_adjoint", ok)
 
 
 def mg_destroy(handle: int) -> None:
@@ -278,6 +278,13 @@ class Solver:
     def residual(self, F, u, r=None):
         return mg_residual(self.handle, F, u, r)
 
+    def adjoint(self, dLdu, dLdf=None, dLdg=None, allow_not_converged: bool = False):
+        """dL/df and dL/dg of a loss of the last solve's u (either output may
+        be None): solves A w = dL/du to the last solve's tolerance."""
+        ok = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
+        mg_adjoint(self.handle, dLdu, dLdf, dLdg, ok)
+        return dLdf, dLdg
+
     def stencil(self, level: int) -> np.ndarray:
         n = mg_level_cells(self.handle, level)
         out = np.zeros((n + 1) * (n + 1) * 9)
@@ -307,3 +314,31 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# --- differentiation --------------------------------------------------------
+
+def solve_diff(solver: "Solver", f, g, tol: float = 1e-10):
+    """u = solve(f, g) as a differentiable torch operation: the backward pass
+    runs mg_adjoint (dL/df = M^T w, dL/dg = G^T w with A w = dL/du).  f and g
+    are (N+1)^2 float64 CUDA tensors; u has the same shape."""
+    import torch
+
+    class _Solve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, f_, g_):
+            u = torch.zeros_like(f_)
+            solver.solve(f_.detach().contiguous(), g_.detach().contiguous(), u, tol=tol)
+            return u
+
+        @staticmethod
+        def backward(ctx, dLdu):
+            need_f, need_g = ctx.needs_input_grad
+            if not (need_f or need_g):
+                return None, None
+            dLdf = torch.zeros_like(dLdu) if need_f else None
+            dLdg = torch.zeros_like(dLdu) if need_g else None
+            solver.adjoint(dLdu.detach().contiguous(), dLdf, dLdg)
+            return dLdf, dLdg
+
+    return _Solve.apply(f, g)
