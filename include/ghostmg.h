@@ -254,6 +254,79 @@ int mg_set_profiling(mg_handle h, int enable);
  * total device milliseconds (ms[MG_PROF_SLOTS]).  Any pointer may be NULL. */
 int mg_get_profile(mg_handle h, long long* launches, long long* counts, double* ms);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves: many independent problems, each with its own level set and
+ * grid size, solved together in mixed precision (the fp32 V(nu1, nu2)-cycle
+ * of mg_solve inside fp64 iterative refinement, with the adaptive check
+ * schedule of mg_stab.inner = 0, or a fixed one).  One persistent kernel
+ * takes the members from a work queue, largest first, and runs each
+ * member's whole solve in one thread block: the levels above 64 x 64 cells
+ * block-wide in global memory, the smaller ones in shared memory.  A solve
+ * is one CUDA graph (input check, right-hand sides, the persistent kernel,
+ * output copy and status read-back).
+ *
+ * Packed arrays: member p has (N_p + 1)^2 nodes, N_p = grids[p].n_cells,
+ * stored row-major as above from offset off_p = sum over q < p of
+ * (N_q + 1)^2 doubles; a packed array holds all members, total_nodes
+ * doubles.
+ * ------------------------------------------------------------------------- */
+typedef struct mg_batch_ctx* mg_batch;
+
+/* Per-member result of mg_batch_solve. */
+typedef struct {
+  int status;        /* MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED, or
+                        MG_ERR_INVALID_ARG (NaN/Inf in the member's f or g;
+                        its u is 0) */
+  int cycles;        /* fp32 V-cycles run */
+  int checks;        /* fp64 residual checks after the initial one */
+  int n_dof;         /* fine-level DOFs */
+  double rel_res;    /* final ||F - A u||_inf / ||F||_inf (fp64) */
+} mg_batch_info;
+
+/* Sets up count >= 1 members: levelsets is a packed array (host or device)
+ * of the members' nodal psi; grids[count] their grids (host).  bc and stab
+ * as for mg_setup and shared by all members; stab->precision must be
+ * MG_MIXED (or stab NULL).  cuda_stream: the caller's stream; the batch
+ * orders its work after the work queued there when a call starts, and runs
+ * on a stream of its own (a graph cannot be captured on the legacy
+ * stream).  Errors as mg_setup, and MG_ERR_UNIMPLEMENTED for MG_FP64. */
+int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double* levelsets,
+                   const mg_bc* bc, const mg_stab* stab, void* cuda_stream);
+
+/* *total_nodes: doubles in a packed array; f, g, u (any may be NULL): the
+ * batch's own device packed arrays.  Passing them to mg_batch_solve skips
+ * the copies in and out; they stay valid until mg_batch_destroy. */
+int mg_batch_buffers(mg_batch b, long long* total_nodes, double** f, double** g, double** u);
+
+/* Solves every member: f, g, u packed arrays (host or device; u is output
+ * only, every member starts from u = 0).  info: count entries or NULL.
+ * Returns MG_OK when every member converged, else the most severe member
+ * status (MG_ERR_INVALID_ARG, then MG_ERR_DIVERGED, then
+ * MG_ERR_NOT_CONVERGED; u and info filled for all members); MG_ERR_TIMEOUT
+ * if a bounded shared-memory copy wait ran out; MG_ERR_CUDA. */
+int mg_batch_solve(mg_batch b, const double* f, const double* g, double* u, double tol,
+                   mg_batch_info* info);
+
+/* Autotuner: times `reps` graph replays (after one warm-up) of the solve of
+ * (f, g) to tol for every candidate launch shape -- threads per block in
+ * {256, 512, 1024} and, with the adaptive schedule, V-cycles before the
+ * first fp64 check in {2, 3, 4, 6} -- and keeps the fastest whose members
+ * all converge.  Outputs (any may be NULL): the choice and its mean time per
+ * solve in ms.  Errors as mg_batch_solve (MG_ERR_NOT_CONVERGED if no
+ * candidate converged everywhere). */
+int mg_batch_tune(mg_batch b, const double* f, const double* g, double tol, int reps,
+                  int* threads, int* first_group, float* ms);
+
+/* Sets the launch shape directly (threads 256, 512 or 1024; first_group
+ * 1..8).  Default 1024 threads, first group 4. */
+int mg_batch_set_tune(mg_batch b, int threads, int first_group);
+
+/* Wall time of mg_batch_setup and device time of the last solve's graph. */
+int mg_batch_timing(mg_batch b, float* setup_ms, float* solve_ms);
+
+/* Releases the batch (NULL is ignored). */
+void mg_batch_destroy(mg_batch b);
+
 #ifdef __cplusplus
 }
 #endif

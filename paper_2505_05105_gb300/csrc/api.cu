@@ -3,6 +3,7 @@
 // iterative refinement.  See include/ghostmg.h for the contract.
 #include "ghostmg.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -1176,6 +1177,397 @@ int mg_adjoint(mg_handle c, const double* dLdu, double* dLdf, double* dLdg) {
   }
   TRY(sync_check(c));
   return status;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched solves (batch.cu): per-member hierarchies built by the setup above,
+// a table of their device arrays, and one CUDA graph per launch shape.
+
+#include "batch.cuh"
+
+struct mg_batch_ctx {
+  cudaStream_t user_st = nullptr;   // the caller's stream (ordering only)
+  cudaStream_t st = nullptr;        // the batch's own stream (captured, launched)
+  int count = 0;
+  mg_stab stab{};
+  std::vector<mg_ctx*> mem;
+  std::vector<void*> allocs;
+  std::vector<size_t> node_off;     // count + 1
+  size_t total_nodes = 0;
+  int total_tiles = 0;
+  BatchProblem* d_probs = nullptr;
+  int* d_order = nullptr;
+  size_t* d_node_off = nullptr;
+  int* d_tile_off = nullptr;
+  unsigned* d_words = nullptr;      // [0] queue counter, [1] error word, [2..] bad flags
+  double* d_params = nullptr;       // tol, max_cycles, fixed group (0: adaptive)
+  double* h_params = nullptr;       // pinned
+  BatchResult* d_res = nullptr;
+  BatchResult* h_res = nullptr;     // pinned (the graph copies into it)
+  unsigned* h_err = nullptr;        // pinned
+  double *f = nullptr, *g = nullptr, *u = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+  BatchTune tune{1024, 4};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev_in = nullptr, ev0 = nullptr, ev1 = nullptr;
+  float setup_ms = 0.f, solve_ms = 0.f;
+};
+
+namespace {
+
+template <class T>
+int balloc(mg_batch_ctx* b, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return MG_ERR_OUT_OF_MEMORY;
+  }
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  b->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, count * sizeof(T), b->st);
+  return e == cudaSuccess ? MG_OK : mg_cuda_fail(e);
+}
+
+// the device table entry of one member (its hierarchy is set up, mixed)
+int batch_member(mg_batch_ctx* b, int p, BatchProblem* out) {
+  mg_ctx* c = b->mem[p];
+  const int t = c->tail_level;
+  if (t < 0 || t > MG_BATCH_MAX_TOP) return MG_ERR_UNIMPLEMENTED;
+  BatchProblem& q = *out;
+  memset(&q, 0, sizeof(q));
+  q.n_top = t;
+  for (int l = 0; l < t; ++l) {
+    Level& v = c->lev[l];
+    BatchLevel& w = q.lev[l];
+    int2* blist;
+    int* boff;
+    TRY(dalloc(c, &blist, (size_t)v.n_bnd));
+    TRY(dalloc(c, &boff, 5));
+    launch_batch_lists(v.L, v.code, v.tile_base, blist, boff, c->st);
+    MG_CUDA_TRY(cudaMemcpyAsync(w.boff, boff, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+    w.L = v.L;
+    w.code = v.code;
+    w.tile_base = v.tile_base;
+    w.rows = v.rows32;
+    w.active = v.active;
+    w.n_active = v.n_active;
+    w.blist = blist;
+    w.u = v.u32[0];
+    w.F = v.F32;
+    w.scr = v.u32[1];           // zero from allocation; the batch writes it on active tiles only
+  }
+  Level& top = c->lev[t];
+  TailArgs<float>& a = q.tail;
+  a.lay = c->tail_lay[0];
+  for (int k = 0; k < a.lay.nlev; ++k) a.rows[k] = c->lev[t + k].rows32;
+  a.L0 = top.L;
+  a.image = c->tail_image[0];
+  a.Ainv = c->Ainv;
+  a.F0 = top.F32;
+  a.u0 = top.u32[0];
+  a.load_u0 = 0;
+  a.eta = c->stab.eta;
+  a.nu1 = c->stab.nu1;
+  a.nu2 = c->stab.nu2;
+  a.err = b->d_words + 1;
+  q.tail_active = top.active;
+  q.tail_n_active = top.n_active;
+  q.tail_F = top.F32;
+  Level& v = c->lev[0];
+  q.L0 = v.L;
+  q.code0 = v.code;
+  q.tile_base0 = v.tile_base;
+  q.rows64 = v.rows64;
+  q.active0 = v.active;
+  q.n_active0 = v.n_active;
+  q.F64 = v.F64;
+  q.u64 = v.u64[0];
+  q.F32 = v.F32;
+  q.e32 = v.u32[0];
+  q.eta = c->stab.eta;
+  q.nu1 = c->stab.nu1;
+  q.nu2 = c->stab.nu2;
+  q.rhs = RhsArgs{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
+  q.f = b->f + b->node_off[p];
+  q.g = b->g + b->node_off[p];
+  q.u_out = b->u + b->node_off[p];
+  return MG_OK;
+}
+
+// (re)captures the solve graph for the current launch shape
+int batch_capture(mg_batch_ctx* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  MG_CUDA_TRY(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(b->d_words, 0, (2 + (size_t)b->count) * sizeof(unsigned), b->st);
+  launch_batch_check(b->d_probs, b->d_node_off, b->count, b->total_nodes, b->d_words + 2, b->st);
+  launch_batch_rhs(b->d_probs, b->d_tile_off, b->count, b->total_tiles, b->st);
+  launch_batch(b->d_probs, b->d_order, b->count, reinterpret_cast<int*>(b->d_words),
+               b->d_words + 2, b->d_params, b->tune, b->grid, b->smem, b->d_res, b->st);
+  launch_batch_unpack(b->d_probs, b->d_node_off, b->count, b->total_nodes, b->st);
+  cudaMemcpyAsync(b->h_res, b->d_res, (size_t)b->count * sizeof(BatchResult),
+                  cudaMemcpyDeviceToHost, b->st);
+  cudaMemcpyAsync(b->h_err, b->d_words + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, b->st);
+  cudaError_t e = cudaStreamEndCapture(b->st, &b->graph);
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  MG_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return MG_OK;
+}
+
+int status_rank(int s) {
+  switch (s) {
+    case MG_OK: return 0;
+    case MG_ERR_NOT_CONVERGED: return 1;
+    case MG_ERR_DIVERGED: return 2;
+    default: return 3;
+  }
+}
+
+// one solve of the inputs already in b->f, b->g; results in b->u, b->h_res
+int batch_run(mg_batch_ctx* b, double tol, int* worst) {
+  b->h_params[0] = tol;
+  b->h_params[1] = (double)b->stab.max_cycles;
+  b->h_params[2] = (double)b->stab.inner;
+  MG_CUDA_TRY(cudaMemcpyAsync(b->d_params, b->h_params, 3 * sizeof(double),
+                              cudaMemcpyHostToDevice, b->st));
+  MG_CUDA_TRY(cudaEventRecord(b->ev0, b->st));
+  MG_CUDA_TRY(cudaGraphLaunch(b->exec, b->st));
+  MG_CUDA_TRY(cudaEventRecord(b->ev1, b->st));
+  MG_CUDA_TRY(cudaStreamSynchronize(b->st));
+  MG_CUDA_TRY(cudaGetLastError());
+  MG_CUDA_TRY(cudaEventElapsedTime(&b->solve_ms, b->ev0, b->ev1));
+  if (*b->h_err) {
+    const unsigned err = *b->h_err;
+    if (err & DEV_ERR_TIMEOUT) return MG_ERR_TIMEOUT;
+    return MG_ERR_INTERNAL;
+  }
+  int w = MG_OK;
+  for (int p = 0; p < b->count; ++p)
+    if (status_rank(b->h_res[p].status) > status_rank(w)) w = b->h_res[p].status;
+  *worst = w;
+  return MG_OK;
+}
+
+int batch_stage(mg_batch_ctx* b, const double* f, const double* g) {
+  MG_CUDA_TRY(cudaEventRecord(b->ev_in, b->user_st));
+  MG_CUDA_TRY(cudaStreamWaitEvent(b->st, b->ev_in, 0));
+  const size_t bytes = b->total_nodes * sizeof(double);
+  if (f != b->f) MG_CUDA_TRY(cudaMemcpyAsync(b->f, f, bytes, cudaMemcpyDefault, b->st));
+  if (g != b->g) MG_CUDA_TRY(cudaMemcpyAsync(b->g, g, bytes, cudaMemcpyDefault, b->st));
+  return MG_OK;
+}
+
+int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levelsets,
+                     const mg_bc* bc) {
+  const int n = b->count;
+  MG_CUDA_TRY(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+  MG_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+  MG_CUDA_TRY(cudaEventCreate(&b->ev0));
+  MG_CUDA_TRY(cudaEventCreate(&b->ev1));
+  MG_CUDA_TRY(cudaEventRecord(b->ev_in, b->user_st));
+  MG_CUDA_TRY(cudaStreamWaitEvent(b->st, b->ev_in, 0));
+  b->node_off.assign(n + 1, 0);
+  for (int p = 0; p < n; ++p) {
+    const size_t m = (size_t)grids[p].n_cells + 1;
+    if (grids[p].n_cells <= 0 || grids[p].n_cells > 32768) return MG_ERR_INVALID_ARG;
+    b->node_off[p + 1] = b->node_off[p] + m * m;
+  }
+  b->total_nodes = b->node_off[n];
+  TRY(balloc(b, &b->f, b->total_nodes));
+  TRY(balloc(b, &b->g, b->total_nodes));
+  TRY(balloc(b, &b->u, b->total_nodes));
+  TRY(balloc(b, &b->d_words, 2 + (size_t)n));
+  TRY(balloc(b, &b->d_params, 4));
+  TRY(balloc(b, &b->d_res, (size_t)n));
+  TRY(balloc(b, &b->d_order, (size_t)n));
+  TRY(balloc(b, &b->d_node_off, (size_t)n + 1));
+  TRY(balloc(b, &b->d_tile_off, (size_t)n + 1));
+  TRY(balloc(b, &b->d_probs, (size_t)n));
+  MG_CUDA_TRY(cudaMallocHost((void**)&b->h_params, 4 * sizeof(double)));
+  MG_CUDA_TRY(cudaMallocHost((void**)&b->h_res, (size_t)n * sizeof(BatchResult)));
+  MG_CUDA_TRY(cudaMallocHost((void**)&b->h_err, sizeof(unsigned)));
+  *b->h_err = 0;
+  for (int p = 0; p < n; ++p) {
+    mg_handle h = nullptr;
+    const double* ls = levelsets + b->node_off[p];
+    TRY(mg_setup(&h, ls, &grids[p], bc, &b->stab, b->st));
+    b->mem.push_back(h);
+  }
+  std::vector<BatchProblem> probs(n);
+  std::vector<int> tile_off(n + 1, 0);
+  size_t smem = 0;
+  for (int p = 0; p < n; ++p) {
+    TRY(batch_member(b, p, &probs[p]));
+    tile_off[p + 1] = tile_off[p] + probs[p].n_active0;
+    smem = std::max(smem, (size_t)b->mem[p]->tail_lay[0].total);
+  }
+  b->total_tiles = tile_off[n];
+  // largest first (fine-level DOFs), ties by index
+  std::vector<int> order(n);
+  for (int p = 0; p < n; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->mem[x]->lev[0].n_dof > b->mem[y]->lev[0].n_dof;
+  });
+  MG_CUDA_TRY(cudaMemcpyAsync(b->d_probs, probs.data(), (size_t)n * sizeof(BatchProblem),
+                              cudaMemcpyHostToDevice, b->st));
+  MG_CUDA_TRY(cudaMemcpyAsync(b->d_order, order.data(), (size_t)n * sizeof(int),
+                              cudaMemcpyHostToDevice, b->st));
+  MG_CUDA_TRY(cudaMemcpyAsync(b->d_node_off, b->node_off.data(), (size_t)(n + 1) * sizeof(size_t),
+                              cudaMemcpyHostToDevice, b->st));
+  MG_CUDA_TRY(cudaMemcpyAsync(b->d_tile_off, tile_off.data(), (size_t)(n + 1) * sizeof(int),
+                              cudaMemcpyHostToDevice, b->st));
+  MG_CUDA_TRY(cudaStreamSynchronize(b->st));
+  b->smem = smem + kSmemSlack;
+  MG_CUDA_TRY(configure_batch(b->smem));
+  int dev = 0, nsm = 0;
+  MG_CUDA_TRY(cudaGetDevice(&dev));
+  MG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  b->grid = std::min(n, nsm);
+  return batch_capture(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double* levelsets,
+                   const mg_bc* bc, const mg_stab* stab, void* cuda_stream) {
+  if (!out) return MG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || !grids || !levelsets) return MG_ERR_INVALID_ARG;
+  mg_stab s;
+  mg_default_stab(&s);
+  if (stab) s = *stab;
+  else s.precision = MG_MIXED;
+  if (s.precision == MG_FP64) return MG_ERR_UNIMPLEMENTED;
+  if (s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
+  mg_batch_ctx* b = new mg_batch_ctx();
+  b->user_st = (cudaStream_t)cuda_stream;
+  b->count = count;
+  b->stab = s;
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = batch_setup_impl(b, grids, levelsets, bc);
+  if (rc != MG_OK) {
+    mg_batch_destroy(b);
+    return rc;
+  }
+  b->setup_ms =
+      std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = b;
+  return MG_OK;
+}
+
+int mg_batch_buffers(mg_batch b, long long* total_nodes, double** f, double** g, double** u) {
+  if (!b) return MG_ERR_INVALID_ARG;
+  if (total_nodes) *total_nodes = (long long)b->total_nodes;
+  if (f) *f = b->f;
+  if (g) *g = b->g;
+  if (u) *u = b->u;
+  return MG_OK;
+}
+
+int mg_batch_solve(mg_batch b, const double* f, const double* g, double* u, double tol,
+                   mg_batch_info* info) {
+  if (!b || !f || !g || !u || !(tol >= 0.0)) return MG_ERR_INVALID_ARG;
+  TRY(batch_stage(b, f, g));
+  int worst = MG_OK;
+  TRY(batch_run(b, tol, &worst));
+  if (u != b->u) {
+    MG_CUDA_TRY(cudaMemcpyAsync(u, b->u, b->total_nodes * sizeof(double), cudaMemcpyDefault,
+                                b->st));
+    MG_CUDA_TRY(cudaStreamSynchronize(b->st));
+  }
+  if (info)
+    for (int p = 0; p < b->count; ++p) {
+      const BatchResult& r = b->h_res[p];
+      info[p].status = r.status;
+      info[p].cycles = r.cycles;
+      info[p].checks = r.checks;
+      info[p].n_dof = b->mem[p]->lev[0].n_dof;
+      info[p].rel_res = r.rel_res;
+    }
+  return worst;
+}
+
+int mg_batch_set_tune(mg_batch b, int threads, int first_group) {
+  if (!b || (threads != 256 && threads != 512 && threads != 1024) || first_group < 1 ||
+      first_group > 8)
+    return MG_ERR_INVALID_ARG;
+  b->tune = BatchTune{threads, first_group};
+  return batch_capture(b);
+}
+
+int mg_batch_tune(mg_batch b, const double* f, const double* g, double tol, int reps,
+                  int* threads, int* first_group, float* ms) {
+  if (!b || !f || !g || !(tol >= 0.0) || reps < 1) return MG_ERR_INVALID_ARG;
+  TRY(batch_stage(b, f, g));
+  const int th[3] = {256, 512, 1024};
+  const int fg_adaptive[4] = {2, 3, 4, 6};
+  const int nfg = b->stab.inner == 0 ? 4 : 1;
+  const BatchTune start = b->tune;
+  BatchTune best{0, 0};
+  float best_ms = 0.f;
+  for (int ti = 0; ti < 3; ++ti)
+    for (int fi = 0; fi < nfg; ++fi) {
+      b->tune = BatchTune{th[ti], b->stab.inner == 0 ? fg_adaptive[fi] : start.first_group};
+      TRY(batch_capture(b));
+      int worst = MG_OK;
+      TRY(batch_run(b, tol, &worst));            // warm-up
+      if (worst != MG_OK) continue;
+      float total = 0.f;
+      bool ok = true;
+      for (int r = 0; r < reps && ok; ++r) {
+        TRY(batch_run(b, tol, &worst));
+        ok = worst == MG_OK;
+        total += b->solve_ms;
+      }
+      if (!ok) continue;
+      const float mean = total / reps;
+      if (best.threads == 0 || mean < best_ms) {
+        best = b->tune;
+        best_ms = mean;
+      }
+    }
+  b->tune = best.threads ? best : start;
+  TRY(batch_capture(b));
+  if (!best.threads) return MG_ERR_NOT_CONVERGED;
+  if (threads) *threads = best.threads;
+  if (first_group) *first_group = best.first_group;
+  if (ms) *ms = best_ms;
+  return MG_OK;
+}
+
+int mg_batch_timing(mg_batch b, float* setup_ms, float* solve_ms) {
+  if (!b) return MG_ERR_INVALID_ARG;
+  if (setup_ms) *setup_ms = b->setup_ms;
+  if (solve_ms) *solve_ms = b->solve_ms;
+  return MG_OK;
+}
+
+void mg_batch_destroy(mg_batch b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (mg_ctx* c : b->mem) mg_destroy(c);
+  for (void* p : b->allocs) cudaFree(p);
+  if (b->h_params) cudaFreeHost(b->h_params);
+  if (b->h_res) cudaFreeHost(b->h_res);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
 }
 
 }  // extern "C"

@@ -1,0 +1,84 @@
+// Batched mixed-precision solves of many independent geometries in one
+// persistent kernel (see batch.cu).
+#pragma once
+
+#include "cycle.cuh"
+#include "tail.cuh"
+
+#define MG_BATCH_MAX_TOP 10      // levels above the tail block (N <= 32768)
+
+// One level solved block-wide in global memory (the levels above the tail).
+struct BatchLevel {
+  Layout L;
+  const uint16_t* code;
+  const int* tile_base;
+  const float* rows;           // fp32 boundary rows
+  const int* active;           // active tiles
+  int n_active;
+  const int2* blist;           // boundary nodes {i | j << 16, row}, grouped by colour
+  int boff[5];                 // colour group offsets into blist
+  float* u;                    // iterate (in place)
+  float* F;                    // right-hand side
+  float* scr;                  // residual scratch (zero outside the active tiles)
+};
+
+struct BatchProblem {
+  int n_top;                   // levels 0 .. n_top-1 block-wide, the tail from level n_top
+  BatchLevel lev[MG_BATCH_MAX_TOP];
+  TailArgs<float> tail;        // the tail block's V-cycle (its top F and u: level n_top)
+  const int* tail_active;      // active tiles of the tail's top level
+  int tail_n_active;
+  float* tail_F;               // the tail's top F (restriction target)
+  // fine level in fp64
+  Layout L0;
+  const uint16_t* code0;
+  const int* tile_base0;
+  const double* rows64;
+  const int* active0;
+  int n_active0;
+  double* F64;
+  double* u64;
+  float* F32;                  // fine fp32 right-hand side (lev[0].F, or the tail's top F)
+  float* e32;                  // fine fp32 correction (lev[0].u, or the tail's top u)
+  int eta, nu1, nu2;
+  // the member's data in the packed user arrays (row-major (N+1)^2 nodes)
+  RhsArgs rhs;
+  const double* f;
+  const double* g;
+  double* u_out;
+};
+
+struct BatchResult {
+  int cycles, checks, status, pad;
+  double rel_res;
+};
+
+// tuning knobs of the persistent kernel (chosen by mg_batch_tune)
+struct BatchTune {
+  int threads;                 // threads per block (256 .. 1024)
+  int first_group;             // V-cycles before the first fp64 residual check
+};
+
+// Per-member input check and right-hand side over all members at once:
+// node_off[p] (count + 1 entries) is member p's first node in the packed user
+// arrays, tile_off[p] its first active fine tile in the flattened tile range.
+// bad[p] |= 1 if member p's f or g holds a NaN or an Inf.
+void launch_batch_check(const BatchProblem* probs, const size_t* node_off, int count,
+                        size_t total_nodes, unsigned* bad, cudaStream_t st);
+void launch_batch_rhs(const BatchProblem* probs, const int* tile_off, int count, int total_tiles,
+                      cudaStream_t st);
+// u_out of every member from its fine fp64 iterate (zero off the DOFs)
+void launch_batch_unpack(const BatchProblem* probs, const size_t* node_off, int count,
+                         size_t total_nodes, cudaStream_t st);
+
+// Launches the persistent kernel: grid blocks take problems order[0..count)
+// from the counter *next (zero on entry), largest first.
+// Members with bad[p] != 0 get u = 0 and status MG_ERR_INVALID_ARG.
+// *params = {tol, max_cycles} (device memory, read at launch).
+void launch_batch(const BatchProblem* probs, const int* order, int count, int* next,
+                  const unsigned* bad, const double* params, BatchTune tune, int grid,
+                  size_t smem, BatchResult* res, cudaStream_t st);
+cudaError_t configure_batch(size_t smem);
+// builds blist / boff of one level from its codes (one block)
+void launch_batch_lists(const Layout& L, const uint16_t* code, const int* tile_base,
+                        int2* blist, int* boff, cudaStream_t st);

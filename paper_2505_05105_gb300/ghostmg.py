@@ -59,6 +59,11 @@ class mg_info(ctypes.Structure):
         return [self.res_hist[k] for k in range(min(self.checks + 1, 64))]
 
 
+class mg_batch_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int), ("checks", ctypes.c_int),
+                ("n_dof", ctypes.c_int), ("rel_res", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -83,6 +88,16 @@ SIGNATURES = {
     "mg_residual_static": (_I, [_P, _P, _P, _P, _P]),
     "mg_set_profiling": (_I, [_P, _I]),
     "mg_get_profile": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _P, _P]),
+    "mg_batch_setup": (_I, [ctypes.POINTER(_P), _I, _P, _P, ctypes.POINTER(mg_bc),
+                            ctypes.POINTER(mg_stab), _P]),
+    "mg_batch_buffers": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_P),
+                              ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "mg_batch_solve": (_I, [_P, _P, _P, _P, _D, _P]),
+    "mg_batch_tune": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                           ctypes.POINTER(ctypes.c_float)]),
+    "mg_batch_set_tune": (_I, [_P, _I, _I]),
+    "mg_batch_timing": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "mg_batch_destroy": (None, [_P]),
 }
 
 PROF_SLOTS = ("sweep", "band", "restrict", "prolong", "residual", "update", "coarse", "io")
@@ -235,6 +250,57 @@ def mg_get_profile(handle: int):
     return n.value, {k: (int(counts[i]), float(ms[i])) for i, k in enumerate(PROF_SLOTS)}
 
 
+def mg_batch_setup(grids, levelsets, bc: Optional[mg_bc] = None,
+                   stab: Optional[mg_stab] = None, stream: int = 0) -> int:
+    """grids: sequence of mg_grid; levelsets: packed array of all members'
+    nodal psi (host or device)."""
+    arr = (mg_grid * len(grids))(*grids)
+    h = _P()
+    _check(load().mg_batch_setup(ctypes.byref(h), len(grids), ctypes.addressof(arr),
+                                 _addr(levelsets), ctypes.byref(bc) if bc is not None else None,
+                                 ctypes.byref(stab) if stab is not None else None,
+                                 _P(stream) if stream else None), "mg_batch_setup")
+    return h.value
+
+
+def mg_batch_buffers(batch: int):
+    """(total_nodes, f, g, u): the batch's own device packed arrays (addresses)."""
+    n = ctypes.c_longlong()
+    f, g, u = _P(), _P(), _P()
+    _check(load().mg_batch_buffers(batch, ctypes.byref(n), ctypes.byref(f), ctypes.byref(g),
+                                   ctypes.byref(u)), "mg_batch_buffers")
+    return n.value, f.value, g.value, u.value
+
+
+def mg_batch_solve(batch: int, f, g, u, tol: float, info=None, ok=(MG_OK,)) -> int:
+    return _check(load().mg_batch_solve(batch, _addr(f), _addr(g), _addr(u, True), tol,
+                                        ctypes.addressof(info) if info is not None else None),
+                  "mg_batch_solve", ok)
+
+
+def mg_batch_tune(batch: int, f, g, tol: float, reps: int = 3):
+    """(threads, first_group, ms) of the fastest launch shape (see the header)."""
+    t, k, ms = _I(), _I(), ctypes.c_float()
+    _check(load().mg_batch_tune(batch, _addr(f), _addr(g), tol, reps, ctypes.byref(t),
+                                ctypes.byref(k), ctypes.byref(ms)), "mg_batch_tune")
+    return t.value, k.value, ms.value
+
+
+def mg_batch_set_tune(batch: int, threads: int, first_group: int) -> int:
+    return _check(load().mg_batch_set_tune(batch, threads, first_group), "mg_batch_set_tune")
+
+
+def mg_batch_timing(batch: int):
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(load().mg_batch_timing(batch, ctypes.byref(a), ctypes.byref(b)), "mg_batch_timing")
+    return a.value, b.value
+
+
+def mg_batch_destroy(batch: int) -> None:
+    if batch:
+        load().mg_batch_destroy(batch)
+
+
 # --- convenience object ------------------------------------------------------------
 
 class Solver:
@@ -301,6 +367,92 @@ class Solver:
     def close(self):
         if getattr(self, "handle", None):
             mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class _DeviceArray:
+    """A raw device allocation seen through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class BatchSolver:
+    """Owns one batch of independent problems (see mg_batch_setup).
+    ``problems``: objects with psi, N, x0, y0, h (workloads.Problem).  Packed
+    arrays put member p's (N_p+1)^2 nodes at offsets()[p]."""
+
+    def __init__(self, problems, *, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
+                 nu1: int = 2, nu2: int = 1, max_cycles: int = 100, inner: int = 0,
+                 stream: int = 0):
+        stab = mg_default_stab()
+        stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta
+        stab.nu1, stab.nu2, stab.max_cycles, stab.inner = nu1, nu2, max_cycles, inner
+        stab.precision = MG_MIXED
+        self.sizes = [int(p.N) for p in problems]
+        grids = [mg_grid(p.N, p.x0, p.y0, p.h, 8) for p in problems]
+        psi = self.pack([p.psi for p in problems])
+        self.handle = mg_batch_setup(grids, psi, mg_bc(MG_BC_DIRICHLET, None), stab, stream)
+        self.count = len(problems)
+        self.total, self._f, self._g, self._u = mg_batch_buffers(self.handle)
+
+    def offsets(self):
+        off = np.zeros(len(self.sizes) + 1, dtype=np.int64)
+        off[1:] = np.cumsum([(n + 1) ** 2 for n in self.sizes])
+        return off
+
+    def pack(self, arrays) -> np.ndarray:
+        return np.concatenate([np.ascontiguousarray(a, dtype=np.float64).ravel() for a in arrays])
+
+    def unpack(self, packed):
+        off = self.offsets()
+        return [packed[off[p]:off[p + 1]] for p in range(len(self.sizes))]
+
+    def buffers(self):
+        """(f, g, u): torch views of the batch's own device packed arrays;
+        solving from them skips every copy."""
+        import torch
+        return tuple(torch.as_tensor(_DeviceArray(ptr, self.total), device="cuda")
+                     for ptr in (self._f, self._g, self._u))
+
+    def solve(self, f, g, u, tol: float = 1e-10, allow_not_converged: bool = False):
+        info = (mg_batch_info * self.count)()
+        ok = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
+        mg_batch_solve(self.handle, f, g, u, tol, info, ok)
+        return list(info)
+
+    def solve_status(self, f, g, u, tol: float = 1e-10):
+        """(return code, per-member info) without raising on member failures."""
+        info = (mg_batch_info * self.count)()
+        code = load().mg_batch_solve(self.handle, _addr(f), _addr(g), _addr(u, True), tol,
+                                     ctypes.addressof(info))
+        return code, list(info)
+
+    def tune(self, f, g, tol: float = 1e-10, reps: int = 3):
+        return mg_batch_tune(self.handle, f, g, tol, reps)
+
+    def set_tune(self, threads: int, first_group: int):
+        mg_batch_set_tune(self.handle, threads, first_group)
+
+    def timing(self):
+        return mg_batch_timing(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mg_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

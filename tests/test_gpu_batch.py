@@ -1,0 +1,234 @@
+"""Batched solves (mg_batch_*) on the GPU.
+
+Every member of a batch is an independent problem (its own level set, grid
+size and data), so each member is held to the single-problem parity bars of
+test_gpu_parity.py's mixed precision tests:
+  * driven to 1e-12, within 1e-9 max|u| + 64 eps S_p of the oracle's direct
+    solution (refined to fp64 exactness);
+  * stopped at 1e-10, the oracle's own residual of the result is
+    <= 1e-10 ||F||_inf, and the error is within 3x that of the single-problem
+    fp64 V-cycle stopped at the same residual.
+The batch's own behaviour: a member with NaN data (status
+MG_ERR_INVALID_ARG, u = 0) and a member with zero data (u = 0, no cycles)
+leave the others bit for bit as in a clean batch; graph replays, host and
+device arrays and the zero-copy buffers give identical results; results do
+not depend on the block size; the autotuner returns a converging choice.
+The full-size case is the seeded 256-member batch (ellipses and flowers,
+N in {64, 128, 256, 512}) in the launch configuration bench.py times.
+"""
+import numpy as np
+import pytest
+
+from oracle import ghostfem as gf
+from paper_2505_05105_gb300 import workloads as wl
+from parity_tol import assert_solution
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2505_05105_gb300 import ghostmg
+    ghostmg.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def small_members():
+    """Members with every tail depth: N = 16..64 run wholly in shared memory,
+    128 and 256 have one and two levels in global memory."""
+    ps = [wl.batch_geometry(i, seed=5, sizes=(16, 32, 64, 128)) for i in range(8)]
+    ps += [wl.batch_geometry(0, seed=6, sizes=(256,)), wl.flower(128, k=7, phase=0.3)]
+    return ps
+
+
+@pytest.fixture(scope="module")
+def members():
+    ps = small_members()
+    sys = [gf.assemble_problem(p) for p in ps]
+    Fs = [s.rhs(p.f, p.g) for p, s in zip(ps, sys)]
+    ud = [gf.direct_solve(s, F) for s, F in zip(sys, Fs)]
+    return ps, sys, Fs, ud
+
+
+def batch(ps, **kw):
+    from paper_2505_05105_gb300 import ghostmg as G
+    return G.BatchSolver(ps, **kw)
+
+
+def test_members_match_oracle(members):
+    from paper_2505_05105_gb300 import ghostmg as G
+    ps, sys, Fs, ud = members
+    with batch(ps) as B:
+        f, g = dev(B.pack([p.f for p in ps])), dev(B.pack([p.g for p in ps]))
+        u = torch.zeros(B.total, dtype=torch.float64, device="cuda")
+        info = B.solve(f, g, u, tol=1e-12)
+        tight = B.unpack(host(u))
+        info10 = B.solve(f, g, u, tol=1e-10)
+        at10 = B.unpack(host(u))
+    for k, (p, s, F, x) in enumerate(zip(ps, sys, Fs, ud)):
+        assert info[k].status == G.MG_OK and info[k].rel_res <= 1e-12, (k, info[k].rel_res)
+        assert info[k].n_dof == int(s.dof.sum())
+        assert_solution(tight[k], x, s, F, 1e-9, what=f"member {k} N={p.N}")
+        assert info10[k].status == G.MG_OK and info10[k].rel_res <= 1e-10
+        r = F - s.A @ at10[k]
+        assert np.abs(r[s.dof]).max() <= 1e-10 * np.abs(F).max(), k
+
+
+def test_members_match_single_problem_solver(members):
+    """The same member solved alone by mg_solve (mixed) and inside the batch,
+    both stopped at 1e-10: the same number of fp64 checks give or take one
+    (the same schedule with a different rounding order), and errors against
+    the direct solution of the same order (the stopping test bounds both; a
+    solve may overshoot the tolerance by a different amount, hence the
+    factor and the floor of 1e-11, a tenth of the tolerance)."""
+    ps, sys, Fs, ud = members
+    with batch(ps) as B:
+        f, g = B.pack([p.f for p in ps]), B.pack([p.g for p in ps])
+        u = np.zeros(B.total)
+        info = B.solve(f, g, u, tol=1e-10)
+        ub = B.unpack(u)
+    from paper_2505_05105_gb300 import ghostmg as G
+    for k, p in enumerate(ps):
+        with G.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h, precision="mixed") as S:
+            us = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
+            si = S.solve(dev(p.f), dev(p.g), us, tol=1e-10)
+        scale = np.abs(ud[k]).max()
+        e_s = np.abs(host(us) - ud[k]).max() / scale
+        e_b = np.abs(ub[k] - ud[k]).max() / scale
+        assert e_b <= 10 * e_s + 1e-11, (k, e_b, e_s)
+        assert abs(si.checks - info[k].checks) <= 1, (k, si.checks, info[k].checks)
+
+
+def test_invalid_and_zero_members_leave_the_rest_unchanged(members):
+    from paper_2505_05105_gb300 import ghostmg as G
+    ps = members[0][:4]
+    with batch(ps) as B:
+        f = B.pack([p.f for p in ps])
+        g = B.pack([p.g for p in ps])
+        u_clean = np.zeros(B.total)
+        B.solve(f, g, u_clean, tol=1e-11)
+        off = B.offsets()
+        f2, g2 = f.copy(), g.copy()
+        f2[off[1]:off[2]] = 0.0
+        g2[off[1]:off[2]] = 0.0                   # member 1: zero data
+        g2[off[2] + 7] = np.nan                   # member 2: NaN in g
+        f2[off[3] + 3] = np.inf                   # member 3: Inf in f
+        u = np.full(B.total, 5.0)
+        code, info = B.solve_status(f2, g2, u, tol=1e-11)
+    assert code == G.MG_ERR_INVALID_ARG
+    assert [i.status for i in info] == [G.MG_OK, G.MG_OK, G.MG_ERR_INVALID_ARG,
+                                        G.MG_ERR_INVALID_ARG]
+    assert info[1].cycles == 0 and info[1].rel_res == 0.0
+    assert np.all(u[off[1]:off[4]] == 0.0)
+    np.testing.assert_array_equal(u[off[0]:off[1]], u_clean[off[0]:off[1]])
+
+
+def test_replays_arrays_and_block_sizes_are_deterministic(members):
+    ps = members[0]
+    with batch(ps) as B:
+        fh, gh = B.pack([p.f for p in ps]), B.pack([p.g for p in ps])
+        a = np.zeros(B.total)
+        B.solve(fh, gh, a, tol=1e-11)
+        b = np.zeros(B.total)
+        B.solve(fh, gh, b, tol=1e-11)                 # graph replay
+        np.testing.assert_array_equal(a, b)
+        ud = torch.zeros(B.total, dtype=torch.float64, device="cuda")
+        B.solve(dev(fh), dev(gh), ud, tol=1e-11)      # device arrays
+        np.testing.assert_array_equal(a, host(ud))
+        f0, g0, u0 = B.buffers()                      # zero-copy
+        f0.copy_(dev(fh))
+        g0.copy_(dev(gh))
+        B.solve(f0, g0, u0, tol=1e-11)
+        np.testing.assert_array_equal(a, host(u0))
+        # Gauss-Seidel colour phases are free of races: the block size does
+        # not change a single bit
+        for threads in (256, 512):
+            B.set_tune(threads, 4)
+            c = np.zeros(B.total)
+            B.solve(fh, gh, c, tol=1e-11)
+            np.testing.assert_array_equal(a, c)
+
+
+def test_autotuner(members):
+    from paper_2505_05105_gb300 import ghostmg as G
+    ps, sys, Fs, ud = members
+    with batch(ps) as B:
+        f, g = dev(B.pack([p.f for p in ps])), dev(B.pack([p.g for p in ps]))
+        threads, first, ms = B.tune(f, g, tol=1e-10, reps=2)
+        assert threads in (256, 512, 1024) and first in (2, 3, 4, 6) and ms > 0.0
+        u = torch.zeros(B.total, dtype=torch.float64, device="cuda")
+        info = B.solve(f, g, u, tol=1e-10)
+        _, solve_ms = B.timing()
+        assert solve_ms > 0.0
+        out = B.unpack(host(u))
+    for k, (s, F) in enumerate(zip(sys, Fs)):
+        assert info[k].status == G.MG_OK
+        r = F - s.A @ out[k]
+        assert np.abs(r[s.dof]).max() <= 1e-10 * np.abs(F).max()
+
+
+def test_fixed_schedule():
+    from paper_2505_05105_gb300 import ghostmg as G
+    ps = small_members()[:3]
+    with batch(ps, inner=3) as B:
+        f, g = B.pack([p.f for p in ps]), B.pack([p.g for p in ps])
+        info = B.solve(f, g, np.zeros(B.total), tol=1e-10)
+    for i in info:
+        assert i.status == G.MG_OK and i.cycles == 3 * i.checks
+
+
+def test_rejects_fp64_and_bad_arguments():
+    from paper_2505_05105_gb300 import ghostmg as G
+    p = wl.circle64(64)
+    with pytest.raises(G.GhostMGError) as e:
+        s = G.mg_default_stab()
+        s.precision = G.MG_FP64
+        G.mg_batch_setup([G.mg_grid(p.N, p.x0, p.y0, p.h, 8)], p.psi.ravel().copy(),
+                         None, s)
+    assert e.value.code == G.MG_ERR_UNIMPLEMENTED
+    with batch([p]) as B:
+        with pytest.raises(G.GhostMGError) as e:
+            B.solve(np.zeros(B.total), np.zeros(B.total), np.zeros(B.total), tol=-1.0)
+        assert e.value.code == G.MG_ERR_INVALID_ARG
+        with pytest.raises(G.GhostMGError):
+            B.set_tune(384, 4)
+
+
+def test_full_batch_256():
+    """The benchmark's batch: 256 seeded members, N in {64, 128, 256, 512},
+    stopped at 1e-10 in the default launch shape; sampled members (the
+    largest of each size) against the oracle's direct solution."""
+    from paper_2505_05105_gb300 import ghostmg as G
+    ps = [wl.batch_geometry(i, seed=0) for i in range(256)]
+    with batch(ps) as B:
+        f, g = dev(B.pack([p.f for p in ps])), dev(B.pack([p.g for p in ps]))
+        u = torch.zeros(B.total, dtype=torch.float64, device="cuda")
+        info = B.solve(f, g, u, tol=1e-10)
+        out = B.unpack(host(u))
+    assert all(i.status == G.MG_OK and i.rel_res <= 1e-10 for i in info)
+    sizes = sorted({p.N for p in ps})
+    assert sizes == [64, 128, 256, 512]
+    for N in sizes:
+        k = max((i for i, p in enumerate(ps) if p.N == N), key=lambda i: info[i].n_dof)
+        s = gf.assemble_problem(ps[k])
+        F = s.rhs(ps[k].f, ps[k].g)
+        assert info[k].n_dof == int(s.dof.sum())
+        r = F - s.A @ out[k]
+        assert np.abs(r[s.dof]).max() <= 1e-10 * np.abs(F).max(), (k, N)
+        if N <= 256:
+            x = gf.direct_solve(s, F)
+            scale = np.abs(x).max()
+            # stopped at 1e-10: the error the stopping test allows, with the
+            # conditioning of a Poisson problem on this grid (~ N^2)
+            assert np.abs(out[k] - x).max() <= 1e-10 * N * N * scale, (k, N)
