@@ -11,6 +11,10 @@ flushed (a 512 MB write) between steps, outside the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The line's "batched" object times the batched workload: 256 seeded
+geometries of uneven size solved together by one graph launch (the
+persistent batch kernel), beside the same members solved one by one.
+
 Under torchrun with N > 1 every rank solves its own replica (no collective
 on the data path); value = the DOFs all ranks solved / the slowest rank's
 time.  ``--impl reference`` times the CPU oracle on a bounded sample of the
@@ -65,6 +69,11 @@ def parse():
                     help="setup and one untimed mixed solve (for single-kernel profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched workload (256 seeded geometries)")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="setup and two solves of the batched workload, untimed (for ncu)")
     return ap.parse_args()
 
 
@@ -295,8 +304,11 @@ def run_ours(args):
         # roofline come from a second pass of the same K solves, not from the
         # headline one
         _, _, _, prof, _ = timed(solvers["mixed"], args.steps, 0, prof=True)
+        total_64, ms_64, cyc_64, _, info_64 = timed(solvers["fp64"], args.steps, args.warmup)
+        batched = None
+        if not args.no_batched and world == 1:
+            batched = run_batched(args, dev, flush)
     clocks = clk.summary()
-    total_64, ms_64, cyc_64, _, info_64 = timed(solvers["fp64"], args.steps, args.warmup)
 
     value = world * ndof * args.steps / (total_mx / 1e3)
     value64 = world * ndof * args.steps / (total_64 / 1e3)
@@ -378,6 +390,7 @@ def run_ours(args):
             "mixed_over_fp64": value / value64,
             "roofline": roofline,
             "kernel_breakdown_mixed": breakdown,
+            "batched": batched,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -388,6 +401,109 @@ def run_ours(args):
         S.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def batch_members(count):
+    from paper_2505_05105_gb300 import workloads as wl
+    return [wl.batch_geometry(i, seed=0) for i in range(count)]
+
+
+def run_batched(args, dev, flush):
+    """The batched workload: `count` seeded geometries (ellipses and flowers,
+    N in {64, 128, 256, 512}, random Fourier f, g = 0) solved together to
+    1e-10 by one graph launch per step (mg_batch_solve on the batch's own
+    device buffers), the launch shape picked by the autotuner; beside it the
+    same members solved one after another by mg_solve, mixed and plain fp64,
+    and the batch end to end from pinned host buffers."""
+    import numpy as np
+    import torch
+    from paper_2505_05105_gb300 import ghostmg
+    ps = batch_members(args.batch_count)
+    B = ghostmg.BatchSolver(ps)
+    fh = torch.from_numpy(B.pack([p.f for p in ps])).pin_memory()
+    gh = torch.from_numpy(B.pack([p.g for p in ps])).pin_memory()
+    f0, g0, u0 = B.buffers()
+    f0.copy_(fh.to(dev))
+    g0.copy_(gh.to(dev))
+    torch.cuda.synchronize(dev)
+    shape, tune_ms = B.tune(f0, g0, tol=TOL, reps=2)
+    info = B.solve(f0, g0, u0, tol=TOL)
+    ndof = sum(i.n_dof for i in info)
+    for _ in range(args.warmup):
+        B.solve(f0, g0, u0, tol=TOL)
+    ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        info = B.solve(f0, g0, u0, tol=TOL)
+        ms.append(B.timing()[1])
+    assert all(i.status == ghostmg.MG_OK for i in info)
+    value = ndof * args.steps / (sum(ms) / 1e3)
+    cyc = [i.cycles for i in info]
+    # end to end: pinned host f, g in, u out, through mg_batch_solve
+    uh = torch.zeros(B.total, dtype=torch.float64).pin_memory()
+    B.solve(fh.data_ptr(), gh.data_ptr(), uh.data_ptr(), tol=TOL)
+    tot = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        B.solve(fh.data_ptr(), gh.data_ptr(), uh.data_ptr(), tol=TOL)
+        tot += time.perf_counter() - t0
+    e2e = {"value": ndof * args.steps / tot, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * B.total * 8, "d2h_bytes_per_step": B.total * 8}
+    setup_ms, _ = B.timing()
+    B.close()
+    # the same members one by one through mg_solve (one warm-up solve each)
+    seq = {}
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(dev)
+    for prec in ("mixed", "fp64"):
+        tot_ms = 0.0
+        for p in ps:
+            S = ghostmg.Solver(t(p.psi), p.N, p.x0, p.y0, p.h, precision=prec)
+            fd, gd = t(p.f), t(p.g)
+            uu = torch.zeros_like(fd)
+            S.solve(fd, gd, uu, tol=TOL)
+            uu.zero_()
+            tot_ms += S.solve(fd, gd, uu, tol=TOL).solve_ms
+            S.close()
+        seq[prec] = {"value": ndof / (tot_ms / 1e3), "unit": UNIT, "ms": tot_ms}
+    sizes = sorted({p.N for p in ps})
+    return {
+        "workload": f"batch of {len(ps)} seeded geometries (ellipses, flowers k=3..7), "
+                    f"N in {sizes}, random Fourier f, g=0",
+        "value": value, "unit": UNIT, "ms_per_step": sum(ms) / args.steps,
+        "n_dof": ndof, "members": len(ps), "steps": args.steps,
+        "cycles_per_member": {"min": min(cyc), "max": max(cyc),
+                              "mean": float(np.mean(cyc))},
+        "launch_shape": dict(zip(("threads", "first_group", "cluster", "coop_min_dof"), shape)),
+        "tuned_ms": tune_ms, "setup_ms": setup_ms,
+        "timing": "CUDA events around the graph launch on the batch's stream; L2 flushed "
+                  "(512 MB write) between steps",
+        "graph_kernels_per_step": 4,
+        "sequential_mg_solve_mixed": seq["mixed"],
+        "sequential_mg_solve_fp64": seq["fp64"],
+        "batched_over_sequential_fp64": value / seq["fp64"]["value"],
+        "e2e": e2e,
+    }
+
+
+def profile_batch(args):
+    """Setup and two solves of the batched workload (default launch shape),
+    untimed: the program batched-kernel profiler captures run."""
+    import torch
+    from paper_2505_05105_gb300 import ghostmg
+    ghostmg.load()
+    ps = batch_members(args.batch_count)
+    B = ghostmg.BatchSolver(ps)
+    f = torch.from_numpy(B.pack([p.f for p in ps])).cuda()
+    g = torch.from_numpy(B.pack([p.g for p in ps])).cuda()
+    u = torch.zeros(B.total, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        info = B.solve(f, g, u, tol=TOL)
+    print(json.dumps({"profile_batch": len(ps), "shape": B.shape(),
+                      "max_cycles": max(i.cycles for i in info)}))
+    B.close()
 
 
 def profile_solve(args):
@@ -411,6 +527,8 @@ def main():
     args = parse()
     if args.profile_solve:
         profile_solve(args)
+    elif args.profile_batch:
+        profile_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

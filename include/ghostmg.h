@@ -307,19 +307,33 @@ int mg_batch_buffers(mg_batch b, long long* total_nodes, double** f, double** g,
 int mg_batch_solve(mg_batch b, const double* f, const double* g, double* u, double tol,
                    mg_batch_info* info);
 
-/* Autotuner: times `reps` graph replays (after one warm-up) of the solve of
- * (f, g) to tol for every candidate launch shape -- threads per block in
- * {256, 512, 1024} and, with the adaptive schedule, V-cycles before the
- * first fp64 check in {2, 3, 4, 6} -- and keeps the fastest whose members
- * all converge.  Outputs (any may be NULL): the choice and its mean time per
- * solve in ms.  Errors as mg_batch_solve (MG_ERR_NOT_CONVERGED if no
- * candidate converged everywhere). */
-int mg_batch_tune(mg_batch b, const double* f, const double* g, double tol, int reps,
-                  int* threads, int* first_group, float* ms);
+/* Launch shape of the persistent kernel. */
+typedef struct {
+  int threads;        /* threads per block: 256, 512 or 1024 */
+  int first_group;    /* V-cycles before the first fp64 check (adaptive
+                         schedule), 1..8 */
+  int cluster;        /* blocks per thread-block cluster: 1, 2, 4 or 8 */
+  int coop_min_dof;   /* members with at least this many fine-level DOFs and
+                         levels above 64 x 64 cells are solved by a whole
+                         cluster, each block on its own SM (cluster > 1) */
+} mg_batch_shape;
 
-/* Sets the launch shape directly (threads 256, 512 or 1024; first_group
- * 1..8).  Default 1024 threads, first group 4. */
-int mg_batch_set_tune(mg_batch b, int threads, int first_group);
+/* Sets the launch shape (default 512 threads, first group 4, no clusters).
+ * MG_ERR_INVALID_ARG for values outside the lists above or a shape that
+ * cannot be resident on the device (the previous shape is kept). */
+int mg_batch_set_shape(mg_batch b, const mg_batch_shape* shape);
+int mg_batch_get_shape(mg_batch b, mg_batch_shape* shape);
+
+/* Autotuner: times `reps` graph replays (after one warm-up) of the solve of
+ * (f, g) to tol for candidate shapes, in three stages -- threads per block
+ * x cluster size; then the sharing threshold coop_min_dof in
+ * {0, 8192, 32768, 131072} (with clusters); then, with the adaptive
+ * schedule, first_group in {2, 3, 4, 6} -- and keeps the fastest shape whose
+ * members all converge.  best and ms (mean time per solve) may be NULL.
+ * Errors as mg_batch_solve (MG_ERR_NOT_CONVERGED if no candidate converged
+ * everywhere; the previous shape is kept). */
+int mg_batch_tune(mg_batch b, const double* f, const double* g, double tol, int reps,
+                  mg_batch_shape* best, float* ms);
 
 /* Wall time of mg_batch_setup and device time of the last solve's graph. */
 int mg_batch_timing(mg_batch b, float* setup_ms, float* solve_ms);

@@ -1201,7 +1201,7 @@ struct mg_batch_ctx {
   int* d_order = nullptr;
   size_t* d_node_off = nullptr;
   int* d_tile_off = nullptr;
-  unsigned* d_words = nullptr;      // [0] queue counter, [1] error word, [2..] bad flags
+  unsigned* d_words = nullptr;      // [0], [2] work counters, [1] error word, [3..] bad flags
   double* d_params = nullptr;       // tol, max_cycles, fixed group (0: adaptive)
   double* h_params = nullptr;       // pinned
   BatchResult* d_res = nullptr;
@@ -1210,7 +1210,9 @@ struct mg_batch_ctx {
   double *f = nullptr, *g = nullptr, *u = nullptr;
   size_t smem = 0;
   int grid = 0;
-  BatchTune tune{1024, 4};
+  int n_coop = 0;
+  BatchTune tune{512, 4, 1, 0};
+  std::vector<int> n_dof, n_top;    // per member
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev_in = nullptr, ev0 = nullptr, ev1 = nullptr;
@@ -1242,6 +1244,13 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out) {
   BatchProblem& q = *out;
   memset(&q, 0, sizeof(q));
   q.n_top = t;
+  // first nodes of the active tiles of every level the batch kernel walks
+  unsigned* xy[MG_BATCH_MAX_TOP + 1];
+  for (int l = 0; l <= t; ++l) {
+    Level& v = c->lev[l];
+    TRY(dalloc(c, &xy[l], (size_t)v.n_active));
+    launch_tile_xy(v.L, v.active, v.n_active, xy[l], c->st);
+  }
   for (int l = 0; l < t; ++l) {
     Level& v = c->lev[l];
     BatchLevel& w = q.lev[l];
@@ -1256,7 +1265,7 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out) {
     w.code = v.code;
     w.tile_base = v.tile_base;
     w.rows = v.rows32;
-    w.active = v.active;
+    w.xy = xy[l];
     w.n_active = v.n_active;
     w.blist = blist;
     w.u = v.u32[0];
@@ -1277,7 +1286,7 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out) {
   a.nu1 = c->stab.nu1;
   a.nu2 = c->stab.nu2;
   a.err = b->d_words + 1;
-  q.tail_active = top.active;
+  q.tail_xy = xy[t];
   q.tail_n_active = top.n_active;
   q.tail_F = top.F32;
   Level& v = c->lev[0];
@@ -1286,6 +1295,7 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out) {
   q.tile_base0 = v.tile_base;
   q.rows64 = v.rows64;
   q.active0 = v.active;
+  q.xy0 = xy[0];
   q.n_active0 = v.n_active;
   q.F64 = v.F64;
   q.u64 = v.u64[0];
@@ -1301,18 +1311,38 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out) {
   return MG_OK;
 }
 
-// (re)captures the solve graph for the current launch shape
+// (re)captures the solve graph for the current launch shape: the work order
+// (members a cluster shares first, each part largest first) and the grid
 int batch_capture(mg_batch_ctx* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
+  const int n = b->count;
+  const BatchTune& tu = b->tune;
+  auto coop = [&](int p) {
+    return tu.cluster > 1 && b->n_top[p] > 0 && b->n_dof[p] >= tu.coop_min_dof;
+  };
+  std::vector<int> order(n);
+  for (int p = 0; p < n; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (coop(x) != coop(y)) return coop(x);
+    return b->n_dof[x] > b->n_dof[y];
+  });
+  b->n_coop = 0;
+  while (b->n_coop < n && coop(order[b->n_coop])) ++b->n_coop;
+  MG_CUDA_TRY(cudaMemcpyAsync(b->d_order, order.data(), (size_t)n * sizeof(int),
+                              cudaMemcpyHostToDevice, b->st));
+  MG_CUDA_TRY(cudaStreamSynchronize(b->st));
+  const int nc = batch_max_clusters(tu, b->smem);
+  if (nc <= 0) return MG_ERR_INVALID_ARG;          // the shape does not fit on the device
+  b->grid = nc * tu.cluster;
   MG_CUDA_TRY(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-  cudaMemsetAsync(b->d_words, 0, (2 + (size_t)b->count) * sizeof(unsigned), b->st);
-  launch_batch_check(b->d_probs, b->d_node_off, b->count, b->total_nodes, b->d_words + 2, b->st);
-  launch_batch_rhs(b->d_probs, b->d_tile_off, b->count, b->total_tiles, b->st);
-  launch_batch(b->d_probs, b->d_order, b->count, reinterpret_cast<int*>(b->d_words),
-               b->d_words + 2, b->d_params, b->tune, b->grid, b->smem, b->d_res, b->st);
+  cudaMemsetAsync(b->d_words, 0, (3 + (size_t)n) * sizeof(unsigned), b->st);
+  launch_batch_check(b->d_probs, b->d_node_off, n, b->total_nodes, b->d_words + 3, b->st);
+  launch_batch_rhs(b->d_probs, b->d_tile_off, n, b->total_tiles, b->st);
+  launch_batch(b->d_probs, b->d_order, n, b->n_coop, b->d_words, b->d_words + 3, b->d_params,
+               tu, b->grid, b->smem, b->d_res, b->st);
   launch_batch_unpack(b->d_probs, b->d_node_off, b->count, b->total_nodes, b->st);
   cudaMemcpyAsync(b->h_res, b->d_res, (size_t)b->count * sizeof(BatchResult),
                   cudaMemcpyDeviceToHost, b->st);
@@ -1366,6 +1396,28 @@ int batch_stage(mg_batch_ctx* b, const double* f, const double* g) {
   return MG_OK;
 }
 
+// mean device time per solve of `reps` replays after one warm-up; false if
+// the shape does not fit or a member did not converge
+int time_shape(mg_batch_ctx* b, const BatchTune& t, double tol, int reps, float* ms, bool* ok) {
+  *ok = false;
+  b->tune = t;
+  const int rc = batch_capture(b);
+  if (rc == MG_ERR_INVALID_ARG) return MG_OK;
+  TRY(rc);
+  int worst = MG_OK;
+  TRY(batch_run(b, tol, &worst));
+  if (worst != MG_OK) return MG_OK;
+  float total = 0.f;
+  for (int r = 0; r < reps; ++r) {
+    TRY(batch_run(b, tol, &worst));
+    if (worst != MG_OK) return MG_OK;
+    total += b->solve_ms;
+  }
+  *ms = total / reps;
+  *ok = true;
+  return MG_OK;
+}
+
 int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levelsets,
                      const mg_bc* bc) {
   const int n = b->count;
@@ -1385,7 +1437,7 @@ int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levels
   TRY(balloc(b, &b->f, b->total_nodes));
   TRY(balloc(b, &b->g, b->total_nodes));
   TRY(balloc(b, &b->u, b->total_nodes));
-  TRY(balloc(b, &b->d_words, 2 + (size_t)n));
+  TRY(balloc(b, &b->d_words, 3 + (size_t)n));
   TRY(balloc(b, &b->d_params, 4));
   TRY(balloc(b, &b->d_res, (size_t)n));
   TRY(balloc(b, &b->d_order, (size_t)n));
@@ -1411,15 +1463,13 @@ int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levels
     smem = std::max(smem, (size_t)b->mem[p]->tail_lay[0].total);
   }
   b->total_tiles = tile_off[n];
-  // largest first (fine-level DOFs), ties by index
-  std::vector<int> order(n);
-  for (int p = 0; p < n; ++p) order[p] = p;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return b->mem[x]->lev[0].n_dof > b->mem[y]->lev[0].n_dof;
-  });
+  b->n_dof.resize(n);
+  b->n_top.resize(n);
+  for (int p = 0; p < n; ++p) {
+    b->n_dof[p] = b->mem[p]->lev[0].n_dof;
+    b->n_top[p] = probs[p].n_top;
+  }
   MG_CUDA_TRY(cudaMemcpyAsync(b->d_probs, probs.data(), (size_t)n * sizeof(BatchProblem),
-                              cudaMemcpyHostToDevice, b->st));
-  MG_CUDA_TRY(cudaMemcpyAsync(b->d_order, order.data(), (size_t)n * sizeof(int),
                               cudaMemcpyHostToDevice, b->st));
   MG_CUDA_TRY(cudaMemcpyAsync(b->d_node_off, b->node_off.data(), (size_t)(n + 1) * sizeof(size_t),
                               cudaMemcpyHostToDevice, b->st));
@@ -1428,10 +1478,6 @@ int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levels
   MG_CUDA_TRY(cudaStreamSynchronize(b->st));
   b->smem = smem + kSmemSlack;
   MG_CUDA_TRY(configure_batch(b->smem));
-  int dev = 0, nsm = 0;
-  MG_CUDA_TRY(cudaGetDevice(&dev));
-  MG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  b->grid = std::min(n, nsm);
   return batch_capture(b);
 }
 
@@ -1498,51 +1544,87 @@ int mg_batch_solve(mg_batch b, const double* f, const double* g, double* u, doub
   return worst;
 }
 
-int mg_batch_set_tune(mg_batch b, int threads, int first_group) {
-  if (!b || (threads != 256 && threads != 512 && threads != 1024) || first_group < 1 ||
-      first_group > 8)
+int mg_batch_set_shape(mg_batch b, const mg_batch_shape* shape) {
+  if (!b || !shape) return MG_ERR_INVALID_ARG;
+  const mg_batch_shape& s = *shape;
+  if ((s.threads != 256 && s.threads != 512 && s.threads != 1024) || s.first_group < 1 ||
+      s.first_group > 8 || (s.cluster != 1 && s.cluster != 2 && s.cluster != 4 && s.cluster != 8) ||
+      s.coop_min_dof < 0)
     return MG_ERR_INVALID_ARG;
-  b->tune = BatchTune{threads, first_group};
-  return batch_capture(b);
+  const BatchTune old = b->tune;
+  b->tune = BatchTune{s.threads, s.first_group, s.cluster, s.coop_min_dof};
+  const int rc = batch_capture(b);
+  if (rc == MG_ERR_INVALID_ARG) {
+    b->tune = old;
+    TRY(batch_capture(b));
+    return MG_ERR_INVALID_ARG;
+  }
+  return rc;
+}
+
+int mg_batch_get_shape(mg_batch b, mg_batch_shape* shape) {
+  if (!b || !shape) return MG_ERR_INVALID_ARG;
+  shape->threads = b->tune.threads;
+  shape->first_group = b->tune.first_group;
+  shape->cluster = b->tune.cluster;
+  shape->coop_min_dof = b->tune.coop_min_dof;
+  return MG_OK;
 }
 
 int mg_batch_tune(mg_batch b, const double* f, const double* g, double tol, int reps,
-                  int* threads, int* first_group, float* ms) {
+                  mg_batch_shape* best_out, float* ms_out) {
   if (!b || !f || !g || !(tol >= 0.0) || reps < 1) return MG_ERR_INVALID_ARG;
   TRY(batch_stage(b, f, g));
-  const int th[3] = {256, 512, 1024};
-  const int fg_adaptive[4] = {2, 3, 4, 6};
-  const int nfg = b->stab.inner == 0 ? 4 : 1;
   const BatchTune start = b->tune;
-  BatchTune best{0, 0};
+  BatchTune best{0, 0, 0, 0};
   float best_ms = 0.f;
-  for (int ti = 0; ti < 3; ++ti)
-    for (int fi = 0; fi < nfg; ++fi) {
-      b->tune = BatchTune{th[ti], b->stab.inner == 0 ? fg_adaptive[fi] : start.first_group};
-      TRY(batch_capture(b));
-      int worst = MG_OK;
-      TRY(batch_run(b, tol, &worst));            // warm-up
-      if (worst != MG_OK) continue;
-      float total = 0.f;
-      bool ok = true;
-      for (int r = 0; r < reps && ok; ++r) {
-        TRY(batch_run(b, tol, &worst));
-        ok = worst == MG_OK;
-        total += b->solve_ms;
-      }
-      if (!ok) continue;
-      const float mean = total / reps;
-      if (best.threads == 0 || mean < best_ms) {
-        best = b->tune;
-        best_ms = mean;
-      }
+  auto consider = [&](const BatchTune& t) -> int {
+    float ms = 0.f;
+    bool ok = false;
+    TRY(time_shape(b, t, tol, reps, &ms, &ok));
+    if (ok && (best.threads == 0 || ms < best_ms)) {
+      best = t;
+      best_ms = ms;
     }
-  b->tune = best.threads ? best : start;
+    return MG_OK;
+  };
+  // 1. block size and cluster size, with the first group and the sharing
+  //    threshold as they are
+  const int th[3] = {256, 512, 1024};
+  const int cl[4] = {1, 2, 4, 8};
+  for (int ti = 0; ti < 3; ++ti)
+    for (int ci = 0; ci < 4; ++ci)
+      TRY(consider(BatchTune{th[ti], start.first_group, cl[ci], start.coop_min_dof}));
+  if (!best.threads) {
+    b->tune = start;
+    TRY(batch_capture(b));
+    return MG_ERR_NOT_CONVERGED;
+  }
+  // 2. which members a cluster shares (by fine-level DOFs)
+  if (best.cluster > 1) {
+    const int thr[4] = {0, 8192, 32768, 131072};
+    const BatchTune base = best;
+    for (int k = 0; k < 4; ++k)
+      if (thr[k] != base.coop_min_dof)
+        TRY(consider(BatchTune{base.threads, base.first_group, base.cluster, thr[k]}));
+  }
+  // 3. V-cycles before the first fp64 check (adaptive schedule only)
+  if (b->stab.inner == 0) {
+    const int fg[4] = {2, 3, 4, 6};
+    const BatchTune base = best;
+    for (int k = 0; k < 4; ++k)
+      if (fg[k] != base.first_group)
+        TRY(consider(BatchTune{base.threads, fg[k], base.cluster, base.coop_min_dof}));
+  }
+  b->tune = best;
   TRY(batch_capture(b));
-  if (!best.threads) return MG_ERR_NOT_CONVERGED;
-  if (threads) *threads = best.threads;
-  if (first_group) *first_group = best.first_group;
-  if (ms) *ms = best_ms;
+  if (best_out) {
+    best_out->threads = best.threads;
+    best_out->first_group = best.first_group;
+    best_out->cluster = best.cluster;
+    best_out->coop_min_dof = best.coop_min_dof;
+  }
+  if (ms_out) *ms_out = best_ms;
   return MG_OK;
 }
 

@@ -21,6 +21,53 @@
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// Threads of a member: one block, or the blocks of a thread-block cluster
+// that share a large member (each block its own SM).  Cluster members stay in
+// step through the hardware cluster barrier (release / acquire at cluster
+// scope, which orders their global-memory accesses); shared values go
+// through distributed shared memory.
+
+struct Team {
+  int t0, ts;      // this thread's first node index and the stride over the team
+  int rank, nr;    // block rank in the team and team size (1: a block alone)
+};
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void team_sync(const Team& tm) {
+  if (tm.nr > 1) cluster_sync_all();
+  else __syncthreads();
+}
+
+// stores v into the shared word at p in block `rank` of the cluster
+__device__ __forceinline__ void dsmem_store_u32(void* p, unsigned rank, unsigned v) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void dsmem_store_f64(void* p, unsigned rank, double v) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+}
+
 __device__ __forceinline__ double block_max(double v) {
   __shared__ double s[32];
   __syncthreads();
@@ -36,181 +83,350 @@ __device__ __forceinline__ double block_max(double v) {
   return s[0];
 }
 
-// node q of the active tiles: q >> 11 selects the tile, the rest the node
-__device__ __forceinline__ bool tile_node(const Layout& L, const int* active, int q, int& i,
-                                          int& j) {
-  const int t = active[q >> 11], w = q & 2047;
-  i = (t % L.ntx) * MG_TX + (w & (MG_TX - 1));
-  j = (t / L.ntx) * MG_TY + (w >> 6);
-  return i <= L.n && j <= L.n;
+constexpr int kMaxCluster = 16;
+
+// max over the team (every block gets the result); `parity` alternates the
+// exchange slots between consecutive reductions
+__device__ double team_max(double v, const Team& tm, int& parity) {
+  v = block_max(v);
+  if (tm.nr == 1) return v;
+  __shared__ double slot[2][kMaxCluster];
+  const int q = parity;
+  parity ^= 1;
+  if (threadIdx.x < (unsigned)tm.nr) dsmem_store_f64(&slot[q][tm.rank], threadIdx.x, v);
+  cluster_sync_all();
+  double m = 0.0;
+  for (int r = 0; r < tm.nr; ++r) m = fmax(m, slot[q][r]);
+  return m;
 }
 
-// node q of colour (ci, cj) of the active tiles (512 per tile)
-__device__ __forceinline__ bool colour_node(const Layout& L, const int* active, int q, int ci,
-                                            int cj, int& i, int& j) {
-  const int t = active[q >> 9], w = q & 511;
-  i = (t % L.ntx) * MG_TX + 2 * (w & 31) + ci;
-  j = (t / L.ntx) * MG_TY + 2 * (w >> 5) + cj;
-  return i <= L.n && j <= L.n;
+// ---------------------------------------------------------------------------
+// Level routines.  Node q of the active tiles: tile xy[q >> 11] (i0 | j0 << 16),
+// node (q & 63, (q >> 6) & 31) in it; node q of colour (ci, cj): tile
+// xy[q >> 9], lattice node (q & 31, (q >> 5) & 15).  kU nodes per thread are
+// in flight at once (all their loads issued before the arithmetic): 4 with up
+// to 512 threads per block, 2 with 1024 (64 registers per thread).
+
+__device__ __forceinline__ int tile_pos(const unsigned* __restrict__ xy, int q, int total, int n,
+                                        int P, bool& ok, int& i, int& j) {
+  const bool in = q < total;
+  const unsigned t = in ? __ldg(xy + (q >> 11)) : 0u;
+  i = (int)(t & 0xffffu) + (q & 63);
+  j = (int)(t >> 16) + ((q >> 6) & 31);
+  ok = in && i <= n && j <= n;
+  return (j + MG_G) * P + (i + MG_G);
+}
+
+__device__ __forceinline__ int tile_pos(const unsigned* __restrict__ xy, int q, int total, int n,
+                                        int P, bool& ok) {
+  int i, j;
+  return tile_pos(xy, q, total, n, P, ok, i, j);
+}
+
+__device__ __forceinline__ int colour_pos(const unsigned* __restrict__ xy, int q, int total,
+                                          int ci, int cj, int n, int P, bool& ok) {
+  const bool in = q < total;
+  const unsigned t = in ? __ldg(xy + (q >> 9)) : 0u;
+  const int i = (int)(t & 0xffffu) + 2 * (q & 31) + ci;
+  const int j = (int)(t >> 16) + 2 * ((q >> 5) & 15) + cj;
+  ok = in && i <= n && j <= n;
+  return (j + MG_G) * P + (i + MG_G);
 }
 
 template <class T>
-__device__ __forceinline__ T row_apply(const T* R, const T* U, int P) {
+__device__ __forceinline__ T row_apply(const T* __restrict__ R, const T* U, int P) {
   return R[0] * U[-P - 1] + R[1] * U[-P] + R[2] * U[-P + 1] + R[3] * U[-1] + R[4] * U[0] +
          R[5] * U[1] + R[6] * U[P - 1] + R[7] * U[P] + R[8] * U[P + 1];
 }
 
-__device__ __forceinline__ void listed_update(const BatchLevel& v, int e) {
-  const int2 en = v.blist[e];
-  const float* R = v.rows + (size_t)en.y * MG_ROW;
-  float* U = v.u + v.L.idx(en.x & 0xffff, en.x >> 16);
-  const float f = v.F[U - v.u];
-  const float acc = row_apply(R, U, v.L.pitch);
-  *U = U[0] + (f - acc) * R[9];
+template <class T>
+__device__ __forceinline__ T sum8(const T* U, int P) {
+  return ((U[-1] + U[1]) + (U[-P] + U[P])) + ((U[-P - 1] + U[-P + 1]) + (U[P - 1] + U[P + 1]));
 }
 
-// one smoothing step of a level in global memory: 4 colour phases (interior
-// nodes by the constant stencil, the colour's boundary nodes from the list),
-// then eta phases per colour over the boundary nodes only
-__device__ void smooth_level(const BatchLevel& v, int eta) {
+// Gauss-Seidel update of boundary node g with its row R and right-hand side f
+__device__ __forceinline__ void row_update(float* u, int g, const float* __restrict__ R, float f,
+                                           int P) {
+  const float* U = u + g;
+  const float acc = row_apply(R, U, P);
+  u[g] = U[0] + (f - acc) * __ldg(R + 9);
+}
+
+// interior nodes of colour (ci, cj): the constant stencil 1/3 [-1 .. 8 .. -1]
+template <int kU>
+__device__ __forceinline__ void colour_interior(const BatchLevel& v, int ci, int cj,
+                                                const Team& tm) {
+  const int P = v.L.pitch, n = v.L.n, total = v.n_active * 512;
+  float* u = v.u;
+  for (int q0 = tm.t0; q0 < total; q0 += kU * tm.ts) {
+    int g[kU];
+    bool ok[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) g[k] = colour_pos(v.xy, q0 + k * tm.ts, total, ci, cj, n, P, ok[k]);
+    float s[kU], f[kU];
+    bool in[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      in[k] = false;
+      s[k] = 0.f;
+      f[k] = 0.f;
+      if (ok[k]) {
+        in[k] = __ldg(v.code + g[k]) == 1;
+        f[k] = v.F[g[k]];
+        s[k] = sum8(u + g[k], P);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kU; ++k)
+      if (in[k]) u[g[k]] = (3.f * f[k] + s[k]) * 0.125f;
+  }
+}
+
+// One smoothing step of a level in global memory (Sec. 4.1, Sec. 5.3): four
+// colour phases (interior nodes by the team, the colour's cut-cell vertices
+// from the level's list by the lead block), then eta colour phases over the
+// cut-cell vertices by the lead block alone.  The lead block's threads keep
+// the position, row and F of one listed node per colour in registers for the
+// whole step; longer colour lists go through the loops marked `more`.
+template <int kU>
+__device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm) {
   const int P = v.L.pitch;
+  const bool lead = tm.rank == 0;
+  int mc = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) mc = max(mc, v.boff[c + 1] - v.boff[c]);
+  const int nt = min((int)blockDim.x, max(32, (mc + 31) & ~31));
+  const bool own = lead && (int)threadIdx.x < nt;
+  const bool more = mc > nt;
+  int pos[4], row[4];
+  float fv[4];
+#pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const int ci = c & 1, cj = c >> 1;
-    for (int q = threadIdx.x; q < v.n_active * 512; q += blockDim.x) {
+    const int e = v.boff[c] + threadIdx.x;
+    pos[c] = -1;
+    row[c] = 0;
+    fv[c] = 0.f;
+    if (own && e < v.boff[c + 1]) {
+      const int2 en = __ldg(v.blist + e);
+      pos[c] = en.x;
+      row[c] = en.y;
+      fv[c] = v.F[en.x];
+    }
+  }
+  auto listed = [&](int c, int stride) {
+    if (pos[c] >= 0) row_update(v.u, pos[c], v.rows + (size_t)row[c] * MG_ROW, fv[c], P);
+    if (more)
+      for (int e = v.boff[c] + nt + threadIdx.x; e < v.boff[c + 1]; e += stride) {
+        const int2 en = __ldg(v.blist + e);
+        row_update(v.u, en.x, v.rows + (size_t)en.y * MG_ROW, v.F[en.x], P);
+      }
+  };
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    colour_interior<kU>(v, c & 1, c >> 1, tm);
+    if (own) listed(c, nt);
+    team_sync(tm);
+  }
+  if (eta > 0 && own) {
+    for (int it = 0; it < eta; ++it)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        listed(c, nt);
+        if (nt == 32) __syncwarp();
+        else asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+      }
+  }
+  if (eta > 0) team_sync(tm);
+}
+
+__device__ void zero_level(const BatchLevel& v, const Team& tm) {
+  const int total = v.n_active * 2048;
+  for (int q = tm.t0; q < total; q += tm.ts) {
+    bool ok;
+    const int g = tile_pos(v.xy, q, total, v.L.n, v.L.pitch, ok);
+    if (ok) v.u[g] = 0.f;
+  }
+}
+
+// F_2h = P^T (F - A u) (Sec. 5.1): the residual of the active tiles into
+// scr, then the 9-point restriction (weights 1, 1/2, 1/4) at every node of
+// the coarse level's active tiles.
+template <int kU>
+__device__ void resid_restrict_level(const BatchLevel& v, const Layout& Lc, const unsigned* cxy,
+                                     int nc_act, float* Fc, const Team& tm) {
+  const int P = v.L.pitch, n = v.L.n, total = v.n_active * 2048;
+  for (int q0 = tm.t0; q0 < total; q0 += kU * tm.ts) {
+    int g[kU], ti[kU];
+    bool ok[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
       int i, j;
-      if (!colour_node(v.L, v.active, q, ci, cj, i, j)) continue;
-      const size_t g = v.L.idx(i, j);
-      if (v.code[g] != 1) continue;
-      const float* U = v.u + g;
-      const float s8 = ((U[-1] + U[1]) + (U[-P] + U[P])) + ((U[-P - 1] + U[-P + 1]) +
-                                                            (U[P - 1] + U[P + 1]));
-      v.u[g] = (3.f * v.F[g] + s8) * 0.125f;
+      g[k] = tile_pos(v.xy, q0 + k * tm.ts, total, n, P, ok[k], i, j);
+      ti[k] = v.L.tile_of(i, j);
     }
-    for (int e = v.boff[c] + threadIdx.x; e < v.boff[c + 1]; e += blockDim.x) listed_update(v, e);
-    __syncthreads();
-  }
-  for (int it = 0; it < eta; ++it)
-    for (int c = 0; c < 4; ++c) {
-      for (int e = v.boff[c] + threadIdx.x; e < v.boff[c + 1]; e += blockDim.x)
-        listed_update(v, e);
-      __syncthreads();
+    float r[kU], f[kU], s[kU], c0[kU];
+    uint16_t cd[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      cd[k] = 0;
+      f[k] = s[k] = c0[k] = 0.f;
+      if (ok[k]) {
+        cd[k] = __ldg(v.code + g[k]);
+        f[k] = v.F[g[k]];
+        c0[k] = v.u[g[k]];
+        s[k] = sum8(v.u + g[k], P);
+      }
     }
-}
-
-__device__ void zero_level(const BatchLevel& v) {
-  for (int q = threadIdx.x; q < v.n_active * 2048; q += blockDim.x) {
-    int i, j;
-    if (tile_node(v.L, v.active, q, i, j)) v.u[v.L.idx(i, j)] = 0.f;
-  }
-  __syncthreads();
-}
-
-// F_2h = P^T (F - A u): the residual of the active tiles into scr, then the
-// 9-point restriction (weights 1, 1/2, 1/4) for every node of the coarse
-// level's active tiles
-__device__ void resid_restrict_level(const BatchLevel& v, const Layout& Lc, const int* cact,
-                                     int nc_act, float* Fc) {
-  const int P = v.L.pitch;
-  for (int q = threadIdx.x; q < v.n_active * 2048; q += blockDim.x) {
-    int i, j;
-    if (!tile_node(v.L, v.active, q, i, j)) continue;
-    const size_t g = v.L.idx(i, j);
-    const uint16_t cd = v.code[g];
-    float r = 0.f;
-    if (cd == 1) {
-      const float* U = v.u + g;
-      const float s8 = ((U[-1] + U[1]) + (U[-P] + U[P])) + ((U[-P - 1] + U[-P + 1]) +
-                                                            (U[P - 1] + U[P + 1]));
-      r = v.F[g] - (8.f * U[0] - s8) * (1.f / 3.f);
-    } else if (cd >= 2) {
-      const float* R = v.rows + (size_t)(v.tile_base[v.L.tile_of(i, j)] + cd - 2) * MG_ROW;
-      r = v.F[g] - row_apply(R, v.u + g, P);
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      r[k] = 0.f;
+      if (cd[k] == 1) {
+        r[k] = f[k] - (8.f * c0[k] - s[k]) * (1.f / 3.f);
+      } else if (cd[k] >= 2) {
+        const float* R = v.rows + (size_t)(__ldg(v.tile_base + ti[k]) + cd[k] - 2) * MG_ROW;
+        r[k] = f[k] - row_apply(R, v.u + g[k], P);
+      }
+      if (ok[k]) v.scr[g[k]] = r[k];
     }
-    v.scr[g] = r;
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < nc_act * 2048; q += blockDim.x) {
-    int I, J;
-    if (!tile_node(Lc, cact, q, I, J)) continue;
-    const float* R = v.scr + v.L.idx(2 * I, 2 * J);
-    const float rc = R[0] + 0.5f * ((R[-1] + R[1]) + (R[-P] + R[P])) +
-                     0.25f * ((R[-P - 1] + R[-P + 1]) + (R[P - 1] + R[P + 1]));
-    Fc[Lc.idx(I, J)] = rc;
+  team_sync(tm);
+  const int Pc = Lc.pitch, nc = Lc.n, totc = nc_act * 2048;
+  for (int q0 = tm.t0; q0 < totc; q0 += kU * tm.ts) {
+    int gc[kU], fo[kU];
+    bool ok[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      int I, J;
+      gc[k] = tile_pos(cxy, q0 + k * tm.ts, totc, nc, Pc, ok[k], I, J);
+      fo[k] = (2 * J + MG_G) * P + (2 * I + MG_G);
+    }
+    float rc[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      rc[k] = 0.f;
+      if (ok[k]) {
+        const float* R = v.scr + fo[k];
+        rc[k] = R[0] + 0.5f * ((R[-1] + R[1]) + (R[-P] + R[P])) +
+                0.25f * ((R[-P - 1] + R[-P + 1]) + (R[P - 1] + R[P + 1]));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kU; ++k)
+      if (ok[k]) Fc[gc[k]] = rc[k];
   }
-  __syncthreads();
+  team_sync(tm);
 }
 
-// u += P e_2h on the DOFs of the active tiles (same association as k_prolong)
-__device__ void prolong_level(const BatchLevel& v, const Layout& Lc, const float* ec) {
-  for (int q = threadIdx.x; q < v.n_active * 2048; q += blockDim.x) {
-    int i, j;
-    if (!tile_node(v.L, v.active, q, i, j)) continue;
-    const size_t g = v.L.idx(i, j);
-    if (!v.code[g]) continue;
-    const float* E = ec + Lc.idx(i >> 1, j >> 1);
-    float e;
-    if (!(i & 1) && !(j & 1)) e = E[0];
-    else if (!(j & 1)) e = 0.5f * (E[0] + E[1]);
-    else if (!(i & 1)) e = 0.5f * (E[0] + E[Lc.pitch]);
-    else e = 0.25f * ((E[0] + E[1]) + (E[Lc.pitch] + E[Lc.pitch + 1]));
-    v.u[g] = v.u[g] + e;
+// u += P e_2h on the DOFs of the active tiles (the arithmetic of k_prolong)
+template <int kU>
+__device__ void prolong_level(const BatchLevel& v, const Layout& Lc, const float* ec,
+                              const Team& tm) {
+  const int P = v.L.pitch, n = v.L.n, total = v.n_active * 2048, Pc = Lc.pitch;
+  for (int q0 = tm.t0; q0 < total; q0 += kU * tm.ts) {
+    int g[kU], ii[kU], jj[kU];
+    bool ok[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) g[k] = tile_pos(v.xy, q0 + k * tm.ts, total, n, P, ok[k], ii[k], jj[k]);
+    float e[kU], u0[kU];
+    bool dof[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      e[k] = u0[k] = 0.f;
+      dof[k] = false;
+      if (ok[k]) {
+        dof[k] = __ldg(v.code + g[k]) != 0;
+        const int i = ii[k], j = jj[k];
+        const float* E = ec + ((j >> 1) + MG_G) * Pc + ((i >> 1) + MG_G);
+        u0[k] = v.u[g[k]];
+        if (!(i & 1) && !(j & 1)) e[k] = E[0];
+        else if (!(j & 1)) e[k] = 0.5f * (E[0] + E[1]);
+        else if (!(i & 1)) e[k] = 0.5f * (E[0] + E[Pc]);
+        else e[k] = 0.25f * ((E[0] + E[1]) + (E[Pc] + E[Pc + 1]));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kU; ++k)
+      if (dof[k]) v.u[g[k]] = u0[k] + e[k];
   }
-  __syncthreads();
+  team_sync(tm);
 }
 
-// one fp32 V-cycle of problem p on the correction equation; load_image: the
-// tail's static image is not yet in shared memory
+// One fp32 V-cycle of problem p on the correction equation.  load_image: the
+// tail's static image is not yet in the lead block's shared memory.
+template <int kU>
 __device__ void vcycle(const BatchProblem& p, bool zero_init, unsigned char* smem,
-                       bool load_image) {
+                       bool load_image, const Team& tm) {
   for (int l = 0; l < p.n_top; ++l) {
     const BatchLevel& v = p.lev[l];
-    if (l > 0 || zero_init) zero_level(v);
-    for (int s = 0; s < p.nu1; ++s) smooth_level(v, p.eta);
-    const bool next_top = l + 1 < p.n_top;
-    const Layout& Lc = next_top ? p.lev[l + 1].L : p.tail.L0;
-    const int* cact = next_top ? p.lev[l + 1].active : nullptr;
-    if (next_top) {
-      resid_restrict_level(v, Lc, cact, p.lev[l + 1].n_active, p.lev[l + 1].F);
+    if (l > 0 || zero_init) {
+      zero_level(v, tm);
+      team_sync(tm);
+    }
+    for (int s = 0; s < p.nu1; ++s) smooth_level<kU>(v, p.eta, tm);
+    if (l + 1 < p.n_top) {
+      const BatchLevel& w = p.lev[l + 1];
+      resid_restrict_level<kU>(v, w.L, w.xy, w.n_active, w.F, tm);
     } else {
       // the tail's top level (its active tiles; the tail ignores F off the DOFs)
-      resid_restrict_level(v, Lc, p.tail_active, p.tail_n_active, p.tail_F);
+      resid_restrict_level<kU>(v, p.tail.L0, p.tail_xy, p.tail_n_active, p.tail_F, tm);
     }
   }
-  tail_vcycle<float>(p.tail, smem, p.n_top == 0 && !zero_init, load_image);
-  __syncthreads();
+  if (tm.rank == 0) tail_vcycle<float>(p.tail, smem, p.n_top == 0 && !zero_init, load_image);
+  team_sync(tm);
   for (int l = p.n_top - 1; l >= 0; --l) {
     const BatchLevel& v = p.lev[l];
     const bool next_top = l + 1 < p.n_top;
-    prolong_level(v, next_top ? p.lev[l + 1].L : p.tail.L0,
-                  next_top ? p.lev[l + 1].u : p.tail.u0);
-    for (int s = 0; s < p.nu2; ++s) smooth_level(v, p.eta);
+    prolong_level<kU>(v, next_top ? p.lev[l + 1].L : p.tail.L0,
+                  next_top ? p.lev[l + 1].u : p.tail.u0, tm);
+    for (int s = 0; s < p.nu2; ++s) smooth_level<kU>(v, p.eta, tm);
   }
 }
 
-// fp64 residual of the fine level: F32 = sigma r on the DOFs, returns ||r||_inf
-__device__ double residual64(const BatchProblem& p, double sigma) {
+// fp64 residual of the fine level: F32 = sigma r on the DOFs (0 elsewhere in
+// the active tiles); returns ||r||_inf over the team
+__device__ double residual64(const BatchProblem& p, double sigma, const Team& tm, int& parity) {
   const Layout& L = p.L0;
-  const int P = L.pitch;
+  const int P = L.pitch, n = L.n, total = p.n_active0 * 2048;
+  constexpr int U = 2;
   double vmax = 0.0;
-  for (int q = threadIdx.x; q < p.n_active0 * 2048; q += blockDim.x) {
-    int i, j;
-    if (!tile_node(L, p.active0, q, i, j)) continue;
-    const size_t g = L.idx(i, j);
-    const uint16_t cd = p.code0[g];
-    double r = 0.0;
-    if (cd == 1) {
-      const double* U = p.u64 + g;
-      const double s8 = ((U[-1] + U[1]) + (U[-P] + U[P])) + ((U[-P - 1] + U[-P + 1]) +
-                                                             (U[P - 1] + U[P + 1]));
-      r = p.F64[g] - (8.0 * U[0] - s8) * (1.0 / 3.0);
-    } else if (cd >= 2) {
-      const double* R = p.rows64 + (size_t)(p.tile_base0[L.tile_of(i, j)] + cd - 2) * MG_ROW;
-      r = p.F64[g] - row_apply(R, p.u64 + g, P);
+  for (int q0 = tm.t0; q0 < total; q0 += U * tm.ts) {
+    int g[U], ti[U];
+    bool ok[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      int i, j;
+      g[k] = tile_pos(p.xy0, q0 + k * tm.ts, total, n, P, ok[k], i, j);
+      ti[k] = L.tile_of(i, j);
     }
-    vmax = fmax(vmax, fabs(r));
-    p.F32[g] = (float)(r * sigma);
+    double f[U], s[U], c0[U];
+    uint16_t cd[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      cd[k] = 0;
+      f[k] = s[k] = c0[k] = 0.0;
+      if (ok[k]) {
+        cd[k] = __ldg(p.code0 + g[k]);
+        f[k] = p.F64[g[k]];
+        c0[k] = p.u64[g[k]];
+        s[k] = sum8(p.u64 + g[k], P);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      double r = 0.0;
+      if (cd[k] == 1) {
+        r = f[k] - (8.0 * c0[k] - s[k]) * (1.0 / 3.0);
+      } else if (cd[k] >= 2) {
+        const double* R = p.rows64 + (size_t)(__ldg(p.tile_base0 + ti[k]) + cd[k] - 2) * MG_ROW;
+        r = f[k] - row_apply(R, p.u64 + g[k], P);
+      }
+      if (ok[k]) {
+        vmax = fmax(vmax, fabs(r));
+        p.F32[g[k]] = (float)(r * sigma);
+      }
+    }
   }
-  return block_max(vmax);
+  return team_max(vmax, tm, parity);
 }
 
 __device__ double pow2_near_inverse(double x) {
@@ -220,90 +436,129 @@ __device__ double pow2_near_inverse(double x) {
   return ldexp(1.0, -e);
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 1)
-k_batch(const BatchProblem* __restrict__ probs, const int* __restrict__ order, int count,
-        int* next, const unsigned* __restrict__ bad, const double* __restrict__ params,
-        int first_group, BatchResult* res) {
-  extern __shared__ __align__(128) unsigned char smem_dyn[];
-  unsigned char* smem = smem_align128(smem_dyn);
-  __shared__ int cur;
+// The whole mixed-precision solve of member pi by team tm (same arithmetic
+// and check schedule as the single-problem solver); the result is written by
+// the lead block.
+template <int kU>
+__device__ void solve_member(const BatchProblem& p, int pi, const unsigned* bad,
+                             const double* params, int first_group, BatchResult* res,
+                             unsigned char* smem, const Team& tm, int& parity) {
   const double tol = params[0];
   const int max_cycles = (int)params[1];
   const int fixed = (int)params[2];           // > 0: fixed group size
+  const Layout& L = p.L0;
+  const int P = L.pitch, n = L.n, total = p.n_active0 * 2048;
+  const bool invalid = bad[pi] != 0;
+  // u = 0 and ||F||_inf
+  double fmax_ = 0.0;
+  for (int q = tm.t0; q < total; q += tm.ts) {
+    bool ok;
+    const int g = tile_pos(p.xy0, q, total, n, P, ok);
+    if (!ok) continue;
+    p.u64[g] = 0.0;
+    if (!invalid) fmax_ = fmax(fmax_, fabs(p.F64[g]));
+  }
+  const double Fn = team_max(fmax_, tm, parity);
+  int cycles = 0, checks = 0, status = invalid ? MG_ERR_INVALID_ARG : MG_OK;
+  double rel = 0.0;
+  if (!invalid && Fn > 0.0) {
+    double sigma = pow2_near_inverse(Fn), rmax = Fn, best = 1.0, rho = 0.1;
+    // u = 0: the first refinement residual is F itself
+    for (int q = tm.t0; q < total; q += tm.ts) {
+      bool ok;
+      const int g = tile_pos(p.xy0, q, total, n, P, ok);
+      if (ok) p.F32[g] = (float)(p.F64[g] * sigma);
+    }
+    team_sync(tm);
+    rel = 1.0;
+    int kk = fixed > 0 ? fixed : first_group;
+    while (rel > tol) {
+      if (cycles >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
+      kk = min(kk, max_cycles - cycles);
+      for (int s = 0; s < kk; ++s) vcycle<kU>(p, s == 0, smem, cycles + s == 0, tm);
+      cycles += kk;
+      // u += e / sigma on the DOFs (same arithmetic as k_update)
+      const double inv = 1.0 / sigma;
+      for (int q0 = tm.t0; q0 < total; q0 += kU * tm.ts) {
+        int g[kU];
+        bool ok[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) g[k] = tile_pos(p.xy0, q0 + k * tm.ts, total, n, P, ok[k]);
+        double u0[kU];
+        float e[kU];
+        bool dof[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+          dof[k] = ok[k] && __ldg(p.code0 + g[k]) != 0;
+          u0[k] = ok[k] ? p.u64[g[k]] : 0.0;
+          e[k] = ok[k] ? p.e32[g[k]] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+          if (dof[k]) p.u64[g[k]] = u0[k] + (double)e[k] * inv;
+      }
+      team_sync(tm);
+      sigma = pow2_near_inverse(rmax * pow(rho, kk));
+      const double rnew = residual64(p, sigma, tm, parity);
+      ++checks;
+      rel = rnew / Fn;
+      if (!isfinite(rel) || rel > 1e3 * best) { status = MG_ERR_DIVERGED; break; }
+      best = fmin(best, rel);
+      rho = fmin(0.9, fmax(0.01, pow(rnew / rmax, 1.0 / kk)));
+      rmax = rnew;
+      if (fixed <= 0 && rel > tol) {
+        const double need = log(tol / rel) / log(rho);
+        kk = max(1, min(8, (int)ceil(need + 0.5)));
+      }
+    }
+  }
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    BatchResult r;
+    r.cycles = cycles;
+    r.checks = checks;
+    r.status = status;
+    r.pad = 0;
+    r.rel_res = rel;
+    res[pi] = r;
+  }
+  team_sync(tm);
+}
+
+// words[0]: next cooperative item (taken by cluster leaders), words[2]: next
+// item taken by single blocks.  order[0 .. n_coop) are solved by whole
+// clusters, the rest by single blocks.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+k_batch(const BatchProblem* __restrict__ probs, const int* __restrict__ order, int count,
+        int n_coop, unsigned* words, const unsigned* __restrict__ bad,
+        const double* __restrict__ params, int first_group, BatchResult* res) {
+  constexpr int kU = THREADS >= 1024 ? 2 : 4;
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem = smem_align128(smem_dyn);
+  __shared__ unsigned cur;
+  int parity = 0;
+  const int nr = (int)cluster_size(), rank = (int)cluster_rank();
+  if (nr > 1) {
+    const Team tm{rank * (int)blockDim.x + (int)threadIdx.x, nr * (int)blockDim.x, rank, nr};
+    for (;;) {
+      if (rank == 0 && threadIdx.x == 0) {
+        const unsigned k = atomicAdd(&words[0], 1u);
+        for (int r = 0; r < nr; ++r) dsmem_store_u32(&cur, r, k);
+      }
+      cluster_sync_all();
+      const int k = (int)cur;
+      if (k >= n_coop) break;
+      solve_member<kU>(probs[order[k]], order[k], bad, params, first_group, res, smem, tm, parity);
+    }
+  }
+  const Team solo{(int)threadIdx.x, (int)blockDim.x, 0, 1};
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) cur = atomicAdd(next, 1);
+    if (threadIdx.x == 0) cur = atomicAdd(&words[2], 1u);
     __syncthreads();
-    const int k = cur;
+    const int k = (nr > 1 ? n_coop : 0) + (int)cur;
     if (k >= count) break;
-    const int pi = order[k];
-    const BatchProblem& p = probs[pi];
-    const Layout& L = p.L0;
-    const bool invalid = bad[pi] != 0;
-    // u = 0 and ||F||_inf
-    double fmax_ = 0.0;
-    for (int q = threadIdx.x; q < p.n_active0 * 2048; q += blockDim.x) {
-      int i, j;
-      if (!tile_node(L, p.active0, q, i, j)) continue;
-      const size_t g = L.idx(i, j);
-      p.u64[g] = 0.0;
-      if (!invalid) fmax_ = fmax(fmax_, fabs(p.F64[g]));
-    }
-    const double Fn = block_max(fmax_);
-    int cycles = 0, checks = 0, status = invalid ? MG_ERR_INVALID_ARG : MG_OK;
-    double rel = 0.0;
-    if (!invalid && Fn > 0.0) {
-      double sigma = pow2_near_inverse(Fn), rmax = Fn, best = 1.0, rho = 0.1;
-      // u = 0: the first refinement residual is F itself
-      for (int q = threadIdx.x; q < p.n_active0 * 2048; q += blockDim.x) {
-        int i, j;
-        if (!tile_node(L, p.active0, q, i, j)) continue;
-        const size_t g = L.idx(i, j);
-        p.F32[g] = (float)(p.F64[g] * sigma);
-      }
-      __syncthreads();
-      rel = 1.0;
-      int kk = fixed > 0 ? fixed : first_group;
-      while (rel > tol) {
-        if (cycles >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
-        kk = min(kk, max_cycles - cycles);
-        for (int s = 0; s < kk; ++s) {
-          vcycle(p, s == 0, smem, cycles + s == 0);
-        }
-        cycles += kk;
-        // u += e / sigma on the DOFs (same arithmetic as k_update)
-        const double inv = 1.0 / sigma;
-        for (int q = threadIdx.x; q < p.n_active0 * 2048; q += blockDim.x) {
-          int i, j;
-          if (!tile_node(L, p.active0, q, i, j)) continue;
-          const size_t g = L.idx(i, j);
-          if (p.code0[g]) p.u64[g] += (double)p.e32[g] * inv;
-        }
-        __syncthreads();
-        sigma = pow2_near_inverse(rmax * pow(rho, kk));
-        const double rnew = residual64(p, sigma);
-        ++checks;
-        rel = rnew / Fn;
-        if (!isfinite(rel) || rel > 1e3 * best) { status = MG_ERR_DIVERGED; break; }
-        best = fmin(best, rel);
-        rho = fmin(0.9, fmax(0.01, pow(rnew / rmax, 1.0 / kk)));
-        rmax = rnew;
-        if (fixed <= 0 && rel > tol) {
-          const double need = log(tol / rel) / log(rho);
-          kk = max(1, min(8, (int)ceil(need + 0.5)));
-        }
-      }
-    }
-    if (threadIdx.x == 0) {
-      BatchResult r;
-      r.cycles = cycles;
-      r.checks = checks;
-      r.status = status;
-      r.pad = 0;
-      r.rel_res = rel;
-      res[pi] = r;
-    }
+    solve_member<kU>(probs[order[k]], order[k], bad, params, first_group, res, smem, solo, parity);
   }
 }
 
@@ -380,7 +635,7 @@ __global__ void k_batch_lists(Layout L, const uint16_t* __restrict__ code,
     const uint16_t cd = code[L.idx(i, j)];
     if (cd < 2) continue;
     const int pos = atomicAdd(&cur[(i & 1) + 2 * (j & 1)], 1);
-    blist[pos] = make_int2(i | (j << 16), tile_base[L.tile_of(i, j)] + cd - 2);
+    blist[pos] = make_int2((int)L.idx(i, j), tile_base[L.tile_of(i, j)] + cd - 2);
   }
 }
 
@@ -388,26 +643,86 @@ __global__ void k_batch_lists(Layout L, const uint16_t* __restrict__ code,
 
 cudaError_t configure_batch(size_t smem) {
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = raise_smem_limit(k_batch<1024>, smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = raise_smem_limit(k_batch<512>, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  return raise_smem_limit(k_batch<256>, smem);
 }
 
-void launch_batch(const BatchProblem* probs, const int* order, int count, int* next,
-                  const unsigned* bad, const double* params, BatchTune tune, int grid,
-                  size_t smem, BatchResult* res, cudaStream_t st) {
+namespace {
+
+template <int THREADS>
+cudaLaunchConfig_t batch_config(const BatchTune& tune, int grid, size_t smem, cudaStream_t st,
+                                cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = tune.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <int THREADS>
+int max_clusters(const BatchTune& tune, size_t smem) {
+  cudaLaunchAttribute attr[1];
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaLaunchConfig_t cfg = batch_config<THREADS>(tune, nsm, smem, nullptr, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_batch<THREADS>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <int THREADS>
+void launch_k(const BatchProblem* probs, const int* order, int count, int n_coop,
+              unsigned* words, const unsigned* bad, const double* params, const BatchTune& tune,
+              int grid, size_t smem, BatchResult* res, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = batch_config<THREADS>(tune, grid, smem, st, attr);
+  cudaLaunchKernelEx(&cfg, k_batch<THREADS>, probs, order, count, n_coop, words, bad, params,
+                     tune.first_group, res);
+}
+
+__global__ void k_tile_xy(Layout L, const int* __restrict__ active, int n,
+                          unsigned* __restrict__ xy) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int t = active[k];
+  xy[k] = (unsigned)((t % L.ntx) * MG_TX) | ((unsigned)((t / L.ntx) * MG_TY) << 16);
+}
+
+}  // namespace
+
+int batch_max_clusters(const BatchTune& tune, size_t smem) {
+  if (tune.threads >= 1024) return max_clusters<1024>(tune, smem);
+  if (tune.threads >= 512) return max_clusters<512>(tune, smem);
+  return max_clusters<256>(tune, smem);
+}
+
+void launch_batch(const BatchProblem* probs, const int* order, int count, int n_coop,
+                  unsigned* words, const unsigned* bad, const double* params, BatchTune tune,
+                  int grid, size_t smem, BatchResult* res, cudaStream_t st) {
   if (tune.threads >= 1024)
-    k_batch<1024><<<grid, 1024, smem, st>>>(probs, order, count, next, bad, params,
-                                            tune.first_group, res);
+    launch_k<1024>(probs, order, count, n_coop, words, bad, params, tune, grid, smem, res, st);
   else if (tune.threads >= 512)
-    k_batch<512><<<grid, 512, smem, st>>>(probs, order, count, next, bad, params,
-                                          tune.first_group, res);
+    launch_k<512>(probs, order, count, n_coop, words, bad, params, tune, grid, smem, res, st);
   else
-    k_batch<256><<<grid, 256, smem, st>>>(probs, order, count, next, bad, params,
-                                          tune.first_group, res);
+    launch_k<256>(probs, order, count, n_coop, words, bad, params, tune, grid, smem, res, st);
+}
+
+void launch_tile_xy(const Layout& L, const int* active, int n, unsigned* xy, cudaStream_t st) {
+  if (n > 0) k_tile_xy<<<(n + 255) / 256, 256, 0, st>>>(L, active, n, xy);
 }
 
 static unsigned flat_grid(size_t total) {

@@ -13,9 +13,9 @@ struct BatchLevel {
   const uint16_t* code;
   const int* tile_base;
   const float* rows;           // fp32 boundary rows
-  const int* active;           // active tiles
+  const unsigned* xy;          // active tiles' first nodes, i0 | j0 << 16
   int n_active;
-  const int2* blist;           // boundary nodes {i | j << 16, row}, grouped by colour
+  const int2* blist;           // boundary nodes {padded offset, row}, grouped by colour
   int boff[5];                 // colour group offsets into blist
   float* u;                    // iterate (in place)
   float* F;                    // right-hand side
@@ -26,7 +26,7 @@ struct BatchProblem {
   int n_top;                   // levels 0 .. n_top-1 block-wide, the tail from level n_top
   BatchLevel lev[MG_BATCH_MAX_TOP];
   TailArgs<float> tail;        // the tail block's V-cycle (its top F and u: level n_top)
-  const int* tail_active;      // active tiles of the tail's top level
+  const unsigned* tail_xy;     // active tiles of the tail's top level (i0 | j0 << 16)
   int tail_n_active;
   float* tail_F;               // the tail's top F (restriction target)
   // fine level in fp64
@@ -34,7 +34,8 @@ struct BatchProblem {
   const uint16_t* code0;
   const int* tile_base0;
   const double* rows64;
-  const int* active0;
+  const int* active0;          // active tiles (ids)
+  const unsigned* xy0;         // and their first nodes, i0 | j0 << 16
   int n_active0;
   double* F64;
   double* u64;
@@ -57,6 +58,9 @@ struct BatchResult {
 struct BatchTune {
   int threads;                 // threads per block (256 .. 1024)
   int first_group;             // V-cycles before the first fp64 residual check
+  int cluster;                 // blocks per thread-block cluster (1, 2, 4, 8)
+  int coop_min_dof;            // members with at least this many DOFs (and levels
+                               // above the tail) are solved by a whole cluster
 };
 
 // Per-member input check and right-hand side over all members at once:
@@ -74,11 +78,19 @@ void launch_batch_unpack(const BatchProblem* probs, const size_t* node_off, int 
 // Launches the persistent kernel: grid blocks take problems order[0..count)
 // from the counter *next (zero on entry), largest first.
 // Members with bad[p] != 0 get u = 0 and status MG_ERR_INVALID_ARG.
-// *params = {tol, max_cycles} (device memory, read at launch).
-void launch_batch(const BatchProblem* probs, const int* order, int count, int* next,
-                  const unsigned* bad, const double* params, BatchTune tune, int grid,
-                  size_t smem, BatchResult* res, cudaStream_t st);
+// params = {tol, max_cycles, fixed group size or 0} (device memory, read at
+// launch).  words[0] and words[2] are the work counters (zero on entry),
+// words[1] the error word.  order[0 .. n_coop) are solved by whole clusters
+// of tune.cluster blocks, the rest by single blocks; grid is a multiple of
+// tune.cluster.
+void launch_batch(const BatchProblem* probs, const int* order, int count, int n_coop,
+                  unsigned* words, const unsigned* bad, const double* params, BatchTune tune,
+                  int grid, size_t smem, BatchResult* res, cudaStream_t st);
 cudaError_t configure_batch(size_t smem);
+// clusters of tune.cluster blocks that can be resident at once (0 if none)
+int batch_max_clusters(const BatchTune& tune, size_t smem);
+// xy[k] = i0 | j0 << 16 of tile active[k] of layout L
+void launch_tile_xy(const Layout& L, const int* active, int n, unsigned* xy, cudaStream_t st);
 // builds blist / boff of one level from its codes (one block)
 void launch_batch_lists(const Layout& L, const uint16_t* code, const int* tile_base,
                         int2* blist, int* boff, cudaStream_t st);

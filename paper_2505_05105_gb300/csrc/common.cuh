@@ -152,6 +152,17 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 
 // Host helpers ----------------------------------------------------------------
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`; never
+// lowers it, since handles with different needs launch the same kernel.
+template <class K>
+cudaError_t raise_smem_limit(K* kernel, size_t bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 #define MG_CUDA_TRY(expr)                                  \
   do {                                                     \
     cudaError_t e__ = (expr);                              \

@@ -745,8 +745,7 @@ cudaError_t configure_kernels(int eta) {
   if (e != cudaSuccess) return e;
   // the largest eta allowed by the ABI, so handles with different eta coexist
   (void)eta;
-  e = cudaFuncSetAttribute(k_band<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)band_smem<T>(8));
+  e = raise_smem_limit(k_band<T>, (int)band_smem<T>(8));
   return e;
 }
 

@@ -457,8 +457,7 @@ cudaError_t configure_fused(size_t smem) {
   if (sizeof(T) != sizeof(float)) return cudaSuccess;
   cudaError_t e;
 #define MG_CFG(Z, P, R)                                                                     \
-  e = cudaFuncSetAttribute(k_smooth_step<Z, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           (int)smem);                                                      \
+  e = raise_smem_limit(k_smooth_step<Z, P, R>, smem);                                       \
   if (e != cudaSuccess) return e;
   MG_CFG(true, false, false)
   MG_CFG(false, false, false)

@@ -141,7 +141,7 @@ void launch_tail_image(const TailLayout& lay, const TailLevelSrc* lv, unsigned c
 
 template <class T>
 cudaError_t configure_tail(size_t smem) {
-  return cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return raise_smem_limit(k_tail<T>, (int)smem);
 }
 
 template <class T>

@@ -59,6 +59,14 @@ class mg_info(ctypes.Structure):
         return [self.res_hist[k] for k in range(min(self.checks + 1, 64))]
 
 
+class mg_batch_shape(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("first_group", ctypes.c_int),
+                ("cluster", ctypes.c_int), ("coop_min_dof", ctypes.c_int)]
+
+    def astuple(self):
+        return (self.threads, self.first_group, self.cluster, self.coop_min_dof)
+
+
 class mg_batch_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int), ("checks", ctypes.c_int),
                 ("n_dof", ctypes.c_int), ("rel_res", ctypes.c_double)]
@@ -93,9 +101,10 @@ SIGNATURES = {
     "mg_batch_buffers": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_P),
                               ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "mg_batch_solve": (_I, [_P, _P, _P, _P, _D, _P]),
-    "mg_batch_tune": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+    "mg_batch_set_shape": (_I, [_P, ctypes.POINTER(mg_batch_shape)]),
+    "mg_batch_get_shape": (_I, [_P, ctypes.POINTER(mg_batch_shape)]),
+    "mg_batch_tune": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(mg_batch_shape),
                            ctypes.POINTER(ctypes.c_float)]),
-    "mg_batch_set_tune": (_I, [_P, _I, _I]),
     "mg_batch_timing": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "mg_batch_destroy": (None, [_P]),
 }
@@ -279,15 +288,21 @@ def mg_batch_solve(batch: int, f, g, u, tol: float, info=None, ok=(MG_OK,)) -> i
 
 
 def mg_batch_tune(batch: int, f, g, tol: float, reps: int = 3):
-    """(threads, first_group, ms) of the fastest launch shape (see the header)."""
-    t, k, ms = _I(), _I(), ctypes.c_float()
-    _check(load().mg_batch_tune(batch, _addr(f), _addr(g), tol, reps, ctypes.byref(t),
-                                ctypes.byref(k), ctypes.byref(ms)), "mg_batch_tune")
-    return t.value, k.value, ms.value
+    """(mg_batch_shape, ms) of the fastest launch shape (see the header)."""
+    best, ms = mg_batch_shape(), ctypes.c_float()
+    _check(load().mg_batch_tune(batch, _addr(f), _addr(g), tol, reps, ctypes.byref(best),
+                                ctypes.byref(ms)), "mg_batch_tune")
+    return best, ms.value
 
 
-def mg_batch_set_tune(batch: int, threads: int, first_group: int) -> int:
-    return _check(load().mg_batch_set_tune(batch, threads, first_group), "mg_batch_set_tune")
+def mg_batch_set_shape(batch: int, shape: mg_batch_shape) -> int:
+    return _check(load().mg_batch_set_shape(batch, ctypes.byref(shape)), "mg_batch_set_shape")
+
+
+def mg_batch_get_shape(batch: int) -> mg_batch_shape:
+    s = mg_batch_shape()
+    _check(load().mg_batch_get_shape(batch, ctypes.byref(s)), "mg_batch_get_shape")
+    return s
 
 
 def mg_batch_timing(batch: int):
@@ -442,10 +457,17 @@ class BatchSolver:
         return code, list(info)
 
     def tune(self, f, g, tol: float = 1e-10, reps: int = 3):
-        return mg_batch_tune(self.handle, f, g, tol, reps)
+        """Autotunes the launch shape; returns (shape tuple, ms per solve)."""
+        best, ms = mg_batch_tune(self.handle, f, g, tol, reps)
+        return best.astuple(), ms
 
-    def set_tune(self, threads: int, first_group: int):
-        mg_batch_set_tune(self.handle, threads, first_group)
+    def set_shape(self, threads: int = 512, first_group: int = 4, cluster: int = 1,
+                  coop_min_dof: int = 0):
+        mg_batch_set_shape(self.handle, mg_batch_shape(threads, first_group, cluster,
+                                                       coop_min_dof))
+
+    def shape(self):
+        return mg_batch_get_shape(self.handle).astuple()
 
     def timing(self):
         return mg_batch_timing(self.handle)

@@ -151,10 +151,13 @@ def test_replays_arrays_and_block_sizes_are_deterministic(members):
         g0.copy_(dev(gh))
         B.solve(f0, g0, u0, tol=1e-11)
         np.testing.assert_array_equal(a, host(u0))
-        # Gauss-Seidel colour phases are free of races: the block size does
-        # not change a single bit
-        for threads in (256, 512):
-            B.set_tune(threads, 4)
+        # Gauss-Seidel colour phases are free of races: neither the block
+        # size nor sharing a member among the blocks of a cluster (each on
+        # its own SM) changes a single bit
+        for shape in ((256, 4, 1, 0), (1024, 4, 1, 0), (512, 4, 2, 0), (512, 4, 4, 0),
+                      (256, 4, 8, 0), (1024, 4, 4, 20000)):
+            B.set_shape(*shape)
+            assert B.shape() == shape
             c = np.zeros(B.total)
             B.solve(fh, gh, c, tol=1e-11)
             np.testing.assert_array_equal(a, c)
@@ -165,8 +168,10 @@ def test_autotuner(members):
     ps, sys, Fs, ud = members
     with batch(ps) as B:
         f, g = dev(B.pack([p.f for p in ps])), dev(B.pack([p.g for p in ps]))
-        threads, first, ms = B.tune(f, g, tol=1e-10, reps=2)
+        (threads, first, cluster, coop), ms = B.tune(f, g, tol=1e-10, reps=2)
         assert threads in (256, 512, 1024) and first in (2, 3, 4, 6) and ms > 0.0
+        assert cluster in (1, 2, 4, 8) and coop in (0, 8192, 32768, 131072)
+        assert B.shape() == (threads, first, cluster, coop)
         u = torch.zeros(B.total, dtype=torch.float64, device="cuda")
         info = B.solve(f, g, u, tol=1e-10)
         _, solve_ms = B.timing()
@@ -201,14 +206,17 @@ def test_rejects_fp64_and_bad_arguments():
         with pytest.raises(G.GhostMGError) as e:
             B.solve(np.zeros(B.total), np.zeros(B.total), np.zeros(B.total), tol=-1.0)
         assert e.value.code == G.MG_ERR_INVALID_ARG
-        with pytest.raises(G.GhostMGError):
-            B.set_tune(384, 4)
+        for bad in ((384, 4, 1, 0), (512, 0, 1, 0), (512, 4, 3, 0), (512, 4, 2, -1)):
+            with pytest.raises(G.GhostMGError):
+                B.set_shape(*bad)
+        assert B.shape() == (512, 4, 1, 0)
 
 
 def test_full_batch_256():
     """The benchmark's batch: 256 seeded members, N in {64, 128, 256, 512},
-    stopped at 1e-10 in the default launch shape; sampled members (the
-    largest of each size) against the oracle's direct solution."""
+    stopped at 1e-10 in the default launch shape and with the large members
+    shared by clusters of 4; sampled members (the largest of each size)
+    against the oracle's direct solution."""
     from paper_2505_05105_gb300 import ghostmg as G
     ps = [wl.batch_geometry(i, seed=0) for i in range(256)]
     with batch(ps) as B:
@@ -216,6 +224,10 @@ def test_full_batch_256():
         u = torch.zeros(B.total, dtype=torch.float64, device="cuda")
         info = B.solve(f, g, u, tol=1e-10)
         out = B.unpack(host(u))
+        B.set_shape(512, 4, 4, 32768)
+        u2 = torch.zeros_like(u)
+        B.solve(f, g, u2, tol=1e-10)
+        assert torch.equal(u, u2)
     assert all(i.status == G.MG_OK and i.rel_res <= 1e-10 for i in info)
     sizes = sorted({p.N for p in ps})
     assert sizes == [64, 128, 256, 512]

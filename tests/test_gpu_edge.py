@@ -162,3 +162,27 @@ def test_check_schedule(precision):
     assert every[1] == every[0]                       # one check per cycle
     assert out[0][0] <= every[0] + 1 and out[0][1] < every[1]
     assert out[5][0] % 5 == 0 and out[5][1] == out[5][0] // 5
+
+
+def test_handles_with_different_shared_memory_needs_coexist():
+    """Handles whose kernels need different amounts of shared memory (the
+    single-block tail's layout depends on the geometry, the fused step's on
+    eta) and a batch are alive at once and solve in any order."""
+    from paper_2505_05105_gb300 import ghostmg as G
+    probs = [(wl.flower(1024, k=7, phase=0.3), dict(eta=8)),
+             (wl.circle64(64), dict(eta=2)),
+             (wl.three_discs(512, seed=1), dict(eta=4))]
+    solvers = [G.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h, precision="mixed", **kw)
+               for p, kw in probs]
+    B = G.BatchSolver([wl.batch_geometry(i, seed=3) for i in range(4)])
+    for rnd in range(2):
+        for (p, _), S in zip(probs, solvers):
+            u = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
+            assert S.solve(dev(p.f), dev(p.g), u, tol=1e-10).rel_res <= 1e-10
+        if rnd == 0:
+            # a new handle in between (its setup configures the kernels again)
+            solvers.append(G.Solver(dev(wl.flower(128).psi), 128, -0.5, -0.5, 1 / 128,
+                                    precision="mixed", eta=1))
+    for x in solvers:
+        x.close()
+    B.close()
