@@ -1236,8 +1236,31 @@ int balloc(mg_batch_ctx* b, T** p, size_t count) {
   return e == cudaSuccess ? MG_OK : mg_cuda_fail(e);
 }
 
-// the device table entry of one member (its hierarchy is set up, mixed)
-int batch_member(mg_batch_ctx* b, int p, BatchProblem* out) {
+// The eta window of one level: the boundary nodes (blist, host copy) and
+// their 8 neighbours, sorted by padded offset; per entry the window index of
+// each stencil position.  Returns false (no window) if it would not fit in
+// `avail` bytes of shared memory or in 16-bit indices.
+bool build_window(const std::vector<int2>& bl, int P, size_t avail, std::vector<int>& win,
+                  std::vector<uint16_t>& slot) {
+  const int d[9] = {-P - 1, -P, -P + 1, -1, 0, 1, P - 1, P, P + 1};
+  win.clear();
+  win.reserve(bl.size() * 9);
+  for (const int2& e : bl)
+    for (int k = 0; k < 9; ++k) win.push_back(e.x + d[k]);
+  std::sort(win.begin(), win.end());
+  win.erase(std::unique(win.begin(), win.end()), win.end());
+  if (win.empty() || win.size() > 65535 || win.size() * sizeof(float) > avail) return false;
+  slot.assign(bl.size() * 10, 0);
+  for (size_t e = 0; e < bl.size(); ++e)
+    for (int k = 0; k < 9; ++k)
+      slot[e * 10 + k] = (uint16_t)(std::lower_bound(win.begin(), win.end(), bl[e].x + d[k]) -
+                                    win.begin());
+  return true;
+}
+
+// the device table entry of one member (its hierarchy is set up, mixed);
+// win_bytes: shared memory the member's eta windows may use
+int batch_member(mg_batch_ctx* b, int p, BatchProblem* out, size_t win_bytes) {
   mg_ctx* c = b->mem[p];
   const int t = c->tail_level;
   if (t < 0 || t > MG_BATCH_MAX_TOP) return MG_ERR_UNIMPLEMENTED;
@@ -1260,7 +1283,34 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out) {
     TRY(dalloc(c, &boff, 5));
     launch_batch_lists(v.L, v.code, v.tile_base, blist, boff, c->st);
     MG_CUDA_TRY(cudaMemcpyAsync(w.boff, boff, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    std::vector<int2> hb((size_t)v.n_bnd);
+    if (v.n_bnd)
+      MG_CUDA_TRY(cudaMemcpyAsync(hb.data(), blist, (size_t)v.n_bnd * sizeof(int2),
+                                  cudaMemcpyDeviceToHost, c->st));
     MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+    float* srows;
+    TRY(dalloc(c, &srows, (size_t)v.n_bnd * MG_ROW));
+    launch_soa_rows(blist, v.n_bnd, v.rows32, srows, c->st);
+    w.srows = srows;
+    std::vector<int> hw;
+    std::vector<uint16_t> hs;
+    w.win = nullptr;
+    w.wslot = nullptr;
+    w.win_n = 0;
+    if (v.n_bnd && build_window(hb, v.L.pitch, win_bytes, hw, hs)) {
+      int* dw;
+      uint16_t* ds;
+      TRY(dalloc(c, &dw, hw.size()));
+      TRY(dalloc(c, &ds, hs.size()));
+      MG_CUDA_TRY(cudaMemcpyAsync(dw, hw.data(), hw.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                  c->st));
+      MG_CUDA_TRY(cudaMemcpyAsync(ds, hs.data(), hs.size() * sizeof(uint16_t),
+                                  cudaMemcpyHostToDevice, c->st));
+      MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+      w.win = dw;
+      w.wslot = ds;
+      w.win_n = (int)hw.size();
+    }
     w.L = v.L;
     w.code = v.code;
     w.tile_base = v.tile_base;
@@ -1457,10 +1507,13 @@ int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levels
   std::vector<BatchProblem> probs(n);
   std::vector<int> tile_off(n + 1, 0);
   size_t smem = 0;
+  for (int p = 0; p < n; ++p) smem = std::max(smem, (size_t)b->mem[p]->tail_lay[0].total);
   for (int p = 0; p < n; ++p) {
-    TRY(batch_member(b, p, &probs[p]));
+    // the eta windows live in the tail's dynamic region, up to the end of
+    // the batch's shared memory
+    const size_t start = b->mem[p]->tail_lay[0].U[0];
+    TRY(batch_member(b, p, &probs[p], smem - kSmemSlack > start ? smem - kSmemSlack - start : 0));
     tile_off[p + 1] = tile_off[p] + probs[p].n_active0;
-    smem = std::max(smem, (size_t)b->mem[p]->tail_lay[0].total);
   }
   b->total_tiles = tile_off[n];
   b->n_dof.resize(n);

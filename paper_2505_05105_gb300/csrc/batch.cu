@@ -182,14 +182,50 @@ __device__ __forceinline__ void colour_interior(const BatchLevel& v, int ci, int
   }
 }
 
+// Rows of the listed boundary nodes are read from a copy laid out by
+// coefficient (R[k * n + e] for list entry e of n), so that a warp's loads of
+// one coefficient are contiguous.  The expressions are those of row_apply.
+__device__ __forceinline__ float row_apply_soa(const float* __restrict__ R, int n, const float* U,
+                                               int P) {
+  return __ldg(R) * U[-P - 1] + __ldg(R + n) * U[-P] + __ldg(R + 2 * n) * U[-P + 1] +
+         __ldg(R + 3 * n) * U[-1] + __ldg(R + 4 * n) * U[0] + __ldg(R + 5 * n) * U[1] +
+         __ldg(R + 6 * n) * U[P - 1] + __ldg(R + 7 * n) * U[P] + __ldg(R + 8 * n) * U[P + 1];
+}
+
+__device__ __forceinline__ void row_update_soa(float* u, int g, const float* __restrict__ R, int n,
+                                               float f, int P) {
+  const float* U = u + g;
+  const float acc = row_apply_soa(R, n, U, P);
+  u[g] = U[0] + (f - acc) * __ldg(R + 9 * n);
+}
+
+// The same update on values held in a shared-memory window: sl[k] is the
+// window index of the node at stencil position k (row order)
+__device__ __forceinline__ void row_update_win(float* w, const uint16_t* __restrict__ sl,
+                                               const float* __restrict__ R, int n, float f) {
+  uint16_t q[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) q[k] = __ldg(sl + k);
+  const float acc = __ldg(R) * w[q[0]] + __ldg(R + n) * w[q[1]] + __ldg(R + 2 * n) * w[q[2]] +
+                    __ldg(R + 3 * n) * w[q[3]] + __ldg(R + 4 * n) * w[q[4]] +
+                    __ldg(R + 5 * n) * w[q[5]] + __ldg(R + 6 * n) * w[q[6]] +
+                    __ldg(R + 7 * n) * w[q[7]] + __ldg(R + 8 * n) * w[q[8]];
+  w[q[4]] = w[q[4]] + (f - acc) * __ldg(R + 9 * n);
+}
+
 // One smoothing step of a level in global memory (Sec. 4.1, Sec. 5.3): four
 // colour phases (interior nodes by the team, the colour's cut-cell vertices
 // from the level's list by the lead block), then eta colour phases over the
 // cut-cell vertices by the lead block alone.  The lead block's threads keep
-// the position, row and F of one listed node per colour in registers for the
-// whole step; longer colour lists go through the loops marked `more`.
+// the position and F of one listed node per colour in registers for the
+// whole step; longer colour lists go through the loops marked `more`.  When
+// the level has a window (v.win_n > 0) the eta phases run in shared memory
+// (sw): the cut-cell vertices and their neighbours are gathered once, the
+// phases update the window (only the vertices change: their neighbours that
+// are not vertices are constant during these phases), and the vertices are
+// written back.
 template <int kU>
-__device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm) {
+__device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm, float* sw) {
   const int P = v.L.pitch;
   const bool lead = tm.rank == 0;
   int mc = 0;
@@ -198,27 +234,25 @@ __device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm) {
   const int nt = min((int)blockDim.x, max(32, (mc + 31) & ~31));
   const bool own = lead && (int)threadIdx.x < nt;
   const bool more = mc > nt;
-  int pos[4], row[4];
+  const int nb = v.boff[4];
+  int pos[4];
   float fv[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int e = v.boff[c] + threadIdx.x;
     pos[c] = -1;
-    row[c] = 0;
     fv[c] = 0.f;
     if (own && e < v.boff[c + 1]) {
-      const int2 en = __ldg(v.blist + e);
-      pos[c] = en.x;
-      row[c] = en.y;
-      fv[c] = v.F[en.x];
+      pos[c] = __ldg(v.blist + e).x;
+      fv[c] = v.F[pos[c]];
     }
   }
   auto listed = [&](int c, int stride) {
-    if (pos[c] >= 0) row_update(v.u, pos[c], v.rows + (size_t)row[c] * MG_ROW, fv[c], P);
+    if (pos[c] >= 0) row_update_soa(v.u, pos[c], v.srows + v.boff[c] + threadIdx.x, nb, fv[c], P);
     if (more)
       for (int e = v.boff[c] + nt + threadIdx.x; e < v.boff[c + 1]; e += stride) {
-        const int2 en = __ldg(v.blist + e);
-        row_update(v.u, en.x, v.rows + (size_t)en.y * MG_ROW, v.F[en.x], P);
+        const int g = __ldg(v.blist + e).x;
+        row_update_soa(v.u, g, v.srows + e, nb, v.F[g], P);
       }
   };
 #pragma unroll
@@ -227,7 +261,57 @@ __device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm) {
     if (own) listed(c, nt);
     team_sync(tm);
   }
-  if (eta > 0 && own) {
+  if (eta > 0 && v.win_n > 0) {
+    if (lead) {
+      // gather: 8 nodes per thread in flight
+      constexpr int GU = 8;
+      for (int k0 = threadIdx.x; k0 < v.win_n; k0 += GU * blockDim.x) {
+        int a[GU];
+#pragma unroll
+        for (int q = 0; q < GU; ++q) {
+          const int k = k0 + q * blockDim.x;
+          a[q] = k < v.win_n ? __ldg(v.win + k) : -1;
+        }
+        float x[GU];
+#pragma unroll
+        for (int q = 0; q < GU; ++q) x[q] = a[q] >= 0 ? v.u[a[q]] : 0.f;
+#pragma unroll
+        for (int q = 0; q < GU; ++q)
+          if (a[q] >= 0) sw[k0 + q * blockDim.x] = x[q];
+      }
+      __syncthreads();
+      if (own) {
+        for (int it = 0; it < eta; ++it)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int e = v.boff[c] + threadIdx.x;
+            if (pos[c] >= 0)
+              row_update_win(sw, v.wslot + (size_t)e * 10, v.srows + e, nb, fv[c]);
+            if (more)
+              for (int e2 = e + nt; e2 < v.boff[c + 1]; e2 += nt)
+                row_update_win(sw, v.wslot + (size_t)e2 * 10, v.srows + e2, nb,
+                               v.F[__ldg(v.blist + e2).x]);
+            if (nt == 32) __syncwarp();
+            else asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+          }
+      }
+      __syncthreads();
+      // scatter the updated vertices, 4 per thread in flight
+      constexpr int SU = 4;
+      for (int e0 = threadIdx.x; e0 < nb; e0 += SU * blockDim.x) {
+        int g[SU], q[SU];
+#pragma unroll
+        for (int k = 0; k < SU; ++k) {
+          const int e = e0 + k * blockDim.x;
+          g[k] = e < nb ? __ldg(v.blist + e).x : -1;
+          q[k] = e < nb ? __ldg(v.wslot + (size_t)e * 10 + 4) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < SU; ++k)
+          if (g[k] >= 0) v.u[g[k]] = sw[q[k]];
+      }
+    }
+  } else if (eta > 0 && own) {
     for (int it = 0; it < eta; ++it)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -356,13 +440,15 @@ __device__ void prolong_level(const BatchLevel& v, const Layout& Lc, const float
 template <int kU>
 __device__ void vcycle(const BatchProblem& p, bool zero_init, unsigned char* smem,
                        bool load_image, const Team& tm) {
+  // the eta windows use the tail's dynamic region (rewritten by every tail call)
+  float* sw = reinterpret_cast<float*>(smem + p.tail.lay.U[0]);
   for (int l = 0; l < p.n_top; ++l) {
     const BatchLevel& v = p.lev[l];
     if (l > 0 || zero_init) {
       zero_level(v, tm);
       team_sync(tm);
     }
-    for (int s = 0; s < p.nu1; ++s) smooth_level<kU>(v, p.eta, tm);
+    for (int s = 0; s < p.nu1; ++s) smooth_level<kU>(v, p.eta, tm, sw);
     if (l + 1 < p.n_top) {
       const BatchLevel& w = p.lev[l + 1];
       resid_restrict_level<kU>(v, w.L, w.xy, w.n_active, w.F, tm);
@@ -378,7 +464,7 @@ __device__ void vcycle(const BatchProblem& p, bool zero_init, unsigned char* sme
     const bool next_top = l + 1 < p.n_top;
     prolong_level<kU>(v, next_top ? p.lev[l + 1].L : p.tail.L0,
                   next_top ? p.lev[l + 1].u : p.tail.u0, tm);
-    for (int s = 0; s < p.nu2; ++s) smooth_level<kU>(v, p.eta, tm);
+    for (int s = 0; s < p.nu2; ++s) smooth_level<kU>(v, p.eta, tm, sw);
   }
 }
 
@@ -562,6 +648,17 @@ k_batch(const BatchProblem* __restrict__ probs, const int* __restrict__ order, i
   }
 }
 
+// rows of a level's listed boundary nodes by coefficient: out[k n + e] =
+// rows[blist[e].y * MG_ROW + k]
+__global__ void k_soa_rows(const int2* __restrict__ blist, int n, const float* __restrict__ rows,
+                           float* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float* R = rows + (size_t)blist[e].y * MG_ROW;
+#pragma unroll
+  for (int k = 0; k < MG_ROW; ++k) out[(size_t)k * n + e] = R[k];
+}
+
 // member p of the flattened range: off[p] <= x < off[p + 1]
 template <class I>
 __device__ __forceinline__ int member_of(const I* off, int count, I x) {
@@ -719,6 +816,10 @@ void launch_batch(const BatchProblem* probs, const int* order, int count, int n_
     launch_k<512>(probs, order, count, n_coop, words, bad, params, tune, grid, smem, res, st);
   else
     launch_k<256>(probs, order, count, n_coop, words, bad, params, tune, grid, smem, res, st);
+}
+
+void launch_soa_rows(const int2* blist, int n, const float* rows, float* out, cudaStream_t st) {
+  if (n > 0) k_soa_rows<<<(n + 255) / 256, 256, 0, st>>>(blist, n, rows, out);
 }
 
 void launch_tile_xy(const Layout& L, const int* active, int n, unsigned* xy, cudaStream_t st) {

@@ -13,10 +13,18 @@ struct BatchLevel {
   const uint16_t* code;
   const int* tile_base;
   const float* rows;           // fp32 boundary rows
+  const float* srows;          // the listed nodes' rows by coefficient: [k n_bnd + e]
   const unsigned* xy;          // active tiles' first nodes, i0 | j0 << 16
   int n_active;
   const int2* blist;           // boundary nodes {padded offset, row}, grouped by colour
   int boff[5];                 // colour group offsets into blist
+  // shared-memory window of the eta phases (win_n = 0: none, the phases run
+  // in global memory): win[k] the padded offset of window node k (the
+  // boundary nodes and their neighbours); wslot[10 e + s] the window index
+  // of stencil position s (0..8, row order) of blist entry e
+  const int* win;
+  const uint16_t* wslot;
+  int win_n;
   float* u;                    // iterate (in place)
   float* F;                    // right-hand side
   float* scr;                  // residual scratch (zero outside the active tiles)
@@ -89,6 +97,8 @@ void launch_batch(const BatchProblem* probs, const int* order, int count, int n_
 cudaError_t configure_batch(size_t smem);
 // clusters of tune.cluster blocks that can be resident at once (0 if none)
 int batch_max_clusters(const BatchTune& tune, size_t smem);
+// out[k n + e] = rows[blist[e].y * MG_ROW + k] (n list entries)
+void launch_soa_rows(const int2* blist, int n, const float* rows, float* out, cudaStream_t st);
 // xy[k] = i0 | j0 << 16 of tile active[k] of layout L
 void launch_tile_xy(const Layout& L, const int* active, int n, unsigned* xy, cudaStream_t st);
 // builds blist / boff of one level from its codes (one block)
