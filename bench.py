@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--profile-batch", action="store_true",
                     help="setup and two solves of the batched workload, untimed (for ncu)")
+    ap.add_argument("--batch-shape", default="",
+                    help="threads,first_group,cluster,coop_min_dof for --profile-batch")
     return ap.parse_args()
 
 
@@ -93,7 +95,7 @@ def measured_peaks():
 
 # source file of each fine-level kernel class
 KERNEL_SOURCE = {"sweep": "sweep32.cu", "restrict": "cycle.cu", "prolong": "cycle.cu",
-                 "residual": "cycle.cu", "update": "cycle.cu"}
+                 "residual": "cycle.cu", "update": "cycle.cu", "batch": "batch.cu"}
 
 
 def profile_traffic(kernel_tag, kind):
@@ -469,6 +471,9 @@ def run_batched(args, dev, flush):
             S.close()
         seq[prec] = {"value": ndof / (tot_ms / 1e3), "unit": UNIT, "ms": tot_ms}
     sizes = sorted({p.N for p in ps})
+    peak, peak_src = measured_peaks()
+    traffic = profile_traffic("batch_k_batch_256members", "batch") if len(ps) == 256 else None
+    per_step_s = sum(ms) / args.steps / 1e3
     return {
         "workload": f"batch of {len(ps)} seeded geometries (ellipses, flowers k=3..7), "
                     f"N in {sizes}, random Fourier f, g=0",
@@ -481,6 +486,14 @@ def run_batched(args, dev, flush):
         "timing": "CUDA events around the graph launch on the batch's stream; L2 flushed "
                   "(512 MB write) between steps",
         "graph_kernels_per_step": 4,
+        "roofline": {"bound": "latency", "kernel": "k_batch (persistent)",
+                     "dram_traffic_per_step": traffic,
+                     "dram_gbs": traffic / per_step_s / 1e9 if traffic else None,
+                     "hbm_peak_gbs": peak,
+                     "frac_of_hbm": traffic / per_step_s / 1e9 / peak if traffic else None,
+                     "note": "DRAM bytes from the committed ncu summary "
+                             "(profiles/batch_k_batch_256members.md) over this run's step time; "
+                             f"{peak_src} HBM peak"},
         "sequential_mg_solve_mixed": seq["mixed"],
         "sequential_mg_solve_fp64": seq["fp64"],
         "batched_over_sequential_fp64": value / seq["fp64"]["value"],
@@ -489,13 +502,15 @@ def run_batched(args, dev, flush):
 
 
 def profile_batch(args):
-    """Setup and two solves of the batched workload (default launch shape),
-    untimed: the program batched-kernel profiler captures run."""
+    """Setup and two solves of the batched workload (default launch shape, or
+    --batch-shape), untimed: the program batched-kernel profiler captures run."""
     import torch
     from paper_2505_05105_gb300 import ghostmg
     ghostmg.load()
     ps = batch_members(args.batch_count)
     B = ghostmg.BatchSolver(ps)
+    if args.batch_shape:
+        B.set_shape(*(int(x) for x in args.batch_shape.split(",")))
     f = torch.from_numpy(B.pack([p.f for p in ps])).cuda()
     g = torch.from_numpy(B.pack([p.g for p in ps])).cuda()
     u = torch.zeros(B.total, dtype=torch.float64, device="cuda")

@@ -318,7 +318,9 @@ typedef struct {
                          cluster, each block on its own SM (cluster > 1) */
 } mg_batch_shape;
 
-/* Sets the launch shape (default 512 threads, first group 4, no clusters).
+/* Sets the launch shape (default 1024 threads, first group 4, clusters of 2
+ * for members above 8192 DOFs; 512 threads without clusters where that
+ * shape cannot be resident).
  * MG_ERR_INVALID_ARG for values outside the lists above or a shape that
  * cannot be resident on the device (the previous shape is kept). */
 int mg_batch_set_shape(mg_batch b, const mg_batch_shape* shape);

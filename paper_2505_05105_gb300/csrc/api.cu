@@ -1211,7 +1211,7 @@ struct mg_batch_ctx {
   size_t smem = 0;
   int grid = 0;
   int n_coop = 0;
-  BatchTune tune{512, 4, 1, 0};
+  BatchTune tune{1024, 4, 2, 8192};
   std::vector<int> n_dof, n_top;    // per member
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1531,6 +1531,10 @@ int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levels
   MG_CUDA_TRY(cudaStreamSynchronize(b->st));
   b->smem = smem + kSmemSlack;
   MG_CUDA_TRY(configure_batch(b->smem));
+  const int rc = batch_capture(b);
+  if (rc != MG_ERR_INVALID_ARG) return rc;
+  // the default shape does not fit on this device: one block per member
+  b->tune = BatchTune{512, 4, 1, 0};
   return batch_capture(b);
 }
 
