@@ -24,6 +24,13 @@ Readings where the paper is silent or garbled (each restated in the design doc):
   is garbled).
 * f and g_D enter through their Q1 interpolants of nodal values, so
   F = M f + G g exactly (M: mass on the active region, G: boundary load).
+* Mixed boundary conditions (Eq. poisson_model_prob with Gamma_N non-empty):
+  each cut cell's piece of the boundary is wholly Dirichlet or wholly
+  Neumann, as a per-cell mask says.  A Neumann cut cell contributes only its
+  volume term to a_h (no Nitsche terms, Eq. disc_bil_form sums them over
+  K cap Gamma_D) and its boundary mass to the load: with the Q1 interpolant
+  of nodal g_N, int_{K cap Gamma_N} g_N phi_i = (Nk g_N)_i, Nk_ij =
+  int_{K cap Gamma} phi_i phi_j (Eq. disc_rhs).  F = M f + G g_D + N g_N.
 
 Pins (tests/test_oracle_*.py): Q1 stiffness closed form and stencil 8/3, -1/3;
 the 1D matrices of Eq. ls1dA / ls1dF on a straight cut; Eq. c_triangle vs the
@@ -32,7 +39,12 @@ polygon areas against closed forms and pi r^2; symmetry and positive
 definiteness by dense eigenvalues; second-order convergence on manufactured
 solutions; the adjoint gradients against central differences of the forward
 solve (exact up to rounding for the quadratic losses used) and their support
-(zero off the DOFs, dL/dg zero away from cut cells).
+(zero off the DOFs, dL/dg zero away from cut cells).  Neumann cells: a
+straight cut reduces to the Neumann end of the 1D system (Eq. ls1dA, the
+theta_2 block, and Eq. ls1dF, F^N); a patch test with a straight Neumann
+side reproduces bilinear harmonic solutions exactly; second-order
+convergence on the annulus with Dirichlet inner and Neumann outer circle
+(Sec. 5.3) and on the leaf with mixed data.
 """
 from __future__ import annotations
 
@@ -356,25 +368,34 @@ class CutCell:
     lam: float
     Ke: np.ndarray   # a_h element matrix
     Mk: np.ndarray   # mass on K cap Omega_h
-    Gk: np.ndarray   # boundary load: lam phi_i phi_j - (n.grad phi_i) phi_j
+    Gk: np.ndarray   # Dirichlet load: lam phi_i phi_j - (n.grad phi_i) phi_j
     ints: CellIntegrals
+    neumann: bool = False
+    Nk: np.ndarray = None   # Neumann load: phi_i phi_j on K cap Gamma_h
 
 
-def cut_cell(psi4, ic, jc, x0, y0, h, gamma) -> CutCell:
+def cut_cell(psi4, ic, jc, x0, y0, h, gamma, neumann=False) -> CutCell:
     """Element matrices of cut cell (ic, jc).  The integrals are invariant
     under translation, so they are taken in cell-local coordinates (origin
     at the cell's lower-left corner, side h): absolute coordinates would add
-    cancellation of order |x0 + ic h| / (size of the cut region)."""
+    cancellation of order |x0 + ic h| / (size of the cut region).
+    neumann: the cell's boundary piece belongs to Gamma_N."""
     config, pieces, thetas = cut_pieces(psi4)
     ints = cell_integrals(pieces, 0.0, 0.0, h)
     C = stabilisation_C(config, psi4, pieces, ints, 0.0, 0.0, h)
     lam = gamma * C
+    if neumann:
+        # Eq. disc_bil_form has no boundary term on Gamma_N; Eq. disc_rhs
+        # has int g_N phi_i over K cap Gamma_N
+        return CutCell(ic, jc, config, thetas, C, lam, ints.S.copy(), ints.Mp.copy(),
+                       np.zeros((4, 4)), ints, True, ints.Ms.copy())
     # a_h(phi_j, phi_i) on K: grad.grad + lam phi phi - (n.grad phi_j) phi_i
     #                          - (n.grad phi_i) phi_j           (Eq. disc_bil_form)
     Ke = ints.S + lam * ints.Ms - ints.Bn - ints.Bn.T
     # l_h with g_h = sum_j g_j phi_j: lam g phi_i - (n.grad phi_i) g  (Eq. disc_rhs)
     Gk = lam * ints.Ms - ints.Bn.T
-    return CutCell(ic, jc, config, thetas, C, lam, Ke, ints.Mp.copy(), Gk, ints)
+    return CutCell(ic, jc, config, thetas, C, lam, Ke, ints.Mp.copy(), Gk, ints, False,
+                   np.zeros((4, 4)))
 
 
 def interior_cell_matrices(h):
@@ -402,13 +423,18 @@ class System:
     M: sp.csr_matrix
     G: sp.csr_matrix
     cut: list               # [CutCell]
+    Gn: sp.csr_matrix = None   # Neumann load (None: all of Gamma is Dirichlet)
 
     @property
     def n_nodes(self):
         return (self.N + 1) ** 2
 
-    def rhs(self, f, g):
-        return self.M @ np.ravel(f) + self.G @ np.ravel(g)
+    def rhs(self, f, g, gN=None):
+        """F = M f + G g_D (+ N g_N), Eq. disc_rhs with Q1 interpolants."""
+        F = self.M @ np.ravel(f) + self.G @ np.ravel(g)
+        if gN is not None and self.Gn is not None:
+            F = F + self.Gn @ np.ravel(gN)
+        return F
 
 
 def cell_nodes(ic, jc, N):
@@ -416,13 +442,16 @@ def cell_nodes(ic, jc, N):
     return np.array([k0, k0 + 1, k0 + N + 1, k0 + N + 2])
 
 
-def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75) -> System:
-    """A, M, G over all (N+1)^2 nodes (Eq. disc_bil_form, Eq. disc_rhs)."""
+def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75, neumann_mask=None) -> System:
+    """A, M, G over all (N+1)^2 nodes (Eq. disc_bil_form, Eq. disc_rhs).
+    neumann_mask: (N, N) cells [jc, ic], nonzero where a cut cell's boundary
+    piece belongs to Gamma_N (ignored on other cells); None: all Dirichlet."""
+    nm = None if neumann_mask is None else np.asarray(neumann_mask).reshape(N, N) != 0
     psi_s = snap(np.asarray(psi, dtype=np.float64).reshape(N + 1, N + 1), h, alpha)
     cls = cell_classes(psi_s)
     S_int, M_int = interior_cell_matrices(h)
 
-    rows, cols, a_val, m_val, g_val = [], [], [], [], []
+    rows, cols, a_val, m_val, g_val, n_val = [], [], [], [], [], []
     jj, ii = np.nonzero(cls == INTERNAL)
     if len(ii):
         nodes = np.stack([cell_nodes(i, j, N) for i, j in zip(ii, jj)])   # (n, 4)
@@ -431,10 +460,12 @@ def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75) -> System:
         a_val.append(np.tile(S_int.ravel(), len(ii)))
         m_val.append(np.tile(M_int.ravel(), len(ii)))
         g_val.append(np.zeros(16 * len(ii)))
+        n_val.append(np.zeros(16 * len(ii)))
     cuts = []
     jj, ii = np.nonzero(cls == CUT)
     for i, j in zip(ii, jj):
-        cc = cut_cell(cell_corner_psi(psi_s, i, j), int(i), int(j), x0, y0, h, gamma)
+        neu = bool(nm[j, i]) if nm is not None else False
+        cc = cut_cell(cell_corner_psi(psi_s, i, j), int(i), int(j), x0, y0, h, gamma, neu)
         cuts.append(cc)
         nodes = cell_nodes(i, j, N)
         rows.append(np.repeat(nodes, 4))
@@ -442,21 +473,24 @@ def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75) -> System:
         a_val.append(cc.Ke.ravel())
         m_val.append(cc.Mk.ravel())
         g_val.append(cc.Gk.ravel())
+        n_val.append(cc.Nk.ravel())
     n = (N + 1) ** 2
     r = np.concatenate(rows) if rows else np.zeros(0, int)
     c = np.concatenate(cols) if cols else np.zeros(0, int)
     mk = lambda v: sp.csr_matrix((np.concatenate(v) if v else np.zeros(0), (r, c)), shape=(n, n))
     A, M, G = mk(a_val), mk(m_val), mk(g_val)
+    Gn = mk(n_val) if nm is not None else None
     dof = np.zeros(n, dtype=bool)
     active = cls != EXTERNAL
     jj, ii = np.nonzero(active)
     for d in (0, 1, N + 1, N + 2):
         dof[ii + jj * (N + 1) + d] = True
-    return System(N, x0, y0, h, gamma, alpha, psi_s, cls, dof, A, M, G, cuts)
+    return System(N, x0, y0, h, gamma, alpha, psi_s, cls, dof, A, M, G, cuts, Gn)
 
 
 def assemble_problem(prob, gamma=2.0, alpha=1.75) -> System:
-    return assemble(prob.psi, prob.N, prob.x0, prob.y0, prob.h, gamma, alpha)
+    return assemble(prob.psi, prob.N, prob.x0, prob.y0, prob.h, gamma, alpha,
+                    getattr(prob, "neumann_mask", None))
 
 
 def direct_solve(system: System, F: np.ndarray, refine: int = 4) -> np.ndarray:

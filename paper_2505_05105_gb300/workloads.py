@@ -23,6 +23,12 @@ Problems
 * ``paper_circle``, ``paper_flower``, ``paper_hourglass`` - the level sets of
   the 2D experiments of Sec. 5.3 (homogeneous data; used for convergence
   factors).
+* ``annulus``, ``leaf``, ``half_disc`` - mixed Dirichlet / Neumann problems:
+  the annulus and leaf of Sec. 5.3 with a manufactured solution, and a disc
+  cut by a straight Neumann side (patch tests).  They carry a per-cell
+  ``neumann_mask`` (N, N) and nodal Neumann data ``gN`` (the outward normal
+  derivative of u, the normal extended off the boundary from the level set
+  that defines that part of it).
 """
 from __future__ import annotations
 
@@ -44,6 +50,8 @@ class Problem:
     g: np.ndarray
     u_exact: Optional[np.ndarray] = None
     meta: dict = field(default_factory=dict)
+    neumann_mask: Optional[np.ndarray] = None   # (N, N) cells [jc, ic], uint8
+    gN: Optional[np.ndarray] = None             # nodal Neumann data
 
     @property
     def shape(self):
@@ -183,3 +191,84 @@ def vertical_line(N: int, theta: float) -> Problem:
     z = np.zeros_like(psi)
     return Problem("vertical_line", N, 0.0, 0.0, h, psi, z, z.copy(),
                    meta={"theta": theta})
+
+
+# --- mixed Dirichlet / Neumann problems ----------------------------------------
+
+def cell_centres(N: int, x0: float, y0: float, h: float):
+    """Cell centres Xc[jc, ic], Yc[jc, ic]."""
+    t = np.arange(N, dtype=np.float64) + 0.5
+    return np.meshgrid(x0 + t * h, y0 + t * h, indexing="xy")
+
+
+def _sin3cos2(X, Y):
+    u = np.sin(3 * X) * np.cos(2 * Y)
+    ux = 3 * np.cos(3 * X) * np.cos(2 * Y)
+    uy = -2 * np.sin(3 * X) * np.sin(2 * Y)
+    return u, ux, uy, 13.0 * u
+
+
+def annulus(N: int = 64, r1: float = 0.5, r2: float = 0.8) -> Problem:
+    """Annulus r1 < r < r2 in [-1, 1]^2 (Sec. 5.3): Dirichlet on the inner
+    circle, Neumann on the outer one; psi = max(r1^2 - r^2, r^2 - r2^2).
+    u = sin 3x cos 2y, g_D = u, g_N = grad u . (x, y) / r.  A cut cell is
+    Neumann when its centre lies outside the middle radius (r1 + r2) / 2."""
+    h = 2.0 / N
+    X, Y = node_grid(N, -1.0, -1.0, h)
+    r2n = X * X + Y * Y
+    psi = np.maximum(r1 * r1 - r2n, r2n - r2 * r2)
+    u, ux, uy, f = _sin3cos2(X, Y)
+    r = np.sqrt(r2n)
+    gN = (ux * X + uy * Y) / np.where(r > 0, r, 1.0)
+    Xc, Yc = cell_centres(N, -1.0, -1.0, h)
+    mask = (np.hypot(Xc, Yc) > 0.5 * (r1 + r2)).astype(np.uint8)
+    return Problem("annulus", N, -1.0, -1.0, h, psi, f, u.copy(), u,
+                   meta={"r1": r1, "r2": r2}, neumann_mask=mask, gN=gN)
+
+
+def leaf(N: int = 64) -> Problem:
+    """Leaf of Sec. 5.3 in [-1, 1]^2: the intersection of two discs of radius
+    0.7 centred at (-0.25 cos(pi/4), 0) and (0.25 sin(pi/4), 0), psi =
+    max(R1 - 0.7, R2 - 0.7) (the paper prints R_1 twice; the second is read
+    as R_2).  Dirichlet where x >= 0, Neumann where x < 0: a cut cell is
+    Neumann when its centre has x < 0 and the second disc's level set is the
+    larger one at all four of its corners, so that its boundary piece lies on
+    that disc alone; the cells at the two corners of the leaf (on x = 0,
+    where the discs meet) stay Dirichlet.  u = sin 3x cos 2y, g_N = grad u . n
+    with n the unit radial direction of the disc whose level set is the
+    larger at the node."""
+    h = 2.0 / N
+    X, Y = node_grid(N, -1.0, -1.0, h)
+    xa, xb = -0.25 * np.cos(np.pi / 4), 0.25 * np.sin(np.pi / 4)
+    R1, R2 = np.hypot(X - xa, Y), np.hypot(X - xb, Y)
+    psi = np.maximum(R1 - 0.7, R2 - 0.7)
+    u, ux, uy, f = _sin3cos2(X, Y)
+    first = R1 - 0.7 >= R2 - 0.7
+    cx = np.where(first, xa, xb)
+    R = np.where(first, R1, R2)
+    gN = (ux * (X - cx) + uy * Y) / np.where(R > 0, R, 1.0)
+    Xc, _ = cell_centres(N, -1.0, -1.0, h)
+    d2 = ~first
+    on2 = d2[:-1, :-1] & d2[:-1, 1:] & d2[1:, :-1] & d2[1:, 1:]
+    mask = ((Xc < 0.0) & on2).astype(np.uint8)
+    return Problem("leaf", N, -1.0, -1.0, h, psi, f, u.copy(), u,
+                   neumann_mask=mask, gN=gN)
+
+
+def half_disc(N: int = 64, c: float = 0.1537) -> Problem:
+    """The disc of circle64 cut by the straight side x = c: psi =
+    max(|x - (0.02, 0.01)| - 0.39, x - c) in [-0.5, 0.5]^2.  A cut cell is
+    Neumann when the straight side's term is the larger one at all four of
+    its corners (its discrete boundary is then exactly on a vertical line,
+    outward normal +x).  Data for u = exp(x) sin y: g_D = u, g_N = du/dx."""
+    x0, y0, h = _unit_box(N)
+    X, Y = node_grid(N, x0, y0, h)
+    circ = np.sqrt((X - 0.02) ** 2 + (Y - 0.01) ** 2) - 0.39
+    line = X - c
+    psi = np.maximum(circ, line)
+    u = np.exp(X) * np.sin(Y)
+    ln = line >= circ
+    mask = (ln[:-1, :-1] & ln[:-1, 1:] & ln[1:, :-1] & ln[1:, 1:]).astype(np.uint8)
+    return Problem("half_disc", N, x0, y0, h, psi, np.zeros_like(u), u.copy(), u,
+                   meta={"c": c}, neumann_mask=mask, gN=u.copy())
+
