@@ -53,7 +53,8 @@ enum {
   MG_ERR_OUT_OF_MEMORY = 9   /* device allocation failed */
 };
 
-enum { MG_BC_DIRICHLET = 0 };     /* weak Dirichlet on the whole of {psi = 0} */
+enum { MG_BC_DIRICHLET = 0,       /* weak Dirichlet on the whole of {psi = 0} */
+       MG_BC_MIXED = 1 };         /* Dirichlet / Neumann by a per-cell mask */
 enum { MG_LAMBDA_LOCAL = 0 };     /* lambda_K = gamma C(K) per cut cell (Sec. 5.2) */
 enum { MG_FP64 = 0,               /* fp64 V-cycles */
        MG_MIXED = 1 };            /* fp32 V-cycle inside fp64 iterative refinement */
@@ -71,8 +72,19 @@ typedef struct {
   int coarsest_cells;
 } mg_grid;
 
-/* Boundary conditions.  kind must be MG_BC_DIRICHLET and neumann_mask NULL:
- * the Neumann term of Eq. disc_rhs is not implemented (MG_ERR_UNIMPLEMENTED). */
+/* Boundary conditions (Eq. poisson_model_prob: u = g_D on Gamma_D,
+ * n . grad u = g_N on Gamma_N).
+ *   kind = MG_BC_DIRICHLET, neumann_mask = NULL: all of {psi = 0} is
+ *     Dirichlet, imposed weakly (Nitsche terms of Eq. disc_bil_form).
+ *   kind = MG_BC_MIXED: neumann_mask holds n_cells^2 bytes (host or device,
+ *     read during mg_setup only), cell (ic, jc) at ic + jc n_cells; a cut
+ *     cell with a nonzero byte has its piece of the boundary in Gamma_N: it
+ *     keeps only its volume stiffness (Eq. disc_bil_form has no boundary
+ *     term on Gamma_N) and adds int_{K cap Gamma_N} g_N phi_i to the load
+ *     (Eq. disc_rhs, g_N through its Q1 interpolant of nodal values, see
+ *     mg_solve_bc).  Bytes of other cells are ignored.  At least one cut
+ *     cell must stay Dirichlet (otherwise A is singular: MG_ERR_NOT_SPD).
+ * Any other combination is MG_ERR_INVALID_ARG. */
 typedef struct {
   int kind;
   const uint8_t* neumann_mask;
@@ -145,6 +157,16 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
 int mg_solve(mg_handle h, const double* f, const double* g, double* u, double tol,
              mg_info* info);
 
+/* mg_solve with Neumann data: F = M f + G g_D + N g_N (Eq. disc_rhs), N
+ * the Neumann cut cells' boundary mass.  g_D and g_N are nodal arrays like
+ * f ((N+1)^2 doubles, device or host); g_N may be NULL (g_N = 0) and is
+ * ignored on a handle without Neumann cells; only its values at vertices of
+ * Neumann cut cells matter (an extension of the Neumann data off Gamma_N,
+ * e.g. grad u . n with n extended smoothly).  Errors as mg_solve (NaN/Inf in
+ * g_N: MG_ERR_INVALID_ARG). */
+int mg_solve_bc(mg_handle h, const double* f, const double* g_D, const double* g_N, double* u,
+                double tol, mg_info* info);
+
 /* Adjoint of mg_solve for a loss L(u): solves A w = dL/du (A is symmetric,
  * Sec. 4.1) to the tolerance of the last mg_solve (1e-10 if none), then
  * dL/df = M^T w and dL/dg = G^T w (F is linear in f and g, Eq. disc_rhs).
@@ -189,6 +211,8 @@ int mg_export_cut_cells(mg_handle h, int max_cells, int* cells, double* data, in
 
 /* F = M f + G g on the fine level (Eq. disc_rhs), zero off the DOFs. */
 int mg_rhs(mg_handle h, const double* f, const double* g, double* F);
+/* F = M f + G g_D + N g_N (as mg_solve_bc; g_N may be NULL). */
+int mg_rhs_bc(mg_handle h, const double* f, const double* g_D, const double* g_N, double* F);
 
 /* Exactly k cycles from u with right-hand side F (no stopping test):
  * precision MG_FP64 runs k V-cycles; MG_MIXED runs k refinement steps (fp64
@@ -289,7 +313,8 @@ typedef struct {
  * MG_MIXED (or stab NULL).  cuda_stream: the caller's stream; the batch
  * orders its work after the work queued there when a call starts, and runs
  * on a stream of its own (a graph cannot be captured on the legacy
- * stream).  Errors as mg_setup, and MG_ERR_UNIMPLEMENTED for MG_FP64. */
+ * stream).  Errors as mg_setup, and MG_ERR_UNIMPLEMENTED for MG_FP64 and
+ * for MG_BC_MIXED (a Neumann mask would be per member). */
 int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double* levelsets,
                    const mg_bc* bc, const mg_stab* stab, void* cuda_stream);
 

@@ -81,7 +81,9 @@ struct mg_ctx {
   unsigned* d_err = nullptr;
   double* d_norms = nullptr;     // 8 slots of (max, sum)
   double* h_norms = nullptr;     // pinned mirror
-  double* stage[3] = {nullptr, nullptr, nullptr};
+  double* stage[4] = {nullptr, nullptr, nullptr, nullptr};
+  const uint8_t* nmask_in = nullptr;   // caller's Neumann cell mask (setup only)
+  double* Nk = nullptr;          // Neumann load per cut cell (null: all Dirichlet)
   std::vector<void*> allocs;
   double last_tol = 1e-10;
   int tail_level = -1;           // first level run by the single-block tail kernel
@@ -709,8 +711,21 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     TRY(dalloc(c, &c->Gk, (size_t)v.n_cut * 16));
     TRY(dalloc(c, &c->Cl, (size_t)v.n_cut * 4));
     TRY(dalloc(c, &c->cfg, (size_t)v.n_cut));
+    const uint8_t* nmask = nullptr;
+    if (c->nmask_in) {
+      // the caller's cell mask (host or device), read only by this launch
+      if (is_device_ptr(c->nmask_in)) {
+        nmask = c->nmask_in;
+      } else {
+        uint8_t* d;
+        TRY(dalloc(c, &d, (size_t)N * N));
+        MG_CUDA_TRY(cudaMemcpyAsync(d, c->nmask_in, (size_t)N * N, cudaMemcpyHostToDevice, c->st));
+        nmask = d;
+      }
+      TRY(dalloc(c, &c->Nk, (size_t)v.n_cut * 16));
+    }
     launch_cut_cells(c->psi_s, N, c->h, c->stab.gamma, v.cut_list, v.n_cut, v.Ke, c->Mk, c->Gk,
-                     c->Cl, c->cfg, c->st);
+                     c->Cl, c->cfg, nmask, c->Nk, c->st);
     TRY(build_nodes(c, v));
   }
   // coarse levels by element-wise Galerkin products
@@ -853,7 +868,11 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
   mg_stab s;
   mg_default_stab(&s);
   if (stab) s = *stab;
-  if (bc && (bc->kind != MG_BC_DIRICHLET || bc->neumann_mask)) return MG_ERR_UNIMPLEMENTED;
+  if (bc) {
+    if (bc->kind == MG_BC_DIRICHLET && bc->neumann_mask) return MG_ERR_INVALID_ARG;
+    if (bc->kind == MG_BC_MIXED && !bc->neumann_mask) return MG_ERR_INVALID_ARG;
+    if (bc->kind != MG_BC_DIRICHLET && bc->kind != MG_BC_MIXED) return MG_ERR_INVALID_ARG;
+  }
   mg_grid g = *grid;
   if (g.coarsest_cells <= 0) g.coarsest_cells = 8;
   if (!pow2(g.n_cells) || g.n_cells < 8 || g.n_cells > 32768) return MG_ERR_INVALID_ARG;
@@ -874,8 +893,10 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
   c->stab = s;
   c->N = g.n_cells;
   c->h = g.h;
+  c->nmask_in = (bc && bc->kind == MG_BC_MIXED) ? bc->neumann_mask : nullptr;
   auto t0 = std::chrono::steady_clock::now();
   int rc = setup_impl(c, levelset);
+  c->nmask_in = nullptr;
   if (rc != MG_OK) {
     mg_destroy(c);
     return rc;
@@ -910,6 +931,11 @@ static int fill_info(mg_ctx* c, mg_info* info) {
 }
 
 int mg_solve(mg_handle c, const double* f, const double* g, double* u, double tol, mg_info* info) {
+  return mg_solve_bc(c, f, g, nullptr, u, tol, info);
+}
+
+int mg_solve_bc(mg_handle c, const double* f, const double* g, const double* gN, double* u,
+                double tol, mg_info* info) {
   if (!c || !f || !g || !u || !(tol >= 0.0)) return MG_ERR_INVALID_ARG;
   if (info) memset(info, 0, sizeof(*info));
   c->last_tol = tol;
@@ -919,6 +945,9 @@ int mg_solve(mg_handle c, const double* f, const double* g, double* u, double to
   TRY(stage_in(c, 0, f, sf));
   TRY(stage_in(c, 1, g, sg));
   TRY(stage_in(c, 2, u, su));
+  Staged sn;
+  const bool neu = gN != nullptr && c->Nk != nullptr;
+  if (neu) TRY(stage_in(c, 3, gN, sn));
   size_t m = (size_t)(c->N + 1) * (c->N + 1);
   // d_norms[0..1]: ||F||; the word at d_norms[2]: u has a nonzero DOF value
   unsigned* d_nz = reinterpret_cast<unsigned*>(c->d_norms + 2);
@@ -926,7 +955,9 @@ int mg_solve(mg_handle c, const double* f, const double* g, double* u, double to
   {
     Launch k(c, MG_PROF_IO, 3);
     launch_check_finite2(sf.dev, sg.dev, m, c->d_err, c->st);
-    RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
+    if (neu) launch_check_finite2(sn.dev, sn.dev, m, c->d_err, c->st);
+    RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
+               neu ? sn.dev : nullptr};
     launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
     v.cur64 = 0;
     launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st, d_nz);
@@ -961,16 +992,23 @@ int mg_solve(mg_handle c, const double* f, const double* g, double* u, double to
 }
 
 int mg_rhs(mg_handle c, const double* f, const double* g, double* F) {
+  return mg_rhs_bc(c, f, g, nullptr, F);
+}
+
+int mg_rhs_bc(mg_handle c, const double* f, const double* g, const double* gN, double* F) {
   if (!c || !f || !g || !F) return MG_ERR_INVALID_ARG;
   Level& v = c->lev[0];
-  Staged sf, sg;
+  Staged sf, sg, sn;
   TRY(stage_in(c, 0, f, sf));
   TRY(stage_in(c, 1, g, sg));
+  const bool neu = gN != nullptr && c->Nk != nullptr;
+  if (neu) TRY(stage_in(c, 3, gN, sn));
   double* Fd;
   bool Fh;
   TRY(stage_out(c, 2, F, &Fd, &Fh));
   MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
-  RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
+  RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
+             neu ? sn.dev : nullptr};
   launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
   launch_unpack(v.L, v.code, v.F64, Fd, c->st);
   TRY(finish_out(c, F, Fd, Fh));
@@ -1553,6 +1591,7 @@ int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double*
   else s.precision = MG_MIXED;
   if (s.precision == MG_FP64) return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
+  if (bc && bc->kind == MG_BC_MIXED) return MG_ERR_UNIMPLEMENTED;
   mg_batch_ctx* b = new mg_batch_ctx();
   b->user_st = (cudaStream_t)cuda_stream;
   b->count = count;

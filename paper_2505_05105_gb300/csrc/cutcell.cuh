@@ -6,6 +6,9 @@
 //   Ke = S + (lambda h) Ms - Bn - Bn^T       (Eq. disc_bil_form on K)
 //   Gk = (lambda h) Ms - Bn^T                 (Eq. disc_rhs boundary load)
 //   Mk = h^2 Mref                             (mass of K cap Omega_h)
+// and for a cell whose boundary piece is Neumann (no boundary terms in
+// Eq. disc_bil_form; the load int g_N phi_i in Eq. disc_rhs):
+//   Ke = S,  Gk = 0,  Nk = h Ms
 // with S_ij = int_P grad phi_i . grad phi_j, Mref_ij = int_P phi_i phi_j over
 // the cut polygon P, and on the boundary segments (reference length, outward
 // normal n) Ms_ij = int phi_i phi_j, Bn_ij = int (n . grad phi_j) phi_i.
@@ -213,14 +216,15 @@ __device__ inline double c_triangle_h(double t1, double t2) {
 }
 
 struct CellOut {
-  double Ke[16], Gk[16], Mk[16];
+  double Ke[16], Gk[16], Mk[16], Nk[16];
   double C, lam;
   double area, length;
   int config;
 };
 
 // Element matrices of one cut cell.  psi: corner values v0..v3 (snapped).
-__device__ inline void cut_cell_matrices(const double psi[4], double h, double gamma, CellOut& o) {
+__device__ inline void cut_cell_matrices(const double psi[4], double h, double gamma, CellOut& o,
+                                         bool neumann = false) {
   Geom g;
   build_geometry(psi, g);
   o.config = g.config;
@@ -297,8 +301,15 @@ __device__ inline void cut_cell_matrices(const double psi[4], double h, double g
   double lamh = gamma * Ch;
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
-      o.Ke[i * 4 + j] = S[i][j] + lamh * Ms[i][j] - Bn[i][j] - Bn[j][i];
-      o.Gk[i * 4 + j] = lamh * Ms[i][j] - Bn[j][i];
+      if (neumann) {
+        o.Ke[i * 4 + j] = S[i][j];
+        o.Gk[i * 4 + j] = 0.0;
+        o.Nk[i * 4 + j] = h * Ms[i][j];
+      } else {
+        o.Ke[i * 4 + j] = S[i][j] + lamh * Ms[i][j] - Bn[i][j] - Bn[j][i];
+        o.Gk[i * 4 + j] = lamh * Ms[i][j] - Bn[j][i];
+        o.Nk[i * 4 + j] = 0.0;
+      }
       o.Mk[i * 4 + j] = h * h * Mr[i][j];
     }
   // exact symmetry of Ke (the two halves are summed in different orders)

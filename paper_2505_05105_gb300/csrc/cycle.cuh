@@ -19,7 +19,9 @@ struct RhsArgs {
   const uint8_t* cls;        // n x n cell classes
   const int* cell_cut;       // n x n, index into the cut list or -1
   const double* Mk;          // 16 per cut cell, mass on K cap Omega_h
-  const double* Gk;          // 16 per cut cell, boundary load
+  const double* Gk;          // 16 per cut cell, Dirichlet load (0 on Neumann cells)
+  const double* Nk = nullptr;  // 16 per cut cell, Neumann load (null: no Neumann cells)
+  const double* gN = nullptr;  // nodal Neumann data, user layout (null: g_N = 0)
 };
 
 // TMA descriptors of a level's two u buffers in one precision (band kernel box)

@@ -81,6 +81,11 @@ __device__ __forceinline__ double rhs_tile(const RhsArgs& a, int t, const double
           const size_t k0 = (size_t)jc * W + ic;
           const size_t vk[4] = {k0, k0 + 1, k0 + W, k0 + W + 1};
           for (int b = 0; b < 4; ++b) s += Mk[b] * fb[b] + Gk[b] * g[vk[b]];
+          if (a.gN != nullptr && a.Nk != nullptr) {
+            // Neumann load of the cell (zero on Dirichlet cells)
+            const double* Nk = a.Nk + (size_t)a.cell_cut[c] * 16 + av * 4;
+            for (int b = 0; b < 4; ++b) s += Nk[b] * a.gN[vk[b]];
+          }
         }
       }
     }

@@ -27,6 +27,7 @@ MG_ERR_UNIMPLEMENTED = 7
 MG_ERR_INTERNAL = 8
 MG_ERR_OUT_OF_MEMORY = 9
 MG_BC_DIRICHLET = 0
+MG_BC_MIXED = 1
 MG_LAMBDA_LOCAL = 0
 MG_FP64 = 0
 MG_MIXED = 1
@@ -82,6 +83,7 @@ SIGNATURES = {
     "mg_setup": (_I, [ctypes.POINTER(_P), _P, ctypes.POINTER(mg_grid), ctypes.POINTER(mg_bc),
                       ctypes.POINTER(mg_stab), _P]),
     "mg_solve": (_I, [_P, _P, _P, _P, _D, ctypes.POINTER(mg_info)]),
+    "mg_solve_bc": (_I, [_P, _P, _P, _P, _P, _D, ctypes.POINTER(mg_info)]),
     "mg_adjoint": (_I, [_P, _P, _P, _P]),
     "mg_destroy": (None, [_P]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
@@ -91,6 +93,7 @@ SIGNATURES = {
     "mg_export_stencil": (_I, [_P, _I, _P]),
     "mg_export_cut_cells": (_I, [_P, _I, _P, _P, ctypes.POINTER(_I)]),
     "mg_rhs": (_I, [_P, _P, _P, _P]),
+    "mg_rhs_bc": (_I, [_P, _P, _P, _P, _P]),
     "mg_cycles": (_I, [_P, _P, _P, _I, _I]),
     "mg_residual": (_I, [_P, _P, _P, _P, _P]),
     "mg_residual_static": (_I, [_P, _P, _P, _P, _P]),
@@ -184,6 +187,18 @@ def mg_solve(handle: int, f, g, u, tol: float, info: Optional[mg_info] = None,
     return _check(load().mg_solve(handle, _addr(f), _addr(g), _addr(u, True), tol,
                                   ctypes.byref(info) if info is not None else None),
                   "mg_solve", ok)
+
+
+def mg_solve_bc(handle: int, f, gD, gN, u, tol: float, info: Optional[mg_info] = None,
+                ok=(MG_OK,)) -> int:
+    return _check(load().mg_solve_bc(handle, _addr(f), _addr(gD), _addr(gN), _addr(u, True),
+                                     tol, ctypes.byref(info) if info is not None else None),
+                  "mg_solve_bc", ok)
+
+
+def mg_rhs_bc(handle: int, f, gD, gN, F) -> int:
+    return _check(load().mg_rhs_bc(handle, _addr(f), _addr(gD), _addr(gN), _addr(F, True)),
+                  "mg_rhs_bc")
 
 
 def mg_adjoint(handle: int, dLdu, dLdf=None, dLdg=None, ok=(MG_OK,)) -> int:
@@ -325,14 +340,28 @@ class Solver:
     def __init__(self, psi, n_cells: int, x0: float, y0: float, h: float, *,
                  coarsest: int = 8, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
                  nu1: int = 2, nu2: int = 1, precision: str = "fp64", max_cycles: int = 100,
-                 inner: int = 0, stream: int = 0):
+                 inner: int = 0, stream: int = 0, neumann_mask=None):
+        """neumann_mask: (n_cells, n_cells) uint8 cells [jc, ic] (host array,
+        or a device tensor), nonzero where a cut cell's boundary piece is
+        Neumann (MG_BC_MIXED); None: all Dirichlet."""
         self.N = n_cells
         stab = mg_default_stab()
         stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta
         stab.nu1, stab.nu2, stab.max_cycles, stab.inner = nu1, nu2, max_cycles, inner
         stab.precision = {"fp64": MG_FP64, "mixed": MG_MIXED}[precision]
         grid = mg_grid(n_cells, x0, y0, h, coarsest)
-        self.handle = mg_setup(psi, grid, mg_bc(MG_BC_DIRICHLET, None), stab, stream)
+        if neumann_mask is None:
+            bc = mg_bc(MG_BC_DIRICHLET, None)
+        else:
+            if isinstance(neumann_mask, np.ndarray):
+                neumann_mask = np.ascontiguousarray(neumann_mask, dtype=np.uint8)
+                if neumann_mask.size != n_cells * n_cells:
+                    raise ValueError("neumann_mask must have n_cells^2 entries")
+                ptr = neumann_mask.ctypes.data
+            else:
+                ptr = neumann_mask.data_ptr()
+            bc = mg_bc(MG_BC_MIXED, ptr)
+        self.handle = mg_setup(psi, grid, bc, stab, stream)
 
     @classmethod
     def from_problem(cls, prob, **kw):
@@ -342,14 +371,23 @@ class Solver:
     def counts(self):
         return mg_get_counts(self.handle)
 
-    def solve(self, f, g, u, tol: float = 1e-10, allow_not_converged: bool = False) -> mg_info:
+    def solve(self, f, g, u, tol: float = 1e-10, allow_not_converged: bool = False,
+              gN=None) -> mg_info:
+        """g: Dirichlet data; gN: nodal Neumann data (mixed boundary
+        conditions; None = 0)."""
         info = mg_info()
         ok = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
-        mg_solve(self.handle, f, g, u, tol, info, ok)
+        if gN is None:
+            mg_solve(self.handle, f, g, u, tol, info, ok)
+        else:
+            mg_solve_bc(self.handle, f, g, gN, u, tol, info, ok)
         return info
 
-    def rhs(self, f, g, F):
-        mg_rhs(self.handle, f, g, F)
+    def rhs(self, f, g, F, gN=None):
+        if gN is None:
+            mg_rhs(self.handle, f, g, F)
+        else:
+            mg_rhs_bc(self.handle, f, g, gN, F)
         return F
 
     def cycles(self, F, u, k: int, precision: str = "fp64"):

@@ -52,9 +52,14 @@ def test_invalid_setups():
     assert setup_status(p.psi, 64, coarsest=3) == G.MG_ERR_INVALID_ARG
     assert setup_status(p.psi, 64, coarsest=128) == G.MG_ERR_INVALID_ARG
     assert setup_status(p.psi, 64, eta=9) == G.MG_ERR_INVALID_ARG
-    mask = (G.ctypes.c_uint8 * 1)()
-    bc = G.mg_bc(0, G.ctypes.cast(mask, G.ctypes.c_void_p))
-    assert setup_status(p.psi, 64, bc=bc) == G.MG_ERR_UNIMPLEMENTED
+    mask = (G.ctypes.c_uint8 * (64 * 64))()
+    # a mask needs kind MG_BC_MIXED, MG_BC_MIXED needs a mask, unknown kinds
+    bc = G.mg_bc(G.MG_BC_DIRICHLET, G.ctypes.cast(mask, G.ctypes.c_void_p))
+    assert setup_status(p.psi, 64, bc=bc) == G.MG_ERR_INVALID_ARG
+    assert setup_status(p.psi, 64, bc=G.mg_bc(G.MG_BC_MIXED, None)) == G.MG_ERR_INVALID_ARG
+    assert setup_status(p.psi, 64, bc=G.mg_bc(5, None)) == G.MG_ERR_INVALID_ARG
+    bc = G.mg_bc(G.MG_BC_MIXED, G.ctypes.cast(mask, G.ctypes.c_void_p))
+    assert setup_status(p.psi, 64, bc=bc) == G.MG_OK           # all-zero mask
     assert setup_status(p.psi, 64, precision=7) == G.MG_ERR_INVALID_ARG
 
 
