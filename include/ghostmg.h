@@ -103,12 +103,15 @@ typedef struct {
  *                 far, as the number predicted to reach tol (first group 4,
  *                 at most 8); k > 0 = always k.  In MG_MIXED each group is
  *                 one refinement step: fp64 residual, `k` fp32 V-cycles on
- *                 the correction equation (the first from e = 0), u += e. */
+ *                 the correction equation (the first from e = 0), u += e.
+ *   cycle = 1     cycles on each coarse level per visit (Alg. 1, gamma*):
+ *                 1 = V-cycle, 2 = W-cycle (batches: V only). */
 typedef struct {
   double gamma, alpha;
   int eta, nu1, nu2;
   int lambda_mode, precision, max_cycles;
   int inner;
+  int cycle;
 } mg_stab;
 
 /* Result summary of a solve. */

@@ -433,7 +433,9 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
     launch_resid_restrict<T>(op_of<T>(v), P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
                              P<T>::F(w), nullptr, c->st);
   }
-  vcycle<T>(c, l + 1, true);
+  // gamma* = stab.cycle cycles on the coarse level (Alg. 1: 1 V, 2 W), the
+  // first from zero
+  for (int k = 0; k < c->stab.cycle; ++k) vcycle<T>(c, l + 1, k == 0);
   a.ec = P<T>::u(w, P<T>::cur(w));
   a.tiles = v.active;
   for (int s = 0; s < nu2; ++s) {
@@ -480,7 +482,9 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
     launch_resid_restrict<T>(op, P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
                              P<T>::F(w), nullptr, c->st);
   }
-  vcycle<T>(c, l + 1, true);
+  // gamma* = stab.cycle cycles on the coarse level (Alg. 1: 1 V, 2 W), the
+  // first from zero
+  for (int k = 0; k < c->stab.cycle; ++k) vcycle<T>(c, l + 1, k == 0);
   if (c->stab.nu2 == 0) {
     Launch k(c, fine ? MG_PROF_PROLONG : MG_PROF_COARSE, v.n_active > 0);
     launch_prolong<T>(op, v.active, v.n_active, P<T>::u(v, cur), w.L, P<T>::u(w, P<T>::cur(w)),
@@ -652,6 +656,7 @@ int mg_default_stab(mg_stab* out) {
   out->precision = MG_FP64;
   out->max_cycles = 100;
   out->inner = 0;
+  out->cycle = 1;
   return MG_OK;
 }
 
@@ -801,7 +806,9 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     MG_CUDA_TRY(cudaGetDevice(&dev));
     MG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     optin -= 1024;   // static shared memory of the kernel
-    if (t < nlev && nlev - t <= MG_TAIL_MAX_LEVELS) {
+    // (the tail block runs a V-cycle below its top level: W-cycles use the
+    // per-level kernels all the way down)
+    if (c->stab.cycle == 1 && t < nlev && nlev - t <= MG_TAIL_MAX_LEVELS) {
       const int nl = nlev - t;
       int n[MG_TAIL_MAX_LEVELS], nb[MG_TAIL_MAX_LEVELS];
       TailLevelSrc src[MG_TAIL_MAX_LEVELS];
@@ -883,7 +890,7 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
     return MG_ERR_INVALID_ARG;
   if (!(s.gamma > 0.0) || !(s.alpha > 0.0) || s.eta < 0 || s.eta > 8 || s.nu1 < 0 || s.nu1 > 8 ||
       s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0 || s.inner < 0 ||
-      s.inner > 8)
+      s.inner > 8 || (s.cycle != 1 && s.cycle != 2))
     return MG_ERR_INVALID_ARG;
   if (s.lambda_mode != MG_LAMBDA_LOCAL) return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_FP64 && s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
@@ -1592,6 +1599,7 @@ int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double*
   if (s.precision == MG_FP64) return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
   if (bc && bc->kind == MG_BC_MIXED) return MG_ERR_UNIMPLEMENTED;
+  if (s.cycle != 1) return s.cycle == 2 ? MG_ERR_UNIMPLEMENTED : MG_ERR_INVALID_ARG;
   mg_batch_ctx* b = new mg_batch_ctx();
   b->user_st = (cudaStream_t)cuda_stream;
   b->count = count;
