@@ -21,6 +21,11 @@ Readings (each restated in the design doc):
   nodes of that level in the same order (Sec. 5.3); applied on every
   non-coarsest level.
 * The coarsest level (8 x 8 cells unless told otherwise) is solved exactly.
+* Coarse re-discretisation (the alternative to Eq. galerkin the paper
+  describes in Sec. 4.3 / Sec. 5): level l is assembled from scratch on its
+  own grid (h_l = 2^l h) from the level set sampled at its nodes, snapped with
+  h_l^alpha, with its own cut cells and lambda_K = gamma C(K); its DOFs are
+  the vertices of its own active cells; P and R = P^T as before.
 * Stop when ||F - A u||_inf / ||F||_inf <= tol.
 
 Pins (tests/test_oracle_multigrid.py): the printed n = 2 restriction matrix
@@ -98,21 +103,34 @@ class Level:
         return (i % 2) + 2 * (j % 2)
 
 
-def build_hierarchy(system: System, coarsest: int = 8) -> list[Level]:
+def build_hierarchy(system: System, coarsest: int = 8, rediscretise_psi=None) -> list[Level]:
     """Levels 0 (fine) .. L (n = coarsest) with Galerkin operators
-    A_{l+1} = P_l^T A_l P_l (Eq. galerkin, read as R A P)."""
+    A_{l+1} = P_l^T A_l P_l (Eq. galerkin, read as R A P), or, given the
+    fine grid's nodal level set (before snapping) as rediscretise_psi, with
+    every coarse level assembled from scratch on its own grid."""
     lev = [Level(system.N, system.A.tocsr(), system.dof.copy(), system.cls.copy(),
                  cut_node_mask(system.cls))]
+    step = 1
     while lev[-1].n > coarsest:
         f = lev[-1]
         nc = f.n // 2
+        step *= 2
         P = prolongation(nc, f.dof)
-        Ac = (P.T @ f.A @ P).tocsr()
-        Ac.eliminate_zeros()
-        dofc = np.asarray(abs(P).sum(axis=0)).ravel() > 0
-        clsc = coarse_cell_classes(f.cls)
         f.P = P
-        lev.append(Level(nc, Ac, dofc, clsc, cut_node_mask(clsc) & dofc))
+        if rediscretise_psi is None:
+            Ac = (P.T @ f.A @ P).tocsr()
+            Ac.eliminate_zeros()
+            dofc = np.asarray(abs(P).sum(axis=0)).ravel() > 0
+            clsc = coarse_cell_classes(f.cls)
+            lev.append(Level(nc, Ac, dofc, clsc, cut_node_mask(clsc) & dofc))
+        else:
+            from .ghostfem import assemble
+            psi = np.asarray(rediscretise_psi, dtype=np.float64).reshape(system.N + 1,
+                                                                        system.N + 1)
+            sc = assemble(psi[::step, ::step], nc, system.x0, system.y0, system.h * step,
+                          system.gamma, system.alpha)
+            lev.append(Level(nc, sc.A.tocsr(), sc.dof.copy(), sc.cls.copy(),
+                             cut_node_mask(sc.cls) & sc.dof))
     return lev
 
 

@@ -174,3 +174,33 @@ def test_vcycle_solves_config1():
     assert hist[-1] <= 1e-10 and k <= 12
     ud = gf.direct_solve(s, F)
     assert np.abs(u - ud).max() <= 1e-9 * np.abs(ud).max()
+
+
+def test_rediscretised_levels_are_the_coarse_grid_discretisations():
+    """Coarse re-discretisation: level l of the 128^2 flower is the ghost-FEM
+    system of the same level set on the 2^-l coarser grid (flower(128 / 2^l)
+    samples the level set at exactly those nodes)."""
+    p = wl.flower(128)
+    s = gf.assemble_problem(p)
+    lev = mg.build_hierarchy(s, rediscretise_psi=p.psi)
+    for l in (1, 2, 3):
+        q = wl.flower(128 >> l)
+        sq = gf.assemble_problem(q)
+        assert lev[l].n == q.N
+        assert abs(lev[l].A - sq.A).max() <= 1e-14 * abs(sq.A).max()
+        np.testing.assert_array_equal(lev[l].dof, sq.dof)
+
+
+@pytest.mark.parametrize("make", [wl.paper_circle, wl.paper_flower, wl.paper_hourglass])
+def test_rediscretised_cycles_converge(make):
+    # the alternative to Eq. galerkin: still a convergent multigrid with the
+    # extra cut-cell sweeps (measured rho 0.06-0.11 for V, <= 0.05 for W)
+    p = make(64)
+    s = gf.assemble_problem(p)
+    lev = mg.build_hierarchy(s, rediscretise_psi=p.psi)
+    rv, _ = mg.convergence_factor(lev, order="color4", eta=4)
+    rw, _ = mg.convergence_factor(lev, order="color4", eta=4, gamma_star=2)
+    assert rv < 0.2 and rw < 0.1, (rv, rw)
+    F = np.random.default_rng(3).standard_normal(s.n_nodes) * s.dof
+    u, hist, k = mg.solve(lev, F, tol=1e-10)
+    assert hist[-1] <= 1e-10 and k <= 15
