@@ -56,6 +56,8 @@ enum {
 enum { MG_BC_DIRICHLET = 0,       /* weak Dirichlet on the whole of {psi = 0} */
        MG_BC_MIXED = 1 };         /* Dirichlet / Neumann by a per-cell mask */
 enum { MG_LAMBDA_LOCAL = 0 };     /* lambda_K = gamma C(K) per cut cell (Sec. 5.2) */
+enum { MG_COARSE_GALERKIN = 0,    /* A_2h = P^T A_h P (Eq. galerkin) */
+       MG_COARSE_REDISCRETISE = 1 };  /* A_2h assembled on the coarse grid */
 enum { MG_FP64 = 0,               /* fp64 V-cycles */
        MG_MIXED = 1 };            /* fp32 V-cycle inside fp64 iterative refinement */
 
@@ -105,13 +107,20 @@ typedef struct {
  *                 one refinement step: fp64 residual, `k` fp32 V-cycles on
  *                 the correction equation (the first from e = 0), u += e.
  *   cycle = 1     cycles on each coarse level per visit (Alg. 1, gamma*):
- *                 1 = V-cycle, 2 = W-cycle (batches: V only). */
+ *                 1 = V-cycle, 2 = W-cycle (batches: V only).
+ *   coarse_op = MG_COARSE_GALERKIN  coarse operators A_2h = P^T A_h P
+ *                 (Eq. galerkin); MG_COARSE_REDISCRETISE: each coarse level
+ *                 assembled from scratch on its own grid from the level set
+ *                 at its nodes (snapped with h_l^alpha, its own cut cells
+ *                 and lambda_K), the alternative the paper describes beside
+ *                 Eq. galerkin (not with MG_BC_MIXED: MG_ERR_UNIMPLEMENTED). */
 typedef struct {
   double gamma, alpha;
   int eta, nu1, nu2;
   int lambda_mode, precision, max_cycles;
   int inner;
   int cycle;
+  int coarse_op;
 } mg_stab;
 
 /* Result summary of a solve. */

@@ -657,6 +657,7 @@ int mg_default_stab(mg_stab* out) {
   out->max_cycles = 100;
   out->inner = 0;
   out->cycle = 1;
+  out->coarse_op = MG_COARSE_GALERKIN;
   return MG_OK;
 }
 
@@ -743,10 +744,32 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     uint8_t* cut_flag;
     TRY(dalloc(c, &v.cls, (size_t)v.n * v.n));
     TRY(dalloc(c, &cut_flag, (size_t)v.n * v.n));
-    launch_coarse_class(f.cls, f.n, v.cls, cut_flag, c->st);
-    TRY(build_cut_list(c, v, cut_flag));
-    CellData fd{f.n, f.cls, f.cell_cut, f.Ke};
-    launch_coarse_cut(fd, v.cut_list, v.n_cut, v.n, v.Ke, c->st);
+    if (c->stab.coarse_op == MG_COARSE_REDISCRETISE) {
+      // the level assembled from scratch on its own grid: the level set at
+      // its nodes, snapped with h_l^alpha, its own cut cells and lambda_K
+      const int step = N / v.n;
+      const double hl = c->h * step;
+      double *raw, *snapped, *Mk, *Gk, *Cl;
+      int* cfg;
+      TRY(dalloc(c, &raw, (size_t)(v.n + 1) * (v.n + 1)));
+      TRY(dalloc(c, &snapped, (size_t)(v.n + 1) * (v.n + 1)));
+      launch_subsample(ps.dev, N, step, raw, v.n, c->st);
+      launch_snap(raw, snapped, v.n, std::pow(hl, c->stab.alpha), c->d_err, c->st);
+      launch_cell_class(snapped, v.n, v.cls, cut_flag, c->st);
+      TRY(sync_check(c));
+      TRY(build_cut_list(c, v, cut_flag));
+      TRY(dalloc(c, &Mk, (size_t)v.n_cut * 16));
+      TRY(dalloc(c, &Gk, (size_t)v.n_cut * 16));
+      TRY(dalloc(c, &Cl, (size_t)v.n_cut * 4));
+      TRY(dalloc(c, &cfg, (size_t)v.n_cut));
+      launch_cut_cells(snapped, v.n, hl, c->stab.gamma, v.cut_list, v.n_cut, v.Ke, Mk, Gk, Cl,
+                       cfg, nullptr, nullptr, c->st);
+    } else {
+      launch_coarse_class(f.cls, f.n, v.cls, cut_flag, c->st);
+      TRY(build_cut_list(c, v, cut_flag));
+      CellData fd{f.n, f.cls, f.cell_cut, f.Ke};
+      launch_coarse_cut(fd, v.cut_list, v.n_cut, v.n, v.Ke, c->st);
+    }
     TRY(build_nodes(c, v));
   }
   {
@@ -890,9 +913,13 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
     return MG_ERR_INVALID_ARG;
   if (!(s.gamma > 0.0) || !(s.alpha > 0.0) || s.eta < 0 || s.eta > 8 || s.nu1 < 0 || s.nu1 > 8 ||
       s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0 || s.inner < 0 ||
-      s.inner > 8 || (s.cycle != 1 && s.cycle != 2))
+      s.inner > 8 || (s.cycle != 1 && s.cycle != 2) ||
+      (s.coarse_op != MG_COARSE_GALERKIN && s.coarse_op != MG_COARSE_REDISCRETISE))
     return MG_ERR_INVALID_ARG;
   if (s.lambda_mode != MG_LAMBDA_LOCAL) return MG_ERR_UNIMPLEMENTED;
+  // a Neumann mask is given for the fine cells only
+  if (s.coarse_op == MG_COARSE_REDISCRETISE && bc && bc->kind == MG_BC_MIXED)
+    return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_FP64 && s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
   mg_ctx* c = new mg_ctx();
   c->st = (cudaStream_t)cuda_stream;

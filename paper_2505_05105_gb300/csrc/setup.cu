@@ -393,6 +393,11 @@ __global__ void k_coarsest(CellData cd, double* __restrict__ A, double* __restri
       for (int k = i + 1; k < m; ++k) s -= A[(size_t)k * m + i] * x[k];
       x[i] = s / A[(size_t)i * m + i];
     }
+    // a node that is not a DOF gets u = 0 whatever F holds there (the unit
+    // diagonal above only keeps the factorisation regular); F off the DOFs
+    // can be nonzero when a coarse level is not the Galerkin one
+    if (node_kind(cd, c % (n + 1), c / (n + 1)) == 0)
+      for (int i = 0; i < m; ++i) x[i] = 0.0;
   }
 }
 
@@ -412,6 +417,24 @@ inline int grid_for(size_t m, int threads = 256) {
 // ------------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------------
+
+// out[(J, I)] = in[(step J, step I)]: a coarse grid's nodal values of a
+// level set given on the (n_in + 1)^2 fine nodes
+__global__ void k_subsample(const double* __restrict__ in, int n_in, int step,
+                            double* __restrict__ out, int n_out) {
+  const size_t m = (size_t)(n_out + 1) * (n_out + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int I = (int)(k % (n_out + 1)), J = (int)(k / (n_out + 1));
+    out[k] = in[(size_t)J * step * (n_in + 1) + (size_t)I * step];
+  }
+}
+
+void launch_subsample(const double* in, int n_in, int step, double* out, int n_out,
+                      cudaStream_t st) {
+  k_subsample<<<grid_for((size_t)(n_out + 1) * (n_out + 1)), 256, 0, st>>>(in, n_in, step, out,
+                                                                            n_out);
+}
 
 void launch_snap(const double* psi, double* psi_s, int n, double thr, unsigned* err,
                  cudaStream_t st) {

@@ -13,6 +13,9 @@ struct CellData {
   const double* Ke;
 };
 
+// out: the nodal values at every step-th node (n_out = n_in / step cells)
+void launch_subsample(const double* in, int n_in, int step, double* out, int n_out,
+                      cudaStream_t st);
 void launch_snap(const double* psi, double* psi_s, int n, double thr, unsigned* err,
                  cudaStream_t st);
 void launch_cell_class(const double* psi_s, int n, uint8_t* cls, uint8_t* cut_flag,

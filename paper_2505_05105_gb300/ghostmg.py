@@ -31,6 +31,8 @@ MG_BC_MIXED = 1
 MG_LAMBDA_LOCAL = 0
 MG_FP64 = 0
 MG_MIXED = 1
+MG_COARSE_GALERKIN = 0
+MG_COARSE_REDISCRETISE = 1
 
 
 class mg_grid(ctypes.Structure):
@@ -46,7 +48,8 @@ class mg_stab(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("alpha", ctypes.c_double), ("eta", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("lambda_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
-                ("inner", ctypes.c_int), ("cycle", ctypes.c_int)]
+                ("inner", ctypes.c_int), ("cycle", ctypes.c_int),
+                ("coarse_op", ctypes.c_int)]
 
 
 class mg_info(ctypes.Structure):
@@ -340,7 +343,8 @@ class Solver:
     def __init__(self, psi, n_cells: int, x0: float, y0: float, h: float, *,
                  coarsest: int = 8, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
                  nu1: int = 2, nu2: int = 1, precision: str = "fp64", max_cycles: int = 100,
-                 inner: int = 0, stream: int = 0, neumann_mask=None, cycle: str = "V"):
+                 inner: int = 0, stream: int = 0, neumann_mask=None, cycle: str = "V",
+                 coarse: str = "galerkin"):
         """neumann_mask: (n_cells, n_cells) uint8 cells [jc, ic] (host array,
         or a device tensor), nonzero where a cut cell's boundary piece is
         Neumann (MG_BC_MIXED); None: all Dirichlet."""
@@ -350,6 +354,8 @@ class Solver:
         stab.nu1, stab.nu2, stab.max_cycles, stab.inner = nu1, nu2, max_cycles, inner
         stab.precision = {"fp64": MG_FP64, "mixed": MG_MIXED}[precision]
         stab.cycle = {"V": 1, "W": 2}[cycle]
+        stab.coarse_op = {"galerkin": MG_COARSE_GALERKIN,
+                          "rediscretise": MG_COARSE_REDISCRETISE}[coarse]
         grid = mg_grid(n_cells, x0, y0, h, coarsest)
         if neumann_mask is None:
             bc = mg_bc(MG_BC_DIRICHLET, None)

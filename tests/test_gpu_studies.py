@@ -125,3 +125,66 @@ def test_convergence_factors_across_sizes():
         print(f"| {name} | {N} | {r['V', 4]:.3f} | {r['V', 0]:.3f} | {r['W', 4]:.3f} | "
               f"{r['W', 0]:.3f} |")
 
+
+
+def oracle_rows(A, n):
+    A = A.tocoo()
+    out = np.zeros(((n + 1) ** 2, 9))
+    di = A.col % (n + 1) - A.row % (n + 1)
+    dj = A.col // (n + 1) - A.row // (n + 1)
+    np.add.at(out, (A.row, (di + 1) + 3 * (dj + 1)), A.data)
+    return out
+
+
+@pytest.mark.parametrize("make,N", [(wl.flower, 128), (wl.paper_hourglass, 64),
+                                    (wl.paper_flower, 128)])
+def test_rediscretised_coarse_levels(make, N):
+    """Coarse re-discretisation (MG_COARSE_REDISCRETISE, the alternative to
+    Eq. galerkin): the rows of every level equal the oracle's from-scratch
+    assembly on that level's grid (1e-13), V- and W-cycle iterates match the
+    oracle's node by node, the convergence factors agree to 1e-6, and a
+    mixed-precision solve reaches 1e-10."""
+    from paper_2505_05105_gb300 import ghostmg as G
+    p = make(N)
+    s = gf.assemble_problem(p)
+    lev = mg.build_hierarchy(s, rediscretise_psi=p.psi)
+    with solver(p, coarse="rediscretise") as S:
+        for l, L in enumerate(lev):
+            ref = oracle_rows(L.A, L.n)
+            err = np.abs(S.stencil(l) - ref).max() / np.abs(ref).max()
+            assert err <= 1e-13, (l, err)
+    F = s.rhs(p.f, p.g)
+    if not np.abs(F).max() > 0:
+        F = np.random.default_rng(13).standard_normal(s.n_nodes) * s.dof
+    for cyc, gs in (("V", 1), ("W", 2)):
+        u_ref = np.zeros(s.n_nodes)
+        with solver(p, coarse="rediscretise", cycle=cyc) as S:
+            u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+            for k in range(1, 4):
+                u_ref = mg.mg_cycle(lev, 0, u_ref, F, nu1=2, nu2=1, eta=4, order="color4",
+                                    gamma_star=gs)
+                S.cycles(dev(F), u, 1)
+                assert_nodewise(host(u), u_ref, node_tolerance(s, F, u_ref, 1e-10, 64 * k),
+                                (p.name, cyc, k))
+        ref, _ = mg.convergence_factor(lev, cycles=20, first=11, order="color4", eta=4,
+                                       gamma_star=gs)
+        got = gpu_rho(p, s.dof, cycle=cyc, coarse="rediscretise")
+        assert got == pytest.approx(ref, rel=1e-6), (cyc, got, ref)
+    # mixed-precision refinement steps (mg_cycles) on the nodal F to 1e-10
+    with solver(p, coarse="rediscretise", precision="mixed") as S:
+        u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+        Fd = dev(F)
+        for _ in range(30):
+            S.cycles(Fd, u, 1, precision="mixed")
+            rn = S.residual(Fd, u)[0]
+            if rn <= 1e-10 * np.abs(F).max():
+                break
+        assert rn <= 1e-10 * np.abs(F).max()
+
+
+def test_coarse_option_rejected_with_neumann_mask():
+    from paper_2505_05105_gb300 import ghostmg as G
+    p = wl.annulus(64)
+    with pytest.raises(G.GhostMGError) as e:
+        solver(p, coarse="rediscretise")
+    assert e.value.code == G.MG_ERR_UNIMPLEMENTED
