@@ -424,16 +424,24 @@ class System:
     G: sp.csr_matrix
     cut: list               # [CutCell]
     Gn: sp.csr_matrix = None   # Neumann load (None: all of Gamma is Dirichlet)
+    B: sp.csr_matrix = None    # couplings of the DOFs to strong Dirichlet box nodes
+    box_strong: bool = False
 
     @property
     def n_nodes(self):
         return (self.N + 1) ** 2
 
     def rhs(self, f, g, gN=None):
-        """F = M f + G g_D (+ N g_N), Eq. disc_rhs with Q1 interpolants."""
+        """F = M f + G g_D (+ N g_N), Eq. disc_rhs with Q1 interpolants; with
+        strong Dirichlet box sides also - B g (the box nodes' values g moved
+        to the right-hand side)."""
         F = self.M @ np.ravel(f) + self.G @ np.ravel(g)
         if gN is not None and self.Gn is not None:
             F = F + self.Gn @ np.ravel(gN)
+        if self.B is not None:
+            F = F - self.B @ np.ravel(g)
+        if self.box_strong:
+            F[~self.dof] = 0.0
         return F
 
 
@@ -442,10 +450,14 @@ def cell_nodes(ic, jc, N):
     return np.array([k0, k0 + 1, k0 + N + 1, k0 + N + 2])
 
 
-def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75, neumann_mask=None) -> System:
+def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75, neumann_mask=None,
+             box_strong=False) -> System:
     """A, M, G over all (N+1)^2 nodes (Eq. disc_bil_form, Eq. disc_rhs).
     neumann_mask: (N, N) cells [jc, ic], nonzero where a cut cell's boundary
-    piece belongs to Gamma_N (ignored on other cells); None: all Dirichlet."""
+    piece belongs to Gamma_N (ignored on other cells); None: all Dirichlet.
+    box_strong: the nodes on the sides of the box (i or j equal to 0 or N)
+    carry strong Dirichlet values (the rectangle of Sec. 5.3): they are not
+    DOFs, and their couplings to the DOFs move to the right-hand side."""
     nm = None if neumann_mask is None else np.asarray(neumann_mask).reshape(N, N) != 0
     psi_s = snap(np.asarray(psi, dtype=np.float64).reshape(N + 1, N + 1), h, alpha)
     cls = cell_classes(psi_s)
@@ -485,12 +497,23 @@ def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75, neumann_mask=None) -> Sys
     jj, ii = np.nonzero(active)
     for d in (0, 1, N + 1, N + 2):
         dof[ii + jj * (N + 1) + d] = True
-    return System(N, x0, y0, h, gamma, alpha, psi_s, cls, dof, A, M, G, cuts, Gn)
+    B = None
+    if box_strong:
+        jn, in_ = np.divmod(np.arange(n), N + 1)
+        ring = (in_ == 0) | (jn == 0) | (in_ == N) | (jn == N)
+        dof &= ~ring
+        keep = sp.diags(dof.astype(np.float64))
+        B = (keep @ A @ sp.diags(ring.astype(np.float64))).tocsr()
+        B.eliminate_zeros()
+        A = (keep @ A @ keep).tocsr()
+        A.eliminate_zeros()
+    return System(N, x0, y0, h, gamma, alpha, psi_s, cls, dof, A, M, G, cuts, Gn, B, box_strong)
 
 
 def assemble_problem(prob, gamma=2.0, alpha=1.75) -> System:
     return assemble(prob.psi, prob.N, prob.x0, prob.y0, prob.h, gamma, alpha,
-                    getattr(prob, "neumann_mask", None))
+                    getattr(prob, "neumann_mask", None),
+                    bool(getattr(prob, "meta", {}).get("box_strong", False)))
 
 
 def direct_solve(system: System, F: np.ndarray, refine: int = 4) -> np.ndarray:

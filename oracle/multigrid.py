@@ -21,6 +21,8 @@ Readings (each restated in the design doc):
   nodes of that level in the same order (Sec. 5.3); applied on every
   non-coarsest level.
 * The coarsest level (8 x 8 cells unless told otherwise) is solved exactly.
+* With strong Dirichlet box sides the box nodes of every level are not DOFs
+  (P has no columns for the coarse ones).
 * Coarse re-discretisation (the alternative to Eq. galerkin the paper
   describes in Sec. 4.3 / Sec. 5): level l is assembled from scratch on its
   own grid (h_l = 2^l h) from the level set sampled at its nodes, snapped with
@@ -116,6 +118,13 @@ def build_hierarchy(system: System, coarsest: int = 8, rediscretise_psi=None) ->
         nc = f.n // 2
         step *= 2
         P = prolongation(nc, f.dof)
+        if system.box_strong:
+            # the coarse box nodes are strong Dirichlet nodes too: their
+            # corrections are zero
+            jn, in_ = np.divmod(np.arange((nc + 1) ** 2), nc + 1)
+            inner = ~((in_ == 0) | (jn == 0) | (in_ == nc) | (jn == nc))
+            P = (P @ sp.diags(inner.astype(np.float64))).tocsr()
+            P.eliminate_zeros()
         f.P = P
         if rediscretise_psi is None:
             Ac = (P.T @ f.A @ P).tocsr()

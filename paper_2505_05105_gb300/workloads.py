@@ -23,6 +23,9 @@ Problems
 * ``paper_circle``, ``paper_flower``, ``paper_hourglass`` - the level sets of
   the 2D experiments of Sec. 5.3 (homogeneous data; used for convergence
   factors).
+* ``rectangle`` - the unit square cut by the vertical line psi = x - 1 +
+  (1 - theta) h (Sec. 5.3): weak Dirichlet on the cut side, strong Dirichlet
+  on the three sides of the box it touches (meta["box_strong"]).
 * ``annulus``, ``leaf``, ``half_disc`` - mixed Dirichlet / Neumann problems:
   the annulus and leaf of Sec. 5.3 with a manufactured solution, and a disc
   cut by a straight Neumann side (patch tests).  They carry a per-cell
@@ -271,4 +274,18 @@ def half_disc(N: int = 64, c: float = 0.1537) -> Problem:
     mask = (ln[:-1, :-1] & ln[:-1, 1:] & ln[1:, :-1] & ln[1:, 1:]).astype(np.uint8)
     return Problem("half_disc", N, x0, y0, h, psi, np.zeros_like(u), u.copy(), u,
                    meta={"c": c}, neumann_mask=mask, gN=u.copy())
+
+
+def rectangle(N: int = 128, theta: float = 0.5) -> Problem:
+    """[0, 1]^2 cut by the vertical line x = 1 - (1 - theta) h (psi = x - 1 +
+    (1 - theta) h, Sec. 5.3): every cut cell is a quadrilateral with cut
+    sides theta h.  Weak (Nitsche) Dirichlet on the cut side, strong on the
+    box sides x = 0, y = 0 and y = 1.  u = sin 3x cos 2y, f = 13 u, g = u at
+    every node (the box nodes' strong values and the weak data)."""
+    h = 1.0 / N
+    X, Y = node_grid(N, 0.0, 0.0, h)
+    psi = X - 1.0 + (1.0 - theta) * h
+    u = np.sin(3 * X) * np.cos(2 * Y)
+    return Problem("rectangle", N, 0.0, 0.0, h, psi, 13.0 * u, u.copy(), u,
+                   meta={"theta": theta, "box_strong": True})
 
