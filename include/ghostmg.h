@@ -86,10 +86,19 @@ typedef struct {
  *     (Eq. disc_rhs, g_N through its Q1 interpolant of nodal values, see
  *     mg_solve_bc).  Bytes of other cells are ignored.  At least one cut
  *     cell must stay Dirichlet (otherwise A is singular: MG_ERR_NOT_SPD).
- * Any other combination is MG_ERR_INVALID_ARG. */
+ * Any other combination is MG_ERR_INVALID_ARG.
+ *   box_sides != 0: strong Dirichlet conditions on the sides of the box
+ *     (the rectangle example of Sec. 5.3): every node with i or j equal to
+ *     0 or n_cells is a Dirichlet node with value g_D (the g array of
+ *     mg_solve), not a DOF; Omega may then reach the box sides.  Its
+ *     couplings to the DOFs move to the right-hand side (F - A_pq g_q), the
+ *     coarse levels keep their box nodes out too, and u is 0 there on
+ *     output.  mg_adjoint and batches do not take it
+ *     (MG_ERR_UNIMPLEMENTED). */
 typedef struct {
   int kind;
   const uint8_t* neumann_mask;
+  int box_sides;
 } mg_bc;
 
 /* Method parameters (defaults from mg_default_stab):

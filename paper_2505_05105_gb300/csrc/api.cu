@@ -84,6 +84,7 @@ struct mg_ctx {
   double* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   const uint8_t* nmask_in = nullptr;   // caller's Neumann cell mask (setup only)
   double* Nk = nullptr;          // Neumann load per cut cell (null: all Dirichlet)
+  int box = 0;                   // strong Dirichlet box sides
   std::vector<void*> allocs;
   double last_tol = 1e-10;
   int tail_level = -1;           // first level run by the single-block tail kernel
@@ -258,7 +259,7 @@ int build_nodes(mg_ctx* c, Level& V) {
   int nbx = (V.n + 1 + 31) / 32, nby = nbx;
   size_t tmpn2 = scan_tmp_ints((size_t)nbx * nby);
   TRY(dalloc(c, &tmp, (tmpn > tmpn2 ? tmpn : tmpn2) + 8));
-  CellData cd{V.n, V.cls, V.cell_cut, V.Ke};
+  CellData cd{V.n, V.cls, V.cell_cut, V.Ke, c->box};
   launch_tile_counts(cd, L, tile_cnt, tile_active, d_cnt + 0, c->st);
   exclusive_scan_int(tile_cnt, V.tile_base, d_cnt + 1, (size_t)ntiles, tmp, c->st);
   int h_cnt[2];
@@ -700,7 +701,7 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
   Staged ps;
   TRY(stage_in(c, 0, levelset, ps));
   TRY(dalloc(c, &c->psi_s, (size_t)(N + 1) * (N + 1)));
-  launch_snap(ps.dev, c->psi_s, N, std::pow(c->h, c->stab.alpha), c->d_err, c->st);
+  launch_snap(ps.dev, c->psi_s, N, std::pow(c->h, c->stab.alpha), c->d_err, c->st, c->box);
   // fine level cells
   c->lev.emplace_back();
   {
@@ -754,7 +755,7 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
       TRY(dalloc(c, &raw, (size_t)(v.n + 1) * (v.n + 1)));
       TRY(dalloc(c, &snapped, (size_t)(v.n + 1) * (v.n + 1)));
       launch_subsample(ps.dev, N, step, raw, v.n, c->st);
-      launch_snap(raw, snapped, v.n, std::pow(hl, c->stab.alpha), c->d_err, c->st);
+      launch_snap(raw, snapped, v.n, std::pow(hl, c->stab.alpha), c->d_err, c->st, c->box);
       launch_cell_class(snapped, v.n, v.cls, cut_flag, c->st);
       TRY(sync_check(c));
       TRY(build_cut_list(c, v, cut_flag));
@@ -767,7 +768,7 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     } else {
       launch_coarse_class(f.cls, f.n, v.cls, cut_flag, c->st);
       TRY(build_cut_list(c, v, cut_flag));
-      CellData fd{f.n, f.cls, f.cell_cut, f.Ke};
+      CellData fd{f.n, f.cls, f.cell_cut, f.Ke, c->box};
       launch_coarse_cut(fd, v.cut_list, v.n_cut, v.n, v.Ke, c->st);
     }
     TRY(build_nodes(c, v));
@@ -777,7 +778,7 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     int m = (v.n + 1) * (v.n + 1);
     TRY(dalloc(c, &c->Adense, (size_t)m * m));
     TRY(dalloc(c, &c->Ainv, (size_t)m * m));
-    CellData cd{v.n, v.cls, v.cell_cut, v.Ke};
+    CellData cd{v.n, v.cls, v.cell_cut, v.Ke, c->box};
     launch_coarsest(cd, c->Adense, c->Ainv, c->d_err, c->st);
   }
   MG_CUDA_TRY(configure_kernels<double>(c->stab.eta));
@@ -928,6 +929,7 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
   c->N = g.n_cells;
   c->h = g.h;
   c->nmask_in = (bc && bc->kind == MG_BC_MIXED) ? bc->neumann_mask : nullptr;
+  c->box = (bc && bc->box_sides) ? 1 : 0;
   auto t0 = std::chrono::steady_clock::now();
   int rc = setup_impl(c, levelset);
   c->nmask_in = nullptr;
@@ -991,7 +993,7 @@ int mg_solve_bc(mg_handle c, const double* f, const double* g, const double* gN,
     launch_check_finite2(sf.dev, sg.dev, m, c->d_err, c->st);
     if (neu) launch_check_finite2(sn.dev, sn.dev, m, c->d_err, c->st);
     RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
-               neu ? sn.dev : nullptr};
+               neu ? sn.dev : nullptr, v.Ke, c->box};
     launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
     v.cur64 = 0;
     launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st, d_nz);
@@ -1042,7 +1044,7 @@ int mg_rhs_bc(mg_handle c, const double* f, const double* g, const double* gN, d
   TRY(stage_out(c, 2, F, &Fd, &Fh));
   MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
   RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
-             neu ? sn.dev : nullptr};
+             neu ? sn.dev : nullptr, v.Ke, c->box};
   launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
   launch_unpack(v.L, v.code, v.F64, Fd, c->st);
   TRY(finish_out(c, F, Fd, Fh));
@@ -1214,6 +1216,8 @@ int mg_get_profile(mg_handle c, long long* launches, long long* counts, double* 
 // linear in f and g (Eq. disc_rhs), so dL/df = M^T w and dL/dg = G^T w.
 int mg_adjoint(mg_handle c, const double* dLdu, double* dLdf, double* dLdg) {
   if (!c || !dLdu || (!dLdf && !dLdg)) return MG_ERR_INVALID_ARG;
+  // dL/dg would also need the transposed couplings to the box nodes
+  if (c->box) return MG_ERR_UNIMPLEMENTED;
   Level& v = c->lev[0];
   const double tol = c->last_tol > 0.0 ? c->last_tol : 1e-10;
   Staged sd;
@@ -1625,7 +1629,7 @@ int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double*
   else s.precision = MG_MIXED;
   if (s.precision == MG_FP64) return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
-  if (bc && bc->kind == MG_BC_MIXED) return MG_ERR_UNIMPLEMENTED;
+  if (bc && (bc->kind == MG_BC_MIXED || bc->box_sides)) return MG_ERR_UNIMPLEMENTED;
   if (s.cycle != 1) return s.cycle == 2 ? MG_ERR_UNIMPLEMENTED : MG_ERR_INVALID_ARG;
   mg_batch_ctx* b = new mg_batch_ctx();
   b->user_st = (cudaStream_t)cuda_stream;

@@ -22,6 +22,8 @@ struct RhsArgs {
   const double* Gk;          // 16 per cut cell, Dirichlet load (0 on Neumann cells)
   const double* Nk = nullptr;  // 16 per cut cell, Neumann load (null: no Neumann cells)
   const double* gN = nullptr;  // nodal Neumann data, user layout (null: g_N = 0)
+  const double* Ke = nullptr;  // 16 per cut cell, element matrices (strong box sides)
+  int box = 0;                 // box nodes are strong Dirichlet nodes: F -= A_pq g_q
 };
 
 // TMA descriptors of a level's two u buffers in one precision (band kernel box)

@@ -89,6 +89,32 @@ __device__ __forceinline__ double rhs_tile(const RhsArgs& a, int t, const double
         }
       }
     }
+    if (a.box && cd && (i == 1 || j == 1 || i == n - 1 || j == n - 1)) {
+      // strong Dirichlet values of the box nodes moved to the right-hand
+      // side: - sum over the adjacent cells of A_K(p, q) g_q, q on the box
+      for (int k = 0; k < 4; ++k) {
+        const int dx = k & 1, dy = k >> 1;
+        const int ic = i - 1 + dx, jc = j - 1 + dy;
+        if (ic < 0 || jc < 0 || ic >= n || jc >= n) continue;
+        const size_t c = (size_t)jc * n + ic;
+        const uint8_t cl = a.cls[c];
+        if (cl == CELL_EXT) continue;
+        const int av = (1 - dx) + 2 * (1 - dy);
+        for (int b = 0; b < 4; ++b) {
+          const int bi = ic + (b & 1), bj = jc + (b >> 1);
+          if (!(bi == 0 || bj == 0 || bi == n || bj == n)) continue;
+          double e;
+          if (cl == CELL_INT) {
+            // whole-cell Q1 stiffness: 4/6 diagonal, -1/6 along edges,
+            // -2/6 across the diagonal
+            e = (b == av) ? 4.0 / 6.0 : ((b ^ av) == 3 ? -2.0 / 6.0 : -1.0 / 6.0);
+          } else {
+            e = a.Ke[(size_t)a.cell_cut[c] * 16 + av * 4 + b];
+          }
+          s -= e * g[(size_t)bj * W + bi];
+        }
+      }
+    }
     F[gk] = s;
     vmax = fmax(vmax, fabs(s));
   }

@@ -16,7 +16,7 @@ __device__ __constant__ double kQ1[16] = {
    -2.0 / 6, -1.0 / 6, -1.0 / 6,  4.0 / 6};
 
 __global__ void k_snap(const double* __restrict__ psi, double* __restrict__ psi_s, int n,
-                       double thr, unsigned* err) {
+                       double thr, unsigned* err, int box) {
   size_t m = (size_t)(n + 1) * (n + 1);
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
        k += (size_t)gridDim.x * blockDim.x) {
@@ -25,7 +25,7 @@ __global__ void k_snap(const double* __restrict__ psi, double* __restrict__ psi_
     if (p < 0.0 && p > -thr) p = 0.0;          // snapping back to grid
     psi_s[k] = p;
     int i = (int)(k % (n + 1)), j = (int)(k / (n + 1));
-    if ((i == 0 || j == 0 || i == n || j == n) && p < 0.0) atomicOr(err, DEV_ERR_EDGE);
+    if (!box && (i == 0 || j == 0 || i == n || j == n) && p < 0.0) atomicOr(err, DEV_ERR_EDGE);
   }
 }
 
@@ -95,6 +95,7 @@ __device__ __forceinline__ bool cell_matrix(const CellData& cd, int ic, int jc, 
 // DOF / interior / boundary status of node (i, j) from its adjacent cells.
 __device__ __forceinline__ int node_kind(const CellData& cd, int i, int j) {
   if (i < 0 || j < 0 || i > cd.n || j > cd.n) return 0;
+  if (cd.box && (i == 0 || j == 0 || i == cd.n || j == cd.n)) return 0;   // strong Dirichlet
   int nact = 0, nint = 0;
   for (int q = 0; q < 4; ++q) {
     int ic = i - 1 + (q & 1), jc = j - 1 + (q >> 1);
@@ -352,7 +353,10 @@ __global__ void k_coarsest(CellData cd, double* __restrict__ A, double* __restri
       if (!cell_matrix(cd, ic, jc, &E)) continue;
       int a = (1 - dx) + 2 * (1 - dy);
       for (int b = 0; b < 4; ++b) {
-        int col = (ic + (b & 1)) + (jc + (b >> 1)) * (n + 1);
+        const int bi = ic + (b & 1), bj = jc + (b >> 1);
+        // couplings to strong Dirichlet box nodes are not part of A
+        if (cd.box && node_kind(cd, bi, bj) == 0) continue;
+        int col = bi + bj * (n + 1);
         A[(size_t)p * m + col] += E[a * 4 + b];
       }
     }
@@ -437,8 +441,8 @@ void launch_subsample(const double* in, int n_in, int step, double* out, int n_o
 }
 
 void launch_snap(const double* psi, double* psi_s, int n, double thr, unsigned* err,
-                 cudaStream_t st) {
-  k_snap<<<grid_for((size_t)(n + 1) * (n + 1)), 256, 0, st>>>(psi, psi_s, n, thr, err);
+                 cudaStream_t st, int box) {
+  k_snap<<<grid_for((size_t)(n + 1) * (n + 1)), 256, 0, st>>>(psi, psi_s, n, thr, err, box);
 }
 
 void launch_cell_class(const double* psi_s, int n, uint8_t* cls, uint8_t* cut_flag,

@@ -11,13 +11,15 @@ struct CellData {
   const uint8_t* cls;
   const int* cell_cut;
   const double* Ke;
+  int box = 0;       // nodes on the box sides are strong Dirichlet nodes (not DOFs)
 };
 
 // out: the nodal values at every step-th node (n_out = n_in / step cells)
 void launch_subsample(const double* in, int n_in, int step, double* out, int n_out,
                       cudaStream_t st);
+// box != 0: the domain may reach the box sides (strong Dirichlet there)
 void launch_snap(const double* psi, double* psi_s, int n, double thr, unsigned* err,
-                 cudaStream_t st);
+                 cudaStream_t st, int box = 0);
 void launch_cell_class(const double* psi_s, int n, uint8_t* cls, uint8_t* cut_flag,
                        cudaStream_t st);
 void launch_fill_int(int* p, size_t m, int v, cudaStream_t st);

@@ -41,7 +41,8 @@ class mg_grid(ctypes.Structure):
 
 
 class mg_bc(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("neumann_mask", ctypes.c_void_p)]
+    _fields_ = [("kind", ctypes.c_int), ("neumann_mask", ctypes.c_void_p),
+                ("box_sides", ctypes.c_int)]
 
 
 class mg_stab(ctypes.Structure):
@@ -344,7 +345,7 @@ class Solver:
                  coarsest: int = 8, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
                  nu1: int = 2, nu2: int = 1, precision: str = "fp64", max_cycles: int = 100,
                  inner: int = 0, stream: int = 0, neumann_mask=None, cycle: str = "V",
-                 coarse: str = "galerkin"):
+                 coarse: str = "galerkin", box_sides: bool = False):
         """neumann_mask: (n_cells, n_cells) uint8 cells [jc, ic] (host array,
         or a device tensor), nonzero where a cut cell's boundary piece is
         Neumann (MG_BC_MIXED); None: all Dirichlet."""
@@ -358,7 +359,7 @@ class Solver:
                           "rediscretise": MG_COARSE_REDISCRETISE}[coarse]
         grid = mg_grid(n_cells, x0, y0, h, coarsest)
         if neumann_mask is None:
-            bc = mg_bc(MG_BC_DIRICHLET, None)
+            bc = mg_bc(MG_BC_DIRICHLET, None, int(box_sides))
         else:
             if isinstance(neumann_mask, np.ndarray):
                 neumann_mask = np.ascontiguousarray(neumann_mask, dtype=np.uint8)
@@ -367,7 +368,7 @@ class Solver:
                 ptr = neumann_mask.ctypes.data
             else:
                 ptr = neumann_mask.data_ptr()
-            bc = mg_bc(MG_BC_MIXED, ptr)
+            bc = mg_bc(MG_BC_MIXED, ptr, int(box_sides))
         self.handle = mg_setup(psi, grid, bc, stab, stream)
 
     @classmethod
