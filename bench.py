@@ -13,7 +13,8 @@ flushed (a 512 MB write) between steps, outside the timed region.
 
 The line's "batched" object times the batched workload: 256 seeded
 geometries of uneven size solved together by one graph launch (the
-persistent batch kernel), beside the same members solved one by one.
+persistent batch kernel), beside the same members solved one by one; its
+"large" object the 8192^2 three-disc problem in both precisions.
 
 Under torchrun with N > 1 every rank solves its own replica (no collective
 on the data path); value = the DOFs all ranks solved / the slowest rank's
@@ -72,6 +73,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched workload (256 seeded geometries)")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large workload (three discs, 8192^2 cells)")
+    ap.add_argument("--large-N", type=int, default=8192)
     ap.add_argument("--profile-batch", action="store_true",
                     help="setup and two solves of the batched workload, untimed (for ncu)")
     ap.add_argument("--batch-shape", default="",
@@ -310,6 +314,9 @@ def run_ours(args):
         batched = None
         if not args.no_batched and world == 1:
             batched = run_batched(args, dev, flush)
+        large = None
+        if not args.no_large and world == 1:
+            large = run_large(args, dev, flush, stream)
     clocks = clk.summary()
 
     value = world * ndof * args.steps / (total_mx / 1e3)
@@ -393,6 +400,7 @@ def run_ours(args):
             "roofline": roofline,
             "kernel_breakdown_mixed": breakdown,
             "batched": batched,
+            "large": large,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -403,6 +411,67 @@ def run_ours(args):
         S.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_large(args, dev, flush, stream):
+    """The large workload: the union of three seeded discs minus a small
+    disc (several cut features), random Fourier f, g = 0, at 8192^2 cells;
+    mixed precision and plain fp64 solves from u = 0 to 1e-10, timed as the
+    headline (CUDA events on the solver's stream, L2 flushed between
+    steps), and the fine fp32 sweep's share and bandwidth from a profiled
+    pass."""
+    import numpy as np
+    import torch
+    from paper_2505_05105_gb300 import ghostmg, workloads as wl
+    N = args.large_N
+    p = wl.three_discs(N, seed=0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(dev)
+    psi, f, g = t(p.psi), t(p.f), t(p.g)
+    u = torch.zeros_like(f)
+    out = {"workload": f"three discs minus a disc (seed 0), random Fourier f, g=0, {N}^2 cells"}
+    for prec in ("mixed", "fp64"):
+        S = ghostmg.Solver(psi, N, p.x0, p.y0, p.h, precision=prec, stream=stream.cuda_stream)
+        ndof = S.counts()[1]
+        for _ in range(max(1, args.warmup)):
+            u.zero_()
+            S.solve(f, g, u, tol=TOL)
+        steps = max(1, min(args.steps, 3))
+        ms = []
+        for k in range(steps):
+            u.zero_()
+            flush.fill_(float(k))
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = S.solve(f, g, u, tol=TOL)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ent = {"value": ndof * steps / (sum(ms) / 1e3), "unit": UNIT,
+               "ms_per_step": sum(ms) / steps, "cycles_per_solve": info.cycles,
+               "rel_res": info.rel_res, "steps": steps}
+        if prec == "mixed":
+            ghostmg.mg_set_profiling(S.handle, True)
+            u.zero_()
+            S.solve(f, g, u, tol=TOL)
+            _, slots = ghostmg.mg_get_profile(S.handle)
+            ghostmg.mg_set_profiling(S.handle, False)
+            n_l, sweep_ms = slots["sweep"]
+            if n_l:
+                algo = ALGO_BYTES[("sweep", "f32")] * ndof
+                peak, src = measured_peaks()
+                gbs = algo / (sweep_ms / n_l / 1e3) / 1e9
+                ent["sweep_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak,
+                                         "unit": "GB/s", "frac": gbs / peak,
+                                         "avg_launch_us": sweep_ms / n_l * 1e3,
+                                         "peak_source": f"{src} hbm_gbs"}
+            out["n_dof"] = ndof
+            out["n_cut"] = S.counts()[2]
+        out[prec] = ent
+        S.close()
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
 
 
 def batch_members(count):
