@@ -556,3 +556,12 @@ def adjoint(system: System, dLdu: np.ndarray):
     d = np.ravel(dLdu).astype(np.float64) * system.dof
     w = direct_solve(system, d)
     return system.M.T @ w, system.G.T @ w
+
+
+def adjoint_neumann(system: System, dLdu: np.ndarray):
+    """dL/dg_N of the same loss with mixed boundary conditions: F also holds
+    N g_N (Eq. disc_rhs), so dL/dg_N = N^T w with the w of ``adjoint``."""
+    d = np.ravel(dLdu).astype(np.float64) * system.dof
+    w = direct_solve(system, d)
+    return system.Gn.T @ w
+

@@ -52,3 +52,35 @@ def test_adjoint_matches_central_differences(make):
         e = np.zeros_like(g0); e[q] = h
         fd = (L(f0, g0 + e) - L(f0, g0 - e)) / (2 * h)
         assert fd == pytest.approx(dLdg[q], abs=1e-9 * scale)
+
+
+def test_neumann_adjoint_matches_central_differences():
+    """dL/dg_N = N^T w on the annulus (Neumann outer circle): central
+    differences of the forward solve, zero away from the Neumann cut cells."""
+    p = wl.annulus(32)
+    s = gf.assemble_problem(p)
+    rng = np.random.default_rng(4)
+    inside = (np.ravel(p.psi) < 0).astype(float)
+    ut = rng.standard_normal(s.n_nodes)
+    f0, g0, n0 = (np.ravel(a).copy() for a in (p.f, p.g, p.gN))
+
+    def L(gN):
+        u = gf.direct_solve(s, s.rhs(f0, g0, gN))
+        return loss_and_grad(s, u, ut, inside)[0]
+
+    u = gf.direct_solve(s, s.rhs(f0, g0, n0))
+    _, dLdu = loss_and_grad(s, u, ut, inside)
+    dLdn = gf.adjoint_neumann(s, dLdu)
+    N = p.N
+    neu = np.zeros((N + 1, N + 1), bool)
+    for c in s.cut:
+        if c.neumann:
+            neu[c.jc:c.jc + 2, c.ic:c.ic + 2] = True
+    assert np.all(dLdn[~neu.ravel()] == 0) and np.abs(dLdn).max() > 0
+    h = 1e-3
+    scale = np.abs(dLdn).max()
+    for q in rng.choice(np.flatnonzero(neu.ravel()), 12, replace=False):
+        e = np.zeros_like(n0); e[q] = h
+        fd = (L(n0 + e) - L(n0 - e)) / (2 * h)
+        assert fd == pytest.approx(dLdn[q], abs=1e-9 * scale)
+
