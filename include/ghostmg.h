@@ -199,6 +199,13 @@ int mg_solve_bc(mg_handle h, const double* f, const double* g_D, const double* g
  * Errors as mg_solve (MG_ERR_NOT_CONVERGED: outputs still written). */
 int mg_adjoint(mg_handle h, const double* dLdu, double* dLdf, double* dLdg);
 
+/* mg_adjoint with mixed boundary conditions: also dL/dg_N = N^T w (F holds
+ * N g_N, Eq. disc_rhs; zero away from Neumann cut cells, and everywhere on
+ * a handle without Neumann cells).  Any of dLdf, dLdg, dLdgN may be NULL
+ * (not all three).  Handles with box_sides: MG_ERR_UNIMPLEMENTED (as
+ * mg_adjoint). */
+int mg_adjoint_bc(mg_handle h, const double* dLdu, double* dLdf, double* dLdg, double* dLdgN);
+
 /* Releases the handle and its device memory (NULL is ignored). */
 void mg_destroy(mg_handle h);
 

@@ -85,6 +85,7 @@ struct mg_ctx {
   const uint8_t* nmask_in = nullptr;   // caller's Neumann cell mask (setup only)
   double* Nk = nullptr;          // Neumann load per cut cell (null: all Dirichlet)
   int box = 0;                   // strong Dirichlet box sides
+  double* adj_tmp = nullptr;     // padded fp64 scratch of mg_adjoint_bc
   std::vector<void*> allocs;
   double last_tol = 1e-10;
   int tail_level = -1;           // first level run by the single-block tail kernel
@@ -1215,7 +1216,11 @@ int mg_get_profile(mg_handle c, long long* launches, long long* counts, double* 
 // cycle and precision, to the tolerance of the last solve; F = M f + G g is
 // linear in f and g (Eq. disc_rhs), so dL/df = M^T w and dL/dg = G^T w.
 int mg_adjoint(mg_handle c, const double* dLdu, double* dLdf, double* dLdg) {
-  if (!c || !dLdu || (!dLdf && !dLdg)) return MG_ERR_INVALID_ARG;
+  return mg_adjoint_bc(c, dLdu, dLdf, dLdg, nullptr);
+}
+
+int mg_adjoint_bc(mg_handle c, const double* dLdu, double* dLdf, double* dLdg, double* dLdgN) {
+  if (!c || !dLdu || (!dLdf && !dLdg && !dLdgN)) return MG_ERR_INVALID_ARG;
   // dL/dg would also need the transposed couplings to the box nodes
   if (c->box) return MG_ERR_UNIMPLEMENTED;
   Level& v = c->lev[0];
@@ -1226,6 +1231,12 @@ int mg_adjoint(mg_handle c, const double* dLdu, double* dLdf, double* dLdg) {
   bool fh = false, gh = false;
   if (dLdf) TRY(stage_out(c, 1, dLdf, &fd, &fh));
   if (dLdg) TRY(stage_out(c, 2, dLdg, &gd, &gh));
+  double* nd = nullptr;
+  bool nh = false;
+  if (dLdgN) {
+    TRY(stage_out(c, 3, dLdgN, &nd, &nh));
+    if (!c->adj_tmp) TRY(dalloc(c, &c->adj_tmp, v.L.size()));
+  }
   // right-hand side dL/du on the DOFs (NaN / Inf rejected), w from 0
   launch_pack<double>(v.L, v.code, sd.dev, v.F64, c->d_err, c->st);
   v.cur64 = 0;
@@ -1241,8 +1252,15 @@ int mg_adjoint(mg_handle c, const double* dLdu, double* dLdf, double* dLdg) {
   const double* w = v.u64[v.cur64];
   double* tf = v.F64;                          // dL/du is no longer needed
   double* tg = v.u64[v.cur64 ^ 1];
-  RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
-  launch_rhs_adj(ra, v.active, v.n_active, w, dLdf ? tf : nullptr, dLdg ? tg : nullptr, c->st);
+  RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk};
+  double* tn = c->adj_tmp;
+  if (dLdgN) MG_CUDA_TRY(cudaMemsetAsync(tn, 0, v.L.size() * sizeof(double), c->st));
+  launch_rhs_adj(ra, v.active, v.n_active, w, dLdf ? tf : nullptr, dLdg ? tg : nullptr, c->st,
+                 dLdgN ? tn : nullptr);
+  if (dLdgN) {
+    launch_unpack(v.L, v.code, tn, nd, c->st);
+    TRY(finish_out(c, dLdgN, nd, nh));
+  }
   if (dLdf) {
     launch_unpack(v.L, v.code, tf, fd, c->st);
     TRY(finish_out(c, dLdf, fd, fh));

@@ -544,7 +544,7 @@ k_rhs(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ f,
 // vertices of cut cells sum the cells one by one with column `av` of Mk, Gk.
 __global__ void __launch_bounds__(kThreads)
 k_rhs_adj(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ w,
-          double* __restrict__ dLdf, double* __restrict__ dLdg) {
+          double* __restrict__ dLdf, double* __restrict__ dLdg, double* __restrict__ dLdn) {
   __shared__ double sw[RHS_Y * RHS_X];       // w on the tile plus one ring
   __shared__ double st[RHS_Y * MG_TX];       // row pass w(i-1) + 4 w(i) + w(i+1)
   const int n = a.L.n;
@@ -567,7 +567,7 @@ k_rhs_adj(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ w
     const int i = i0 + x, j = j0 + y;
     const size_t gk = a.L.idx(i, j);
     const uint16_t cd = a.code[gk];
-    double sf = 0.0, sg = 0.0;
+    double sf = 0.0, sg = 0.0, sn = 0.0;
     if (cd == 1) {
       const double* c = st + y * MG_TX + x;
       sf = h2 * fma(4.0, c[MG_TX], c[0] + c[2 * MG_TX]);
@@ -594,11 +594,16 @@ k_rhs_adj(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ w
             sf += Mk[b * 4 + av] * wb[b];
             sg += Gk[b * 4 + av] * wb[b];
           }
+          if (dLdn && a.Nk) {
+            const double* Nk = a.Nk + (size_t)a.cell_cut[c] * 16;
+            for (int b = 0; b < 4; ++b) sn += Nk[b * 4 + av] * wb[b];
+          }
         }
       }
     }
     if (dLdf) dLdf[gk] = sf;
     if (dLdg) dLdg[gk] = sg;
+    if (dLdn) dLdn[gk] = sn;
   }
 }
 
@@ -817,9 +822,9 @@ void launch_rhs(const RhsArgs& a, const int* tiles, int ntiles, const double* f,
 }
 
 void launch_rhs_adj(const RhsArgs& a, const int* tiles, int ntiles, const double* w,
-                    double* dLdf, double* dLdg, cudaStream_t st) {
+                    double* dLdf, double* dLdg, cudaStream_t st, double* dLdn) {
   if (!ntiles) return;
-  k_rhs_adj<<<ntiles, kThreads, 0, st>>>(a, tiles, w, dLdf, dLdg);
+  k_rhs_adj<<<ntiles, kThreads, 0, st>>>(a, tiles, w, dLdf, dLdg, dLdn);
 }
 
 template <class T>

@@ -64,10 +64,10 @@ template <class T>
 void launch_coarse_solve(const Layout& Lc, const double* Ainv, const T* Fc, T* uc, cudaStream_t st);
 void launch_rhs(const RhsArgs& a, const int* tiles, int ntiles, const double* f, const double* g,
                 double* F, double* norms, cudaStream_t st);
-// dLdf = M^T w, dLdg = G^T w for w in the padded layout (either output may
-// be null): the adjoint of launch_rhs
+// dLdf = M^T w, dLdg = G^T w, dLdn = N^T w (a.Nk) for w in the padded
+// layout (any output may be null): the adjoint of launch_rhs
 void launch_rhs_adj(const RhsArgs& a, const int* tiles, int ntiles, const double* w,
-                    double* dLdf, double* dLdg, cudaStream_t st);
+                    double* dLdf, double* dLdg, cudaStream_t st, double* dLdn = nullptr);
 template <class T>
 void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* dst, unsigned* err,
                  cudaStream_t st, unsigned* nz = nullptr);

@@ -89,6 +89,7 @@ SIGNATURES = {
     "mg_solve": (_I, [_P, _P, _P, _P, _D, ctypes.POINTER(mg_info)]),
     "mg_solve_bc": (_I, [_P, _P, _P, _P, _P, _D, ctypes.POINTER(mg_info)]),
     "mg_adjoint": (_I, [_P, _P, _P, _P]),
+    "mg_adjoint_bc": (_I, [_P, _P, _P, _P, _P]),
     "mg_destroy": (None, [_P]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_get_counts": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -208,6 +209,11 @@ def mg_rhs_bc(handle: int, f, gD, gN, F) -> int:
 def mg_adjoint(handle: int, dLdu, dLdf=None, dLdg=None, ok=(MG_OK,)) -> int:
     return _check(load().mg_adjoint(handle, _addr(dLdu), _addr(dLdf, True), _addr(dLdg, True)),
                   "mg_adjoint", ok)
+
+
+def mg_adjoint_bc(handle: int, dLdu, dLdf=None, dLdg=None, dLdgN=None, ok=(MG_OK,)) -> int:
+    return _check(load().mg_adjoint_bc(handle, _addr(dLdu), _addr(dLdf, True), _addr(dLdg, True),
+                                       _addr(dLdgN, True)), "mg_adjoint_bc", ok)
 
 
 def mg_destroy(handle: int) -> None:
@@ -405,12 +411,17 @@ class Solver:
     def residual(self, F, u, r=None):
         return mg_residual(self.handle, F, u, r)
 
-    def adjoint(self, dLdu, dLdf=None, dLdg=None, allow_not_converged: bool = False):
-        """dL/df and dL/dg of a loss of the last solve's u (either output may
-        be None): solves A w = dL/du to the last solve's tolerance."""
+    def adjoint(self, dLdu, dLdf=None, dLdg=None, allow_not_converged: bool = False,
+                dLdgN=None):
+        """dL/df, dL/dg (and dL/dg_N with mixed conditions) of a loss of the
+        last solve's u (outputs may be None): solves A w = dL/du to the last
+        solve's tolerance."""
         ok = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
-        mg_adjoint(self.handle, dLdu, dLdf, dLdg, ok)
-        return dLdf, dLdg
+        if dLdgN is None:
+            mg_adjoint(self.handle, dLdu, dLdf, dLdg, ok)
+            return dLdf, dLdg
+        mg_adjoint_bc(self.handle, dLdu, dLdf, dLdg, dLdgN, ok)
+        return dLdf, dLdg, dLdgN
 
     def stencil(self, level: int) -> np.ndarray:
         n = mg_level_cells(self.handle, level)

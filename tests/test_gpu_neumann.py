@@ -177,3 +177,28 @@ def test_neumann_data_ignored_without_neumann_cells():
         S.solve(dev(p.f), dev(p.g), a, tol=1e-11)
         S.solve(dev(p.f), dev(p.g), b, tol=1e-11, gN=dev(np.ones_like(p.f)))
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["annulus64", "leaf64"])
+def test_adjoint_with_neumann_data(name, cache):
+    """mg_adjoint_bc: dL/df, dL/dg_D and dL/dg_N against the oracle's dense
+    adjoint (w = A^{-1} dL/du; M^T w, G^T w, N^T w) at 1e-9 of each
+    gradient's largest entry, after a solve to 1e-13."""
+    p, s, lev = oracle_for(name, cache)
+    rng = np.random.default_rng(41)
+    dLdu = rng.standard_normal(s.n_nodes)
+    ref_f, ref_g = gf.adjoint(s, dLdu)
+    ref_n = gf.adjoint_neumann(s, dLdu)
+    with solver(p, precision="fp64") as S:
+        u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+        S.solve(dev(p.f), dev(p.g), u, tol=1e-13, gN=dev(p.gN))
+        outs = [torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda") for _ in range(3)]
+        S.adjoint(dev(dLdu), outs[0], outs[1], dLdgN=outs[2])
+        for got, ref in zip(outs, (ref_f, ref_g, ref_n)):
+            got = host(got)
+            assert np.all(got[~s.dof] == 0)
+            assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+        # only the Neumann gradient, host arrays
+        gn = np.zeros(s.n_nodes)
+        S.adjoint(dLdu, None, None, dLdgN=gn)
+        assert np.abs(gn - ref_n).max() <= 1e-9 * np.abs(ref_n).max()
