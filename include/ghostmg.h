@@ -381,8 +381,8 @@ int mg_batch_get_shape(mg_batch b, mg_batch_shape* shape);
 
 /* Autotuner: times `reps` graph replays (after one warm-up) of the solve of
  * (f, g) to tol for candidate shapes, in three stages -- threads per block
- * x cluster size; then the sharing threshold coop_min_dof in
- * {0, 8192, 32768, 131072} (with clusters); then, with the adaptive
+ * x cluster size; then cluster size in {2, 4, 8} x the sharing threshold
+ * coop_min_dof in {0, 8192, 32768, 65536, 131072}; then, with the adaptive
  * schedule, first_group in {2, 3, 4, 6} -- and keeps the fastest shape whose
  * members all converge.  best and ms (mean time per solve) may be NULL.
  * Errors as mg_batch_solve (MG_ERR_NOT_CONVERGED if no candidate converged

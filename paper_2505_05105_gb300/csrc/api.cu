@@ -1753,13 +1753,17 @@ int mg_batch_tune(mg_batch b, const double* f, const double* g, double tol, int 
     TRY(batch_capture(b));
     return MG_ERR_NOT_CONVERGED;
   }
-  // 2. which members a cluster shares (by fine-level DOFs)
-  if (best.cluster > 1) {
-    const int thr[4] = {0, 8192, 32768, 131072};
+  // 2. cluster size x which members a cluster shares (by fine-level DOFs):
+  //    larger clusters pay only when few, large members share them
+  {
+    const int thr[5] = {0, 8192, 32768, 65536, 131072};
     const BatchTune base = best;
-    for (int k = 0; k < 4; ++k)
-      if (thr[k] != base.coop_min_dof)
-        TRY(consider(BatchTune{base.threads, base.first_group, base.cluster, thr[k]}));
+    for (int ci = 1; ci < 4; ++ci)
+      for (int k = 0; k < 5; ++k) {
+        const BatchTune t{base.threads, base.first_group, cl[ci], thr[k]};
+        if (t.cluster == base.cluster && t.coop_min_dof == base.coop_min_dof) continue;
+        TRY(consider(t));
+      }
   }
   // 3. V-cycles before the first fp64 check (adaptive schedule only)
   if (b->stab.inner == 0) {

@@ -170,7 +170,7 @@ def test_autotuner(members):
         f, g = dev(B.pack([p.f for p in ps])), dev(B.pack([p.g for p in ps]))
         (threads, first, cluster, coop), ms = B.tune(f, g, tol=1e-10, reps=2)
         assert threads in (256, 512, 1024) and first in (2, 3, 4, 6) and ms > 0.0
-        assert cluster in (1, 2, 4, 8) and coop in (0, 8192, 32768, 131072)
+        assert cluster in (1, 2, 4, 8) and coop in (0, 8192, 32768, 65536, 131072)
         assert B.shape() == (threads, first, cluster, coop)
         u = torch.zeros(B.total, dtype=torch.float64, device="cuda")
         info = B.solve(f, g, u, tol=1e-10)
