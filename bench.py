@@ -57,7 +57,7 @@ ALGO_BYTES = {
 }
 
 
-def parse():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -80,7 +80,11 @@ def parse():
                     help="setup and two solves of the batched workload, untimed (for ncu)")
     ap.add_argument("--batch-shape", default="",
                     help="threads,first_group,cluster,coop_min_dof for --profile-batch")
-    return ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def parse():
+    return parse_args()
 
 
 def workload_name(N):
@@ -210,6 +214,23 @@ def cpu_threads():
     return 1 if n >= 1 else 1
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value of a time (all ranks get it); x itself on
+    one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, ndof, steps, seconds):
+    """Whole-job throughput: the DOFs all ranks solved over the slowest
+    rank's time (each rank solves its own replica: weak scaling)."""
+    return world * ndof * steps / seconds
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -296,11 +317,7 @@ def run_ours(args):
         prof_out = ghostmg.mg_get_profile(S.handle) if prof else None
         if prof:
             ghostmg.mg_set_profiling(S.handle, False)
-        total = sum(ms)
-        if dist is not None:
-            tt = torch.tensor([total], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total = float(tt.item())
+        total = max_over_ranks(sum(ms), dist, dev)
         return total, ms, cycles, prof_out, info
 
     with ClockSampler(local) as clk:
@@ -319,8 +336,8 @@ def run_ours(args):
             large = run_large(args, dev, flush, stream)
     clocks = clk.summary()
 
-    value = world * ndof * args.steps / (total_mx / 1e3)
-    value64 = world * ndof * args.steps / (total_64 / 1e3)
+    value = job_value(world, ndof, args.steps, total_mx / 1e3)
+    value64 = job_value(world, ndof, args.steps, total_64 / 1e3)
 
     # roofline of the dominant fine-level kernel (live CUDA-event timing)
     launches, slots = prof
@@ -364,12 +381,9 @@ def run_ours(args):
             S.solve(fh.data_ptr(), gh.data_ptr(), uh.data_ptr(), tol=TOL)
             tot += time.perf_counter() - t0
         barrier()
-        if dist is not None:
-            tt = torch.tensor([tot], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tot = float(tt.item())
+        tot = max_over_ranks(tot, dist, dev)
         nb = fh.numel() * 8
-        e2e = {"value": world * ndof * args.steps / tot, "unit": UNIT,
+        e2e = {"value": job_value(world, ndof, args.steps, tot), "unit": UNIT,
                "h2d_bytes_per_step": 3 * nb, "d2h_bytes_per_step": nb}
 
     cpu = None
