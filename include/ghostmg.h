@@ -93,8 +93,7 @@ typedef struct {
  *     mg_solve), not a DOF; Omega may then reach the box sides.  Its
  *     couplings to the DOFs move to the right-hand side (F - A_pq g_q), the
  *     coarse levels keep their box nodes out too, and u is 0 there on
- *     output.  mg_adjoint and batches do not take it
- *     (MG_ERR_UNIMPLEMENTED). */
+ *     output.  mg_adjoint does not take it (MG_ERR_UNIMPLEMENTED). */
 typedef struct {
   int kind;
   const uint8_t* neumann_mask;
@@ -337,12 +336,14 @@ typedef struct {
 
 /* Sets up count >= 1 members: levelsets is a packed array (host or device)
  * of the members' nodal psi; grids[count] their grids (host).  bc and stab
- * as for mg_setup and shared by all members; stab->precision must be
- * MG_MIXED (or stab NULL).  cuda_stream: the caller's stream; the batch
- * orders its work after the work queued there when a call starts, and runs
- * on a stream of its own (a graph cannot be captured on the legacy
- * stream).  Errors as mg_setup, and MG_ERR_UNIMPLEMENTED for MG_FP64 and
- * for MG_BC_MIXED (a Neumann mask would be per member). */
+ * as for mg_setup and shared by all members, except that with MG_BC_MIXED
+ * bc->neumann_mask holds the members' cell masks one after another (member
+ * p's n_cells^2 bytes after those of members 0 .. p-1); stab->precision
+ * must be MG_MIXED (or stab NULL).  cuda_stream: the caller's stream; the
+ * batch orders its work after the work queued there when a call starts, and
+ * runs on a stream of its own (a graph cannot be captured on the legacy
+ * stream).  Errors as mg_setup, and MG_ERR_UNIMPLEMENTED for MG_FP64 or a
+ * W-cycle. */
 int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double* levelsets,
                    const mg_bc* bc, const mg_stab* stab, void* cuda_stream);
 
@@ -359,6 +360,12 @@ int mg_batch_buffers(mg_batch b, long long* total_nodes, double** f, double** g,
  * if a bounded shared-memory copy wait ran out; MG_ERR_CUDA. */
 int mg_batch_solve(mg_batch b, const double* f, const double* g, double* u, double tol,
                    mg_batch_info* info);
+
+/* mg_batch_solve with Neumann data: g_N a packed array like f (ignored on a
+ * batch set up without MG_BC_MIXED; NULL: g_N = 0).  A member with NaN/Inf
+ * in its g_N fails alone with MG_ERR_INVALID_ARG. */
+int mg_batch_solve_bc(mg_batch b, const double* f, const double* g, const double* g_N, double* u,
+                      double tol, mg_batch_info* info);
 
 /* Launch shape of the persistent kernel. */
 typedef struct {

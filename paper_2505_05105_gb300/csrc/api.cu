@@ -1302,6 +1302,8 @@ struct mg_batch_ctx {
   BatchResult* h_res = nullptr;     // pinned (the graph copies into it)
   unsigned* h_err = nullptr;        // pinned
   double *f = nullptr, *g = nullptr, *u = nullptr;
+  double* gN = nullptr;             // packed Neumann data (members with Neumann cells)
+  bool mixed = false;
   size_t smem = 0;
   int grid = 0;
   int n_coop = 0;
@@ -1448,7 +1450,9 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out, size_t win_bytes) {
   q.eta = c->stab.eta;
   q.nu1 = c->stab.nu1;
   q.nu2 = c->stab.nu2;
-  q.rhs = RhsArgs{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk};
+  q.rhs = RhsArgs{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
+                 (b->gN && c->Nk) ? b->gN + b->node_off[p] : nullptr, v.Ke, c->box};
+  q.gN = b->gN ? b->gN + b->node_off[p] : nullptr;
   q.f = b->f + b->node_off[p];
   q.g = b->g + b->node_off[p];
   q.u_out = b->u + b->node_off[p];
@@ -1592,10 +1596,20 @@ int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levels
   MG_CUDA_TRY(cudaMallocHost((void**)&b->h_res, (size_t)n * sizeof(BatchResult)));
   MG_CUDA_TRY(cudaMallocHost((void**)&b->h_err, sizeof(unsigned)));
   *b->h_err = 0;
+  b->mixed = bc && bc->kind == MG_BC_MIXED;
+  if (b->mixed) TRY(balloc(b, &b->gN, b->total_nodes));
+  size_t cell_off = 0;
   for (int p = 0; p < n; ++p) {
     mg_handle h = nullptr;
     const double* ls = levelsets + b->node_off[p];
-    TRY(mg_setup(&h, ls, &grids[p], bc, &b->stab, b->st));
+    mg_bc mb{MG_BC_DIRICHLET, nullptr, 0};
+    if (bc) {
+      mb = *bc;
+      // a batch's Neumann mask holds the members' masks one after another
+      if (b->mixed) mb.neumann_mask = bc->neumann_mask + cell_off;
+    }
+    cell_off += (size_t)grids[p].n_cells * grids[p].n_cells;
+    TRY(mg_setup(&h, ls, &grids[p], bc ? &mb : nullptr, &b->stab, b->st));
     b->mem.push_back(h);
   }
   std::vector<BatchProblem> probs(n);
@@ -1647,7 +1661,6 @@ int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double*
   else s.precision = MG_MIXED;
   if (s.precision == MG_FP64) return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
-  if (bc && (bc->kind == MG_BC_MIXED || bc->box_sides)) return MG_ERR_UNIMPLEMENTED;
   if (s.cycle != 1) return s.cycle == 2 ? MG_ERR_UNIMPLEMENTED : MG_ERR_INVALID_ARG;
   mg_batch_ctx* b = new mg_batch_ctx();
   b->user_st = (cudaStream_t)cuda_stream;
@@ -1676,8 +1689,20 @@ int mg_batch_buffers(mg_batch b, long long* total_nodes, double** f, double** g,
 
 int mg_batch_solve(mg_batch b, const double* f, const double* g, double* u, double tol,
                    mg_batch_info* info) {
+  return mg_batch_solve_bc(b, f, g, nullptr, u, tol, info);
+}
+
+int mg_batch_solve_bc(mg_batch b, const double* f, const double* g, const double* gN, double* u,
+                      double tol, mg_batch_info* info) {
   if (!b || !f || !g || !u || !(tol >= 0.0)) return MG_ERR_INVALID_ARG;
   TRY(batch_stage(b, f, g));
+  if (b->gN) {
+    // g_N = 0 when none is given
+    const size_t bytes = b->total_nodes * sizeof(double);
+    if (gN == nullptr) MG_CUDA_TRY(cudaMemsetAsync(b->gN, 0, bytes, b->st));
+    else if (gN != b->gN)
+      MG_CUDA_TRY(cudaMemcpyAsync(b->gN, gN, bytes, cudaMemcpyDefault, b->st));
+  }
   int worst = MG_OK;
   TRY(batch_run(b, tol, &worst));
   if (u != b->u) {

@@ -680,7 +680,9 @@ k_batch_check(const BatchProblem* __restrict__ probs, const size_t* __restrict__
   if (x >= total) return;
   const int p = member_of(node_off, count, x);
   const size_t k = x - node_off[p];
-  if (!isfinite(probs[p].f[k]) || !isfinite(probs[p].g[k])) atomicOr(&bad[p], 1u);
+  const BatchProblem& b = probs[p];
+  if (!isfinite(b.f[k]) || !isfinite(b.g[k]) || (b.gN && !isfinite(b.gN[k])))
+    atomicOr(&bad[p], 1u);
 }
 
 __global__ void __launch_bounds__(kFlatThreads)

@@ -54,6 +54,7 @@ struct BatchProblem {
   RhsArgs rhs;
   const double* f;
   const double* g;
+  const double* gN;            // Neumann data (null: the batch has no Neumann masks)
   double* u_out;
 };
 

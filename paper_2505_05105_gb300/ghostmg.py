@@ -109,6 +109,7 @@ SIGNATURES = {
     "mg_batch_buffers": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_P),
                               ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "mg_batch_solve": (_I, [_P, _P, _P, _P, _D, _P]),
+    "mg_batch_solve_bc": (_I, [_P, _P, _P, _P, _P, _D, _P]),
     "mg_batch_set_shape": (_I, [_P, ctypes.POINTER(mg_batch_shape)]),
     "mg_batch_get_shape": (_I, [_P, ctypes.POINTER(mg_batch_shape)]),
     "mg_batch_tune": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(mg_batch_shape),
@@ -469,7 +470,10 @@ class BatchSolver:
 
     def __init__(self, problems, *, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
                  nu1: int = 2, nu2: int = 1, max_cycles: int = 100, inner: int = 0,
-                 stream: int = 0):
+                 stream: int = 0, box_sides: bool = False):
+        """Members with a ``neumann_mask`` attribute make a MG_BC_MIXED batch
+        (members without one get an all-zero mask); box_sides applies to all
+        members."""
         stab = mg_default_stab()
         stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta
         stab.nu1, stab.nu2, stab.max_cycles, stab.inner = nu1, nu2, max_cycles, inner
@@ -477,7 +481,16 @@ class BatchSolver:
         self.sizes = [int(p.N) for p in problems]
         grids = [mg_grid(p.N, p.x0, p.y0, p.h, 8) for p in problems]
         psi = self.pack([p.psi for p in problems])
-        self.handle = mg_batch_setup(grids, psi, mg_bc(MG_BC_DIRICHLET, None), stab, stream)
+        masks = [getattr(p, "neumann_mask", None) for p in problems]
+        if any(m is not None for m in masks):
+            self._mask = np.concatenate([
+                (np.zeros(p.N * p.N, np.uint8) if m is None
+                 else np.ascontiguousarray(m, dtype=np.uint8).ravel())
+                for p, m in zip(problems, masks)])
+            bc = mg_bc(MG_BC_MIXED, self._mask.ctypes.data, int(box_sides))
+        else:
+            bc = mg_bc(MG_BC_DIRICHLET, None, int(box_sides))
+        self.handle = mg_batch_setup(grids, psi, bc, stab, stream)
         self.count = len(problems)
         self.total, self._f, self._g, self._u = mg_batch_buffers(self.handle)
 
@@ -500,10 +513,15 @@ class BatchSolver:
         return tuple(torch.as_tensor(_DeviceArray(ptr, self.total), device="cuda")
                      for ptr in (self._f, self._g, self._u))
 
-    def solve(self, f, g, u, tol: float = 1e-10, allow_not_converged: bool = False):
+    def solve(self, f, g, u, tol: float = 1e-10, allow_not_converged: bool = False, gN=None):
         info = (mg_batch_info * self.count)()
         ok = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
-        mg_batch_solve(self.handle, f, g, u, tol, info, ok)
+        if gN is None:
+            mg_batch_solve(self.handle, f, g, u, tol, info, ok)
+        else:
+            _check(load().mg_batch_solve_bc(self.handle, _addr(f), _addr(g), _addr(gN),
+                                            _addr(u, True), tol, ctypes.addressof(info)),
+                   "mg_batch_solve_bc", ok)
         return list(info)
 
     def solve_status(self, f, g, u, tol: float = 1e-10):

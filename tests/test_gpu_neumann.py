@@ -160,11 +160,6 @@ def test_bad_neumann_data_rejected():
         with pytest.raises(G.GhostMGError) as e:
             S.solve(dev(p.f), dev(p.g), u, gN=dev(gN))
         assert e.value.code == G.MG_ERR_INVALID_ARG
-    # a batch does not take per-member masks
-    with pytest.raises(G.GhostMGError) as e:
-        G.mg_batch_setup([G.mg_grid(p.N, p.x0, p.y0, p.h, 8)], p.psi.ravel().copy(),
-                         G.mg_bc(G.MG_BC_MIXED, p.neumann_mask.ctypes.data))
-    assert e.value.code == G.MG_ERR_UNIMPLEMENTED
 
 
 def test_neumann_data_ignored_without_neumann_cells():
