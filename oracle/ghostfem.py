@@ -555,7 +555,11 @@ def adjoint(system: System, dLdu: np.ndarray):
     matter: u is 0 there whatever f and g are."""
     d = np.ravel(dLdu).astype(np.float64) * system.dof
     w = direct_solve(system, d)
-    return system.M.T @ w, system.G.T @ w
+    dLdg = system.G.T @ w
+    if system.B is not None:
+        # strong box values enter F as - B g
+        dLdg = dLdg - system.B.T @ w
+    return system.M.T @ w, dLdg
 
 
 def adjoint_neumann(system: System, dLdu: np.ndarray):

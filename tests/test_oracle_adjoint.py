@@ -84,3 +84,32 @@ def test_neumann_adjoint_matches_central_differences():
         fd = (L(n0 + e) - L(n0 - e)) / (2 * h)
         assert fd == pytest.approx(dLdn[q], abs=1e-9 * scale)
 
+
+def test_box_adjoint_matches_central_differences():
+    """With strong box sides g also enters F as - B g: dL/dg = G^T w - B^T w,
+    nonzero on the box nodes next to the domain; central differences."""
+    p = wl.rectangle(16, 0.37)
+    s = gf.assemble_problem(p)
+    rng = np.random.default_rng(5)
+    inside = ((np.ravel(p.psi) < 0) & s.dof).astype(float)
+    ut = rng.standard_normal(s.n_nodes)
+    f0, g0 = np.ravel(p.f).copy(), np.ravel(p.g).copy()
+
+    def L(g):
+        u = gf.direct_solve(s, s.rhs(f0, g))
+        return loss_and_grad(s, u, ut, inside)[0]
+
+    u = gf.direct_solve(s, s.rhs(f0, g0))
+    _, dLdu = loss_and_grad(s, u, ut, inside)
+    _, dLdg = gf.adjoint(s, dLdu)
+    ring = np.zeros((p.N + 1, p.N + 1), bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    assert np.abs(dLdg[ring.ravel()]).max() > 0
+    scale = np.abs(dLdg).max()
+    h = 1e-3
+    for q in list(rng.choice(np.flatnonzero(ring.ravel() & (dLdg != 0)), 8, replace=False)) + \
+            list(rng.choice(np.flatnonzero(dLdg != 0), 8, replace=False)):
+        e = np.zeros_like(g0); e[q] = h
+        fd = (L(g0 + e) - L(g0 - e)) / (2 * h)
+        assert fd == pytest.approx(dLdg[q], abs=1e-9 * scale)
+
