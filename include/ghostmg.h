@@ -93,7 +93,8 @@ typedef struct {
  *     mg_solve), not a DOF; Omega may then reach the box sides.  Its
  *     couplings to the DOFs move to the right-hand side (F - A_pq g_q), the
  *     coarse levels keep their box nodes out too, and u is 0 there on
- *     output.  mg_adjoint does not take it (MG_ERR_UNIMPLEMENTED). */
+ *     output; mg_adjoint's dL/dg then also holds the box nodes' share,
+ *     -(B^T w)_q for the couplings B moved to the right-hand side. */
 typedef struct {
   int kind;
   const uint8_t* neumann_mask;
@@ -201,8 +202,7 @@ int mg_adjoint(mg_handle h, const double* dLdu, double* dLdf, double* dLdg);
 /* mg_adjoint with mixed boundary conditions: also dL/dg_N = N^T w (F holds
  * N g_N, Eq. disc_rhs; zero away from Neumann cut cells, and everywhere on
  * a handle without Neumann cells).  Any of dLdf, dLdg, dLdgN may be NULL
- * (not all three).  Handles with box_sides: MG_ERR_UNIMPLEMENTED (as
- * mg_adjoint). */
+ * (not all three). */
 int mg_adjoint_bc(mg_handle h, const double* dLdu, double* dLdf, double* dLdg, double* dLdgN);
 
 /* Releases the handle and its device memory (NULL is ignored). */

@@ -86,6 +86,7 @@ struct mg_ctx {
   double* Nk = nullptr;          // Neumann load per cut cell (null: all Dirichlet)
   int box = 0;                   // strong Dirichlet box sides
   double* adj_tmp = nullptr;     // padded fp64 scratch of mg_adjoint_bc
+  int* all_tiles = nullptr;      // every tile of the fine level (box adjoint)
   std::vector<void*> allocs;
   double last_tol = 1e-10;
   int tail_level = -1;           // first level run by the single-block tail kernel
@@ -1221,8 +1222,6 @@ int mg_adjoint(mg_handle c, const double* dLdu, double* dLdf, double* dLdg) {
 
 int mg_adjoint_bc(mg_handle c, const double* dLdu, double* dLdf, double* dLdg, double* dLdgN) {
   if (!c || !dLdu || (!dLdf && !dLdg && !dLdgN)) return MG_ERR_INVALID_ARG;
-  // dL/dg would also need the transposed couplings to the box nodes
-  if (c->box) return MG_ERR_UNIMPLEMENTED;
   Level& v = c->lev[0];
   const double tol = c->last_tol > 0.0 ? c->last_tol : 1e-10;
   Staged sd;
@@ -1252,21 +1251,41 @@ int mg_adjoint_bc(mg_handle c, const double* dLdu, double* dLdf, double* dLdg, d
   const double* w = v.u64[v.cur64];
   double* tf = v.F64;                          // dL/du is no longer needed
   double* tg = v.u64[v.cur64 ^ 1];
-  RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk};
+  RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk, nullptr, v.Ke, c->box};
+  const int* atiles = v.active;
+  int n_atiles = v.n_active;
+  if (c->box) {
+    // box nodes can sit in tiles without DOFs (the last tile row or column):
+    // visit every tile
+    const int nt = v.L.ntx * v.L.nty;
+    if (!c->all_tiles) {
+      std::vector<int> all(nt);
+      for (int t = 0; t < nt; ++t) all[t] = t;
+      TRY(dalloc(c, &c->all_tiles, (size_t)nt));
+      MG_CUDA_TRY(cudaMemcpyAsync(c->all_tiles, all.data(), (size_t)nt * sizeof(int),
+                                  cudaMemcpyHostToDevice, c->st));
+      MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+    }
+    atiles = c->all_tiles;
+    n_atiles = nt;
+    // the outputs are read on every tile
+    if (dLdf) MG_CUDA_TRY(cudaMemsetAsync(tf, 0, v.L.size() * sizeof(double), c->st));
+    if (dLdg) MG_CUDA_TRY(cudaMemsetAsync(tg, 0, v.L.size() * sizeof(double), c->st));
+  }
   double* tn = c->adj_tmp;
   if (dLdgN) MG_CUDA_TRY(cudaMemsetAsync(tn, 0, v.L.size() * sizeof(double), c->st));
-  launch_rhs_adj(ra, v.active, v.n_active, w, dLdf ? tf : nullptr, dLdg ? tg : nullptr, c->st,
+  launch_rhs_adj(ra, atiles, n_atiles, w, dLdf ? tf : nullptr, dLdg ? tg : nullptr, c->st,
                  dLdgN ? tn : nullptr);
   if (dLdgN) {
     launch_unpack(v.L, v.code, tn, nd, c->st);
     TRY(finish_out(c, dLdgN, nd, nh));
   }
   if (dLdf) {
-    launch_unpack(v.L, v.code, tf, fd, c->st);
+    launch_unpack(v.L, v.code, tf, fd, c->st, c->box);
     TRY(finish_out(c, dLdf, fd, fh));
   }
   if (dLdg) {
-    launch_unpack(v.L, v.code, tg, gd, c->st);
+    launch_unpack(v.L, v.code, tg, gd, c->st, c->box);
     TRY(finish_out(c, dLdg, gd, gh));
   }
   TRY(sync_check(c));

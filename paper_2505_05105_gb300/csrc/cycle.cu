@@ -571,7 +571,9 @@ k_rhs_adj(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ w
     if (cd == 1) {
       const double* c = st + y * MG_TX + x;
       sf = h2 * fma(4.0, c[MG_TX], c[0] + c[2 * MG_TX]);
-    } else if (cd) {
+    } else if (cd || (a.box && i <= n && j <= n && (i == 0 || j == 0 || i == n || j == n))) {
+      // (a strong box node: f and g there still enter the load of its
+      // neighbours through M and G)
       for (int k = 0; k < 4; ++k) {
         const int dx = k & 1, dy = k >> 1;
         const int ic = i - 1 + dx, jc = j - 1 + dy;
@@ -598,6 +600,29 @@ k_rhs_adj(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ w
             const double* Nk = a.Nk + (size_t)a.cell_cut[c] * 16;
             for (int b = 0; b < 4; ++b) sn += Nk[b * 4 + av] * wb[b];
           }
+        }
+      }
+    }
+    if (a.box && !cd && (i == 0 || j == 0 || i == n || j == n) && i <= n && j <= n) {
+      // a strong Dirichlet box node: g_q enters F as - A_pq g_q, so its
+      // gradient is - sum over the adjacent cells of A_K(p, q) w_p
+      for (int k = 0; k < 4; ++k) {
+        const int dx = k & 1, dy = k >> 1;
+        const int ic = i - 1 + dx, jc = j - 1 + dy;
+        if (ic < 0 || jc < 0 || ic >= n || jc >= n) continue;
+        const size_t c = (size_t)jc * n + ic;
+        const uint8_t cl = a.cls[c];
+        if (cl == CELL_EXT) continue;
+        const int av = (1 - dx) + 2 * (1 - dy);
+        const double* wv = sw + (y + dy) * RHS_X + (x + dx);
+        const double wb[4] = {wv[0], wv[1], wv[RHS_X], wv[RHS_X + 1]};
+        for (int b = 0; b < 4; ++b) {
+          const int bi = ic + (b & 1), bj = jc + (b >> 1);
+          if (bi == 0 || bj == 0 || bi == n || bj == n) continue;     // box nodes: w = 0
+          const double e = cl == CELL_INT
+                               ? ((b == av) ? 4.0 / 6.0 : ((b ^ av) == 3 ? -2.0 / 6.0 : -1.0 / 6.0))
+                               : a.Ke[(size_t)a.cell_cut[c] * 16 + b * 4 + av];
+          sg -= e * wb[b];
         }
       }
     }
@@ -649,14 +674,16 @@ __global__ void k_pack(Layout L, const uint16_t* __restrict__ code, const double
   if (nz && __any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(nz, 1u);
 }
 
-// Padded layout -> user layout, zero on nodes that are not DOFs.
+// Padded layout -> user layout, zero on nodes that are not DOFs (box: the
+// box-side nodes are kept as well).
 __global__ void k_unpack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
-                         double* __restrict__ dst) {
+                         double* __restrict__ dst, int box) {
   const int n = L.n, j = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > n) return;
   const size_t g = L.idx(i, j);
-  dst[(size_t)j * (n + 1) + i] = code[g] ? src[g] : 0.0;
+  const bool keep = code[g] || (box && (i == 0 || j == 0 || i == n || j == n));
+  dst[(size_t)j * (n + 1) + i] = keep ? src[g] : 0.0;
 }
 
 
@@ -835,9 +862,9 @@ void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* ds
 }
 
 void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
-                   cudaStream_t st) {
+                   cudaStream_t st, int box) {
   dim3 grid((L.n + 1 + kThreads - 1) / kThreads, L.n + 1);
-  k_unpack<<<grid, kThreads, 0, st>>>(L, code, src, dst);
+  k_unpack<<<grid, kThreads, 0, st>>>(L, code, src, dst, box);
 }
 
 void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,

@@ -71,8 +71,9 @@ void launch_rhs_adj(const RhsArgs& a, const int* tiles, int ntiles, const double
 template <class T>
 void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* dst, unsigned* err,
                  cudaStream_t st, unsigned* nz = nullptr);
+// box != 0: the box-side nodes are copied too (gradients on strong box nodes)
 void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
-                   cudaStream_t st);
+                   cudaStream_t st, int box = 0);
 void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,
                           cudaStream_t st);
 // dst = (float)(src * scale) on the DOFs of the tiles (the refinement
