@@ -116,7 +116,11 @@ typedef struct {
  *                 one refinement step: fp64 residual, `k` fp32 V-cycles on
  *                 the correction equation (the first from e = 0), u += e.
  *   cycle = 1     cycles on each coarse level per visit (Alg. 1, gamma*):
- *                 1 = V-cycle, 2 = W-cycle (batches: V only).
+ *                 1 = V-cycle, 2 = W-cycle (batches: V only); 0 = the
+ *                 two-grid correction scheme of Alg. 1 (the coarse equation
+ *                 of the finest level solved exactly -- by 40 V-cycles of
+ *                 the coarser hierarchy, which leave an error at rounding
+ *                 level -- for convergence studies; MG_FP64 only).
  *   coarse_op = MG_COARSE_GALERKIN  coarse operators A_2h = P^T A_h P
  *                 (Eq. galerkin); MG_COARSE_REDISCRETISE: each coarse level
  *                 assembled from scratch on its own grid from the level set

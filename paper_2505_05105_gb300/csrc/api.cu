@@ -374,6 +374,17 @@ void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine, Level* coarse = nullpt
   }
 }
 
+// Cycles on level l + 1 per visit of level l: gamma* of Alg. 1 (1 V, 2 W);
+// the two-grid scheme (stab.cycle = 0) solves the coarse equation of the
+// finest level exactly, here by kTwoGridInner V-cycles of the coarser
+// hierarchy (their contraction makes the error vanish to rounding), and
+// runs V-cycles below.
+constexpr int kTwoGridInner = 40;
+int coarse_cycles(const mg_ctx* c, int l) {
+  if (c->stab.cycle == 0) return l == 0 ? kTwoGridInner : 1;
+  return c->stab.cycle;
+}
+
 template <class T>
 void tail_cycle(mg_ctx* c, int l, bool zero_init) {
   const int pi = sizeof(T) == 8 ? 1 : 0;
@@ -436,9 +447,9 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
     launch_resid_restrict<T>(op_of<T>(v), P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
                              P<T>::F(w), nullptr, c->st);
   }
-  // gamma* = stab.cycle cycles on the coarse level (Alg. 1: 1 V, 2 W), the
-  // first from zero
-  for (int k = 0; k < c->stab.cycle; ++k) vcycle<T>(c, l + 1, k == 0);
+  // gamma* cycles on the coarse level (Alg. 1: 1 V, 2 W), the first from zero
+  const int gs = coarse_cycles(c, l);
+  for (int k = 0; k < gs; ++k) vcycle<T>(c, l + 1, k == 0);
   a.ec = P<T>::u(w, P<T>::cur(w));
   a.tiles = v.active;
   for (int s = 0; s < nu2; ++s) {
@@ -485,9 +496,9 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
     launch_resid_restrict<T>(op, P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
                              P<T>::F(w), nullptr, c->st);
   }
-  // gamma* = stab.cycle cycles on the coarse level (Alg. 1: 1 V, 2 W), the
-  // first from zero
-  for (int k = 0; k < c->stab.cycle; ++k) vcycle<T>(c, l + 1, k == 0);
+  // gamma* cycles on the coarse level (Alg. 1: 1 V, 2 W), the first from zero
+  const int gs = coarse_cycles(c, l);
+  for (int k = 0; k < gs; ++k) vcycle<T>(c, l + 1, k == 0);
   if (c->stab.nu2 == 0) {
     Launch k(c, fine ? MG_PROF_PROLONG : MG_PROF_COARSE, v.n_active > 0);
     launch_prolong<T>(op, v.active, v.n_active, P<T>::u(v, cur), w.L, P<T>::u(w, P<T>::cur(w)),
@@ -828,13 +839,15 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     const int nlev = (int)c->lev.size();
     int t = 0;
     while (t < nlev && c->lev[t].n > MG_TAIL_MAX_N) ++t;
+    // the two-grid scheme treats the finest level on its own
+    if (c->stab.cycle == 0 && t == 0) t = 1;
     int dev = 0, optin = 0;
     MG_CUDA_TRY(cudaGetDevice(&dev));
     MG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     optin -= 1024;   // static shared memory of the kernel
     // (the tail block runs a V-cycle below its top level: W-cycles use the
     // per-level kernels all the way down)
-    if (c->stab.cycle == 1 && t < nlev && nlev - t <= MG_TAIL_MAX_LEVELS) {
+    if (c->stab.cycle != 2 && t < nlev && nlev - t <= MG_TAIL_MAX_LEVELS) {
       const int nl = nlev - t;
       int n[MG_TAIL_MAX_LEVELS], nb[MG_TAIL_MAX_LEVELS];
       TailLevelSrc src[MG_TAIL_MAX_LEVELS];
@@ -916,10 +929,12 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
     return MG_ERR_INVALID_ARG;
   if (!(s.gamma > 0.0) || !(s.alpha > 0.0) || s.eta < 0 || s.eta > 8 || s.nu1 < 0 || s.nu1 > 8 ||
       s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0 || s.inner < 0 ||
-      s.inner > 8 || (s.cycle != 1 && s.cycle != 2) ||
+      s.inner > 8 || s.cycle < 0 || s.cycle > 2 ||
       (s.coarse_op != MG_COARSE_GALERKIN && s.coarse_op != MG_COARSE_REDISCRETISE))
     return MG_ERR_INVALID_ARG;
   if (s.lambda_mode != MG_LAMBDA_LOCAL) return MG_ERR_UNIMPLEMENTED;
+  // the two-grid scheme's "exact" coarse solve needs fp64 cycles
+  if (s.cycle == 0 && s.precision != MG_FP64) return MG_ERR_UNIMPLEMENTED;
   // a Neumann mask is given for the fine cells only
   if (s.coarse_op == MG_COARSE_REDISCRETISE && bc && bc->kind == MG_BC_MIXED)
     return MG_ERR_UNIMPLEMENTED;
@@ -1680,7 +1695,7 @@ int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double*
   else s.precision = MG_MIXED;
   if (s.precision == MG_FP64) return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
-  if (s.cycle != 1) return s.cycle == 2 ? MG_ERR_UNIMPLEMENTED : MG_ERR_INVALID_ARG;
+  if (s.cycle != 1) return (s.cycle == 0 || s.cycle == 2) ? MG_ERR_UNIMPLEMENTED : MG_ERR_INVALID_ARG;
   mg_batch_ctx* b = new mg_batch_ctx();
   b->user_st = (cudaStream_t)cuda_stream;
   b->count = count;

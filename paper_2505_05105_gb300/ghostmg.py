@@ -361,7 +361,7 @@ class Solver:
         stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta
         stab.nu1, stab.nu2, stab.max_cycles, stab.inner = nu1, nu2, max_cycles, inner
         stab.precision = {"fp64": MG_FP64, "mixed": MG_MIXED}[precision]
-        stab.cycle = {"V": 1, "W": 2}[cycle]
+        stab.cycle = {"V": 1, "W": 2, "two-grid": 0}[cycle]
         stab.coarse_op = {"galerkin": MG_COARSE_GALERKIN,
                           "rediscretise": MG_COARSE_REDISCRETISE}[coarse]
         grid = mg_grid(n_cells, x0, y0, h, coarsest)

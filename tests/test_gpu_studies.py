@@ -188,3 +188,26 @@ def test_coarse_option_rejected_with_neumann_mask():
     with pytest.raises(G.GhostMGError) as e:
         solver(p, coarse="rediscretise")
     assert e.value.code == G.MG_ERR_UNIMPLEMENTED
+
+
+@pytest.mark.parametrize("make", [wl.paper_circle, wl.paper_flower, wl.paper_hourglass,
+                                  wl.annulus, wl.leaf])
+def test_two_grid_factor(make):
+    """The paper's measured quantity: the convergence factor of the two-grid
+    correction scheme (stab.cycle = 0, the coarse equation solved to
+    rounding) equals the oracle's (exact sparse solve) to 1e-6, and with
+    lambda = 2 C(K), eta = 4 it is ~0.1 or below (Sec. 5.3); without the
+    extra sweeps it is above 0.2."""
+    p = make(64)
+    s = gf.assemble_problem(p)
+    lev = mg.build_hierarchy(s)
+    for eta, bound in ((4, 0.1), (0, None)):
+        ref, _ = mg.convergence_factor(lev, cycles=20, first=11, order="color4", eta=eta,
+                                       two_grid=True)
+        got = gpu_rho(p, s.dof, eta=eta, cycle="two-grid")
+        assert got == pytest.approx(ref, rel=1e-6), (eta, got, ref)
+        if bound is not None:
+            assert got < bound, got
+        else:
+            assert got > 0.2, got
+
