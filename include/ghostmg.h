@@ -84,8 +84,10 @@ typedef struct {
  *     keeps only its volume stiffness (Eq. disc_bil_form has no boundary
  *     term on Gamma_N) and adds int_{K cap Gamma_N} g_N phi_i to the load
  *     (Eq. disc_rhs, g_N through its Q1 interpolant of nodal values, see
- *     mg_solve_bc).  Bytes of other cells are ignored.  At least one cut
- *     cell must stay Dirichlet (otherwise A is singular: MG_ERR_NOT_SPD).
+ *     mg_solve_bc).  Bytes of other cells are ignored.  Some Dirichlet
+ *     data must remain (a Dirichlet cut cell or box_sides): with Neumann
+ *     data alone u is fixed only up to a constant, A is singular, and setup
+ *     fails with MG_ERR_NOT_SPD or the solves do not converge.
  * Any other combination is MG_ERR_INVALID_ARG.
  *   box_sides != 0: strong Dirichlet conditions on the sides of the box
  *     (the rectangle example of Sec. 5.3): every node with i or j equal to
