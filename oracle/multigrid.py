@@ -137,7 +137,7 @@ def build_hierarchy(system: System, coarsest: int = 8, rediscretise_psi=None) ->
             psi = np.asarray(rediscretise_psi, dtype=np.float64).reshape(system.N + 1,
                                                                         system.N + 1)
             sc = assemble(psi[::step, ::step], nc, system.x0, system.y0, system.h * step,
-                          system.gamma, system.alpha)
+                          system.gamma, system.alpha, box_strong=system.box_strong)
             lev.append(Level(nc, sc.A.tocsr(), sc.dof.copy(), sc.cls.copy(),
                              cut_node_mask(sc.cls) & sc.dof))
     return lev
