@@ -55,7 +55,8 @@ enum {
 
 enum { MG_BC_DIRICHLET = 0,       /* weak Dirichlet on the whole of {psi = 0} */
        MG_BC_MIXED = 1 };         /* Dirichlet / Neumann by a per-cell mask */
-enum { MG_LAMBDA_LOCAL = 0 };     /* lambda_K = gamma C(K) per cut cell (Sec. 5.2) */
+enum { MG_LAMBDA_LOCAL = 0,       /* lambda_K = gamma C(K) per cut cell (Sec. 5.2) */
+       MG_LAMBDA_GLOBAL = 1 };    /* lambda = gamma c_global on every cut cell (Sec. 5.2) */
 enum { MG_COARSE_GALERKIN = 0,    /* A_2h = P^T A_h P (Eq. galerkin) */
        MG_COARSE_REDISCRETISE = 1 };  /* A_2h assembled on the coarse grid */
 enum { MG_FP64 = 0,               /* fp64 V-cycles */
@@ -108,7 +109,18 @@ typedef struct {
  *   alpha = 1.75  snapping threshold h^alpha                   (Sec. 5.3)
  *   eta = 4       extra cut-cell sweeps per smoothing step     (Sec. 5.3), 0..8
  *   nu1 = 2, nu2 = 1  pre/post smoothing steps                 (Sec. 5.3), 0..8
- *   lambda_mode = MG_LAMBDA_LOCAL
+ *   lambda_mode = MG_LAMBDA_LOCAL: lambda_K = gamma C(K), C(K) the largest
+ *                 generalized eigenvalue of the cell's pencil (Sec. 5.2);
+ *                 MG_LAMBDA_GLOBAL: lambda = gamma c_global on every cut
+ *                 cell, c_global the largest generalized eigenvalue of the
+ *                 global pencil K v = Lambda M v of Sec. 5.2 (K: normal
+ *                 derivatives on Gamma_D, M: stiffness on Omega_h, both over
+ *                 the whole FE space).  That eigenvalue is the caller's (a
+ *                 setup-time computation for convergence studies, in 1/length
+ *                 units): c_global must be finite and > 0
+ *                 (MG_ERR_INVALID_ARG otherwise); not with
+ *                 MG_COARSE_REDISCRETISE nor in batches
+ *                 (MG_ERR_UNIMPLEMENTED).  C(K) is still reported per cell.
  *   precision = MG_FP64 or MG_MIXED
  *   max_cycles = 100  V-cycles in total (both precisions)
  *   inner = 0     V-cycles between two fp64 residual checks, 0..8:
@@ -136,6 +148,7 @@ typedef struct {
   int inner;
   int cycle;
   int coarse_op;
+  double c_global;        /* MG_LAMBDA_GLOBAL only; default 0 */
 } mg_stab;
 
 /* Result summary of a solve. */

@@ -44,7 +44,11 @@ straight cut reduces to the Neumann end of the 1D system (Eq. ls1dA, the
 theta_2 block, and Eq. ls1dF, F^N); a patch test with a straight Neumann
 side reproduces bilinear harmonic solutions exactly; second-order
 convergence on the annulus with Dirichlet inner and Neumann outer circle
-(Sec. 5.3) and on the leaf with mixed data.
+(Sec. 5.3) and on the leaf with mixed data.  The global constant of Sec. 5.2
+(``global_C``): 1 / (theta h) on a straight cut through the box (the 1D value
+of Sec. 4.4 carried over by the tensor-product structure), 1 / (min theta h)
+on a strip with two cuts, at most the largest local C(K), 0 with every cut
+cell Neumann (tests/test_oracle_global_lambda.py).
 """
 from __future__ import annotations
 
@@ -374,16 +378,18 @@ class CutCell:
     Nk: np.ndarray = None   # Neumann load: phi_i phi_j on K cap Gamma_h
 
 
-def cut_cell(psi4, ic, jc, x0, y0, h, gamma, neumann=False) -> CutCell:
+def cut_cell(psi4, ic, jc, x0, y0, h, gamma, neumann=False, c_global=None) -> CutCell:
     """Element matrices of cut cell (ic, jc).  The integrals are invariant
     under translation, so they are taken in cell-local coordinates (origin
     at the cell's lower-left corner, side h): absolute coordinates would add
     cancellation of order |x0 + ic h| / (size of the cut region).
-    neumann: the cell's boundary piece belongs to Gamma_N."""
+    neumann: the cell's boundary piece belongs to Gamma_N.
+    c_global: the global constant of Sec. 5.2 (``global_C``); when given,
+    lambda = gamma c_global on every cut cell instead of gamma C(K)."""
     config, pieces, thetas = cut_pieces(psi4)
     ints = cell_integrals(pieces, 0.0, 0.0, h)
     C = stabilisation_C(config, psi4, pieces, ints, 0.0, 0.0, h)
-    lam = gamma * C
+    lam = gamma * (C if c_global is None else c_global)
     if neumann:
         # Eq. disc_bil_form has no boundary term on Gamma_N; Eq. disc_rhs
         # has int g_N phi_i over K cap Gamma_N
@@ -451,13 +457,15 @@ def cell_nodes(ic, jc, N):
 
 
 def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75, neumann_mask=None,
-             box_strong=False) -> System:
+             box_strong=False, c_global=None) -> System:
     """A, M, G over all (N+1)^2 nodes (Eq. disc_bil_form, Eq. disc_rhs).
     neumann_mask: (N, N) cells [jc, ic], nonzero where a cut cell's boundary
     piece belongs to Gamma_N (ignored on other cells); None: all Dirichlet.
     box_strong: the nodes on the sides of the box (i or j equal to 0 or N)
     carry strong Dirichlet values (the rectangle of Sec. 5.3): they are not
-    DOFs, and their couplings to the DOFs move to the right-hand side."""
+    DOFs, and their couplings to the DOFs move to the right-hand side.
+    c_global: lambda = gamma c_global on every cut cell (the global choice of
+    Sec. 5.2) instead of the local lambda_K = gamma C(K)."""
     nm = None if neumann_mask is None else np.asarray(neumann_mask).reshape(N, N) != 0
     psi_s = snap(np.asarray(psi, dtype=np.float64).reshape(N + 1, N + 1), h, alpha)
     cls = cell_classes(psi_s)
@@ -477,7 +485,8 @@ def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75, neumann_mask=None,
     jj, ii = np.nonzero(cls == CUT)
     for i, j in zip(ii, jj):
         neu = bool(nm[j, i]) if nm is not None else False
-        cc = cut_cell(cell_corner_psi(psi_s, i, j), int(i), int(j), x0, y0, h, gamma, neu)
+        cc = cut_cell(cell_corner_psi(psi_s, i, j), int(i), int(j), x0, y0, h, gamma, neu,
+                      c_global)
         cuts.append(cc)
         nodes = cell_nodes(i, j, N)
         rows.append(np.repeat(nodes, 4))
@@ -510,10 +519,52 @@ def assemble(psi, N, x0, y0, h, gamma=2.0, alpha=1.75, neumann_mask=None,
     return System(N, x0, y0, h, gamma, alpha, psi_s, cls, dof, A, M, G, cuts, Gn, B, box_strong)
 
 
-def assemble_problem(prob, gamma=2.0, alpha=1.75) -> System:
+def assemble_problem(prob, gamma=2.0, alpha=1.75, c_global=None) -> System:
     return assemble(prob.psi, prob.N, prob.x0, prob.y0, prob.h, gamma, alpha,
                     getattr(prob, "neumann_mask", None),
-                    bool(getattr(prob, "meta", {}).get("box_strong", False)))
+                    bool(getattr(prob, "meta", {}).get("box_strong", False)), c_global)
+
+
+def global_C(psi, N, x0, y0, h, alpha=1.75, neumann_mask=None) -> float:
+    """The global constant of Sec. 5.2: the largest generalized eigenvalue of
+    K v = Lambda M v over the whole FE space, with
+      K_ij = int_{Gamma_D} (n . grad phi_i)(n . grad phi_j) dS,
+      M_ij = int_{Omega_h} grad phi_i . grad phi_j dx,
+    both summed cell by cell from the same element integrals as the local
+    pencil (K: the Dirichlet cut cells' Kn; M: every active cell's S).  Both
+    annihilate the constants, so (rank-based definition, Sec. 4.4) the
+    pencil is taken modulo constants: with w = 1 / |1|, every v = c 1 + v'
+    with w . v' = 0 has the quotient of v', so max Lambda of (K, M + w w^T)
+    is the same value, and M + w w^T is positive definite when the active
+    region is connected.  Dense: for grids up to a few thousand DOFs."""
+    psi_s = snap(np.asarray(psi, dtype=np.float64).reshape(N + 1, N + 1), h, alpha)
+    cls = cell_classes(psi_s)
+    nm = None if neumann_mask is None else np.asarray(neumann_mask).reshape(N, N) != 0
+    S_int, _ = interior_cell_matrices(h)
+    n = (N + 1) ** 2
+    K = np.zeros((n, n))
+    M = np.zeros((n, n))
+    jj, ii = np.nonzero(cls != EXTERNAL)
+    for i, j in zip(ii, jj):
+        nodes = cell_nodes(i, j, N)
+        if cls[j, i] == INTERNAL:
+            M[np.ix_(nodes, nodes)] += S_int
+            continue
+        _, pieces, _ = cut_pieces(cell_corner_psi(psi_s, i, j))
+        ints = cell_integrals(pieces, 0.0, 0.0, h)
+        M[np.ix_(nodes, nodes)] += ints.S
+        if nm is None or not nm[j, i]:
+            K[np.ix_(nodes, nodes)] += ints.Kn
+    dof = np.zeros(n, dtype=bool)
+    for d in (0, 1, N + 1, N + 2):
+        dof[ii + jj * (N + 1) + d] = True
+    K = K[np.ix_(dof, dof)]
+    M = M[np.ix_(dof, dof)]
+    m = int(dof.sum())
+    w = np.full(m, 1.0 / np.sqrt(m))
+    ev = scipy.linalg.eigh(K, M + np.outer(w, w), eigvals_only=True,
+                           subset_by_index=[m - 1, m - 1])
+    return float(ev[-1])
 
 
 def direct_solve(system: System, F: np.ndarray, refine: int = 4) -> np.ndarray:

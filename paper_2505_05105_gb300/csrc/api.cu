@@ -672,6 +672,7 @@ int mg_default_stab(mg_stab* out) {
   out->inner = 0;
   out->cycle = 1;
   out->coarse_op = MG_COARSE_GALERKIN;
+  out->c_global = 0.0;
   return MG_OK;
 }
 
@@ -744,8 +745,10 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
       }
       TRY(dalloc(c, &c->Nk, (size_t)v.n_cut * 16));
     }
+    const double ch_global =
+        c->stab.lambda_mode == MG_LAMBDA_GLOBAL ? c->stab.c_global * c->h : -1.0;
     launch_cut_cells(c->psi_s, N, c->h, c->stab.gamma, v.cut_list, v.n_cut, v.Ke, c->Mk, c->Gk,
-                     c->Cl, c->cfg, nmask, c->Nk, c->st);
+                     c->Cl, c->cfg, nmask, c->Nk, c->st, ch_global);
     TRY(build_nodes(c, v));
   }
   // coarse levels by element-wise Galerkin products
@@ -932,7 +935,14 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
       s.inner > 8 || s.cycle < 0 || s.cycle > 2 ||
       (s.coarse_op != MG_COARSE_GALERKIN && s.coarse_op != MG_COARSE_REDISCRETISE))
     return MG_ERR_INVALID_ARG;
-  if (s.lambda_mode != MG_LAMBDA_LOCAL) return MG_ERR_UNIMPLEMENTED;
+  if (s.lambda_mode != MG_LAMBDA_LOCAL && s.lambda_mode != MG_LAMBDA_GLOBAL)
+    return MG_ERR_INVALID_ARG;
+  if (s.lambda_mode == MG_LAMBDA_GLOBAL && !(s.c_global > 0.0 && std::isfinite(s.c_global)))
+    return MG_ERR_INVALID_ARG;
+  // the global constant belongs to the fine grid; re-discretised coarse
+  // levels would each need their own
+  if (s.lambda_mode == MG_LAMBDA_GLOBAL && s.coarse_op == MG_COARSE_REDISCRETISE)
+    return MG_ERR_UNIMPLEMENTED;
   // the two-grid scheme's "exact" coarse solve needs fp64 cycles
   if (s.cycle == 0 && s.precision != MG_FP64) return MG_ERR_UNIMPLEMENTED;
   // a Neumann mask is given for the fine cells only
@@ -1696,6 +1706,9 @@ int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double*
   if (s.precision == MG_FP64) return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
   if (s.cycle != 1) return (s.cycle == 0 || s.cycle == 2) ? MG_ERR_UNIMPLEMENTED : MG_ERR_INVALID_ARG;
+  // one global constant per geometry would need a per-member value
+  if (s.lambda_mode != MG_LAMBDA_LOCAL)
+    return s.lambda_mode == MG_LAMBDA_GLOBAL ? MG_ERR_UNIMPLEMENTED : MG_ERR_INVALID_ARG;
   mg_batch_ctx* b = new mg_batch_ctx();
   b->user_st = (cudaStream_t)cuda_stream;
   b->count = count;

@@ -223,8 +223,10 @@ struct CellOut {
 };
 
 // Element matrices of one cut cell.  psi: corner values v0..v3 (snapped).
+// ch_global >= 0: lambda h = gamma ch_global on this cell (the global
+// constant of Sec. 5.2 times h) instead of the local gamma C(K) h.
 __device__ inline void cut_cell_matrices(const double psi[4], double h, double gamma, CellOut& o,
-                                         bool neumann = false) {
+                                         bool neumann = false, double ch_global = -1.0) {
   Geom g;
   build_geometry(psi, g);
   o.config = g.config;
@@ -298,7 +300,7 @@ __device__ inline void cut_cell_matrices(const double psi[4], double h, double g
   else if (g.config == CFG_PENT || g.config == CFG_HEX) Ch = 3.0 * sqrt(2.0);
   else if (length > 0.0) Ch = gen3_max_eig(K3, M3);
   else Ch = 0.0;
-  double lamh = gamma * Ch;
+  double lamh = gamma * (ch_global >= 0.0 ? ch_global : Ch);
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
       if (neumann) {
@@ -319,7 +321,7 @@ __device__ inline void cut_cell_matrices(const double psi[4], double h, double g
       o.Ke[i * 4 + j] = o.Ke[j * 4 + i] = v;
     }
   o.C = Ch / h;
-  o.lam = gamma * o.C;
+  o.lam = lamh / h;
   o.area = area * h * h;
   o.length = length * h;
 }

@@ -59,7 +59,7 @@ __global__ void k_cut_cells(const double* __restrict__ psi_s, int n, double h, d
                             const int* __restrict__ list, int ncut, double* __restrict__ Ke,
                             double* __restrict__ Mk, double* __restrict__ Gk, double* __restrict__ Cl,
                             int* __restrict__ cfg, const uint8_t* __restrict__ nmask,
-                            double* __restrict__ Nk) {
+                            double* __restrict__ Nk, double ch_global) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ncut) return;
   int c = list[t];
@@ -67,7 +67,7 @@ __global__ void k_cut_cells(const double* __restrict__ psi_s, int n, double h, d
   size_t k0 = (size_t)jc * (n + 1) + ic;
   double psi[4] = {psi_s[k0], psi_s[k0 + 1], psi_s[k0 + n + 1], psi_s[k0 + n + 2]};
   cutcell::CellOut o;
-  cutcell::cut_cell_matrices(psi, h, gamma, o, nmask != nullptr && nmask[c] != 0);
+  cutcell::cut_cell_matrices(psi, h, gamma, o, nmask != nullptr && nmask[c] != 0, ch_global);
   for (int k = 0; k < 16; ++k) {
     Ke[(size_t)t * 16 + k] = o.Ke[k];
     Mk[(size_t)t * 16 + k] = o.Mk[k];
@@ -460,10 +460,10 @@ void launch_scatter_cut_id(const int* list, int ncut, int* cell_cut, cudaStream_
 
 void launch_cut_cells(const double* psi_s, int n, double h, double gamma, const int* list,
                       int ncut, double* Ke, double* Mk, double* Gk, double* Cl, int* cfg,
-                      const uint8_t* nmask, double* Nk, cudaStream_t st) {
+                      const uint8_t* nmask, double* Nk, cudaStream_t st, double ch_global) {
   if (ncut)
     k_cut_cells<<<(ncut + 127) / 128, 128, 0, st>>>(psi_s, n, h, gamma, list, ncut, Ke, Mk, Gk,
-                                                    Cl, cfg, nmask, Nk);
+                                                    Cl, cfg, nmask, Nk, ch_global);
 }
 
 void launch_tile_counts(const CellData& cd, const Layout& L, int* tile_cnt, uint8_t* tile_active,

@@ -25,10 +25,12 @@ void launch_cell_class(const double* psi_s, int n, uint8_t* cls, uint8_t* cut_fl
 void launch_fill_int(int* p, size_t m, int v, cudaStream_t st);
 void launch_scatter_cut_id(const int* list, int ncut, int* cell_cut, cudaStream_t st);
 // nmask (n x n cells, may be null): nonzero marks a cut cell whose boundary
-// piece is Neumann; Nk (16 per cut cell, may be null) gets its Neumann load
+// piece is Neumann; Nk (16 per cut cell, may be null) gets its Neumann load;
+// ch_global >= 0 sets lambda = gamma ch_global / h on every cut cell
 void launch_cut_cells(const double* psi_s, int n, double h, double gamma, const int* list,
                       int ncut, double* Ke, double* Mk, double* Gk, double* Cl, int* cfg,
-                      const uint8_t* nmask, double* Nk, cudaStream_t st);
+                      const uint8_t* nmask, double* Nk, cudaStream_t st,
+                      double ch_global = -1.0);
 void launch_tile_counts(const CellData& cd, const Layout& L, int* tile_cnt, uint8_t* tile_active,
                         int* ndof, cudaStream_t st);
 void launch_tile_assemble(const CellData& cd, const Layout& L, const int* tile_base,

@@ -29,6 +29,7 @@ MG_ERR_OUT_OF_MEMORY = 9
 MG_BC_DIRICHLET = 0
 MG_BC_MIXED = 1
 MG_LAMBDA_LOCAL = 0
+MG_LAMBDA_GLOBAL = 1
 MG_FP64 = 0
 MG_MIXED = 1
 MG_COARSE_GALERKIN = 0
@@ -50,7 +51,7 @@ class mg_stab(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("lambda_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner", ctypes.c_int), ("cycle", ctypes.c_int),
-                ("coarse_op", ctypes.c_int)]
+                ("coarse_op", ctypes.c_int), ("c_global", ctypes.c_double)]
 
 
 class mg_info(ctypes.Structure):
@@ -352,10 +353,12 @@ class Solver:
                  coarsest: int = 8, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
                  nu1: int = 2, nu2: int = 1, precision: str = "fp64", max_cycles: int = 100,
                  inner: int = 0, stream: int = 0, neumann_mask=None, cycle: str = "V",
-                 coarse: str = "galerkin", box_sides: bool = False):
+                 coarse: str = "galerkin", box_sides: bool = False, c_global=None):
         """neumann_mask: (n_cells, n_cells) uint8 cells [jc, ic] (host array,
         or a device tensor), nonzero where a cut cell's boundary piece is
-        Neumann (MG_BC_MIXED); None: all Dirichlet."""
+        Neumann (MG_BC_MIXED); None: all Dirichlet.
+        c_global: the global constant C of Sec. 5.2 (MG_LAMBDA_GLOBAL:
+        lambda = gamma c_global on every cut cell); None: local lambda_K."""
         self.N = n_cells
         stab = mg_default_stab()
         stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta
@@ -364,6 +367,8 @@ class Solver:
         stab.cycle = {"V": 1, "W": 2, "two-grid": 0}[cycle]
         stab.coarse_op = {"galerkin": MG_COARSE_GALERKIN,
                           "rediscretise": MG_COARSE_REDISCRETISE}[coarse]
+        if c_global is not None:
+            stab.lambda_mode, stab.c_global = MG_LAMBDA_GLOBAL, float(c_global)
         grid = mg_grid(n_cells, x0, y0, h, coarsest)
         if neumann_mask is None:
             bc = mg_bc(MG_BC_DIRICHLET, None, int(box_sides))

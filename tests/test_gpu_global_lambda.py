@@ -1,0 +1,137 @@
+"""The global stabilisation parameter of Sec. 5.2 on the GPU
+(stab.lambda_mode = MG_LAMBDA_GLOBAL, lambda = gamma c_global on every cut
+cell), with c_global the oracle's largest generalized eigenvalue of the
+global pencil (a setup-time value the caller supplies).
+
+* Cut-cell lambda and Ke, and the operator rows of every level, against the
+  oracle assembled with the same c_global (1e-13, as tests/test_gpu_parity.py;
+  C(K) is still the local constant).
+* The solution driven to 1e-13 against the oracle's direct solution
+  (1e-10 max|u| + 64 eps S_p, tests/parity_tol.py).
+* The convergence factor rho of the V-cycle (the oracle's
+  convergence_factor through the C ABI) agrees with the oracle's to 1e-6,
+  and on the circle and the flower the global choice converges more slowly
+  than the local one (Sec. 5.2).
+* Invalid values and unsupported combinations are refused.
+"""
+import numpy as np
+import pytest
+
+from oracle import ghostfem as gf
+from oracle import multigrid as mg
+from paper_2505_05105_gb300 import workloads as wl
+from parity_tol import assert_solution
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2505_05105_gb300 import ghostmg
+    ghostmg.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def solver(p, **kw):
+    from paper_2505_05105_gb300 import ghostmg
+    return ghostmg.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h, **kw)
+
+
+def oracle_rows(A, n):
+    A = A.tocoo()
+    out = np.zeros(((n + 1) ** 2, 9))
+    di = A.col % (n + 1) - A.row % (n + 1)
+    dj = A.col // (n + 1) - A.row // (n + 1)
+    np.add.at(out, (A.row, (di + 1) + 3 * (dj + 1)), A.data)
+    return out
+
+
+PROBLEMS = {
+    "circle64": lambda: wl.circle64(64),
+    "flower64": lambda: wl.flower(64),
+}
+_cache = {}
+
+
+def setup(name):
+    if name not in _cache:
+        p = PROBLEMS[name]()
+        C = gf.global_C(p.psi, p.N, p.x0, p.y0, p.h)
+        s = gf.assemble_problem(p, c_global=C)
+        _cache[name] = (p, C, s, mg.build_hierarchy(s))
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_cells_and_rows(name):
+    p, C, s, lev = setup(name)
+    with solver(p, c_global=C) as S:
+        cells, data = S.cut_cells()
+        rows = [S.stencil(l) for l in range(len(lev))]
+    assert len(cells) == len(s.cut)
+    for t, c in enumerate(s.cut):
+        assert data[t][0] == pytest.approx(c.C, rel=1e-13)
+        assert data[t][1] == pytest.approx(2.0 * C, rel=1e-13)
+        sc = np.abs(c.Ke).max()
+        assert np.abs(data[t][4:20] - c.Ke.ravel()).max() <= 1e-13 * sc
+    for l, L in enumerate(lev):
+        ref = oracle_rows(L.A, L.n)
+        assert np.abs(rows[l] - ref).max() <= 1e-13 * np.abs(ref).max(), l
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_solution(name):
+    p, C, s, lev = setup(name)
+    F = s.rhs(p.f, p.g)
+    ud = gf.direct_solve(s, F)
+    with solver(p, c_global=C, max_cycles=300) as S:
+        u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+        info = S.solve(dev(p.f), dev(p.g), u, tol=2e-15)
+        got = host(u)
+    assert info.rel_res <= 2e-15
+    assert_solution(got, ud, s, F, 1e-10, what=name)
+
+
+def gpu_rho(p, dof, cycles=30, first=21, **kw):
+    with solver(p, **kw) as S:
+        F = torch.zeros(dof.size, dtype=torch.float64, device="cuda")
+        u = dev(dof.astype(np.float64))
+        rn = [S.residual(F, u)[0]]
+        for _ in range(cycles):
+            S.cycles(F, u, 1)
+            rn.append(S.residual(F, u)[0])
+    return float(np.mean([rn[m] / rn[m - 1] for m in range(first, cycles + 1)]))
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_rho_global_vs_local(name):
+    p, C, s, lev = setup(name)
+    ref_g, _ = mg.convergence_factor(lev, cycles=30, first=21)
+    got_g = gpu_rho(p, s.dof, c_global=C)
+    got_l = gpu_rho(p, s.dof)
+    assert abs(got_g - ref_g) <= 1e-6, (got_g, ref_g)
+    print(f"{name}: C_global h = {C * p.h:.4f}, rho global {got_g:.4f}, local {got_l:.4f}")
+    assert got_g > 1.5 * got_l
+
+
+def test_refused_values():
+    from paper_2505_05105_gb300 import ghostmg as G
+    p = wl.circle64(64)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(G.GhostMGError) as e:
+            solver(p, c_global=bad)
+        assert e.value.code == G.MG_ERR_INVALID_ARG
+    with pytest.raises(G.GhostMGError) as e:
+        solver(p, c_global=40.0 / p.h, coarse="rediscretise")
+    assert e.value.code == G.MG_ERR_UNIMPLEMENTED
