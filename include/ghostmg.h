@@ -422,6 +422,45 @@ int mg_batch_timing(mg_batch b, float* setup_ms, float* solve_ms);
 /* Releases the batch (NULL is ignored). */
 void mg_batch_destroy(mg_batch b);
 
+/* ---------------------------------------------------------------------------
+ * The one-dimensional model of Sec. 4 (convergence studies of Sec. 4.5).
+ *
+ * Omega_art = [0, 1] with n_cells cells of side h = 1/n_cells, Omega = (a, b),
+ * a = (1 - theta1) h, b = 1 - (1 - theta2) h; the P1 hats phi_0..phi_n are all
+ * DOFs; Dirichlet data at a by Nitsche's terms with penalty lambda, Neumann
+ * data at b: the matrix of Eq. ls1dA.  Smoother: lexicographic Gauss-Seidel
+ * (P = L_h, Sec. 4.1); restriction Eq. resop, prolongation its transpose;
+ * Galerkin coarse operators (Eq. galerkin) down to 8 cells, solved exactly.
+ * ------------------------------------------------------------------------- */
+#define MG1D_MAX_CELLS 2048
+
+typedef struct {
+  int n_cells;            /* power of two, 16..MG1D_MAX_CELLS */
+  double theta1, theta2;  /* in (0, 1] (taken as given: no snapping) */
+  double lambda;          /* Nitsche penalty, finite and > 0 (Sec. 4.4:
+                             lambda = gamma / (theta1 h) is the local choice) */
+} mg1d_problem;
+
+/* Runs `cycles` multigrid cycles on each of `count` independent problems
+ * (one thread block each, all on cuda_stream).
+ *   problems: host array of count problems.
+ *   F: device, the right-hand sides packed one after another (n_cells + 1
+ *      values per problem, in the order of problems), or NULL for F = 0 (the
+ *      homogeneous problem of Sec. 4.5).
+ *   u: device, packed the same way; in: the first iterate (u^(0) = 1 for
+ *      Sec. 4.5), out: the iterate after `cycles` cycles.
+ *   res: host, count x (cycles + 1) values: ||F - A u^(m)||_inf for
+ *      m = 0..cycles, problem by problem (the convergence factor of Sec. 3.1
+ *      is the ratio of successive entries).
+ *   cycle: 0 = the two-grid correction scheme of Alg. 1 (coarse equation
+ *      solved exactly), 1 = V-cycle, 2 = W-cycle (gamma* of Sec. 3.2);
+ *   nu1, nu2 in 0..8 (not both 0); cycles in 0..1000.
+ * Returns MG_ERR_INVALID_ARG for values outside these ranges or pointers of
+ * the wrong kind, MG_ERR_NOT_SPD if an exact solve met a pivot <= 0, and
+ * MG_ERR_CUDA on a CUDA error.  Blocks until the results are on the host. */
+int mg1d_cycles(int count, const mg1d_problem* problems, int cycle, int nu1, int nu2,
+                int cycles, const double* F, double* u, double* res, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,14 @@ class mg_info(ctypes.Structure):
         return [self.res_hist[k] for k in range(min(self.checks + 1, 64))]
 
 
+class mg1d_problem(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int), ("theta1", ctypes.c_double),
+                ("theta2", ctypes.c_double), ("lambda_", ctypes.c_double)]
+
+
+MG1D_MAX_CELLS = 2048
+
+
 class mg_batch_shape(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("first_group", ctypes.c_int),
                 ("cluster", ctypes.c_int), ("coop_min_dof", ctypes.c_int)]
@@ -117,6 +125,7 @@ SIGNATURES = {
                            ctypes.POINTER(ctypes.c_float)]),
     "mg_batch_timing": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "mg_batch_destroy": (None, [_P]),
+    "mg1d_cycles": (_I, [_I, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
 }
 
 PROF_SLOTS = ("sweep", "band", "restrict", "prolong", "residual", "update", "coarse", "io")
@@ -270,6 +279,27 @@ def mg_residual_static(handle: int, F, u, r=None):
     _check(load().mg_residual_static(handle, _addr(F), _addr(u), _addr(r, True),
                                      norms.ctypes.data), "mg_residual_static")
     return float(norms[0]), float(norms[1])
+
+
+def mg1d_cycles(problems, u, F=None, cycle: str = "two-grid", nu1: int = 2, nu2: int = 1,
+                cycles: int = 50, stream: int = 0):
+    """The 1D model of Sec. 4 (include/ghostmg.h, mg1d_cycles).
+    problems: list of (n_cells, theta1, theta2, lambda); u: device float64
+    tensor holding the packed first iterates (updated in place); F: packed
+    device right-hand sides or None (F = 0).  cycle: "two-grid", "V" or "W".
+    Returns the residual norms, one list of cycles + 1 values per problem."""
+    total = sum(int(n) + 1 for (n, *_) in problems)
+    for x in (u, F):
+        if x is not None and not isinstance(x, int) and x.numel() < total:
+            raise ValueError(f"packed arrays need {total} values")
+    arr = (mg1d_problem * len(problems))(*[mg1d_problem(int(n), t1, t2, lam)
+                                           for (n, t1, t2, lam) in problems])
+    res = np.zeros(len(problems) * (cycles + 1))
+    code = {"two-grid": 0, "V": 1, "W": 2}[cycle]
+    _check(load().mg1d_cycles(len(problems), ctypes.addressof(arr), code, nu1, nu2, cycles,
+                              _addr(F), _addr(u, True), res.ctypes.data, stream),
+           "mg1d_cycles")
+    return res.reshape(len(problems), cycles + 1)
 
 
 def mg_set_profiling(handle: int, enable: bool) -> int:

@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "ghostmg.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mg_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mg(?:1d)?_[a-z_0-9]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -25,14 +25,15 @@ def lib_path():
 
 def test_header_declares_the_boundary():
     fns = declared_functions()
-    for name in ("mg_setup", "mg_solve", "mg_adjoint", "mg_destroy", "mg_strerror"):
+    for name in ("mg_setup", "mg_solve", "mg_adjoint", "mg_destroy", "mg_strerror",
+                 "mg1d_cycles"):
         assert name in fns
 
 
 def test_library_exports_every_declared_symbol(lib_path):
     out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r"\bT (mg_[a-z_0-9]+)$", out, flags=re.M))
+    exported = set(re.findall(r"\bT (mg(?:1d)?_[a-z_0-9]+)$", out, flags=re.M))
     missing = [f for f in declared_functions() if f not in exported]
     assert not missing, missing
 
