@@ -190,8 +190,15 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
  * nodes).  u holds the initial guess on entry (non-DOF entries ignored) and
  * the solution on exit, with 0 on nodes that are not DOFs.  Cycles stop when
  * ||F - A u||_inf / ||F||_inf <= tol (fp64 residual) or after max_cycles.
- * info may be NULL.  f, g, u: (N+1)^2 doubles, device or host.
- * Errors: MG_ERR_INVALID_ARG (NULL pointer, NaN/Inf in f, g or u),
+ * info may be NULL.  f, g, u: (N+1)^2 doubles, device or host.  Host arrays
+ * in page-locked memory mapped into the device's address space (pinned
+ * allocations) are read and written in place by the kernels, which touch
+ * only the entries the computation uses; other host arrays are copied
+ * through device buffers.  Only these entries are read: f at the vertices
+ * of active cells, g at the vertices of cut cells (and the box nodes with
+ * strong box sides), u at the DOFs.
+ * Errors: MG_ERR_INVALID_ARG (NULL pointer, NaN/Inf in an entry that is
+ * read: f or g where it enters F, u at a DOF),
  * MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED (u and info still filled),
  * MG_ERR_CUDA. */
 int mg_solve(mg_handle h, const double* f, const double* g, double* u, double tol,
@@ -202,8 +209,8 @@ int mg_solve(mg_handle h, const double* f, const double* g, double* u, double to
  * f ((N+1)^2 doubles, device or host); g_N may be NULL (g_N = 0) and is
  * ignored on a handle without Neumann cells; only its values at vertices of
  * Neumann cut cells matter (an extension of the Neumann data off Gamma_N,
- * e.g. grad u . n with n extended smoothly).  Errors as mg_solve (NaN/Inf in
- * g_N: MG_ERR_INVALID_ARG). */
+ * e.g. grad u . n with n extended smoothly, and only those are read).
+ * Errors as mg_solve (NaN/Inf in g_N at such a vertex: MG_ERR_INVALID_ARG). */
 int mg_solve_bc(mg_handle h, const double* f, const double* g_D, const double* g_N, double* u,
                 double tol, mg_info* info);
 

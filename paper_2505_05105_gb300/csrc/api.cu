@@ -616,10 +616,29 @@ struct Staged {
   bool host = false;
 };
 
+// Page-locked host memory mapped into the device address space (cudaHostAlloc,
+// cudaMallocHost, cudaHostRegister, pinned torch tensors): the kernels read
+// and write it in place over the host link, touching only the entries the
+// computation uses, instead of copying whole arrays.  nullptr otherwise.
+const double* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+  return static_cast<const double*>(a.devicePointer);
+}
+
 int stage_in(mg_ctx* c, int slot, const double* p, Staged& s) {
   size_t m = (size_t)(c->N + 1) * (c->N + 1);
   if (is_device_ptr(p)) {
     s.dev = p;
+    s.host = false;
+    return MG_OK;
+  }
+  if (const double* d = mapped_host(p)) {
+    s.dev = d;
     s.host = false;
     return MG_OK;
   }
@@ -635,6 +654,11 @@ int stage_out(mg_ctx* c, int slot, double* p, double** dev, bool* host) {
   size_t m = (size_t)(c->N + 1) * (c->N + 1);
   if (is_device_ptr(p)) {
     *dev = p;
+    *host = false;
+    return MG_OK;
+  }
+  if (const double* d = mapped_host(p)) {
+    *dev = const_cast<double*>(d);
     *host = false;
     return MG_OK;
   }
@@ -1011,16 +1035,16 @@ int mg_solve_bc(mg_handle c, const double* f, const double* g, const double* gN,
   Staged sn;
   const bool neu = gN != nullptr && c->Nk != nullptr;
   if (neu) TRY(stage_in(c, 3, gN, sn));
-  size_t m = (size_t)(c->N + 1) * (c->N + 1);
   // d_norms[0..1]: ||F||; the word at d_norms[2]: u has a nonzero DOF value
   unsigned* d_nz = reinterpret_cast<unsigned*>(c->d_norms + 2);
   MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 3 * sizeof(double), c->st));
   {
-    Launch k(c, MG_PROF_IO, 3);
-    launch_check_finite2(sf.dev, sg.dev, m, c->d_err, c->st);
-    if (neu) launch_check_finite2(sn.dev, sn.dev, m, c->d_err, c->st);
+    // f, g, g_N are read only where they enter F (the vertices of active
+    // cells, of cut cells for g and g_N): a NaN/Inf there makes some F_p
+    // non-finite, which k_rhs flags; u only on the DOFs (k_pack flags it)
+    Launch k(c, MG_PROF_IO, 2);
     RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
-               neu ? sn.dev : nullptr, v.Ke, c->box};
+               neu ? sn.dev : nullptr, v.Ke, c->box, c->d_err};
     launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
     v.cur64 = 0;
     launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st, d_nz);

@@ -654,7 +654,8 @@ __global__ void k_check_finite2(const double* __restrict__ p, const double* __re
 }
 
 // User layout (row-major (n+1)^2) -> padded layout, zero on nodes that are
-// not DOFs; flags NaN/Inf (err) and any nonzero DOF value (nz).  One block
+// not DOFs; flags NaN/Inf in a DOF entry (err) and any nonzero DOF value
+// (nz).  One block
 // row per node row: blockIdx.y = j.
 template <class T>
 __global__ void k_pack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
@@ -664,11 +665,12 @@ __global__ void k_pack(Layout L, const uint16_t* __restrict__ code, const double
   bool bad = false, any = false;
   if (i <= n) {
     const size_t g = L.idx(i, j);
-    const double v = src[(size_t)j * (n + 1) + i];
-    bad = !isfinite(v);
+    // entries off the DOFs are neither read nor checked
     const bool dof = code[g] != 0;
-    any = dof && v != 0.0;
-    dst[g] = dof ? (T)v : T(0);
+    const double v = dof ? src[(size_t)j * (n + 1) + i] : 0.0;
+    bad = !isfinite(v);
+    any = v != 0.0;
+    dst[g] = (T)v;
   }
   if (err && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, DEV_ERR_NAN);
   if (nz && __any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(nz, 1u);

@@ -24,6 +24,7 @@ struct RhsArgs {
   const double* gN = nullptr;  // nodal Neumann data, user layout (null: g_N = 0)
   const double* Ke = nullptr;  // 16 per cut cell, element matrices (strong box sides)
   int box = 0;                 // box nodes are strong Dirichlet nodes: F -= A_pq g_q
+  unsigned* err = nullptr;     // gets DEV_ERR_NAN where an F value is not finite
 };
 
 // TMA descriptors of a level's two u buffers in one precision (band kernel box)

@@ -116,6 +116,9 @@ __device__ __forceinline__ double rhs_tile(const RhsArgs& a, int t, const double
       }
     }
     F[gk] = s;
+    // every f, g (and g_N) value that enters F_p is in s with a weight:
+    // a NaN or Inf among them (0 * Inf included) leaves s not finite
+    if (a.err != nullptr && !isfinite(s)) atomicOr(a.err, DEV_ERR_NAN);
     vmax = fmax(vmax, fabs(s));
   }
   return vmax;

@@ -64,14 +64,37 @@ def test_invalid_setups():
 
 
 def test_nan_in_data_rejected():
+    """NaN/Inf where the data enter F (f at a vertex of an active cell, g at
+    a vertex of a cut cell) or in a DOF entry of u: MG_ERR_INVALID_ARG, the
+    handle stays usable.  Entries that never enter the computation (f and u
+    outside the domain's cells) are not read: the solve is unchanged."""
     from paper_2505_05105_gb300 import ghostmg as G
+    from oracle import ghostfem as gf
     p = wl.circle64(64)
+    cls = gf.cell_classes(gf.snap(p.psi, p.h, 1.75))
+    jc, ic = np.argwhere(cls == gf.CUT)[0]
     S = G.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h)
-    f = p.f.copy(); f[3, 4] = np.inf
-    u = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
+    m = (p.N + 1) ** 2
+    u = torch.zeros(m, dtype=torch.float64, device="cuda")
+    ref = torch.zeros_like(u)
+    S.solve(dev(p.f), dev(p.g), ref, tol=1e-10)
+    bad_f = p.f.copy(); bad_f[p.N // 2, p.N // 2] = np.inf
+    bad_g = p.g.copy(); bad_g[jc, ic] = np.nan
+    for f, g in ((bad_f, p.g), (p.f, bad_g)):
+        with pytest.raises(G.GhostMGError) as e:
+            S.solve(dev(f), dev(g), u)
+        assert e.value.code == G.MG_ERR_INVALID_ARG
+    u_bad = torch.zeros_like(u)
+    u_bad[(p.N // 2) * (p.N + 1) + p.N // 2] = float("nan")
     with pytest.raises(G.GhostMGError) as e:
-        S.solve(dev(f), dev(p.g), u)
+        S.solve(dev(p.f), dev(p.g), u_bad)
     assert e.value.code == G.MG_ERR_INVALID_ARG
+    # outside every active cell: ignored
+    far_f = p.f.copy(); far_f[3, 4] = np.inf
+    u_far = torch.zeros_like(u)
+    u_far[3 * (p.N + 1) + 4] = float("nan")
+    info = S.solve(dev(far_f), dev(p.g), u_far, tol=1e-10)
+    assert info.rel_res <= 1e-10 and torch.equal(u_far, ref)
     # the handle stays usable
     info = S.solve(dev(p.f), dev(p.g), u, tol=1e-10)
     assert info.rel_res <= 1e-10

@@ -151,15 +151,25 @@ def test_solution_parity(name, precision, cache):
 
 
 def test_bad_neumann_data_rejected():
+    """NaN in g_N at a vertex of a Neumann cut cell (where it enters F):
+    MG_ERR_INVALID_ARG; away from the Neumann cells g_N is not read."""
     from paper_2505_05105_gb300 import ghostmg as G
     p = wl.annulus(64)
+    cls = gf.cell_classes(gf.snap(p.psi, p.h, 1.75))
+    jc, ic = np.argwhere((cls == gf.CUT) & (np.asarray(p.neumann_mask) != 0))[0]
     with solver(p) as S:
-        gN = p.gN.copy()
-        gN[10, 10] = np.nan
         u = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
+        gN = p.gN.copy()
+        gN[jc, ic] = np.nan
         with pytest.raises(G.GhostMGError) as e:
             S.solve(dev(p.f), dev(p.g), u, gN=dev(gN))
         assert e.value.code == G.MG_ERR_INVALID_ARG
+        ref = torch.zeros_like(u)
+        S.solve(dev(p.f), dev(p.g), ref, tol=1e-10, gN=dev(p.gN))
+        gN = p.gN.copy()
+        gN[p.N // 2, p.N // 2] = np.nan        # the annulus' hole: no cell uses it
+        S.solve(dev(p.f), dev(p.g), u, tol=1e-10, gN=dev(gN))
+        assert torch.equal(u, ref)
 
 
 def test_neumann_data_ignored_without_neumann_cells():
