@@ -39,6 +39,7 @@ struct Level {
   float* rows32 = nullptr;
   int n_active = 0;
   int* active = nullptr;
+  uint8_t* tile_act = nullptr;  // per tile: holds a DOF
   int n_band = 0;
   int* band = nullptr;
   int* band_off = nullptr;      // [5 n_band + 1] group offsets into band_ent
@@ -98,6 +99,10 @@ struct mg_ctx {
   float setup_ms = 0.f;
   float solve_ms = 0.f;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // side stream that zeroes a mapped host u outside the active tiles while
+  // the solve runs
+  cudaStream_t st_zero = nullptr;
+  cudaEvent_t ev_z0 = nullptr, ev_z1 = nullptr;
   // profiling: device time per kernel class between event pairs
   bool prof = false;
   long long launches = 0;
@@ -276,6 +281,7 @@ int build_nodes(mg_ctx* c, Level& V) {
   launch_tile_assemble(cd, L, V.tile_base, V.code, V.rows64, V.bnode, c->d_err, c->st);
   launch_rows_to_f32(V.rows64, V.rows32, (size_t)V.n_bnd * MG_ROW, c->st);
   TRY(dalloc(c, &V.active, ntiles));
+  V.tile_act = tile_active;
   compact_flags_u8(tile_active, V.active, d_cnt + 2, (size_t)ntiles, tmp, nullptr, c->st);
   TRY(read_int(c, d_cnt + 2, &V.n_active));
   uint8_t* bflag;
@@ -675,6 +681,37 @@ int finish_out(mg_ctx* c, double* user, const double* dev, bool host) {
   return MG_OK;
 }
 
+// The zeroing of a mapped host u outside the active tiles, on the side
+// stream: start() after the inputs were read, join() makes the solver's
+// stream wait for it; a call that returns early waits for it here, so no
+// write to the caller's memory outlives the call.
+struct ZeroSide {
+  mg_ctx* c;
+  bool running = false;
+  int start(const Level& v, double* dst) {
+    if (!c->st_zero) {
+      MG_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_zero, cudaStreamNonBlocking));
+      MG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_z0, cudaEventDisableTiming));
+      MG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_z1, cudaEventDisableTiming));
+    }
+    MG_CUDA_TRY(cudaEventRecord(c->ev_z0, c->st));
+    MG_CUDA_TRY(cudaStreamWaitEvent(c->st_zero, c->ev_z0, 0));
+    launch_zero_inactive(v.L, v.tile_act, dst, 16, c->st_zero);
+    c->launches += 1;
+    MG_CUDA_TRY(cudaEventRecord(c->ev_z1, c->st_zero));
+    running = true;
+    return MG_OK;
+  }
+  int join() {
+    if (running) MG_CUDA_TRY(cudaStreamWaitEvent(c->st, c->ev_z1, 0));
+    running = false;
+    return MG_OK;
+  }
+  ~ZeroSide() {
+    if (running) cudaStreamSynchronize(c->st_zero);
+  }
+};
+
 }  // namespace
 
 // ===========================================================================
@@ -723,6 +760,12 @@ void mg_destroy(mg_handle c) {
   if (c->h_norms) cudaFreeHost(c->h_norms);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->st_zero) {
+    cudaStreamSynchronize(c->st_zero);
+    cudaStreamDestroy(c->st_zero);
+  }
+  if (c->ev_z0) cudaEventDestroy(c->ev_z0);
+  if (c->ev_z1) cudaEventDestroy(c->ev_z1);
   harvest(c);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   delete c;
@@ -1035,6 +1078,10 @@ int mg_solve_bc(mg_handle c, const double* f, const double* g, const double* gN,
   Staged sn;
   const bool neu = gN != nullptr && c->Nk != nullptr;
   if (neu) TRY(stage_in(c, 3, gN, sn));
+  // u in mapped host memory: its tiles without DOFs are zeroed on a side
+  // stream during the solve, so the end writes only the active tiles
+  const bool u_mapped = !su.host && !is_device_ptr(u);
+  ZeroSide zs{c};
   // d_norms[0..1]: ||F||; the word at d_norms[2]: u has a nonzero DOF value
   unsigned* d_nz = reinterpret_cast<unsigned*>(c->d_norms + 2);
   MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 3 * sizeof(double), c->st));
@@ -1052,6 +1099,7 @@ int mg_solve_bc(mg_handle c, const double* f, const double* g, const double* gN,
   MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                               c->st));
   TRY(sync_check(c));
+  if (u_mapped) TRY(zs.start(c->lev[0], const_cast<double*>(su.dev)));
   double Fn = c->h_norms[0];
   unsigned nz = 0;
   memcpy(&nz, c->h_norms + 2, sizeof(unsigned));
@@ -1067,7 +1115,12 @@ int mg_solve_bc(mg_handle c, const double* f, const double* g, const double* gN,
   double* ud = const_cast<double*>(su.dev);
   {
     Launch k(c, MG_PROF_IO, 1);
-    launch_unpack(v.L, v.code, v.u64[v.cur64], ud, c->st);
+    if (u_mapped) {
+      launch_unpack_tiles(v.L, v.code, v.active, v.n_active, v.u64[v.cur64], ud, c->st);
+      TRY(zs.join());
+    } else {
+      launch_unpack(v.L, v.code, v.u64[v.cur64], ud, c->st);
+    }
   }
   if (su.host) TRY(finish_out(c, u, ud, true));
   MG_CUDA_TRY(cudaEventRecord(c->ev1, c->st));

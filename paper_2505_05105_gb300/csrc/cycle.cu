@@ -688,6 +688,36 @@ __global__ void k_unpack(Layout L, const uint16_t* __restrict__ code, const doub
   dst[(size_t)j * (n + 1) + i] = keep ? src[g] : 0.0;
 }
 
+// k_unpack restricted to the listed tiles (64 x 32 nodes each, clipped to
+// the grid): the nodes of tiles without DOFs are written by k_zero_inactive.
+__global__ void k_unpack_tiles(Layout L, const uint16_t* __restrict__ code,
+                               const int* __restrict__ tiles, const double* __restrict__ src,
+                               double* __restrict__ dst, int box) {
+  const int n = L.n, t = tiles[blockIdx.x];
+  const int i0 = (t % L.ntx) * MG_TX, j0 = (t / L.ntx) * MG_TY;
+  for (int q = threadIdx.x; q < MG_TX * MG_TY; q += blockDim.x) {
+    const int i = i0 + (q % MG_TX), j = j0 + q / MG_TX;
+    if (i > n || j > n) continue;
+    const size_t g = L.idx(i, j);
+    const bool keep = code[g] || (box && (i == 0 || j == 0 || i == n || j == n));
+    dst[(size_t)j * (n + 1) + i] = keep ? src[g] : 0.0;
+  }
+}
+
+// Zero in the user layout the nodes of every tile that holds no DOF; a few
+// blocks stride over the tiles, so it can run beside the solve.
+__global__ void k_zero_inactive(Layout L, const uint8_t* __restrict__ tile_active,
+                                double* __restrict__ dst) {
+  const int n = L.n, ntiles = L.ntx * L.nty;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (tile_active[t]) continue;
+    const int i0 = (t % L.ntx) * MG_TX, j0 = (t / L.ntx) * MG_TY;
+    for (int q = threadIdx.x; q < MG_TX * MG_TY; q += blockDim.x) {
+      const int i = i0 + (q % MG_TX), j = j0 + q / MG_TX;
+      if (i <= n && j <= n) dst[(size_t)j * (n + 1) + i] = 0.0;
+    }
+  }
+}
 
 // dst = (float)(src * scale) over the tiles (both padded layouts)
 __global__ void k_scale_to_f32(Layout L, const int* __restrict__ tiles,
@@ -867,6 +897,16 @@ void launch_unpack(const Layout& L, const uint16_t* code, const double* src, dou
                    cudaStream_t st, int box) {
   dim3 grid((L.n + 1 + kThreads - 1) / kThreads, L.n + 1);
   k_unpack<<<grid, kThreads, 0, st>>>(L, code, src, dst, box);
+}
+
+void launch_unpack_tiles(const Layout& L, const uint16_t* code, const int* tiles, int ntiles,
+                         const double* src, double* dst, cudaStream_t st, int box) {
+  if (ntiles) k_unpack_tiles<<<ntiles, kThreads, 0, st>>>(L, code, tiles, src, dst, box);
+}
+
+void launch_zero_inactive(const Layout& L, const uint8_t* tile_active, double* dst, int blocks,
+                          cudaStream_t st) {
+  k_zero_inactive<<<blocks, kThreads, 0, st>>>(L, tile_active, dst);
 }
 
 void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,

@@ -75,6 +75,12 @@ void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* ds
 // box != 0: the box-side nodes are copied too (gradients on strong box nodes)
 void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
                    cudaStream_t st, int box = 0);
+// launch_unpack split in two: the listed (active) tiles, and zeros on the
+// tiles without DOFs (`blocks` blocks striding over all tiles)
+void launch_unpack_tiles(const Layout& L, const uint16_t* code, const int* tiles, int ntiles,
+                         const double* src, double* dst, cudaStream_t st, int box = 0);
+void launch_zero_inactive(const Layout& L, const uint8_t* tile_active, double* dst, int blocks,
+                          cudaStream_t st);
 void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,
                           cudaStream_t st);
 // dst = (float)(src * scale) on the DOFs of the tiles (the refinement
