@@ -685,15 +685,20 @@ int finish_out(mg_ctx* c, double* user, const double* dev, bool host) {
 // stream: start() after the inputs were read, join() makes the solver's
 // stream wait for it; a call that returns early waits for it here, so no
 // write to the caller's memory outlives the call.
+int ensure_side_stream(mg_ctx* c) {
+  if (!c->st_zero) {
+    MG_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_zero, cudaStreamNonBlocking));
+    MG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_z0, cudaEventDisableTiming));
+    MG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_z1, cudaEventDisableTiming));
+  }
+  return MG_OK;
+}
+
 struct ZeroSide {
   mg_ctx* c;
   bool running = false;
   int start(const Level& v, double* dst) {
-    if (!c->st_zero) {
-      MG_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_zero, cudaStreamNonBlocking));
-      MG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_z0, cudaEventDisableTiming));
-      MG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_z1, cudaEventDisableTiming));
-    }
+    TRY(ensure_side_stream(c));
     MG_CUDA_TRY(cudaEventRecord(c->ev_z0, c->st));
     MG_CUDA_TRY(cudaStreamWaitEvent(c->st_zero, c->ev_z0, 0));
     launch_zero_inactive(v.L, v.tile_act, dst, 16, c->st_zero);
@@ -1089,12 +1094,26 @@ int mg_solve_bc(mg_handle c, const double* f, const double* g, const double* gN,
     // f, g, g_N are read only where they enter F (the vertices of active
     // cells, of cut cells for g and g_N): a NaN/Inf there makes some F_p
     // non-finite, which k_rhs flags; u only on the DOFs (k_pack flags it)
+    // with u in mapped host memory, its read (k_pack) runs beside k_rhs on
+    // the side stream: both wait on the host link's latency more than on
+    // its bandwidth
     Launch k(c, MG_PROF_IO, 2);
+    cudaStream_t sp = c->st;
+    if (u_mapped) {
+      TRY(ensure_side_stream(c));
+      MG_CUDA_TRY(cudaEventRecord(c->ev_z0, c->st));
+      MG_CUDA_TRY(cudaStreamWaitEvent(c->st_zero, c->ev_z0, 0));
+      sp = c->st_zero;
+    }
     RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
                neu ? sn.dev : nullptr, v.Ke, c->box, c->d_err};
     launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
     v.cur64 = 0;
-    launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st, d_nz);
+    launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, sp, d_nz);
+    if (u_mapped) {
+      MG_CUDA_TRY(cudaEventRecord(c->ev_z1, c->st_zero));
+      MG_CUDA_TRY(cudaStreamWaitEvent(c->st, c->ev_z1, 0));
+    }
   }
   MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                               c->st));
