@@ -352,8 +352,8 @@ typedef struct mg_batch_ctx* mg_batch;
 /* Per-member result of mg_batch_solve. */
 typedef struct {
   int status;        /* MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED, or
-                        MG_ERR_INVALID_ARG (NaN/Inf in the member's f or g;
-                        its u is 0) */
+                        MG_ERR_INVALID_ARG (NaN/Inf in the member's f or g
+                        where it enters F; its u is 0) */
   int cycles;        /* fp32 V-cycles run */
   int checks;        /* fp64 residual checks after the initial one */
   int n_dof;         /* fine-level DOFs */
@@ -374,12 +374,15 @@ int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double*
                    const mg_bc* bc, const mg_stab* stab, void* cuda_stream);
 
 /* *total_nodes: doubles in a packed array; f, g, u (any may be NULL): the
- * batch's own device packed arrays.  Passing them to mg_batch_solve skips
- * the copies in and out; they stay valid until mg_batch_destroy. */
+ * batch's own device packed arrays, valid until mg_batch_destroy. */
 int mg_batch_buffers(mg_batch b, long long* total_nodes, double** f, double** g, double** u);
 
 /* Solves every member: f, g, u packed arrays (host or device; u is output
- * only, every member starts from u = 0).  info: count entries or NULL.
+ * only, every member starts from u = 0).  Device arrays and host arrays in
+ * mapped page-locked memory are read and written in place (f and g only
+ * where they enter F: f at the vertices of active cells, g at the vertices
+ * of cut cells); other host arrays are copied through the batch's own
+ * buffers.  info: count entries or NULL.
  * Returns MG_OK when every member converged, else the most severe member
  * status (MG_ERR_INVALID_ARG, then MG_ERR_DIVERGED, then
  * MG_ERR_NOT_CONVERGED; u and info filled for all members); MG_ERR_TIMEOUT
@@ -389,7 +392,8 @@ int mg_batch_solve(mg_batch b, const double* f, const double* g, double* u, doub
 
 /* mg_batch_solve with Neumann data: g_N a packed array like f (ignored on a
  * batch set up without MG_BC_MIXED; NULL: g_N = 0).  A member with NaN/Inf
- * in its g_N fails alone with MG_ERR_INVALID_ARG. */
+ * in its g_N at a vertex of a Neumann cut cell fails alone with
+ * MG_ERR_INVALID_ARG. */
 int mg_batch_solve_bc(mg_batch b, const double* f, const double* g, const double* g_N, double* u,
                       double tol, mg_batch_info* info);
 

@@ -1443,6 +1443,11 @@ struct mg_batch_ctx {
   unsigned* h_err = nullptr;        // pinned
   double *f = nullptr, *g = nullptr, *u = nullptr;
   double* gN = nullptr;             // packed Neumann data (members with Neumann cells)
+  // the member table on the host, and the packed arrays it points at now
+  // (the batch's own buffers, or the caller's device or mapped host arrays)
+  std::vector<BatchProblem> h_probs;
+  const double *io_f = nullptr, *io_g = nullptr, *io_gN = nullptr;
+  double* io_u = nullptr;
   bool mixed = false;
   size_t smem = 0;
   int grid = 0;
@@ -1590,9 +1595,10 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out, size_t win_bytes) {
   q.eta = c->stab.eta;
   q.nu1 = c->stab.nu1;
   q.nu2 = c->stab.nu2;
+  // a NaN/Inf in f, g or g_N where it enters F marks the member bad
   q.rhs = RhsArgs{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
-                 (b->gN && c->Nk) ? b->gN + b->node_off[p] : nullptr, v.Ke, c->box};
-  q.gN = b->gN ? b->gN + b->node_off[p] : nullptr;
+                 (b->gN && c->Nk) ? b->gN + b->node_off[p] : nullptr, v.Ke, c->box,
+                 b->d_words + 3 + p};
   q.f = b->f + b->node_off[p];
   q.g = b->g + b->node_off[p];
   q.u_out = b->u + b->node_off[p];
@@ -1627,7 +1633,6 @@ int batch_capture(mg_batch_ctx* b) {
   b->grid = nc * tu.cluster;
   MG_CUDA_TRY(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
   cudaMemsetAsync(b->d_words, 0, (3 + (size_t)n) * sizeof(unsigned), b->st);
-  launch_batch_check(b->d_probs, b->d_node_off, n, b->total_nodes, b->d_words + 3, b->st);
   launch_batch_rhs(b->d_probs, b->d_tile_off, n, b->total_tiles, b->st);
   launch_batch(b->d_probs, b->d_order, n, b->n_coop, b->d_words, b->d_words + 3, b->d_params,
                tu, b->grid, b->smem, b->d_res, b->st);
@@ -1650,7 +1655,8 @@ int status_rank(int s) {
   }
 }
 
-// one solve of the inputs already in b->f, b->g; results in b->u, b->h_res
+// one solve of the inputs the member table points at; results where it
+// points (u_out) and in b->h_res
 int batch_run(mg_batch_ctx* b, double tol, int* worst) {
   b->h_params[0] = tol;
   b->h_params[1] = (double)b->stab.max_cycles;
@@ -1675,12 +1681,55 @@ int batch_run(mg_batch_ctx* b, double tol, int* worst) {
   return MG_OK;
 }
 
-int batch_stage(mg_batch_ctx* b, const double* f, const double* g) {
+// The packed arrays of one solve.  Device arrays and mapped host arrays are
+// used in place (the kernels read f, g, g_N only where they enter F and
+// write u); pageable host arrays are copied through the batch's buffers.
+// gN_given: a g_N argument exists (NULL meaning g_N = 0).  Re-points the
+// member table when the arrays differ from the last solve's.
+int batch_io(mg_batch_ctx* b, const double* f, const double* g, bool gN_given,
+             const double* gN, double* u, double** u_used) {
   MG_CUDA_TRY(cudaEventRecord(b->ev_in, b->user_st));
   MG_CUDA_TRY(cudaStreamWaitEvent(b->st, b->ev_in, 0));
   const size_t bytes = b->total_nodes * sizeof(double);
-  if (f != b->f) MG_CUDA_TRY(cudaMemcpyAsync(b->f, f, bytes, cudaMemcpyDefault, b->st));
-  if (g != b->g) MG_CUDA_TRY(cudaMemcpyAsync(b->g, g, bytes, cudaMemcpyDefault, b->st));
+  auto direct = [](const double* p) -> const double* {
+    return is_device_ptr(p) ? p : mapped_host(p);
+  };
+  auto input = [&](const double* p, double* own, const double** out) -> int {
+    const double* d = direct(p);
+    if (!d) {
+      MG_CUDA_TRY(cudaMemcpyAsync(own, p, bytes, cudaMemcpyHostToDevice, b->st));
+      d = own;
+    }
+    *out = d;
+    return MG_OK;
+  };
+  const double *F, *G, *GN = b->gN;
+  TRY(input(f, b->f, &F));
+  TRY(input(g, b->g, &G));
+  if (b->gN && gN_given) {
+    if (gN == nullptr) MG_CUDA_TRY(cudaMemsetAsync(b->gN, 0, bytes, b->st));
+    else TRY(input(gN, b->gN, &GN));
+  }
+  double* U = const_cast<double*>(direct(u));
+  if (!U) U = b->u;
+  *u_used = U;
+  if (F != b->io_f || G != b->io_g || GN != b->io_gN || U != b->io_u) {
+    for (int p = 0; p < b->count; ++p) {
+      BatchProblem& q = b->h_probs[p];
+      const size_t o = b->node_off[p];
+      q.f = F + o;
+      q.g = G + o;
+      if (q.rhs.Nk) q.rhs.gN = GN ? GN + o : nullptr;
+      q.u_out = U + o;
+    }
+    MG_CUDA_TRY(cudaMemcpyAsync(b->d_probs, b->h_probs.data(),
+                                (size_t)b->count * sizeof(BatchProblem), cudaMemcpyHostToDevice,
+                                b->st));
+    b->io_f = F;
+    b->io_g = G;
+    b->io_gN = GN;
+    b->io_u = U;
+  }
   return MG_OK;
 }
 
@@ -1772,6 +1821,11 @@ int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levels
   }
   MG_CUDA_TRY(cudaMemcpyAsync(b->d_probs, probs.data(), (size_t)n * sizeof(BatchProblem),
                               cudaMemcpyHostToDevice, b->st));
+  b->h_probs = probs;
+  b->io_f = b->f;
+  b->io_g = b->g;
+  b->io_gN = b->gN;
+  b->io_u = b->u;
   MG_CUDA_TRY(cudaMemcpyAsync(b->d_node_off, b->node_off.data(), (size_t)(n + 1) * sizeof(size_t),
                               cudaMemcpyHostToDevice, b->st));
   MG_CUDA_TRY(cudaMemcpyAsync(b->d_tile_off, tile_off.data(), (size_t)(n + 1) * sizeof(int),
@@ -1838,17 +1892,11 @@ int mg_batch_solve(mg_batch b, const double* f, const double* g, double* u, doub
 int mg_batch_solve_bc(mg_batch b, const double* f, const double* g, const double* gN, double* u,
                       double tol, mg_batch_info* info) {
   if (!b || !f || !g || !u || !(tol >= 0.0)) return MG_ERR_INVALID_ARG;
-  TRY(batch_stage(b, f, g));
-  if (b->gN) {
-    // g_N = 0 when none is given
-    const size_t bytes = b->total_nodes * sizeof(double);
-    if (gN == nullptr) MG_CUDA_TRY(cudaMemsetAsync(b->gN, 0, bytes, b->st));
-    else if (gN != b->gN)
-      MG_CUDA_TRY(cudaMemcpyAsync(b->gN, gN, bytes, cudaMemcpyDefault, b->st));
-  }
+  double* U = nullptr;
+  TRY(batch_io(b, f, g, true, gN, u, &U));
   int worst = MG_OK;
   TRY(batch_run(b, tol, &worst));
-  if (u != b->u) {
+  if (U != u) {
     MG_CUDA_TRY(cudaMemcpyAsync(u, b->u, b->total_nodes * sizeof(double), cudaMemcpyDefault,
                                 b->st));
     MG_CUDA_TRY(cudaStreamSynchronize(b->st));
@@ -1895,7 +1943,8 @@ int mg_batch_get_shape(mg_batch b, mg_batch_shape* shape) {
 int mg_batch_tune(mg_batch b, const double* f, const double* g, double tol, int reps,
                   mg_batch_shape* best_out, float* ms_out) {
   if (!b || !f || !g || !(tol >= 0.0) || reps < 1) return MG_ERR_INVALID_ARG;
-  TRY(batch_stage(b, f, g));
+  double* U = nullptr;
+  TRY(batch_io(b, f, g, true, nullptr, b->u, &U));
   const BatchTune start = b->tune;
   BatchTune best{0, 0, 0, 0};
   float best_ms = 0.f;

@@ -674,18 +674,6 @@ __device__ __forceinline__ int member_of(const I* off, int count, I x) {
 constexpr int kFlatThreads = 256;
 
 __global__ void __launch_bounds__(kFlatThreads)
-k_batch_check(const BatchProblem* __restrict__ probs, const size_t* __restrict__ node_off,
-              int count, size_t total, unsigned* __restrict__ bad) {
-  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (x >= total) return;
-  const int p = member_of(node_off, count, x);
-  const size_t k = x - node_off[p];
-  const BatchProblem& b = probs[p];
-  if (!isfinite(b.f[k]) || !isfinite(b.g[k]) || (b.gN && !isfinite(b.gN[k])))
-    atomicOr(&bad[p], 1u);
-}
-
-__global__ void __launch_bounds__(kFlatThreads)
 k_batch_rhs(const BatchProblem* __restrict__ probs, const int* __restrict__ tile_off,
             int count) {
   const int p = member_of(tile_off, count, (int)blockIdx.x);
@@ -830,13 +818,6 @@ void launch_tile_xy(const Layout& L, const int* active, int n, unsigned* xy, cud
 
 static unsigned flat_grid(size_t total) {
   return (unsigned)((total + kFlatThreads - 1) / kFlatThreads);
-}
-
-void launch_batch_check(const BatchProblem* probs, const size_t* node_off, int count,
-                        size_t total_nodes, unsigned* bad, cudaStream_t st) {
-  if (total_nodes == 0) return;
-  k_batch_check<<<flat_grid(total_nodes), kFlatThreads, 0, st>>>(probs, node_off, count,
-                                                                 total_nodes, bad);
 }
 
 void launch_batch_rhs(const BatchProblem* probs, const int* tile_off, int count, int total_tiles,

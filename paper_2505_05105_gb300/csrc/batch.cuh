@@ -54,7 +54,6 @@ struct BatchProblem {
   RhsArgs rhs;
   const double* f;
   const double* g;
-  const double* gN;            // Neumann data (null: the batch has no Neumann masks)
   double* u_out;
 };
 
@@ -75,9 +74,8 @@ struct BatchTune {
 // Per-member input check and right-hand side over all members at once:
 // node_off[p] (count + 1 entries) is member p's first node in the packed user
 // arrays, tile_off[p] its first active fine tile in the flattened tile range.
-// bad[p] |= 1 if member p's f or g holds a NaN or an Inf.
-void launch_batch_check(const BatchProblem* probs, const size_t* node_off, int count,
-                        size_t total_nodes, unsigned* bad, cudaStream_t st);
+// F of every member (k_rhs's tile code); bad[p] (the member's RhsArgs.err)
+// gets DEV_ERR_NAN where a NaN or Inf in f, g or g_N enters its F.
 void launch_batch_rhs(const BatchProblem* probs, const int* tile_off, int count, int total_tiles,
                       cudaStream_t st);
 // u_out of every member from its fine fp64 iterate (zero off the DOFs)

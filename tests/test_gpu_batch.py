@@ -122,8 +122,15 @@ def test_invalid_and_zero_members_leave_the_rest_unchanged(members):
         f2, g2 = f.copy(), g.copy()
         f2[off[1]:off[2]] = 0.0
         g2[off[1]:off[2]] = 0.0                   # member 1: zero data
-        g2[off[2] + 7] = np.nan                   # member 2: NaN in g
-        f2[off[3] + 3] = np.inf                   # member 3: Inf in f
+        # member 2: NaN in g at a vertex of a cut cell, member 3: Inf in f at
+        # the domain's centre (both enter F); NaN at a box corner of member 0,
+        # which no cell uses, is not read
+        q = ps[2]
+        jc, ic = np.argwhere(gf.cell_classes(gf.snap(q.psi, q.h, 1.75)) == gf.CUT)[0]
+        g2[off[2] + jc * (q.N + 1) + ic] = np.nan
+        c3 = ps[3].N // 2
+        f2[off[3] + c3 * (ps[3].N + 1) + c3] = np.inf
+        f2[off[0]] = np.nan
         u = np.full(B.total, 5.0)
         code, info = B.solve_status(f2, g2, u, tol=1e-11)
     assert code == G.MG_ERR_INVALID_ARG
@@ -146,9 +153,20 @@ def test_replays_arrays_and_block_sizes_are_deterministic(members):
         ud = torch.zeros(B.total, dtype=torch.float64, device="cuda")
         B.solve(dev(fh), dev(gh), ud, tol=1e-11)      # device arrays
         np.testing.assert_array_equal(a, host(ud))
-        f0, g0, u0 = B.buffers()                      # zero-copy
+        f0, g0, u0 = B.buffers()                      # the batch's own buffers
         f0.copy_(dev(fh))
         g0.copy_(dev(gh))
+        B.solve(f0, g0, u0, tol=1e-11)
+        np.testing.assert_array_equal(a, host(u0))
+        # pinned host arrays, read and written in place by the kernels; then
+        # the own buffers again (the member table is re-pointed both times)
+        fp = torch.from_numpy(fh).pin_memory()
+        gp = torch.from_numpy(gh).pin_memory()
+        up = torch.full((B.total,), 3.0, dtype=torch.float64).pin_memory()
+        B.solve(fp, gp, up, tol=1e-11)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(a, up.numpy())
+        u0.zero_()
         B.solve(f0, g0, u0, tol=1e-11)
         np.testing.assert_array_equal(a, host(u0))
         # Gauss-Seidel colour phases are free of races: neither the block
@@ -252,8 +270,8 @@ def test_batch_with_neumann_masks_and_box_sides():
     """Members with Neumann cut cells (annulus, leaf, half disc), strong box
     sides (the rectangle) and plain Dirichlet members (a flower, a seeded
     member) in one batch: each member driven to 1e-12 is within 1e-9 max|u|
-    of the oracle's direct solution; NaN in one member's g_N fails that
-    member alone."""
+    of the oracle's direct solution; NaN in one member's g_N where it enters
+    F fails the call (MG_ERR_INVALID_ARG)."""
     from paper_2505_05105_gb300 import ghostmg as G
     ps = [wl.annulus(64), wl.leaf(64), wl.half_disc(64), wl.rectangle(64, 0.37),
           wl.flower(64), wl.batch_geometry(2, seed=7, sizes=(128,))]
@@ -265,8 +283,12 @@ def test_batch_with_neumann_masks_and_box_sides():
         u = torch.zeros(B.total, dtype=torch.float64, device="cuda")
         info = B.solve(f, g, u, tol=1e-12, gN=gN)
         out = B.unpack(host(u))
+        # NaN in g_N at a vertex of one of the leaf's Neumann cut cells
+        q = ps[1]
+        cls = gf.cell_classes(gf.snap(q.psi, q.h, 1.75))
+        jc, ic = np.argwhere((cls == gf.CUT) & (np.asarray(q.neumann_mask) != 0))[0]
         bad = gN.clone()
-        bad[int(B.offsets()[1]) + 5] = float("nan")
+        bad[int(B.offsets()[1]) + int(jc) * (q.N + 1) + int(ic)] = float("nan")
         with pytest.raises(G.GhostMGError) as e:
             B.solve(f, g, u, tol=1e-12, gN=bad)
         assert e.value.code == G.MG_ERR_INVALID_ARG
