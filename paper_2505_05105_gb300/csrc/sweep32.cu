@@ -11,21 +11,22 @@
 //   * two neighbouring nodes of a colour per thread: 8-byte shared loads
 //     and paired fp32 arithmetic (add/fma/mul .f32x2, each lane an ordinary
 //     IEEE fp32 operation, so results are bit for bit those of the scalar
-//     code), and
+//     code), 384 threads so that each colour phase (19 rows of 18 pairs) is
+//     one pass of the block with no thread doing a second, and
 //   * the prolongation P e_2h (Sec. 5.1) added while loading, when asked.
 #include "cycle.cuh"
 
 namespace {
 
-constexpr int kT = 256;
+constexpr int kT = 384;
 constexpr int H = 4;                       // halo: one node per colour phase
 constexpr int RX = MG_TX + 2 * H;          // 72
 constexpr int RY = MG_TY + 2 * H;          // 40
 constexpr int PX = RX / 2, PY = RY / 2;    // parity plane 36 x 20
 constexpr int PL = PX * PY;
 constexpr int QX = RX / 4;                 // 16-byte groups per region row (18)
-constexpr int kLoadIt = (RY * QX + kT - 1) / kT;                  // 3
-constexpr int kStoreIt = MG_TY * (MG_TX / 4) / kT;                // 2
+constexpr int kLoadIt = (RY * QX + kT - 1) / kT;                  // 2
+constexpr int kStoreIt = (MG_TY * (MG_TX / 4) + kT - 1) / kT;    // 2
 
 enum : int { kPlain = 0, kZero = 1, kProlong = 2 };
 
@@ -146,7 +147,7 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
   //    neighbours is itself stale, and staleness still moves inward by one
   //    node per phase, so the owned tile is exact after the 4 phases.
   constexpr int kPairCols = PX / 2;                 // 18
-  constexpr int kRowStep = kT / kPairCols;          // 14 rows per pass
+  constexpr int kRowStep = kT / kPairCols;          // 21 rows per pass
   const int tb = threadIdx.x / kPairCols;
   const int ta = 2 * (threadIdx.x - tb * kPairCols);
   const bool lane_on = tb < kRowStep;
@@ -233,6 +234,7 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
 #pragma unroll
   for (int k = 0; k < kStoreIt; ++k) {
     const int it = threadIdx.x + k * kT;
+    if (it >= MG_TY * (MG_TX / 4)) break;
     const int rr = it / (MG_TX / 4), q = it - rr * (MG_TX / 4);
     const int rj = H + rr;
     const int pe = (rj & 1) * 2 * PL + (rj >> 1) * PX + H / 2 + 2 * q, po = pe + PL;
