@@ -71,11 +71,16 @@ def test_adjoint_rejects_bad_input():
     p = wl.circle64(64)
     S = G.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h)
     d = np.zeros((p.N + 1) ** 2)
-    d[100] = np.nan
+    d[(p.N // 2) * (p.N + 1) + p.N // 2] = np.nan      # a DOF: rejected
     out = torch.zeros((p.N + 1) ** 2, dtype=torch.float64, device="cuda")
     with pytest.raises(G.GhostMGError) as e:
         S.adjoint(dev(d), out, None)
     assert e.value.code == G.MG_ERR_INVALID_ARG
+    # dL/du off the DOFs is not read (node (35, 1), outside the disc)
+    d = np.zeros((p.N + 1) ** 2)
+    d[100] = np.nan
+    S.adjoint(dev(d), out, None)
+    assert torch.count_nonzero(out) == 0
     with pytest.raises(G.GhostMGError):
         S.adjoint(dev(np.zeros_like(d)), None, None)
     S.close()
