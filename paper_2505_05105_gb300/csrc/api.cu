@@ -522,12 +522,13 @@ int fine_residual(mg_ctx* c, double sigma, bool to_f32, double* rmax) {
   OpArgs<double> op = op_of<double>(v);
   {
     Launch k(c, MG_PROF_RESIDUAL, v.n_active > 0);
+    // the stop test and the scaling need only max |r|
     if (to_f32)
       launch_residual<double, float>(op, v.active, v.n_active, v.u64[v.cur64], v.F64, v.F32,
-                                     sigma, c->d_norms, c->st);
+                                     sigma, c->d_norms, c->st, false);
     else
       launch_residual<double, double>(op, v.active, v.n_active, v.u64[v.cur64], v.F64,
-                                      (double*)nullptr, 1.0, c->d_norms, c->st);
+                                      (double*)nullptr, 1.0, c->d_norms, c->st, false);
   }
   MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                               c->st));

@@ -56,8 +56,9 @@ template <class T>
 void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const Layout& Lc,
                            const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st);
 template <class T, class TR>
+// norms[0] gets max |r| (atomic max); with l2 norms[1] gets sum r^2
 void launch_residual(const OpArgs<T>& op, const int* tiles, int ntiles, const T* u, const T* F,
-                     TR* rout, T scale, double* norms, cudaStream_t st);
+                     TR* rout, T scale, double* norms, cudaStream_t st, bool l2 = true);
 template <class T>
 void launch_prolong(const OpArgs<T>& op, const int* tiles, int ntiles, T* uf, const Layout& Lc,
                     const T* ec, cudaStream_t st);
