@@ -262,7 +262,9 @@ int mg_export_stencil(mg_handle h, int level, double* out);
  * cells in *n_total.  cells/data: host or device. */
 int mg_export_cut_cells(mg_handle h, int max_cells, int* cells, double* data, int* n_total);
 
-/* F = M f + G g on the fine level (Eq. disc_rhs), zero off the DOFs. */
+/* F = M f + G g on the fine level (Eq. disc_rhs), zero off the DOFs.  Reads
+ * f and g as mg_solve does; MG_ERR_INVALID_ARG if a NaN/Inf among them
+ * enters F. */
 int mg_rhs(mg_handle h, const double* f, const double* g, double* F);
 /* F = M f + G g_D + N g_N (as mg_solve_bc; g_N may be NULL). */
 int mg_rhs_bc(mg_handle h, const double* f, const double* g_D, const double* g_N, double* F);

@@ -1168,7 +1168,7 @@ int mg_rhs_bc(mg_handle c, const double* f, const double* g, const double* gN, d
   TRY(stage_out(c, 2, F, &Fd, &Fh));
   MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
   RhsArgs ra{v.L, c->h, v.code, v.cls, v.cell_cut, c->Mk, c->Gk, c->Nk,
-             neu ? sn.dev : nullptr, v.Ke, c->box};
+             neu ? sn.dev : nullptr, v.Ke, c->box, c->d_err};
   launch_rhs(ra, v.active, v.n_active, sf.dev, sg.dev, v.F64, c->d_norms, c->st);
   launch_unpack(v.L, v.code, v.F64, Fd, c->st);
   TRY(finish_out(c, F, Fd, Fh));

@@ -652,31 +652,9 @@ k_rhs_adj(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ w
   }
 }
 
-// Any NaN or Inf in two arrays of m doubles (vectorised reads).
-__global__ void k_check_finite2(const double* __restrict__ p, const double* __restrict__ q,
-                                size_t m, unsigned* err) {
-  bool bad = false;
-  const size_t m2 = m / 2;
-  const bool al = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0;
-  if (al) {
-    const double2* p2 = reinterpret_cast<const double2*>(p);
-    const double2* q2 = reinterpret_cast<const double2*>(q);
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m2;
-         k += (size_t)gridDim.x * blockDim.x) {
-      double2 a = p2[k], b = q2[k];
-      bad |= !isfinite(a.x) || !isfinite(a.y) || !isfinite(b.x) || !isfinite(b.y);
-    }
-  }
-  for (size_t k = (al ? 2 * m2 : 0) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
-       k += (size_t)gridDim.x * blockDim.x)
-    bad |= !isfinite(p[k]) || !isfinite(q[k]);
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEV_ERR_NAN);
-}
-
 // User layout (row-major (n+1)^2) -> padded layout, zero on nodes that are
 // not DOFs; flags NaN/Inf in a DOF entry (err) and any nonzero DOF value
-// (nz).  One block
-// row per node row: blockIdx.y = j.
+// (nz).  One block row per node row: blockIdx.y = j.
 template <class T>
 __global__ void k_pack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
                        T* __restrict__ dst, unsigned* err, unsigned* nz) {
@@ -928,11 +906,6 @@ void launch_unpack_tiles(const Layout& L, const uint16_t* code, const int* tiles
 void launch_zero_inactive(const Layout& L, const uint8_t* tile_active, double* dst, int blocks,
                           cudaStream_t st) {
   k_zero_inactive<<<blocks, kThreads, 0, st>>>(L, tile_active, dst);
-}
-
-void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,
-                          cudaStream_t st) {
-  k_check_finite2<<<grid_for(m / 2 + 1), kThreads, 0, st>>>(p, q, m, err);
 }
 
 void launch_update(const Layout& L, const int* tiles, int ntiles, const uint16_t* code, double* u,

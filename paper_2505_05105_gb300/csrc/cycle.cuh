@@ -82,8 +82,6 @@ void launch_unpack_tiles(const Layout& L, const uint16_t* code, const int* tiles
                          const double* src, double* dst, cudaStream_t st, int box = 0);
 void launch_zero_inactive(const Layout& L, const uint8_t* tile_active, double* dst, int blocks,
                           cudaStream_t st);
-void launch_check_finite2(const double* p, const double* q, size_t m, unsigned* err,
-                          cudaStream_t st);
 // dst = (float)(src * scale) on the DOFs of the tiles (the refinement
 // residual when u = 0: r = F)
 void launch_scale_to_f32(const Layout& L, const int* tiles, int ntiles, const double* src,

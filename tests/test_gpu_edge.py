@@ -84,6 +84,9 @@ def test_nan_in_data_rejected():
         with pytest.raises(G.GhostMGError) as e:
             S.solve(dev(f), dev(g), u)
         assert e.value.code == G.MG_ERR_INVALID_ARG
+        with pytest.raises(G.GhostMGError) as e:
+            S.rhs(dev(f), dev(g), torch.zeros_like(u))
+        assert e.value.code == G.MG_ERR_INVALID_ARG
     u_bad = torch.zeros_like(u)
     u_bad[(p.N // 2) * (p.N + 1) + p.N // 2] = float("nan")
     with pytest.raises(G.GhostMGError) as e:
