@@ -205,13 +205,44 @@ def oracle_sample(N_sample, steps, warmup):
 
 
 def cpu_threads():
+    """Threads the oracle's timed solve uses: its sparse kernels (SciPy CSR
+    products and the colour-wise NumPy updates) run on one thread."""
+    return 1
+
+
+def host_info():
+    """nproc and the CPU model of this host (/proc/cpuinfo: "model name" on
+    x86, the implementer / part codes on Arm)."""
+    import platform
+    info = {"nproc": os.cpu_count(), "machine": platform.machine()}
     try:
-        from threadpoolctl import threadpool_info
-        n = max((d.get("num_threads", 1) for d in threadpool_info()), default=1)
-    except Exception:
-        n = 1
-    # the oracle's sparse kernels (SciPy CSR) are single-threaded
-    return 1 if n >= 1 else 1
+        fields = {}
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = (x.strip() for x in line.split(":", 1))
+                fields.setdefault(k, v)
+        info["cpu_model"] = fields.get("model name") or " ".join(
+            f"{k} {fields[k]}" for k in ("CPU implementer", "CPU part") if k in fields) or None
+    except OSError:
+        info["cpu_model"] = None
+    return info
+
+
+def sparse_direct_sample(N):
+    """SciPy's sparse LU (SuperLU) solve of the flower system at N cells per
+    side, assembly and factorisation of the oracle's matrix included (the
+    direct alternative the paper sets against multigrid)."""
+    from oracle import ghostfem as gf
+    from paper_2505_05105_gb300 import workloads as wl
+    p = wl.flower(N)
+    s = gf.assemble_problem(p)
+    F = s.rhs(p.f, p.g)
+    t0 = time.perf_counter()
+    gf.direct_solve(s, F, refine=0)
+    dt = time.perf_counter() - t0
+    ndof = int(s.dof.sum())
+    return {"N": N, "value": ndof / dt, "unit": UNIT, "seconds": dt, "n_dof": ndof,
+            "kind": "SciPy sparse LU of the oracle's matrix (factorisation and solve), 1 core"}
 
 
 def max_over_ranks(x, dist, device):
@@ -395,7 +426,8 @@ def run_ours(args):
         val, sdof, sec, scyc = oracle_sample(Ns, steps=2, warmup=0)
         cpu = {"value": val, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                "sample": f"flower level set at {Ns}x{Ns} cells ({sdof} DOFs), full fp64 "
-                         f"4-colour V(2,1) solve to 1e-10 ({scyc} cycles), setup excluded"}
+                         f"4-colour V(2,1) solve to 1e-10 ({scyc} cycles), setup excluded",
+               "host": host_info(), "sparse_direct": sparse_direct_sample(1024)}
 
     if rank == 0:
         line = {
