@@ -8,6 +8,10 @@
 * Dense solve = sparse direct solve = converged V-cycle on 8..16 cells.
 * Convergence factor of the two-grid scheme with gamma = 2, eta = 4 is about
   0.1, and much worse without the extra cut-cell sweeps (Sec. 5.3).
+* The unsmoothed two-grid correction is an A-orthogonal projection
+  (Galerkin coarse operator, exact coarse solve); W-cycles and the two-grid
+  scheme reach the dense solution, and coincide with the V-cycle on two
+  levels.
 """
 import os
 
@@ -204,3 +208,52 @@ def test_rediscretised_cycles_converge(make):
     F = np.random.default_rng(3).standard_normal(s.n_nodes) * s.dof
     u, hist, k = mg.solve(lev, F, tol=1e-10)
     assert hist[-1] <= 1e-10 and k <= 15
+
+
+@pytest.mark.parametrize("make", [wl.circle64, wl.flower])
+def test_coarse_correction_is_an_a_orthogonal_projection(make):
+    """With no smoothing, one two-grid step maps the error e to
+    (I - P A_2h^-1 P^T A) e, which for the Galerkin operator A_2h = P^T A P
+    (Eq. galerkin) is a projection: applying it twice changes nothing, and
+    the corrected error is A-orthogonal to the coarse space (P^T A e = 0).
+    A wrong transfer, a non-Galerkin coarse matrix or an inexact coarse solve
+    breaks both."""
+    p = make(32)
+    s = gf.assemble_problem(p)
+    lev = mg.build_hierarchy(s)
+    rng = np.random.default_rng(3)
+    F = np.zeros(s.n_nodes)
+    e0 = rng.standard_normal(s.n_nodes) * s.dof
+    e1 = mg.mg_cycle(lev, 0, e0.copy(), F, nu1=0, nu2=0, exact_below=1)
+    e2 = mg.mg_cycle(lev, 0, e1.copy(), F, nu1=0, nu2=0, exact_below=1)
+    scale = np.abs(e1).max()
+    assert np.abs(e2 - e1).max() <= 1e-9 * scale
+    Ae = lev[0].A @ e1
+    assert np.abs(lev[0].P.T @ Ae).max() <= 1e-9 * np.abs(lev[0].A).max() * scale
+    assert np.abs(e1 - e0).max() > 1e-3 * np.abs(e0).max()   # it did correct
+
+
+@pytest.mark.parametrize("make", [wl.circle64, wl.flower])
+def test_w_and_two_grid_cycles_reach_the_dense_solution(make):
+    """W-cycles (gamma* = 2) and the two-grid scheme (Alg. 1) converge to the
+    dense solution, and on a two-level hierarchy (the coarse level is the
+    coarsest, solved exactly) V, W and two-grid steps are the same."""
+    p = make(16)
+    s = gf.assemble_problem(p)
+    F = s.rhs(p.f, p.g)
+    d = np.flatnonzero(s.dof)
+    ud = np.zeros(s.n_nodes)
+    ud[d] = np.linalg.solve(s.A[d][:, d].toarray(), F[d])
+    scale = np.abs(ud).max()
+    lev = mg.build_hierarchy(s, coarsest=4)
+    for kw in (dict(gamma_star=2), dict(exact_below=1)):
+        u = np.zeros(s.n_nodes)
+        for _ in range(40):
+            u = mg.mg_cycle(lev, 0, u, F, **kw)
+        assert np.abs(u - ud).max() <= 1e-11 * scale, kw
+    two = mg.build_hierarchy(s, coarsest=8)
+    assert len(two) == 2
+    outs = []
+    for kw in (dict(gamma_star=1), dict(gamma_star=2), dict(exact_below=1)):
+        outs.append(mg.mg_cycle(two, 0, np.zeros(s.n_nodes), F, **kw))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
