@@ -605,7 +605,7 @@ def run_batched(args, dev, flush):
         "tuned_ms": tune_ms, "setup_ms": setup_ms,
         "timing": "CUDA events around the graph launch on the batch's stream; L2 flushed "
                   "(512 MB write) between steps",
-        "graph_kernels_per_step": 4,
+        "graph_kernels_per_step": 3,
         "roofline": {"bound": "latency", "kernel": "k_batch (persistent)",
                      "dram_traffic_per_step": traffic,
                      "dram_gbs": traffic / per_step_s / 1e9 if traffic else None,
