@@ -9,17 +9,25 @@
  * discretised with Q1 elements on the active cells of an N x N Cartesian grid
  * (Eq. Vhact) and Nitsche terms on the cut cells (Eq. disc_bil_form,
  * Eq. disc_rhs), with the local stabilisation lambda_K = gamma C(K) of
- * Sec. 5.2 and snapping back to grid with threshold h^alpha (Sec. 2).  The
+ * Sec. 5.2 (or one global lambda, MG_LAMBDA_GLOBAL) and snapping back to
+ * grid with threshold h^alpha (Sec. 2).  Neumann data on marked cut cells
+ * and strong Dirichlet box sides are options (mg_bc).  The
  * system A u = F is solved by V(nu1, nu2)-cycles (Sec. 3.2) with a 4-colour
  * Gauss-Seidel smoother (Sec. 4.1) plus eta extra sweeps on the cut-cell
  * vertices (Sec. 5.3), bilinear prolongation P and restriction R = P^T
- * (Sec. 5.1) and Galerkin coarse operators (Eq. galerkin).
+ * (Sec. 5.1) and Galerkin coarse operators (Eq. galerkin); W-cycles, the
+ * two-grid scheme (Alg. 1) and re-discretised coarse levels are options
+ * (mg_stab).  Batches of independent problems (mg_batch_*) and the 1D model
+ * of Sec. 4 (mg1d_cycles) have their own calls at the end of this file.
  *
  * Arrays: every nodal array has (N+1)^2 doubles, row-major with node index
  * k = i + j (N+1) (Sec. 5.1), node (i, j) at (x0 + i h, y0 + j h).
  * Array arguments may be device pointers (used on the handle's stream) or
- * host pointers (pageable or pinned; staged through handle-owned device
- * buffers, and the call returns after the copies back have completed).
+ * host pointers.  Pinned host memory mapped into the device's address space
+ * is read and written in place by the kernels (only the entries they use);
+ * pageable host memory is staged through handle-owned device buffers, and
+ * the mg_export_* calls always copy.  Every call returns after its results
+ * are in the caller's arrays.
  * The caller owns every array; no pointer is kept after a call returns.
  *
  * Errors: every int-returning call returns MG_OK (0) or one of the MG_ERR_*
