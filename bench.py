@@ -483,7 +483,7 @@ def run_large(args, dev, flush, stream):
         ndof = S.counts()[1]
         for _ in range(max(1, args.warmup)):
             u.zero_()
-            S.solve(f, g, u, tol=TOL)
+            S.solve(f, g, u, tol=TOL, allow_not_converged=True)
         steps = max(1, min(args.steps, 3))
         ms = []
         for k in range(steps):
@@ -493,17 +493,17 @@ def run_large(args, dev, flush, stream):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            info = S.solve(f, g, u, tol=TOL)
+            info = S.solve(f, g, u, tol=TOL, allow_not_converged=True)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         ent = {"value": ndof * steps / (sum(ms) / 1e3), "unit": UNIT,
                "ms_per_step": sum(ms) / steps, "cycles_per_solve": info.cycles,
-               "rel_res": info.rel_res, "steps": steps}
+               "rel_res": info.rel_res, "converged": info.rel_res <= TOL, "steps": steps}
         if prec == "mixed":
             ghostmg.mg_set_profiling(S.handle, True)
             u.zero_()
-            S.solve(f, g, u, tol=TOL)
+            S.solve(f, g, u, tol=TOL, allow_not_converged=True)
             _, slots = ghostmg.mg_get_profile(S.handle)
             ghostmg.mg_set_profiling(S.handle, False)
             n_l, sweep_ms = slots["sweep"]
