@@ -8,7 +8,7 @@ problems" (arXiv 2505.05105).  Integrals are evaluated in physical
 coordinates with Gauss-Legendre rules far above the polynomial degree of every
 integrand, so they are exact up to rounding.
 
-Readings where the paper is silent or garbled (each restated in the design doc):
+Readings where the paper is silent or garbled:
 * Snapping acts on nodal values: a node with -h^alpha < psi < 0 gets psi = 0.
 * A node is internal iff psi < 0; psi = 0 counts as external (Sec. 5.2).
 * A cell with two internal vertices on a diagonal (not covered by Sec. 5.2) is

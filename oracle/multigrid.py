@@ -6,7 +6,7 @@ R = P^T, Galerkin coarse operator, Eq. galerkin) and Sec. 5.1 (bilinear
 transfer between Omega_h and Omega_2h) and Sec. 5.3 (eta extra smoothing
 iterations on the cut cells).
 
-Readings (each restated in the design doc):
+Readings:
 * Eq. galerkin is read as A_2h = R A_h P with R = P^T (as printed it is not
   conformable); P is bilinear interpolation, rows restricted to fine DOFs.
 * A coarse node is a DOF iff its column of P is non-zero.  A coarse cell is

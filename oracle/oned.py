@@ -23,7 +23,7 @@ Stabilisation (Sec. 4.4): the local 2 x 2 pencil on the cut cell [x_0, x_1]
 and the global pencil over V_h, both taken modulo constants (the rank-based
 definition), give C = 1 / (theta_1 h).
 
-Readings (each restated in the design doc): the source enters through the P1
+Readings: the source enters through the P1
 interpolant of nodal f (F^I = M f, M the mass on Omega); Eq.
 shape_fun_relation's indices are off by one and are read as
 1/2 phi_{2i-1} + phi_{2i} + 1/2 phi_{2i+1}; the snapping threshold written
