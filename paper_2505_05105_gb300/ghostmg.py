@@ -290,7 +290,10 @@ def mg1d_cycles(problems, u, F=None, cycle: str = "two-grid", nu1: int = 2, nu2:
     Returns the residual norms, one list of cycles + 1 values per problem."""
     total = sum(int(n) + 1 for (n, *_) in problems)
     for x in (u, F):
-        if x is not None and not isinstance(x, int) and x.numel() < total:
+        if x is None or isinstance(x, int):
+            continue
+        size = x.numel() if hasattr(x, "numel") else x.size
+        if size < total:
             raise ValueError(f"packed arrays need {total} values")
     arr = (mg1d_problem * len(problems))(*[mg1d_problem(int(n), t1, t2, lam)
                                            for (n, t1, t2, lam) in problems])

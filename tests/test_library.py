@@ -53,3 +53,16 @@ def test_binding_matches_header(lib_path):
 def test_build_targets_sm103a_only():
     from paper_2505_05105_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_checks_packed_sizes_before_any_call(lib_path):
+    """mg1d_cycles refuses packed arrays shorter than the problems need on
+    the host, before the library is called."""
+    import numpy as np
+    import pytest
+    from paper_2505_05105_gb300 import ghostmg
+    with pytest.raises(ValueError):
+        ghostmg.mg1d_cycles([(64, 0.5, 0.5, 10.0), (32, 0.3, 0.2, 5.0)], np.zeros(97))
+    # the stab structure carries the global-penalty fields
+    s = ghostmg.mg_default_stab()
+    assert s.lambda_mode == ghostmg.MG_LAMBDA_LOCAL and s.c_global == 0.0
