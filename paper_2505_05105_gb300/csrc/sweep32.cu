@@ -63,6 +63,92 @@ __device__ __forceinline__ float boundary_update(const OpArgs<float>& op, int i,
   return uc + (f - acc) * R[9];
 }
 
+// One colour phase (CI, CJ) = (i mod 2, j mod 2) over the parity planes: a
+// thread updates plane nodes (a, b) and (a + 1, b) of row b = b0 + tb (the
+// block covers all of the colour's rows in one pass).  Every node off the
+// region's rim is updated in every phase: a node near the rim computed from
+// stale neighbours is itself stale, and staleness still moves inward by one
+// node per phase, so the owned tile is exact after the 4 phases.  The colour
+// is a template argument, so plane bases and neighbour offsets are constants.
+template <int CI, int CJ>
+__device__ __forceinline__ void colour_phase(const OpArgs<float>& op, float* sU,
+                                             const float* sF, const uint16_t* sC, int tb,
+                                             int ta, bool lane_on, int ri0, int rj0) {
+  float* P = sU + (CJ * 2 + CI) * PL;
+  const float* PXn = sU + (CJ * 2 + (CI ^ 1)) * PL;
+  const float* PYn = sU + ((CJ ^ 1) * 2 + CI) * PL;
+  const float* PDn = sU + ((CJ ^ 1) * 2 + (CI ^ 1)) * PL;
+  const float* PF = sF + (CJ * 2 + CI) * PL;
+  const uint16_t* PC = sC + (CJ * 2 + CI) * PL;
+  // rows with 1 <= 2b + cj <= RY - 2; columns: the rim node of the first or
+  // last pair is masked
+  constexpr int b0 = CJ ? 0 : 1, b1 = CJ ? PY - 2 : PY - 1;
+  const int b = b0 + tb;
+  if (!lane_on || b > b1) return;
+  const int a = ta;
+  const uint32_t mask = (CI == 0 && ta == 0) ? 0xffff0000u
+                        : (CI == 1 && ta == PX - 2) ? 0x0000ffffu : 0xffffffffu;
+  const int q = b * PX + a;                          // (a, b) in the plane
+  constexpr int dm = (CJ - 1) * PX, dp = CJ * PX;    // rows ym = b + cj - 1, yp = b + cj
+  const uint32_t cc = *reinterpret_cast<const uint32_t*>(PC + q) & mask;
+  if (cc == 0u) return;
+  // x neighbours: columns a + ci - 1 .. a + ci + 1 of the neighbour planes
+  float2 W, E, SW, SE, NW, NE;
+  if (CI) {
+    const float2 m = *reinterpret_cast<const float2*>(PXn + q);
+    const float r = PXn[q + 2];
+    W = m;
+    E = make_float2(m.y, r);
+    const float2 dmv = *reinterpret_cast<const float2*>(PDn + q + dm);
+    const float dr = PDn[q + dm + 2];
+    SW = dmv;
+    SE = make_float2(dmv.y, dr);
+    const float2 um = *reinterpret_cast<const float2*>(PDn + q + dp);
+    const float ur = PDn[q + dp + 2];
+    NW = um;
+    NE = make_float2(um.y, ur);
+  } else {
+    const float l = PXn[q - 1];
+    const float2 m = *reinterpret_cast<const float2*>(PXn + q);
+    W = make_float2(l, m.x);
+    E = m;
+    const float dl = PDn[q + dm - 1];
+    const float2 dmv = *reinterpret_cast<const float2*>(PDn + q + dm);
+    SW = make_float2(dl, dmv.x);
+    SE = dmv;
+    const float ul = PDn[q + dp - 1];
+    const float2 um = *reinterpret_cast<const float2*>(PDn + q + dp);
+    NW = make_float2(ul, um.x);
+    NE = um;
+  }
+  const float2 S = *reinterpret_cast<const float2*>(PYn + q + dm);
+  const float2 N = *reinterpret_cast<const float2*>(PYn + q + dp);
+  const float2 f = *reinterpret_cast<const float2*>(PF + q);
+  // interior rows: 8/3 u_p - 1/3 (sum of 8 neighbours) = F_p, i.e.
+  // u_p = (3 F_p + sum) / 8 with the association of k_gs_sweep
+  const float2 A = add2(add2(W, E), add2(S, N));
+  const float2 Bd = add2(add2(SW, SE), add2(NW, NE));
+  const float2 in = mul2(add2(fma2(make_float2(3.f, 3.f), f, A), Bd),
+                         make_float2(0.125f, 0.125f));
+  if (cc == 0x00010001u) {       // both interior: the common case
+    *reinterpret_cast<float2*>(P + q) = in;
+    return;
+  }
+  const uint32_t c0 = cc & 0xffffu, c1 = cc >> 16;
+  const float2 uc = *reinterpret_cast<const float2*>(P + q);
+  const int rj = 2 * b + CJ;
+  float r0 = uc.x, r1 = uc.y;
+  if (c0 == 1u) r0 = in.x;
+  else if (c0 >= 2u)
+    r0 = boundary_update(op, ri0 + 2 * a + CI, rj0 + rj, (int)c0, uc.x, f.x, W.x, E.x, S.x,
+                         N.x, SW.x, SE.x, NW.x, NE.x);
+  if (c1 == 1u) r1 = in.y;
+  else if (c1 >= 2u)
+    r1 = boundary_update(op, ri0 + 2 * a + 2 + CI, rj0 + rj, (int)c1, uc.y, f.y, W.y, E.y,
+                         S.y, N.y, SW.y, SE.y, NW.y, NE.y);
+  *reinterpret_cast<float2*>(P + q) = make_float2(r0, r1);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kT)
 k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __restrict__ uin,
@@ -141,93 +227,21 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
   }
   __syncthreads();
 
-  // 2. colour phases; a thread updates plane nodes (a, b) and (a + 1, b) of
-  //    rows b = tb, tb + kRowStep, ...  Every node off the region's rim is
-  //    updated in every phase: a node near the rim computed from stale
-  //    neighbours is itself stale, and staleness still moves inward by one
-  //    node per phase, so the owned tile is exact after the 4 phases.
+  // 2. the four colour phases, (0,0), (1,0), (0,1), (1,1)
   constexpr int kPairCols = PX / 2;                 // 18
   constexpr int kRowStep = kT / kPairCols;          // 21 rows per pass
+  static_assert(kRowStep >= PY - 1, "a colour phase must be one pass of the block");
   const int tb = threadIdx.x / kPairCols;
   const int ta = 2 * (threadIdx.x - tb * kPairCols);
   const bool lane_on = tb < kRowStep;
-#pragma unroll 1
-  for (int k = 0; k < 4; ++k) {
-    const int ci = k & 1, cj = k >> 1;
-    float* P = sU + (cj * 2 + ci) * PL;
-    const float* PXn = sU + (cj * 2 + (ci ^ 1)) * PL;
-    const float* PYn = sU + ((cj ^ 1) * 2 + ci) * PL;
-    const float* PDn = sU + ((cj ^ 1) * 2 + (ci ^ 1)) * PL;
-    const float* PF = sF + (cj * 2 + ci) * PL;
-    const uint16_t* PC = sC + (cj * 2 + ci) * PL;
-    // rows with 1 <= 2b + cj <= RY - 2; columns: the rim node of the first
-    // or last pair is masked
-    const int b0 = cj ? 0 : 1, b1 = cj ? PY - 2 : PY - 1;
-    const uint32_t mask = (ta == 0 && ci == 0) ? 0xffff0000u
-                          : (ta == PX - 2 && ci == 1) ? 0x0000ffffu : 0xffffffffu;
-    for (int b = b0 + tb; lane_on && b <= b1; b += kRowStep) {
-      const int a = ta;
-      const uint32_t cc = *reinterpret_cast<const uint32_t*>(PC + b * PX + a) & mask;
-      if (cc == 0u) continue;
-      const int ym = b + cj - 1, yp = b + cj;
-      // x neighbours: columns a + ci - 1 .. a + ci + 1 of the neighbour planes
-      float2 W, E, SW, SE, NW, NE;
-      if (ci) {
-        const float2 m = *reinterpret_cast<const float2*>(PXn + b * PX + a);
-        const float r = PXn[b * PX + a + 2];
-        W = m;
-        E = make_float2(m.y, r);
-        const float2 dm = *reinterpret_cast<const float2*>(PDn + ym * PX + a);
-        const float dr = PDn[ym * PX + a + 2];
-        SW = dm;
-        SE = make_float2(dm.y, dr);
-        const float2 um = *reinterpret_cast<const float2*>(PDn + yp * PX + a);
-        const float ur = PDn[yp * PX + a + 2];
-        NW = um;
-        NE = make_float2(um.y, ur);
-      } else {
-        const float l = PXn[b * PX + a - 1];
-        const float2 m = *reinterpret_cast<const float2*>(PXn + b * PX + a);
-        W = make_float2(l, m.x);
-        E = m;
-        const float dl = PDn[ym * PX + a - 1];
-        const float2 dm = *reinterpret_cast<const float2*>(PDn + ym * PX + a);
-        SW = make_float2(dl, dm.x);
-        SE = dm;
-        const float ul = PDn[yp * PX + a - 1];
-        const float2 um = *reinterpret_cast<const float2*>(PDn + yp * PX + a);
-        NW = make_float2(ul, um.x);
-        NE = um;
-      }
-      const float2 S = *reinterpret_cast<const float2*>(PYn + ym * PX + a);
-      const float2 N = *reinterpret_cast<const float2*>(PYn + yp * PX + a);
-      const float2 f = *reinterpret_cast<const float2*>(PF + b * PX + a);
-      // interior rows: 8/3 u_p - 1/3 (sum of 8 neighbours) = F_p, i.e.
-      // u_p = (3 F_p + sum) / 8 with the association of k_gs_sweep
-      const float2 A = add2(add2(W, E), add2(S, N));
-      const float2 Bd = add2(add2(SW, SE), add2(NW, NE));
-      const float2 in = mul2(add2(fma2(make_float2(3.f, 3.f), f, A), Bd),
-                             make_float2(0.125f, 0.125f));
-      if (cc == 0x00010001u) {       // both interior: the common case
-        *reinterpret_cast<float2*>(P + b * PX + a) = in;
-        continue;
-      }
-      const uint32_t c0 = cc & 0xffffu, c1 = cc >> 16;
-      const float2 uc = *reinterpret_cast<const float2*>(P + b * PX + a);
-      const int rj = 2 * b + cj;
-      float r0 = uc.x, r1 = uc.y;
-      if (c0 == 1u) r0 = in.x;
-      else if (c0 >= 2u)
-        r0 = boundary_update(op, ri0 + 2 * a + ci, rj0 + rj, (int)c0, uc.x, f.x, W.x, E.x, S.x,
-                             N.x, SW.x, SE.x, NW.x, NE.x);
-      if (c1 == 1u) r1 = in.y;
-      else if (c1 >= 2u)
-        r1 = boundary_update(op, ri0 + 2 * a + 2 + ci, rj0 + rj, (int)c1, uc.y, f.y, W.y, E.y,
-                             S.y, N.y, SW.y, SE.y, NW.y, NE.y);
-      *reinterpret_cast<float2*>(P + b * PX + a) = make_float2(r0, r1);
-    }
-    __syncthreads();
-  }
+  colour_phase<0, 0>(op, sU, sF, sC, tb, ta, lane_on, ri0, rj0);
+  __syncthreads();
+  colour_phase<1, 0>(op, sU, sF, sC, tb, ta, lane_on, ri0, rj0);
+  __syncthreads();
+  colour_phase<0, 1>(op, sU, sF, sC, tb, ta, lane_on, ri0, rj0);
+  __syncthreads();
+  colour_phase<1, 1>(op, sU, sF, sC, tb, ta, lane_on, ri0, rj0);
+  __syncthreads();
 
   // 3. owned tile out (16-byte stores), boundary values to bval
   const int base = bval ? op.tile_base[t] : 0;
