@@ -36,7 +36,9 @@
  * last CUDA error text when there was one.
  *
  * Threading: one handle per CUDA stream; calls on different handles are
- * independent.  A handle must not be used from two threads at once.
+ * independent, with one exception: mg_residual_static calls share one
+ * library-wide scratch array, so those that overlap on the GPU race (see
+ * there).  A handle must not be used from two threads at once.
  */
 #ifndef GHOSTMG_H
 #define GHOSTMG_H
@@ -148,7 +150,15 @@ typedef struct {
  *                 assembled from scratch on its own grid from the level set
  *                 at its nodes (snapped with h_l^alpha, its own cut cells
  *                 and lambda_K), the alternative the paper describes beside
- *                 Eq. galerkin (not with MG_BC_MIXED: MG_ERR_UNIMPLEMENTED). */
+ *                 Eq. galerkin (not with MG_BC_MIXED: MG_ERR_UNIMPLEMENTED).
+ *   fuse_max_tiles = 0  kernel choice on the levels between the finest and
+ *                 the 64 x 64-cell tail (MG_MIXED only; the arithmetic is
+ *                 the same either way): a level with at most this many
+ *                 active 64 x 32-node tiles runs each smoothing step as one
+ *                 fused kernel, a larger one runs the separate sweep, extra
+ *                 sweep, restriction and prolongation kernels.  0 = twice
+ *                 the device's SM count; -1 = never fused; >= -1 otherwise
+ *                 (MG_ERR_INVALID_ARG). */
 typedef struct {
   double gamma, alpha;
   int eta, nu1, nu2;
@@ -157,6 +167,7 @@ typedef struct {
   int cycle;
   int coarse_op;
   double c_global;        /* MG_LAMBDA_GLOBAL only; default 0 */
+  int fuse_max_tiles;
 } mg_stab;
 
 /* Result summary of a solve. */
@@ -279,7 +290,8 @@ int mg_rhs_bc(mg_handle h, const double* f, const double* g_D, const double* g_N
 
 /* Exactly k cycles from u with right-hand side F (no stopping test):
  * precision MG_FP64 runs k V-cycles; MG_MIXED runs k refinement steps (fp64
- * residual, one fp32 V-cycle, fp64 update).  u in/out. */
+ * residual, stab.inner fp32 V-cycles -- one if inner = 0 -- on the
+ * correction equation from e = 0, fp64 update).  u in/out. */
 int mg_cycles(mg_handle h, const double* F, double* u, int k, int precision);
 
 /* r = F - A u on the fine level (fp64); norms[0] = ||r||_inf,
@@ -289,10 +301,10 @@ int mg_residual(mg_handle h, const double* F, const double* u, double* r, double
 /* ---------------------------------------------------------------------------
  * Allocation-free residual.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory while they use the
- * solver -- work being captured into a CUDA graph (cudaMalloc cannot be
- * captured), real-time loops that cannot take the device-wide
- * synchronisation an allocation may cause, frameworks whose own allocator
- * must own all device memory.
+ * solver -- real-time loops that cannot take the device-wide
+ * synchronisation that cudaMalloc or cudaFree may cause, and frameworks
+ * whose own caching allocator must own all device memory (a hard memory
+ * cap, no fragmentation by a library's private allocations).
  *
  * Same result as mg_residual (r = F - A u on the fine level, norms[0] =
  * ||r||_inf, norms[1] = ||r||_2), but it allocates nothing and uses no
@@ -301,17 +313,23 @@ int mg_residual(mg_handle h, const double* F, const double* u, double* r, double
  * array of 2 MG_NOALLOC_MAX_TILES + 2 doubles (1 MiB), which every GPU that
  * loads the library keeps until the process exits.  ||r||_2 is summed in a
  * fixed order, so it is reproducible.
- *   F, u, r  device pointers; r may be NULL (norms only); u is read as 0 on
- *            nodes that are not DOFs; r gets 0 there.
+ *   F, u, r  device pointers on the handle's device; r may be NULL (norms
+ *            only); u is read as 0 on nodes that are not DOFs; r gets 0
+ *            there.
  *   norms    host or device array of 2 doubles, or NULL.
- * The call returns after the results are written.  Errors:
- * MG_ERR_INVALID_ARG for NULL or host F/u/r, or a fine level with more than
+ * The work runs on the handle's stream and device (the caller's current
+ * device is restored), and the call waits for it: it synchronises the
+ * handle's stream before returning, so the results are in place on return.
+ * Errors: MG_ERR_INVALID_ARG for NULL or host F/u/r, arrays on another
+ * device than the handle's, or a fine level with more than
  * MG_NOALLOC_MAX_TILES active 64 x 32-node tiles (every n_cells <= 8192
  * fits); MG_ERR_CUDA.
  * The first call on a device looks up the device address of the scratch
- * array (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
- * (other threads, streams or handles) race and must be serialised.
+ * array (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls share the one array, and each
+ * call writes every slot it reads before reading it, so nothing carries
+ * over from one call to the next; but calls that overlap on the GPU (other
+ * threads, streams or handles) race on it and must be serialised.
  * ------------------------------------------------------------------------- */
 #define MG_NOALLOC_MAX_TILES 65536
 int mg_residual_static(mg_handle h, const double* F, const double* u, double* r, double* norms);

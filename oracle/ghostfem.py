@@ -4,9 +4,10 @@ Plain fp64 restatement of Sec. 2 (Eq. Vhact, Eq. disc_bil_form, Eq. disc_rhs,
 snapping back to grid) and Sec. 5.2 (cut configurations, cut lengths theta,
 local stabilisation C(K), Eq. c_triangle, Eq. c_pentagon) of Dilip & Coco,
 "Multigrid methods for the ghost finite element approximation of elliptic
-problems" (arXiv 2505.05105).  Integrals are evaluated in physical
-coordinates with Gauss-Legendre rules far above the polynomial degree of every
-integrand, so they are exact up to rounding.
+problems" (arXiv 2505.05105).  Integrals are evaluated in cell-local
+coordinates (relative to the cell's lower-left node, so thin cut regions lose
+no digits to cancellation) with Gauss-Legendre rules far above the polynomial
+degree of every integrand, so they are exact up to rounding.
 
 Readings where the paper is silent or garbled:
 * Snapping acts on nodal values: a node with -h^alpha < psi < 0 gets psi = 0.

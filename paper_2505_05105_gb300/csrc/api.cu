@@ -67,6 +67,7 @@ struct Level {
 
 struct mg_ctx {
   cudaStream_t st = nullptr;
+  int device = 0;                // current device at setup
   mg_grid grid{};
   mg_stab stab{};
   int N = 0;
@@ -740,6 +741,7 @@ int mg_default_stab(mg_stab* out) {
   out->cycle = 1;
   out->coarse_op = MG_COARSE_GALERKIN;
   out->c_global = 0.0;
+  out->fuse_max_tiles = 0;
   return MG_OK;
 }
 
@@ -779,6 +781,7 @@ void mg_destroy(mg_handle c) {
 
 static int setup_impl(mg_ctx* c, const double* levelset) {
   const int N = c->N;
+  MG_CUDA_TRY(cudaGetDevice(&c->device));
   MG_CUDA_TRY(cudaMallocHost((void**)&c->h_norms, 16 * sizeof(double)));
   MG_CUDA_TRY(cudaEventCreate(&c->ev0));
   MG_CUDA_TRY(cudaEventCreate(&c->ev1));
@@ -883,7 +886,8 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
     // the fused step recomputes a wide halo per tile: it pays while the level
     // fits in about two waves of one block per SM; beyond that the separate
     // sweep, band, restriction and prolongation kernels move less data
-    c->fused_max_tiles = 2 * nsm;
+    c->fused_max_tiles = c->stab.fuse_max_tiles == 0 ? 2 * nsm
+                         : c->stab.fuse_max_tiles < 0 ? -1 : c->stab.fuse_max_tiles;
     // fp32 only: on GB300 the redundant halo arithmetic of the fused step is
     // cheap in fp32 but fp64 arithmetic is a small fraction of the fp32 rate
     for (int pi = 0; pi < 1; ++pi) {
@@ -1005,7 +1009,7 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
     return MG_ERR_INVALID_ARG;
   if (!(s.gamma > 0.0) || !(s.alpha > 0.0) || s.eta < 0 || s.eta > 8 || s.nu1 < 0 || s.nu1 > 8 ||
       s.nu2 < 0 || s.nu2 > 8 || s.nu1 + s.nu2 == 0 || s.max_cycles < 0 || s.inner < 0 ||
-      s.inner > 8 || s.cycle < 0 || s.cycle > 2 ||
+      s.inner > 8 || s.cycle < 0 || s.cycle > 2 || s.fuse_max_tiles < -1 ||
       (s.coarse_op != MG_COARSE_GALERKIN && s.coarse_op != MG_COARSE_REDISCRETISE))
     return MG_ERR_INVALID_ARG;
   if (s.lambda_mode != MG_LAMBDA_LOCAL && s.lambda_mode != MG_LAMBDA_GLOBAL)
@@ -1196,7 +1200,7 @@ int mg_cycles(mg_handle c, const double* F, double* u, int k, int precision) {
       OpArgs<double> op = op_of<double>(v);
       launch_residual<double, float>(op, v.active, v.n_active, v.u64[v.cur64], v.F64, v.F32, sigma,
                                      (double*)nullptr, c->st);
-      refinement_step(c, sigma, 1);
+      refinement_step(c, sigma, c->stab.inner > 0 ? c->stab.inner : 1);
     }
   }
   double* ud = const_cast<double*>(su.dev);
@@ -1305,6 +1309,7 @@ int mg_internal_fine_view(mg_handle c, FineOpView* out) {
   out->active = v.active;
   out->n_active = v.n_active;
   out->N = c->N;
+  out->device = c->device;
   out->st = c->st;
   return MG_OK;
 }

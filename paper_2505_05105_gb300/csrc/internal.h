@@ -13,6 +13,7 @@ struct FineOpView {
   const int* active;     // active tiles of the fine level
   int n_active;
   int N;
+  int device;            // the device the handle was set up on
   cudaStream_t st;
 };
 

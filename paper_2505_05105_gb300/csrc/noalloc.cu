@@ -1,14 +1,14 @@
 // mg_residual_static: the fine-level residual r = F - A u and its norms
 // without allocating anything.
 //
-// Some callers cannot call cudaMalloc while they use the solver: code being
-// captured into a CUDA graph (cudaMalloc is not stream-ordered and cannot be
-// captured), real-time loops that cannot afford the device-wide
-// synchronisation an allocation may cause, and frameworks whose allocator
-// must own every byte of device memory.  This entry point reads and writes
-// only the caller's arrays and the handle's read-only operator; its
-// reduction scratch is the file-scope device array below, which every GPU
-// that loads the library holds until the process exits.
+// Some callers cannot call cudaMalloc while they use the solver: real-time
+// loops that cannot take the device-wide synchronisation an allocation (or
+// the release of one) may cause, and frameworks whose own caching allocator
+// must own every byte of device memory (a memory cap, no fragmentation from
+// a library's private allocations).  This entry point reads and writes only
+// the caller's arrays and the handle's read-only operator; its reduction
+// scratch is the file-scope device array below, which every GPU that loads
+// the library holds until the process exits.
 #include <mutex>
 
 #include "ghostmg.h"
@@ -25,31 +25,36 @@ constexpr int kMaxDevices = 64;
 double* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-// Device address of g_residual_scratch on the current device, looked up once
-// per device (host code may not use the symbol itself as a device address).
-int scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return mg_cuda_fail(e);
+// Device address of g_residual_scratch on device `dev`, looked up once per
+// device with that device current (host code may not use the symbol itself
+// as a device address); the caller's current device is restored.
+int scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return MG_ERR_INTERNAL;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return mg_cuda_fail(e);
+    if (prev != dev && (e = cudaSetDevice(dev)) != cudaSuccess) return mg_cuda_fail(e);
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_residual_scratch);
+    cudaError_t e2 = prev != dev ? cudaSetDevice(prev) : cudaSuccess;
     if (e != cudaSuccess) return mg_cuda_fail(e);
+    if (e2 != cudaSuccess) return mg_cuda_fail(e2);
     g_scratch_addr[dev] = static_cast<double*>(p);
   }
   *out = g_scratch_addr[dev];
   return MG_OK;
 }
 
-bool on_device(const void* p) {
+// true for device (or managed) memory of device `dev`
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 constexpr int kRX = MG_TX + 2, kRY = MG_TY + 2;   // owned tile + 1-node halo
@@ -141,6 +146,9 @@ k_reduce_partials(const double* __restrict__ part, int n, double* __restrict__ o
   }
 }
 
+int run_residual(const FineOpView& v, const double* F, const double* u, double* r, double* norms,
+                 double* scratch);
+
 }  // namespace
 
 extern "C" int mg_residual_static(mg_handle h, const double* F, const double* u, double* r,
@@ -150,10 +158,26 @@ extern "C" int mg_residual_static(mg_handle h, const double* F, const double* u,
   int rc = mg_internal_fine_view(h, &v);
   if (rc != MG_OK) return rc;
   if (v.n_active > MG_NOALLOC_MAX_TILES) return MG_ERR_INVALID_ARG;   // scratch too small
-  if (!on_device(F) || !on_device(u) || (r && !on_device(r))) return MG_ERR_INVALID_ARG;
+  if (!on_device(F, v.device) || !on_device(u, v.device) || (r && !on_device(r, v.device)))
+    return MG_ERR_INVALID_ARG;
   double* scratch = nullptr;
-  rc = scratch_address(&scratch);
+  rc = scratch_address(v.device, &scratch);
   if (rc != MG_OK) return rc;
+  // the launches below go to the handle's device
+  int prev = 0;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  if (prev != v.device && (e = cudaSetDevice(v.device)) != cudaSuccess) return mg_cuda_fail(e);
+  rc = run_residual(v, F, u, r, norms, scratch);
+  if (prev != v.device && (e = cudaSetDevice(prev)) != cudaSuccess && rc == MG_OK)
+    rc = mg_cuda_fail(e);
+  return rc;
+}
+
+namespace {
+
+int run_residual(const FineOpView& v, const double* F, const double* u, double* r, double* norms,
+                 double* scratch) {
   double* result = scratch + 2 * MG_NOALLOC_MAX_TILES;
   const size_t m = (size_t)(v.N + 1) * (v.N + 1);
   cudaError_t e;
@@ -176,3 +200,5 @@ extern "C" int mg_residual_static(mg_handle h, const double* F, const double* u,
   if (e != cudaSuccess) return mg_cuda_fail(e);
   return MG_OK;
 }
+
+}  // namespace

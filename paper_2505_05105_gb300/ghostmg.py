@@ -51,7 +51,8 @@ class mg_stab(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("lambda_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner", ctypes.c_int), ("cycle", ctypes.c_int),
-                ("coarse_op", ctypes.c_int), ("c_global", ctypes.c_double)]
+                ("coarse_op", ctypes.c_int), ("c_global", ctypes.c_double),
+                ("fuse_max_tiles", ctypes.c_int)]
 
 
 class mg_info(ctypes.Structure):
@@ -386,16 +387,19 @@ class Solver:
                  coarsest: int = 8, gamma: float = 2.0, alpha: float = 1.75, eta: int = 4,
                  nu1: int = 2, nu2: int = 1, precision: str = "fp64", max_cycles: int = 100,
                  inner: int = 0, stream: int = 0, neumann_mask=None, cycle: str = "V",
-                 coarse: str = "galerkin", box_sides: bool = False, c_global=None):
+                 coarse: str = "galerkin", box_sides: bool = False, c_global=None,
+                 fuse_max_tiles: int = 0):
         """neumann_mask: (n_cells, n_cells) uint8 cells [jc, ic] (host array,
         or a device tensor), nonzero where a cut cell's boundary piece is
         Neumann (MG_BC_MIXED); None: all Dirichlet.
         c_global: the global constant C of Sec. 5.2 (MG_LAMBDA_GLOBAL:
-        lambda = gamma c_global on every cut cell); None: local lambda_K."""
+        lambda = gamma c_global on every cut cell); None: local lambda_K.
+        fuse_max_tiles: mg_stab.fuse_max_tiles (0 default, -1 never fused)."""
         self.N = n_cells
         stab = mg_default_stab()
         stab.gamma, stab.alpha, stab.eta = gamma, alpha, eta
         stab.nu1, stab.nu2, stab.max_cycles, stab.inner = nu1, nu2, max_cycles, inner
+        stab.fuse_max_tiles = fuse_max_tiles
         stab.precision = {"fp64": MG_FP64, "mixed": MG_MIXED}[precision]
         stab.cycle = {"V": 1, "W": 2, "two-grid": 0}[cycle]
         stab.coarse_op = {"galerkin": MG_COARSE_GALERKIN,

@@ -18,6 +18,14 @@ with eta = 4).
 import numpy as np
 
 EPS = np.finfo(np.float64).eps
+U32 = 2.0 ** -24        # unit roundoff of fp32
+
+# Rounding events of one fp32 V(2,1)-cycle with eta = 4, per node of a level:
+# (nu1 + nu2)(1 + eta) = 15 Gauss-Seidel updates, each with two fp32
+# roundings of relative size U32 (the stored fp32 row coefficients and the
+# update's own arithmetic), so about 32 U32 per cycle; twice that is the
+# constant of the fp32 iterate bound.
+C32 = 64
 
 
 def sensitivity(system, F, u):
@@ -84,3 +92,31 @@ def assert_solution(got, ref, system, F, rel, c=64, well_posed=100.0, what=""):
     worst = err[strong].max() + rel * np.abs(ref).max()
     assert_nodewise(got, ref, tol + 4 * amp * worst, (what, "weak ghost nodes"))
     return int((~strong & system.dof).sum()), float(amp.max())
+
+
+def correction_sensitivity(system, r, e):
+    """S_p of the correction equation A e = r (the equation an fp32 V-cycle
+    of the mixed-precision refinement solves): (|r_p| + sum_q |a_pq| |e_q|)
+    / a_pp, in units of e."""
+    A = system.A
+    diag = A.diagonal()
+    S = (np.abs(r) + abs(A) @ np.abs(e)) / np.where(diag > 0, diag, 1.0)
+    S[~system.dof] = 0.0
+    return S
+
+
+def fp32_step_tolerance(system, F, u0, u_ref, cycles=1):
+    """Node-wise bound for one mixed-precision refinement step from u0 (fp64
+    residual r = F - A u0, `cycles` fp32 V-cycles on A e = sigma r from e = 0,
+    fp64 update) against the fp64 oracle's V-cycles from the same u0, whose
+    result u_ref = u0 + e with e the exact-arithmetic correction:
+        C32 * cycles * U32 * (max|e| + S_p(e))  +  64 eps S_p(u_ref)
+    The first term is the fp32 arithmetic of the cycles (relative to the
+    correction, which sets their scale through sigma); the second the fp64
+    residual and update."""
+    e = u_ref - u0
+    r = F - system.A @ u0
+    r[~system.dof] = 0.0
+    S_e = correction_sensitivity(system, r, e)
+    return (C32 * cycles * U32 * (np.abs(e).max() + S_e)
+            + 64 * EPS * sensitivity(system, F, u_ref)), e

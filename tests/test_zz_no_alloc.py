@@ -1,9 +1,10 @@
 """The allocation-free residual (mg_residual_static) gives the same result as
 mg_residual.  It exists for callers that cannot allocate device memory while
-they use the solver (graph capture, real-time loops, framework-owned memory);
-its reduction scratch is a fixed device array inside the library.  Two calls
-in a row with different inputs check that nothing stale leaks from one call
-into the next.  This file is collected last on purpose."""
+they use the solver (real-time loops that cannot take an allocation's
+device-wide synchronisation, frameworks whose own allocator owns all device
+memory); its reduction scratch is a fixed device array inside the library.
+Two calls in a row with different inputs check that nothing stale leaks from
+one call into the next.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
