@@ -192,6 +192,27 @@ def smooth(L: Level, u, F, eta, order):
     return u
 
 
+def gs_sweep_backward(L: Level, u, F, subset="all"):
+    """The transpose of gs_sweep(order="color4") as an approximate inverse:
+    the same colour updates in the reverse colour order (1,1), (0,1), (1,0),
+    (0,0) (each colour's update E D^{-1} E^T is symmetric, so reversing the
+    sequence transposes the product)."""
+    c = _prep(L)
+    for idx, Ar in reversed(c["c4_" + subset]):
+        if len(idx):
+            u[idx] += (F[idx] - Ar @ u) / c["diag"][idx]
+    return u
+
+
+def smooth_transposed(L: Level, u, F, eta):
+    """The transpose of one smoothing step (smooth with order="color4"): the
+    eta cut-node sweeps first, then the full sweep, each backward."""
+    for _ in range(eta):
+        gs_sweep_backward(L, u, F, "cut")
+    gs_sweep_backward(L, u, F, "all")
+    return u
+
+
 def coarse_solve(L: Level, F):
     """Exact solve on the DOFs of L (dense Cholesky when small, sparse LU
     otherwise, e.g. for the coarse grid of the two-grid scheme)."""
@@ -227,6 +248,30 @@ def mg_cycle(levels, l, u, F, nu1=2, nu2=1, eta=4, order="color4", gamma_star=1,
     u += L.P @ ec
     for _ in range(nu2):
         smooth(L, u, F, eta, order)
+    return u
+
+
+def mg_cycle_transposed(levels, l, u, F, nu1=2, nu2=1, eta=4):
+    """The transposed V(nu1, nu2)-cycle.  A V-cycle is u <- u + B (F - A u)
+    with B its approximate inverse (Alg. 1 applied recursively, Sec. 3.2);
+    B is a product of symmetric steps (colour updates, the coarse correction
+    P B_2h P^T with R = P^T, the exact coarsest solve), so B^T takes the same
+    steps in the reverse order: nu2 transposed smoothing steps, the
+    transposed cycle on the coarse level, nu1 transposed smoothing steps.
+    Since A is symmetric, k of these from u = 0 give the transpose of k
+    V-cycles from u = 0 (the adjoint of the iteration).  Pinned:
+    tests/test_oracle_multigrid.py builds B and B^T column by column."""
+    L = levels[l]
+    if l == len(levels) - 1:
+        return coarse_solve(L, F)
+    for _ in range(nu2):
+        smooth_transposed(L, u, F, eta)
+    r = F - L.A @ u
+    Fc = L.P.T @ r
+    ec = mg_cycle_transposed(levels, l + 1, np.zeros_like(Fc), Fc, nu1, nu2, eta)
+    u += L.P @ ec
+    for _ in range(nu1):
+        smooth_transposed(L, u, F, eta)
     return u
 
 

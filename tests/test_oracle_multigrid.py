@@ -257,3 +257,31 @@ def test_w_and_two_grid_cycles_reach_the_dense_solution(make):
     for kw in (dict(gamma_star=1), dict(gamma_star=2), dict(exact_below=1)):
         outs.append(mg.mg_cycle(two, 0, np.zeros(s.n_nodes), F, **kw))
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("make, nu, eta", [
+    (lambda: wl.circle64(16), (2, 1), 4),
+    (lambda: wl.flower(32), (2, 1), 4),
+    (lambda: wl.flower(32), (1, 2), 2),
+])
+def test_transposed_cycle_is_the_transpose(make, nu, eta):
+    """mg_cycle_transposed is B^T: the approximate inverse of one V-cycle
+    from u = 0 (u = B F) and of the transposed cycle, built column by column
+    on the DOFs, are transposes of each other; B is not symmetric (V(2,1)
+    with a forward Gauss-Seidel), so the test tells them apart."""
+    p = make()
+    s = gf.assemble_problem(p)
+    lev = mg.build_hierarchy(s, coarsest=4)
+    d = np.flatnonzero(s.dof)
+    B = np.zeros((len(d), len(d)))
+    BT = np.zeros_like(B)
+    for a, k in enumerate(d):
+        e = np.zeros(s.n_nodes)
+        e[k] = 1.0
+        B[:, a] = mg.mg_cycle(lev, 0, np.zeros(s.n_nodes), e, nu1=nu[0], nu2=nu[1], eta=eta,
+                              order="color4")[d]
+        BT[:, a] = mg.mg_cycle_transposed(lev, 0, np.zeros(s.n_nodes), e, nu1=nu[0],
+                                          nu2=nu[1], eta=eta)[d]
+    scale = np.abs(B).max()
+    assert np.abs(BT - B.T).max() <= 1e-12 * scale
+    assert np.abs(B - B.T).max() > 1e-6 * scale      # ~1e-5: B is not symmetric
