@@ -20,6 +20,24 @@ import numpy as np
 EPS = np.finfo(np.float64).eps
 U32 = 2.0 ** -24        # unit roundoff of fp32
 
+# Row data: both sides integrate the same exact element integrals (Eq.
+# disc_bil_form) with different quadrature and summation orders.  On the cut
+# cells the Nitsche terms cancel (a penalty term of size ~gamma C(K) |Gamma|
+# against the normal-derivative terms), so an entry is only defined to a few
+# hundred ulp of the largest entry of its row; the operator-row tests hold
+# every row to ROW_REL of its own largest entry.  A relative change delta of
+# node p's row moves a Gauss-Seidel update, and the exact solution at a node
+# whose equation is dominated by its own row, by delta S_p (first order): the
+# data term of the node-wise bounds.  It matters only at weak ghost nodes
+# (S_p up to 1e6 |u|, below); elsewhere S_p ~ 2 |u| and it is ~1e-12 |u|.
+ROW_REL = 2e-13
+# Coarse rows are Galerkin sums P^T A P of up to 81 fine contributions each
+# (Eq. galerkin), with the same cancellation compounded (row-relative
+# differences up to ~3e-11 on the 8 x 8 level at 4096^2); they are held to
+# 1e-13 of their level's largest entry only, since they reach the node-wise
+# bounds through the coarse-grid correction alone, whose effect on a fine
+# iterate is smooth and covered by the rel max|u| term.
+
 # Rounding events of one fp32 V(2,1)-cycle with eta = 4, per node of a level:
 # (nu1 + nu2)(1 + eta) = 15 Gauss-Seidel updates, each with two fp32
 # roundings of relative size U32 (the stored fp32 row coefficients and the
@@ -37,7 +55,17 @@ def sensitivity(system, F, u):
 
 
 def node_tolerance(system, F, u, rel, c):
-    return rel * np.abs(u).max() + c * EPS * sensitivity(system, F, u)
+    """rel max|u| + (c eps + ROW_REL) S_p: the benchmark spec bound, the
+    rounding of c Gauss-Seidel updates and the row-data term."""
+    return rel * np.abs(u).max() + (c * EPS + ROW_REL) * sensitivity(system, F, u)
+
+
+def row_rel_diff(got_rows, ref_rows):
+    """Per row: max |difference| / the reference row's largest entry (0 on
+    empty rows)."""
+    scale = np.abs(ref_rows).max(axis=1)
+    d = np.abs(got_rows - ref_rows).max(axis=1)
+    return np.where(scale > 0, d / np.where(scale > 0, scale, 1.0), d)
 
 
 def residual(system, F, u):
@@ -67,10 +95,10 @@ def assert_nodewise(got, ref, tol, what=""):
 def amplification(system):
     """A_p = sum_{q != p} |a_pq| / a_pp: how much node p's equation amplifies
     errors of its neighbours.  It is O(1) for every internal node; a ghost
-    node on a tiny cut triangle can reach 1e4-1e5 (its diagonal ~1e-8 against
-    couplings ~1e-4 to a heavily penalised neighbour), so its computed value
-    is only as good as its neighbours' values times A_p -- in any fp64
-    implementation."""
+    node on a tiny cut triangle can reach 1e4-1e6 (its diagonal ~1e-12-1e-8
+    against couplings ~1e-6-1e-4 to a heavily penalised neighbour).  Such
+    "weak ghost nodes" (A_p > 100) are reported by the tests; their bound is
+    the same as every other node's."""
     A = system.A
     diag = A.diagonal()
     off = abs(A) @ np.ones(A.shape[0]) - np.abs(diag)
@@ -79,19 +107,16 @@ def amplification(system):
     return amp
 
 
-def assert_solution(got, ref, system, F, rel, c=64, well_posed=100.0, what=""):
-    """Node-wise comparison of a converged solution with the exact one:
-    strict (rel max|u| + c eps S_p + 2 |r_p|/a_pp) on the well-posed nodes
-    (A_p <= well_posed), and on the few weak ghost nodes the neighbours'
-    worst error amplified by A_p (plus the same rounding and residual terms)."""
+def assert_solution(got, ref, system, F, rel, c=64, what=""):
+    """Node-wise comparison of a converged solution with the exact one, at
+    every DOF: rel max|u| + (c eps + ROW_REL) S_p + 2 |r_p| / a_pp (the
+    the benchmark spec bound, rounding, the row-data term, and what the stopping
+    residual leaves at a node dominated by its diagonal).  Returns the
+    number of weak ghost nodes (A_p > 100) and the largest A_p."""
     tol = node_tolerance(system, F, ref, rel, c) + 2 * residual_term(system, F, got)
+    assert_nodewise(got, ref, tol, what)
     amp = amplification(system)
-    strong = amp <= well_posed
-    err = np.abs(got - ref)
-    assert_nodewise(np.where(strong, got, ref), ref, tol, (what, "well-posed nodes"))
-    worst = err[strong].max() + rel * np.abs(ref).max()
-    assert_nodewise(got, ref, tol + 4 * amp * worst, (what, "weak ghost nodes"))
-    return int((~strong & system.dof).sum()), float(amp.max())
+    return int(((amp > 100) & system.dof).sum()), float(amp.max())
 
 
 def correction_sensitivity(system, r, e):
@@ -113,10 +138,10 @@ def fp32_step_tolerance(system, F, u0, u_ref, cycles=1):
         C32 * cycles * U32 * (max|e| + S_p(e))  +  64 eps S_p(u_ref)
     The first term is the fp32 arithmetic of the cycles (relative to the
     correction, which sets their scale through sigma); the second the fp64
-    residual and update."""
+    residual and update (with the row-data term)."""
     e = u_ref - u0
     r = F - system.A @ u0
     r[~system.dof] = 0.0
     S_e = correction_sensitivity(system, r, e)
     return (C32 * cycles * U32 * (np.abs(e).max() + S_e)
-            + 64 * EPS * sensitivity(system, F, u_ref)), e
+            + (64 * EPS + ROW_REL) * sensitivity(system, F, u_ref)), e

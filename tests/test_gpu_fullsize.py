@@ -2,18 +2,16 @@
 5,022,066 DOFs), in the solver configuration bench.py times (default
 parameters, mixed precision, adaptive residual checks).
 
-The oracle cannot assemble or solve this system in a test, so it computes
-sampled outputs one by one, each from its own element matrices (Eq.
-disc_bil_form, Eq. disc_rhs):
+Here the oracle computes sampled outputs one by one, each from its own
+element matrices (Eq. disc_bil_form, Eq. disc_rhs):
   * cut cells: C(K), lambda_K, Ke, Mk, Gk of sampled cut cells;
   * operator rows and F at sampled nodes (vertices of cut cells, interior
     nodes, nodes on 64 x 32 tile edges), summed from the adjacent cells;
   * the GPU solution: the oracle's residual F_p - sum_q A_pq u_q at the
     sampled nodes is within the solve's tolerance;
-  * the level-1 operator: sampled rows equal (P^T A_0 P) formed locally from
-    the exported level-0 rows and the bilinear weights (Eq. galerkin, read as
-    R A P with R = P^T), the same property the small-grid tests check on
-    whole matrices.
+The operators of every level, fp64 V-cycle iterates and mixed-precision
+refinement steps at this size are compared with the whole oracle in
+test_gpu_fullsize_oracle.py.
 Tolerances as in test_gpu_parity.py: 1e-13 of the largest entry for rows
 and element data (the same exact integrals in a different order).
 """
@@ -162,53 +160,3 @@ def test_rows_rhs_solution_fullsize(full):
             assert abs(r) <= 1e-10 * Fmax + slack, (prec, i, j, r)
         if Sx is not S:
             Sx.close()
-
-
-def test_galerkin_level1_fullsize(full):
-    """Rows of level 1 = (P^T A_0 P) at sampled coarse nodes, from the
-    exported level-0 rows: P the bilinear weights restricted to fine DOFs."""
-    rng = np.random.default_rng(13)
-    S = full["S"]
-    A0 = S.stencil(0).reshape(N + 1, N + 1, 9)
-    A1 = S.stencil(1)
-    nc = N // 2
-    fdof = A0[:, :, 4] > 0                 # fine DOFs: positive diagonal (coercivity)
-    cdiag = A1.reshape(nc + 1, nc + 1, 9)[:, :, 4]
-    cj, ci = np.nonzero(cdiag > 0)
-    # coarse nodes near the interface and elsewhere
-    cut_c = gf.cell_classes(full["psi_s"][::2, ::2])      # only for picking near the band
-    jb, ib = np.nonzero(cut_c == gf.CUT)
-    pick = [(int(ib[k]), int(jb[k])) for k in rng.choice(len(ib), 20, replace=False)]
-    pick += [(int(ci[k]), int(cj[k])) for k in rng.choice(len(ci), 20, replace=False)]
-    w = {-1: 0.5, 0: 1.0, 1: 0.5}
-
-    def P(a, c):
-        # weight of coarse node c at fine node a (zero off the fine DOFs)
-        dx, dy = a[0] - 2 * c[0], a[1] - 2 * c[1]
-        if abs(dx) > 1 or abs(dy) > 1 or not fdof[a[1], a[0]]:
-            return 0.0
-        return w[dx] * w[dy]
-
-    scale = np.abs(A1).max()
-    for (I, J) in pick:
-        if not (0 < I < nc and 0 < J < nc):
-            continue
-        row = np.zeros(9)
-        for dJ in (-1, 0, 1):
-            for dI in (-1, 0, 1):
-                q = (I + dI, J + dJ)
-                acc = 0.0
-                for ay in (-1, 0, 1):
-                    for ax in (-1, 0, 1):
-                        a = (2 * I + ax, 2 * J + ay)
-                        pa = P(a, (I, J))
-                        if pa == 0.0:
-                            continue
-                        for s in range(9):
-                            b = (a[0] + s % 3 - 1, a[1] + s // 3 - 1)
-                            pb = P(b, q)
-                            if pb:
-                                acc += pa * A0[a[1], a[0], s] * pb
-                row[(dI + 1) + 3 * (dJ + 1)] = acc
-        got = A1[I + J * (nc + 1)]
-        assert np.abs(got - row).max() <= 1e-13 * scale, (I, J)
