@@ -55,6 +55,11 @@ ALGO_BYTES = {
     ("residual", "f64"): 8 + 8 + 1,
     ("update", "mixed"): 8 + 4 + 1 + 8,       # u64 in, e32 in, u64 out
 }
+# one extra-sweep launch per boundary node: u read and written, F, its row
+BAND_BYTES = 4 + 4 + 4 + 4 * 10
+# a mixed refinement cycle over all levels (fp32 V(2,1) ~ 80 B, fp64
+# residual and update ~ 40 B per fine DOF)
+SOLVE_BYTES_PER_DOF_CYCLE = 120
 
 
 def parse_args(argv=None):
@@ -73,6 +78,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched workload (256 seeded geometries)")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the 64^2 circle and the 512^2 adjoint workloads")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large workload (three discs, 8192^2 cells)")
     ap.add_argument("--large-N", type=int, default=8192)
@@ -182,32 +189,34 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(N_sample, steps, warmup):
-    """Time the CPU oracle (fp64 4-colour V(2,1) with eta = 4, same stopping
-    test) on the flower level set with N_sample cells per side; setup is
-    excluded, like the GPU metric.  Returns (DOF/s, dofs, per-solve s, cycles)."""
+def oracle_hierarchy(N):
+    """The oracle's system and hierarchy for the flower at N cells per side
+    (assembly and Galerkin products in Python: setup, never timed)."""
     from oracle import ghostfem as gf
     from oracle import multigrid as mg
     from paper_2505_05105_gb300 import workloads as wl
-    p = wl.flower(N_sample)
+    p = wl.flower(N)
     s = gf.assemble_problem(p)
     lev = mg.build_hierarchy(s)
-    F = s.rhs(p.f, p.g)
-    times, cyc = [], 0
+    return p, s, lev, s.rhs(p.f, p.g)
+
+
+def cpu_vcycle(lev, F, threads, steps, warmup, tol=TOL):
+    """Time the oracle's 4-colour V(2,1) (eta = 4) solve from u = 0 to tol in
+    its plain-C OpenMP restatement (oracle/vcycle.c) with `threads` threads
+    (0: all cores).  Returns (seconds per solve, cycles, threads used, u)."""
+    from oracle import cvcycle
+    C = cvcycle.CVCycle(lev)
+    times, cyc, u = [], 0, None
     for k in range(warmup + steps):
         t0 = time.perf_counter()
-        u, hist, cyc = mg.solve(lev, F, tol=TOL)
+        u, hist, cyc = C.solve(F, tol=tol, threads=threads)
         dt = time.perf_counter() - t0
         if k >= warmup:
             times.append(dt)
-    ndof = int(s.dof.sum())
-    return ndof / statistics.mean(times), ndof, statistics.mean(times), cyc
-
-
-def cpu_threads():
-    """Threads the oracle's timed solve uses: its sparse kernels (SciPy CSR
-    products and the colour-wise NumPy updates) run on one thread."""
-    return 1
+    used = cvcycle.CVCycle.threads(threads)
+    C.close()
+    return statistics.mean(times), cyc, used, u
 
 
 def host_info():
@@ -266,21 +275,25 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    Ns = 2048
+    N = args.N
     steps = max(1, args.steps)
     warm = max(0, args.warmup)
-    val, ndof, sec, cyc = oracle_sample(Ns, steps, warm)
-    sample = (f"flower level set at {Ns}x{Ns} cells ({ndof} DOFs, 1/{(args.N // Ns) ** 2} of the "
-              f"nodes), full fp64 solve to 1e-10 ({cyc} V(2,1) cycles), setup excluded")
+    p, s, lev, F = oracle_hierarchy(N)
+    ndof = int(s.dof.sum())
+    sec, cyc, cores, _ = cpu_vcycle(lev, F, 0, steps, warm)
+    val = ndof / sec
+    sample = (f"the whole {N}x{N} flower workload ({ndof} DOFs): full fp64 4-colour V(2,1) "
+              f"solve from u = 0 to 1e-10 ({cyc} cycles) per step, by the oracle's V-cycle in "
+              f"plain C with OpenMP (oracle/vcycle.c) on {cores} host threads; assembly and "
+              f"hierarchy (Python) excluded")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
         "n_gpus": args.gpus, "steps": steps, "warmup": warm, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_name(args.N), "N": args.N, "tol": TOL,
-                   "sample_N": Ns},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": sample},
+        "config": {"workload": workload_name(N), "N": N, "n_dof": ndof, "tol": TOL},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample, "host": host_info()},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -358,37 +371,96 @@ def run_ours(args):
         # roofline come from a second pass of the same K solves, not from the
         # headline one
         _, _, _, prof, _ = timed(solvers["mixed"], args.steps, 0, prof=True)
+        u_mixed = u.cpu().numpy().copy()
         total_64, ms_64, cyc_64, _, info_64 = timed(solvers["fp64"], args.steps, args.warmup)
+        u_fp64 = u.cpu().numpy().copy()
         batched = None
         if not args.no_batched and world == 1:
             batched = run_batched(args, dev, flush)
         large = None
         if not args.no_large and world == 1:
             large = run_large(args, dev, flush, stream)
+        small = adjoint = None
+        if world == 1 and not args.no_small:
+            small = run_small(args, dev, stream)
+            adjoint = run_adjoint(args, dev, stream)
     clocks = clk.summary()
 
     value = job_value(world, ndof, args.steps, total_mx / 1e3)
     value64 = job_value(world, ndof, args.steps, total_64 / 1e3)
 
-    # roofline of the dominant fine-level kernel (live CUDA-event timing)
+    # roofline: every kernel class timed live (CUDA events around each launch
+    # on the solver's stream, second pass), its algorithmic bytes per launch,
+    # and the dominant class (most device time) as the line's "roofline"
     launches, slots = prof
-    kinds = {"sweep": "f32", "restrict": "f32", "prolong": "f32", "residual": "mixed",
-             "update": "mixed"}
-    cand = {k: v for k, v in slots.items() if k in kinds and v[0] > 0}
-    dom = max(cand, key=lambda k: cand[k][1])
-    n_launch, dom_ms = cand[dom]
-    per_launch_s = dom_ms / n_launch / 1e3
-    algo = ALGO_BYTES[(dom, kinds[dom])] * ndof
     peak, peak_src = measured_peaks()
+    H = solvers["mixed"].handle
+    lev_dofs = [ghostmg.mg_level_dofs(H, l) for l in range(n_levels)]
+    inter = sum(lev_dofs[1:-1])          # the levels between the finest and the coarsest
+    per_launch_bytes = {
+        "sweep": ALGO_BYTES[("sweep", "f32")] * ndof,
+        "band": BAND_BYTES * nbnd,
+        "restrict": ALGO_BYTES[("restrict", "f32")] * ndof,
+        "residual": ALGO_BYTES[("residual", "mixed")] * ndof,
+        "update": ALGO_BYTES[("update", "mixed")] * ndof,
+    }
+    cycles_prof = sum(cyc_mx) / len(cyc_mx) * args.steps
+    # the intermediate levels' kernels (separate, fused, tail) per V-cycle:
+    # three sweeps and one residual + restriction of each level's DOFs
+    per_step_bytes_coarse = (3 * ALGO_BYTES[("sweep", "f32")] + ALGO_BYTES[("restrict", "f32")]) \
+        * inter * cycles_prof / args.steps
+    kernel_roofline = {}
+    total_ms = sum(v[1] for v in slots.values())
+    for k, (n_l, ms) in slots.items():
+        if n_l == 0 or ms <= 0:
+            continue
+        ent = {"launch_groups": n_l, "ms_per_step": ms / args.steps,
+               "share": ms / total_ms, "avg_launch_us": ms / n_l * 1e3}
+        if k in per_launch_bytes:
+            gbs = per_launch_bytes[k] / (ms / n_l / 1e3) / 1e9
+            ent.update({"algorithmic_bytes_per_launch": per_launch_bytes[k],
+                        "achieved_gbs": gbs, "frac": gbs / peak})
+        kernel_roofline[k] = ent
+    coarse_ms = sum(slots[k][1] for k in ("levels", "fused", "tail", "coarse") if k in slots)
+    if coarse_ms > 0:
+        gbs = per_step_bytes_coarse / (coarse_ms / args.steps / 1e3) / 1e9
+        kernel_roofline["intermediate_levels_all"] = {
+            "classes": ["levels", "fused", "tail", "coarse"],
+            "algorithmic_bytes_per_step": per_step_bytes_coarse, "achieved_gbs": gbs,
+            "frac": gbs / peak, "level_dofs": lev_dofs}
+    dom = max((k for k in slots if slots[k][0] > 0), key=lambda k: slots[k][1])
+    n_launch, dom_ms = slots[dom]
+    per_launch_s = dom_ms / n_launch / 1e3
+    names = {"sweep": "k_gs_sweep_f32 (fine level)", "band": "k_band<float> (fine level)",
+             "restrict": "k_resid_restrict<float> (fine level)",
+             "residual": "k_residual<double,float> (fp64 refinement residual)",
+             "update": "k_update", "levels": "separate kernels of the intermediate levels",
+             "fused": "k_smooth_step (fused smoothing steps)", "tail": "k_tail<float>",
+             "coarse": "coarsest solve", "io": "right-hand side, pack, unpack",
+             "prolong": "k_prolong"}
+    if dom in per_launch_bytes:
+        algo = per_launch_bytes[dom]
+        bound = "hbm"
+    else:
+        # the intermediate levels' share of the algorithmic bytes over this class's time
+        algo = per_step_bytes_coarse * (dom_ms / coarse_ms) / (n_launch / args.steps)
+        bound = "hbm"
     achieved = algo / per_launch_s / 1e9
     traffic = profile_traffic(f"{dom}_f32_flower{N}", dom)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_gs_sweep_f32 (fine level)" if dom == "sweep" else dom,
-                "algorithmic_bytes_per_launch": algo, "launches": n_launch,
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": names.get(dom, dom),
+                "class": dom, "algorithmic_bytes_per_launch": algo, "launches": n_launch,
                 "avg_launch_us": per_launch_s * 1e6, "peak_source": f"{peak_src} hbm_gbs",
                 "timing": f"CUDA events around each launch on the solver stream, over {args.steps} "
                           "profiled solves run after the timed ones"}
+    # the whole solve against the HBM roofline: 120 B per fine DOF and mixed
+    # refinement cycle (fp32 V(2,1) over all levels plus the fp64 residual
+    # and update)
+    solve_level = {"algorithmic_bytes_per_dof_cycle": SOLVE_BYTES_PER_DOF_CYCLE,
+                   "cycles_per_solve": cyc_mx[-1],
+                   "achieved_gbs": SOLVE_BYTES_PER_DOF_CYCLE * cyc_mx[-1] * ndof
+                   / (total_mx / args.steps / 1e3) / 1e9}
+    solve_level["frac"] = solve_level["achieved_gbs"] / peak
     breakdown = {k: {"launch_groups": v[0], "ms_per_step": v[1] / args.steps}
                  for k, v in slots.items()}
 
@@ -421,13 +493,32 @@ def run_ours(args):
                            "all of u written); bytes above are the arrays' sizes"}
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        Ns = 2048
-        val, sdof, sec, scyc = oracle_sample(Ns, steps=2, warmup=0)
-        cpu = {"value": val, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"flower level set at {Ns}x{Ns} cells ({sdof} DOFs), full fp64 "
-                         f"4-colour V(2,1) solve to 1e-10 ({scyc} cycles), setup excluded",
+        # the oracle's V-cycle in plain C (oracle/vcycle.c) on the same
+        # workload, on one host thread and on all of them
+        _, s_o, lev_o, F_o = oracle_hierarchy(N)
+        sec_all, cyc_o, cores, _ = cpu_vcycle(lev_o, F_o, 0, steps=2, warmup=1)
+        sec_one, _, _, _ = cpu_vcycle(lev_o, F_o, 1, steps=1, warmup=0)
+        odof = int(s_o.dof.sum())
+        cpu = {"value": odof / sec_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"the whole {N}x{N} flower workload ({odof} DOFs): full fp64 4-colour "
+                         f"V(2,1) solve from u = 0 to 1e-10 ({cyc_o} cycles), the oracle's "
+                         f"V-cycle in plain C with OpenMP (oracle/vcycle.c), {cores} threads; "
+                         f"assembly and hierarchy (Python) excluded",
+               "one_thread": {"value": odof / sec_one, "unit": UNIT, "seconds": sec_one},
+               "all_threads": {"value": odof / sec_all, "unit": UNIT, "seconds": sec_all,
+                               "threads": cores},
                "host": host_info(), "sparse_direct": sparse_direct_sample(1024)}
+        # error of the GPU results against the fp64 oracle: its V-cycle
+        # driven to the attainable residual (2e-15)
+        _, _, _, u_ref = cpu_vcycle(lev_o, F_o, 0, steps=1, warmup=0, tol=2e-15)
+        scale = float(np.abs(u_ref).max())
+        accuracy = {"reference": "the oracle's fp64 4-colour V(2,1) solution of the same "
+                                 "system driven to ||F - Au||_inf/||F||_inf <= 2e-15",
+                    "mixed_max_rel_error": float(np.abs(u_mixed - u_ref).max()) / scale,
+                    "fp64_max_rel_error": float(np.abs(u_fp64 - u_ref).max()) / scale,
+                    "mixed_rel_res": info_mx.rel_res, "fp64_rel_res": info_64.rel_res}
 
     if rank == 0:
         line = {
@@ -447,10 +538,15 @@ def run_ours(args):
                      "cycles_per_solve": cyc_64[-1], "dtype": "f64"},
             "mixed_over_fp64": value / value64,
             "roofline": roofline,
+            "kernel_roofline": kernel_roofline,
+            "solve_roofline": solve_level,
             "kernel_breakdown_mixed": breakdown,
             "batched": batched,
             "large": large,
+            "small_circle64": small,
+            "adjoint_flower512": adjoint,
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -521,6 +617,92 @@ def run_large(args, dev, flush, stream):
         S.close()
     out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
     return out
+
+
+def run_small(args, dev, stream):
+    """The circle at 64^2 (2157 DOFs; plain fp64 V(2,1), f = 0, g = u): a
+    launch-latency-bound solve, by mg_solve (stream-ordered launches with a
+    host residual check after each group of cycles: no graph) and as a
+    one-member batch (mixed precision, the whole solve one CUDA graph)."""
+    import numpy as np
+    import torch
+    from paper_2505_05105_gb300 import ghostmg, workloads as wl
+    p = wl.circle64(64)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(dev)
+    psi, f, g = t(p.psi), t(p.f), t(p.g)
+    u = torch.zeros_like(f)
+    steps = max(5, args.steps)
+    out = {"workload": "circle sqrt((x-.02)^2+(y-.01)^2)-.39, 64^2 cells, u=e^x sin y, f=0, g=u"}
+    S = ghostmg.Solver(psi, 64, p.x0, p.y0, p.h, precision="fp64", stream=stream.cuda_stream)
+    ndof = S.counts()[1]
+    for _ in range(3):
+        u.zero_()
+        S.solve(f, g, u, tol=TOL)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u.zero_()
+        info = S.solve(f, g, u, tol=TOL)
+    torch.cuda.synchronize(dev)
+    sec = (time.perf_counter() - t0) / steps
+    out["n_dof"] = ndof
+    out["fp64_mg_solve"] = {"value": ndof / sec, "unit": UNIT, "ms_per_step": sec * 1e3,
+                            "cycles_per_solve": info.cycles, "graph": False,
+                            "timing": "wall clock around mg_solve, which returns with u written"}
+    S.close()
+    B = ghostmg.BatchSolver([p])
+    f0, g0, u0 = B.buffers()
+    f0.copy_(f)
+    g0.copy_(g)
+    for _ in range(3):
+        B.solve(f0, g0, u0, tol=TOL)
+    ms = []
+    for _ in range(steps):
+        info_b = B.solve(f0, g0, u0, tol=TOL)
+        ms.append(B.timing()[1])
+    out["mixed_one_graph"] = {"value": ndof / (statistics.mean(ms) / 1e3), "unit": UNIT,
+                              "ms_per_step": statistics.mean(ms), "graph": True,
+                              "cycles_per_solve": info_b[0].cycles,
+                              "timing": "CUDA events around the graph launch"}
+    B.close()
+    return out
+
+
+def run_adjoint(args, dev, stream):
+    """The adjoint workload: flower 512^2, one forward fp64 solve to 1e-10,
+    then 16 adjoints (L = 1/2 sum over internal nodes of (u - u_t)^2, u_t
+    seeded) by mg_adjoint: transposed fp64 V-cycles to the solve's tolerance,
+    then dL/df = M^T w and dL/dg = G^T w."""
+    import numpy as np
+    import torch
+    from paper_2505_05105_gb300 import ghostmg, workloads as wl
+    p = wl.flower(512)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(dev)
+    f, g = t(p.f), t(p.g)
+    S = ghostmg.Solver(t(p.psi), 512, p.x0, p.y0, p.h, precision="fp64",
+                       stream=stream.cuda_stream)
+    ndof = S.counts()[1]
+    u = torch.zeros_like(f)
+    S.solve(f, g, u, tol=TOL)
+    inside = t((np.ravel(p.psi) < 0).astype(float))
+    dLdu = [(u - t(wl.adjoint_target(p, seed))) * inside for seed in range(16)]
+    dLdf, dLdg = torch.zeros_like(u), torch.zeros_like(u)
+    S.adjoint(dLdu[0], dLdf, dLdg)                 # warm-up
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for d in dLdu:
+        S.adjoint(d, dLdf, dLdg)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    S.close()
+    return {"workload": "flower 512^2, 16 adjoints of L = 1/2 sum_internal (u - u_t)^2 "
+                        "(seeded targets), fp64, to 1e-10",
+            "n_dof": ndof, "members": 16, "value": 16 * ndof / (ms / 1e3), "unit": UNIT,
+            "ms_per_adjoint": ms / 16,
+            "timing": "CUDA events around the 16 mg_adjoint calls on the solver's stream"}
 
 
 def batch_members(count):

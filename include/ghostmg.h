@@ -57,7 +57,7 @@ enum {
   MG_ERR_NOT_CONVERGED = 3,  /* max_cycles reached; outputs and info filled */
   MG_ERR_DIVERGED = 4,       /* residual not finite or 1e3 x above its best */
   MG_ERR_NOT_SPD = 5,        /* coarsest Cholesky met a pivot <= 0 */
-  MG_ERR_TIMEOUT = 6,        /* reserved for bounded device waits */
+  MG_ERR_TIMEOUT = 6,        /* a bounded device wait ran out (mg_set_wait_limit) */
   MG_ERR_UNIMPLEMENTED = 7,  /* option not supported (e.g. Neumann data) */
   MG_ERR_INTERNAL = 8,       /* internal consistency check failed */
   MG_ERR_OUT_OF_MEMORY = 9   /* device allocation failed */
@@ -125,10 +125,13 @@ typedef struct {
  *                 cell, c_global the largest generalized eigenvalue of the
  *                 global pencil K v = Lambda M v of Sec. 5.2 (K: normal
  *                 derivatives on Gamma_D, M: stiffness on Omega_h, both over
- *                 the whole FE space).  That eigenvalue is the caller's (a
- *                 setup-time computation for convergence studies, in 1/length
- *                 units): c_global must be finite and > 0
- *                 (MG_ERR_INVALID_ARG otherwise); not with
+ *                 the whole FE space), in 1/length units: the caller's
+ *                 value when c_global > 0; with c_global = 0 mg_setup
+ *                 computes it on the GPU (the pencil taken modulo constants,
+ *                 Lanczos with inner conjugate-gradient solves; n_cells <=
+ *                 1024 and no box_sides, else MG_ERR_UNIMPLEMENTED;
+ *                 mg_get_c_global reads it back).  Negative or non-finite
+ *                 c_global: MG_ERR_INVALID_ARG.  Not with
  *                 MG_COARSE_REDISCRETISE nor in batches
  *                 (MG_ERR_UNIMPLEMENTED).  C(K) is still reported per cell.
  *   precision = MG_FP64 or MG_MIXED
@@ -234,7 +237,9 @@ int mg_solve_bc(mg_handle h, const double* f, const double* g_D, const double* g
                 double tol, mg_info* info);
 
 /* Adjoint of mg_solve for a loss L(u): solves A w = dL/du (A is symmetric,
- * Sec. 4.1) to the tolerance of the last mg_solve (1e-10 if none), then
+ * Sec. 4.1) to the tolerance of the last mg_solve (1e-10 if none) by
+ * transposed V-cycles in fp64 (mg_cycles_transposed; the same stop test
+ * and check schedule as mg_solve, whatever the handle's precision), then
  * dL/df = M^T w and dL/dg = G^T w (F is linear in f and g, Eq. disc_rhs).
  * dLdu, dLdf, dLdg: (N+1)^2 doubles, device or host; dLdf or dLdg may be
  * NULL to skip it (not both).  dL/du off the DOFs is ignored; both outputs
@@ -262,12 +267,33 @@ const char* mg_strerror(int code);
  * each step can be checked on its own).  Arrays as above.
  * ------------------------------------------------------------------------- */
 
+/* The global constant of Sec. 5.2 a handle set up with MG_LAMBDA_GLOBAL
+ * uses (the caller's c_global, or the one mg_setup computed when c_global
+ * was 0; 0 under MG_LAMBDA_LOCAL), and for a computed one the Lanczos steps
+ * and conjugate-gradient iterations it took (0 otherwise).  Any output may
+ * be NULL. */
+int mg_get_c_global(mg_handle h, double* c_global, int* lanczos_steps, int* cg_iterations);
+
+/* Poll budget of the handle's bounded device waits (the completion waits of
+ * the shared-memory tensor and bulk copies; not a part of the method).
+ * Every such wait gives up after `polls` polls of its mbarrier (polls < 0:
+ * the default, 2^22, seconds at least); the kernel then records the timeout,
+ * waits with the default budget for its own copy still in flight, and stops
+ * without using the data, and the call returns MG_ERR_TIMEOUT at its next
+ * check (u is then not a solution).  polls = 0 makes every wait give up at
+ * once: a way to exercise that path.  The handle stays usable.
+ * MG_ERR_INVALID_ARG for a NULL handle or polls above 2^32 - 1. */
+int mg_set_wait_limit(mg_handle h, long long polls);
+
 /* Sizes of the hierarchy: levels, fine DOFs, fine cut cells, boundary nodes
  * (vertices of cut cells) on the fine level.  Any pointer may be NULL. */
 int mg_get_counts(mg_handle h, int* n_levels, int* n_dof, int* n_cut, int* n_boundary);
 
 /* Cells per side of level `level` (0 = finest), or -1 for a bad level. */
 int mg_level_cells(mg_handle h, int level);
+
+/* DOFs of level `level` (0 = finest), or -1 for a bad level. */
+int mg_level_dofs(mg_handle h, int level);
 
 /* The 9-point rows of the level-`level` operator: out[9 k + s] = A_{k, k'}
  * with k' the neighbour at offset (s mod 3 - 1, s / 3 - 1), k = i + j (n+1);
@@ -293,6 +319,15 @@ int mg_rhs_bc(mg_handle h, const double* f, const double* g_D, const double* g_N
  * residual, stab.inner fp32 V-cycles -- one if inner = 0 -- on the
  * correction equation from e = 0, fp64 update).  u in/out. */
 int mg_cycles(mg_handle h, const double* F, double* u, int k, int precision);
+
+/* Exactly k transposed V-cycles (fp64) from u with right-hand side F: the
+ * cycle whose approximate inverse is B^T for the V-cycle's B (u <- u +
+ * B (F - A u), Sec. 3.2): nu2 transposed smoothing steps (the eta cut-node
+ * sweeps, then the full sweep, colours in the reverse order), restriction,
+ * the transposed cycle below, prolongation, nu1 transposed smoothing steps.
+ * A is symmetric, so k of them from u = 0 give the transpose of k V-cycles
+ * from 0; mg_adjoint solves with them.  u in/out. */
+int mg_cycles_transposed(mg_handle h, const double* F, double* u, int k);
 
 /* r = F - A u on the fine level (fp64); norms[0] = ||r||_inf,
  * norms[1] = ||r||_2 (host array of 2, may be NULL); r may be NULL. */
@@ -346,9 +381,15 @@ enum {
   MG_PROF_PROLONG = 3,   /* fine-level prolongation + correction */
   MG_PROF_RESIDUAL = 4,  /* fine-level fp64 residual (stopping test, refinement) */
   MG_PROF_UPDATE = 5,    /* refinement update u += e */
-  MG_PROF_COARSE = 6,    /* every kernel on the coarser levels */
+  MG_PROF_COARSE = 6,    /* other coarse-level kernels (coarsest solve,
+                            the fp64 transposed cycle) */
   MG_PROF_IO = 7,        /* right-hand side, input checks, pack/unpack */
-  MG_PROF_SLOTS = 8
+  MG_PROF_LEVELS = 8,    /* sweeps, extra sweeps, restriction, prolongation
+                            on the levels between the finest and the tail
+                            that do not run fused steps */
+  MG_PROF_FUSED = 9,     /* fused smoothing steps (fp32 intermediate levels) */
+  MG_PROF_TAIL = 10,     /* the single-block V-cycle of the smallest levels */
+  MG_PROF_SLOTS = 11
 };
 
 /* enable != 0: clear the accumulators and start recording; 0: stop. */

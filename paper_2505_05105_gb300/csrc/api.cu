@@ -16,6 +16,7 @@
 #include "setup.cuh"
 #include "fused.cuh"
 #include "tail.cuh"
+#include "global.cuh"
 
 namespace {
 
@@ -45,6 +46,9 @@ struct Level {
   int* band_off = nullptr;      // [5 n_band + 1] group offsets into band_ent
   int2* band_ent = nullptr;     // boundary nodes of each band tile's region
   BandMaps bmap[2]{};           // TMA maps of u32[0..1] (fp32) and u64[0..1] (fp64)
+  // the fp32 sweep's region lists (active tiles, 4-node halo)
+  int* soff = nullptr;
+  int2* sent = nullptr;
   int nbx = 0;
   int n_dof = 0;
   int n_rtiles = 0;
@@ -91,12 +95,15 @@ struct mg_ctx {
   int* all_tiles = nullptr;      // every tile of the fine level (box adjoint)
   std::vector<void*> allocs;
   double last_tol = 1e-10;
+  double c_global = 0.0;         // the global constant used (given or computed)
+  int global_steps = 0, global_cg = 0;   // Lanczos steps / CG iterations when computed
   int tail_level = -1;           // first level run by the single-block tail kernel
   TailLayout tail_lay[2];          // [float, double] shared-memory layout of the tail block
   unsigned char* tail_image[2] = {nullptr, nullptr};   // its static image
   bool fused[2] = {false, false};  // fused smoothing steps on the intermediate levels
   size_t fused_smem[2] = {0, 0};
   int fused_max_tiles = 0;         // levels with more active tiles use the separate kernels
+  unsigned wait_polls = kMbarSpinLimit;   // poll budget of every bounded device wait
   float setup_ms = 0.f;
   float solve_ms = 0.f;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -367,17 +374,25 @@ void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine, Level* coarse = nullpt
   int& cur = P<T>::cur(v);
   const int eta = c->stab.eta;
   {
-    Launch k(c, fine ? MG_PROF_SWEEP : MG_PROF_COARSE, v.n_active > 0);
-    launch_gs_sweep<T>(op, v.active, v.n_active, P<T>::u(v, cur), P<T>::u(v, cur ^ 1), P<T>::F(v),
-                       eta > 0 ? P<T>::bval(v) : (T*)nullptr, zero_in,
-                       coarse ? &coarse->L : nullptr,
-                       coarse ? P<T>::u(*coarse, P<T>::cur(*coarse)) : (const T*)nullptr, c->st);
+    Launch k(c, fine ? MG_PROF_SWEEP : MG_PROF_LEVELS, v.n_active > 0);
+    if constexpr (sizeof(T) == 4) {
+      launch_gs_sweep_f32(op, v.active, v.n_active, v.u32[cur], v.u32[cur ^ 1], v.F32,
+                          eta > 0 ? v.bval32 : nullptr, zero_in, coarse ? &coarse->L : nullptr,
+                          coarse ? coarse->u32[coarse->cur32] : nullptr, v.soff, v.sent, c->st);
+    } else {
+      launch_gs_sweep<T>(op, v.active, v.n_active, P<T>::u(v, cur), P<T>::u(v, cur ^ 1),
+                         P<T>::F(v), eta > 0 ? P<T>::bval(v) : (T*)nullptr, zero_in,
+                         coarse ? &coarse->L : nullptr,
+                         coarse ? P<T>::u(*coarse, P<T>::cur(*coarse)) : (const T*)nullptr,
+                         c->st);
+    }
   }
   cur ^= 1;
   if (eta > 0 && v.n_band > 0) {
-    Launch k(c, fine ? MG_PROF_BAND : MG_PROF_COARSE, 1);
+    Launch k(c, fine ? MG_PROF_BAND : MG_PROF_LEVELS, 1);
     launch_band<T>(op, v.band, v.n_band, v.nbx, eta, P<T>::u(v, cur), P<T>::F(v), P<T>::bval(v),
-                   v.band_off, v.band_ent, v.bmap[sizeof(T) == 8 ? 1 : 0], cur, c->d_err, c->st);
+                   v.band_off, v.band_ent, v.bmap[sizeof(T) == 8 ? 1 : 0], cur, c->d_err,
+                   c->wait_polls, c->st);
   }
 }
 
@@ -393,7 +408,7 @@ int coarse_cycles(const mg_ctx* c, int l) {
 }
 
 template <class T>
-void tail_cycle(mg_ctx* c, int l, bool zero_init) {
+void tail_cycle(mg_ctx* c, int l, bool zero_init, bool transposed = false) {
   const int pi = sizeof(T) == 8 ? 1 : 0;
   TailArgs<T> a;
   a.lay = c->tail_lay[pi];
@@ -409,7 +424,9 @@ void tail_cycle(mg_ctx* c, int l, bool zero_init) {
   a.nu1 = c->stab.nu1;
   a.nu2 = c->stab.nu2;
   a.err = c->d_err;
-  Launch k(c, MG_PROF_COARSE, 1);
+  a.wait_polls = c->wait_polls;
+  a.transposed = transposed ? 1 : 0;
+  Launch k(c, MG_PROF_TAIL, 1);
   launch_tail<T>(a, c->st);
 }
 
@@ -443,14 +460,14 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
     a.uin = P<T>::u(v, cur);
     a.uout = P<T>::u(v, cur ^ 1);
     a.tiles = last ? v.rtiles : v.active;
-    Launch k(c, MG_PROF_COARSE, 1);
+    Launch k(c, MG_PROF_FUSED, 1);
     launch_smooth_step<T>(a, last ? v.n_rtiles : v.n_active, zero_init && s == 0, false, last,
                           smem, c->st);
     cur ^= 1;
   }
   if (nu1 == 0) {
     if (zero_init) cudaMemsetAsync(P<T>::u(v, cur), 0, v.L.size() * sizeof(T), c->st);
-    Launch k(c, MG_PROF_COARSE, w.n_active > 0);
+    Launch k(c, MG_PROF_FUSED, w.n_active > 0);
     launch_resid_restrict<T>(op_of<T>(v), P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
                              P<T>::F(w), nullptr, c->st);
   }
@@ -462,12 +479,12 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
   for (int s = 0; s < nu2; ++s) {
     a.uin = P<T>::u(v, cur);
     a.uout = P<T>::u(v, cur ^ 1);
-    Launch k(c, MG_PROF_COARSE, 1);
+    Launch k(c, MG_PROF_FUSED, 1);
     launch_smooth_step<T>(a, v.n_active, false, s == 0, false, smem, c->st);
     cur ^= 1;
   }
   if (nu2 == 0) {
-    Launch k(c, MG_PROF_COARSE, v.n_active > 0);
+    Launch k(c, MG_PROF_FUSED, v.n_active > 0);
     launch_prolong<T>(op_of<T>(v), v.active, v.n_active, P<T>::u(v, cur), w.L,
                       P<T>::u(w, P<T>::cur(w)), c->st);
   }
@@ -499,7 +516,7 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
   Level& w = c->lev[l + 1];
   OpArgs<T> op = op_of<T>(v);
   {
-    Launch k(c, fine ? MG_PROF_RESTRICT : MG_PROF_COARSE, w.n_active > 0);
+    Launch k(c, fine ? MG_PROF_RESTRICT : MG_PROF_LEVELS, w.n_active > 0);
     launch_resid_restrict<T>(op, P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
                              P<T>::F(w), nullptr, c->st);
   }
@@ -507,12 +524,72 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
   const int gs = coarse_cycles(c, l);
   for (int k = 0; k < gs; ++k) vcycle<T>(c, l + 1, k == 0);
   if (c->stab.nu2 == 0) {
-    Launch k(c, fine ? MG_PROF_PROLONG : MG_PROF_COARSE, v.n_active > 0);
+    Launch k(c, fine ? MG_PROF_PROLONG : MG_PROF_LEVELS, v.n_active > 0);
     launch_prolong<T>(op, v.active, v.n_active, P<T>::u(v, cur), w.L, P<T>::u(w, P<T>::cur(w)),
                       c->st);
   }
   // the first post-smoothing sweep adds the prolongated correction itself
   for (int s = 0; s < c->stab.nu2; ++s) smooth<T>(c, v, false, fine, s == 0 ? &w : nullptr);
+}
+
+// The transposed smoothing step (fp64): the eta band sweeps first (on a
+// snapshot of the boundary values in bval, since no full sweep has just
+// written it), then the full sweep, all colours in the reverse order.
+void smooth_transposed(mg_ctx* c, Level& v) {
+  OpArgs<double> op = op_of<double>(v);
+  int& cur = v.cur64;
+  const int eta = c->stab.eta;
+  if (eta > 0 && v.n_band > 0) {
+    Launch k(c, MG_PROF_COARSE, 2);
+    launch_gather_bval<double>(v.L, v.bnode, v.n_bnd, v.u64[cur], v.bval64, c->st);
+    launch_band_rev<double>(op, v.band, v.n_band, v.nbx, eta, v.u64[cur], v.F64, v.bval64,
+                            v.band_off, v.band_ent, v.bmap[1], cur, c->d_err, c->wait_polls,
+                            c->st);
+  }
+  {
+    Launch k(c, MG_PROF_COARSE, v.n_active > 0);
+    launch_gs_sweep_rev<double>(op, v.active, v.n_active, v.u64[cur], v.u64[cur ^ 1], v.F64,
+                                nullptr, c->st);
+  }
+  cur ^= 1;
+}
+
+// The transposed V-cycle (fp64): a V-cycle is u <- u + B (F - A u); B^T
+// takes B's steps in the reverse order, each transposed: nu2 transposed
+// smoothing steps, restriction, the transposed cycle(s) on the coarse level,
+// prolongation, nu1 transposed smoothing steps (Sec. 3.2 with R = P^T,
+// Sec. 4.1, Sec. 5.3).  A is symmetric, so k of these from w = 0 applied to
+// dL/du give the gradient of k V-cycles from 0: the adjoint of the iteration.
+void vcycle_transposed(mg_ctx* c, int l, bool zero_init) {
+  Level& v = c->lev[l];
+  const int nlev = (int)c->lev.size();
+  if (l == c->tail_level) {
+    tail_cycle<double>(c, l, zero_init, true);
+    return;
+  }
+  if (l == nlev - 1) {
+    Launch k(c, MG_PROF_COARSE, 1);
+    launch_coarse_solve<double>(v.L, c->Ainv, v.F64, v.u64[0], c->st);
+    v.cur64 = 0;
+    return;
+  }
+  if (zero_init) cudaMemsetAsync(v.u64[v.cur64], 0, v.L.size() * sizeof(double), c->st);
+  for (int s = 0; s < c->stab.nu2; ++s) smooth_transposed(c, v);
+  Level& w = c->lev[l + 1];
+  OpArgs<double> op = op_of<double>(v);
+  {
+    Launch k(c, MG_PROF_COARSE, w.n_active > 0);
+    launch_resid_restrict<double>(op, v.u64[v.cur64], v.F64, w.L, w.active, w.n_active, w.F64,
+                                  nullptr, c->st);
+  }
+  const int gs = coarse_cycles(c, l);
+  for (int k = 0; k < gs; ++k) vcycle_transposed(c, l + 1, k == 0);
+  {
+    Launch k(c, MG_PROF_COARSE, v.n_active > 0);
+    launch_prolong<double>(op, v.active, v.n_active, v.u64[v.cur64], w.L, w.u64[w.cur64],
+                           c->st);
+  }
+  for (int s = 0; s < c->stab.nu1; ++s) smooth_transposed(c, v);
 }
 
 // ||F - A u||_inf of the fine level in fp64 (host value); optionally writes
@@ -533,9 +610,14 @@ int fine_residual(mg_ctx* c, double sigma, bool to_f32, double* rmax) {
   }
   MG_CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                               c->st));
+  // a kernel of the cycles that stopped on a device error (a bounded wait
+  // that ran out, a failed copy check) ends the solve at this check
+  unsigned* h_err = reinterpret_cast<unsigned*>(c->h_norms + 4);
+  MG_CUDA_TRY(cudaMemcpyAsync(h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
   MG_CUDA_TRY(cudaStreamSynchronize(c->st));
   if (c->prof) harvest(c);
   *rmax = c->h_norms[0];
+  if (*h_err) return sync_check(c);
   return MG_OK;
 }
 
@@ -565,8 +647,9 @@ void refinement_step(mg_ctx* c, double sigma, int inner) {
 // sigma r is scaled by a power of two sigma chosen from the predicted
 // residual, so the fp32 V-cycles work on O(1) values; the update divides by
 // the same sigma exactly.
-int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info, bool u_zero) {
-  const bool mixed = c->stab.precision == MG_MIXED;
+int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info, bool u_zero,
+               bool transposed = false) {
+  const bool mixed = c->stab.precision == MG_MIXED && !transposed;
   const bool adaptive = c->stab.inner == 0;
   double rmax;
   int cycles = 0, checks = 0, status = MG_OK;
@@ -589,6 +672,8 @@ int solve_loop(mg_ctx* c, double Fn, double tol, int max_cycles, mg_info* info, 
     if (cycles >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
     k = std::min(k, max_cycles - cycles);
     if (mixed) refinement_step(c, sigma, k);
+    else if (transposed)
+      for (int s = 0; s < k; ++s) vcycle_transposed(c, 0, false);
     else
       for (int s = 0; s < k; ++s) vcycle<double>(c, 0, false);
     cycles += k;
@@ -779,6 +864,60 @@ void mg_destroy(mg_handle c) {
   delete c;
 }
 
+// The global constant of Sec. 5.2, Lambda_max of the fine level's global
+// pencil (K, M) modulo constants, times h (cell units), on the GPU: per
+// cut-cell pencils, the pencil's rows, Lanczos with inner CG solves
+// (global.cu).  Work space is allocated here and released before return.
+static int global_constant(mg_ctx* c, Level& v, const uint8_t* nmask, double* ch) {
+  const int N = c->N;
+  const size_t m = (size_t)(N + 1) * (N + 1);
+  constexpr int kmax = 100, cg_max = 20000;
+  constexpr double cg_tol = 1e-13;
+  int blocks = 1;
+  MG_CUDA_TRY(lanczos_blocks(N, &blocks));
+  double *S = nullptr, *Kn = nullptr, *Mr = nullptr, *Kr = nullptr, *work = nullptr;
+  double* out = nullptr;
+  uint8_t* dof = nullptr;
+  std::vector<uint8_t> hdof(m);
+  double hout[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+  };
+  A((void**)&S, (size_t)v.n_cut * 16 * sizeof(double));
+  A((void**)&Kn, (size_t)v.n_cut * 16 * sizeof(double));
+  A((void**)&Mr, m * 9 * sizeof(double));
+  A((void**)&Kr, m * 9 * sizeof(double));
+  A((void**)&dof, m);
+  A((void**)&work, lanczos_doubles(N, kmax, blocks) * sizeof(double));
+  A((void**)&out, 4 * sizeof(double));
+  if (e == cudaSuccess) {
+    launch_cut_pencil(c->psi_s, N, v.cut_list, v.n_cut, nmask, S, Kn, c->st);
+    launch_pencil_rows(N, v.cls, v.cell_cut, S, Kn, Mr, Kr, dof, c->st);
+    e = cudaMemcpyAsync(hdof.data(), dof, m, cudaMemcpyDeviceToHost, c->st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  int ndof = 0;
+  for (uint8_t d : hdof) ndof += d != 0;
+  if (e == cudaSuccess && ndof > 0)
+    e = launch_lanczos(N, Mr, Kr, dof, ndof, work, kmax, cg_max, cg_tol, blocks, out, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hout, out, sizeof(hout), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  for (void* p : {(void*)S, (void*)Kn, (void*)Mr, (void*)Kr, (void*)dof, (void*)work, (void*)out})
+    if (p) cudaFree(p);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return MG_ERR_OUT_OF_MEMORY;
+  }
+  if (e != cudaSuccess) return mg_cuda_fail(e);
+  if (!(hout[0] > 0.0) || !std::isfinite(hout[0])) return MG_ERR_INTERNAL;
+  *ch = hout[0];
+  c->global_steps = (int)hout[1];
+  c->global_cg = (int)hout[2];
+  return MG_OK;
+}
+
 static int setup_impl(mg_ctx* c, const double* levelset) {
   const int N = c->N;
   MG_CUDA_TRY(cudaGetDevice(&c->device));
@@ -821,8 +960,16 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
       }
       TRY(dalloc(c, &c->Nk, (size_t)v.n_cut * 16));
     }
-    const double ch_global =
-        c->stab.lambda_mode == MG_LAMBDA_GLOBAL ? c->stab.c_global * c->h : -1.0;
+    double ch_global = -1.0;
+    if (c->stab.lambda_mode == MG_LAMBDA_GLOBAL) {
+      if (c->stab.c_global > 0.0) {
+        ch_global = c->stab.c_global * c->h;
+        c->c_global = c->stab.c_global;
+      } else {
+        TRY(global_constant(c, v, nmask, &ch_global));
+        c->c_global = ch_global / c->h;
+      }
+    }
     launch_cut_cells(c->psi_s, N, c->h, c->stab.gamma, v.cut_list, v.n_cut, v.Ke, c->Mk, c->Gk,
                      c->Cl, c->cfg, nmask, c->Nk, c->st, ch_global);
     TRY(build_nodes(c, v));
@@ -982,6 +1129,18 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
       v.fused_ok = true;
     }
   }
+  {
+    // region lists of the fp32 sweep on the levels that run it (the finest,
+    // and those above the tail without fused steps)
+    const int nlev = (int)c->lev.size();
+    const int end = c->tail_level >= 0 ? c->tail_level : nlev - 1;
+    for (int l = 0; l < end; ++l) {
+      Level& v = c->lev[l];
+      if (v.fused_ok || v.n_active == 0) continue;
+      TRY(build_region_lists(c, v, v.active, v.n_active, v.L.ntx, MG_TX, MG_TY, 4, &v.soff,
+                             &v.sent));
+    }
+  }
   TRY(sync_check(c));
   return MG_OK;
 }
@@ -1014,8 +1173,12 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
     return MG_ERR_INVALID_ARG;
   if (s.lambda_mode != MG_LAMBDA_LOCAL && s.lambda_mode != MG_LAMBDA_GLOBAL)
     return MG_ERR_INVALID_ARG;
-  if (s.lambda_mode == MG_LAMBDA_GLOBAL && !(s.c_global > 0.0 && std::isfinite(s.c_global)))
+  // c_global = 0: computed at setup (the global eigenvalue problem on the GPU)
+  if (s.lambda_mode == MG_LAMBDA_GLOBAL && !(s.c_global >= 0.0 && std::isfinite(s.c_global)))
     return MG_ERR_INVALID_ARG;
+  if (s.lambda_mode == MG_LAMBDA_GLOBAL && s.c_global == 0.0 &&
+      (g.n_cells > 1024 || (bc && bc->box_sides)))
+    return MG_ERR_UNIMPLEMENTED;
   // the global constant belongs to the fine grid; re-discretised coarse
   // levels would each need their own
   if (s.lambda_mode == MG_LAMBDA_GLOBAL && s.coarse_op == MG_COARSE_REDISCRETISE)
@@ -1046,6 +1209,20 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
   return MG_OK;
 }
 
+int mg_get_c_global(mg_handle c, double* c_global, int* lanczos_steps, int* cg_iterations) {
+  if (!c) return MG_ERR_INVALID_ARG;
+  if (c_global) *c_global = c->c_global;
+  if (lanczos_steps) *lanczos_steps = c->global_steps;
+  if (cg_iterations) *cg_iterations = c->global_cg;
+  return MG_OK;
+}
+
+int mg_set_wait_limit(mg_handle c, long long polls) {
+  if (!c || polls > 0xffffffffLL) return MG_ERR_INVALID_ARG;
+  c->wait_polls = polls < 0 ? kMbarSpinLimit : (unsigned)polls;
+  return MG_OK;
+}
+
 int mg_get_counts(mg_handle c, int* n_levels, int* n_dof, int* n_cut, int* n_boundary) {
   if (!c) return MG_ERR_INVALID_ARG;
   if (n_levels) *n_levels = (int)c->lev.size();
@@ -1058,6 +1235,11 @@ int mg_get_counts(mg_handle c, int* n_levels, int* n_dof, int* n_cut, int* n_bou
 int mg_level_cells(mg_handle c, int level) {
   if (!c || level < 0 || level >= (int)c->lev.size()) return -1;
   return c->lev[level].n;
+}
+
+int mg_level_dofs(mg_handle c, int level) {
+  if (!c || level < 0 || level >= (int)c->lev.size()) return -1;
+  return c->lev[level].n_dof;
 }
 
 static int fill_info(mg_ctx* c, mg_info* info) {
@@ -1203,6 +1385,22 @@ int mg_cycles(mg_handle c, const double* F, double* u, int k, int precision) {
       refinement_step(c, sigma, c->stab.inner > 0 ? c->stab.inner : 1);
     }
   }
+  double* ud = const_cast<double*>(su.dev);
+  launch_unpack(v.L, v.code, v.u64[v.cur64], ud, c->st);
+  if (su.host) TRY(finish_out(c, u, ud, true));
+  return sync_check(c);
+}
+
+int mg_cycles_transposed(mg_handle c, const double* F, double* u, int k) {
+  if (!c || !F || !u || k < 0) return MG_ERR_INVALID_ARG;
+  Level& v = c->lev[0];
+  Staged sF, su;
+  TRY(stage_in(c, 0, F, sF));
+  TRY(stage_in(c, 2, u, su));
+  launch_pack<double>(v.L, v.code, sF.dev, v.F64, c->d_err, c->st);
+  v.cur64 = 0;
+  launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st);
+  for (int s = 0; s < k; ++s) vcycle_transposed(c, 0, false);
   double* ud = const_cast<double*>(su.dev);
   launch_unpack(v.L, v.code, v.u64[v.cur64], ud, c->st);
   if (su.host) TRY(finish_out(c, u, ud, true));
@@ -1372,7 +1570,8 @@ int mg_adjoint_bc(mg_handle c, const double* dLdu, double* dLdf, double* dLdg, d
   TRY(fine_residual(c, 1.0, false, &Fn));     // ||dL/du||_inf on the DOFs (w = 0)
   int status = MG_OK;
   if (Fn > 0.0) {
-    status = solve_loop(c, Fn, tol, c->stab.max_cycles, nullptr, true);
+    // w by transposed fp64 V-cycles (whatever the handle's precision)
+    status = solve_loop(c, Fn, tol, c->stab.max_cycles, nullptr, true, true);
     if (status == MG_ERR_CUDA) return status;
   }
   const double* w = v.u64[v.cur64];
@@ -1583,6 +1782,7 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out, size_t win_bytes) {
   a.nu1 = c->stab.nu1;
   a.nu2 = c->stab.nu2;
   a.err = b->d_words + 1;
+  a.wait_polls = kMbarSpinLimit;
   q.tail_xy = xy[t];
   q.tail_n_active = top.n_active;
   q.tail_F = top.F32;

@@ -14,7 +14,8 @@
 // g[c] + nt (a colour with more nodes than threads) go through extra(e)
 // every phase.  Phases are separated by __syncwarp (nt == 32) or by named
 // barrier 1 over the nt threads.
-template <class T, class Stage, class Extra>
+// REV: the colours in the reverse order (the transposed sweep).
+template <class T, class Stage, class Extra, bool REV = false>
 __device__ __forceinline__ void band_phases_reg(T* sU, int RS, const int* g, int eta, int nt,
                                                 Stage stage, Extra extra) {
   T w[4][MG_ROW + 1];
@@ -33,7 +34,8 @@ __device__ __forceinline__ void band_phases_reg(T* sU, int RS, const int* g, int
   }
   for (int it = 0; it < eta; ++it) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int cc = 0; cc < 4; ++cc) {
+      const int c = REV ? 3 - cc : cc;
       if (has[c]) {
         const T* Up = sU + p[c];
         const T* W = w[c];
@@ -53,7 +55,7 @@ __device__ __forceinline__ void band_phases_reg(T* sU, int RS, const int* g, int
 // As band_phases_reg, but each thread keeps only the position, F and the
 // row index of its nodes (rows read from `rows`, normally shared memory):
 // for kernels whose register budget cannot hold four rows.  stage(e, r, f, p).
-template <class T, class Stage, class Extra>
+template <class T, class Stage, class Extra, bool REV = false>
 __device__ __forceinline__ void band_phases_idx(T* sU, int RS, const T* rows, const int* g,
                                                 int eta, int nt, Stage stage, Extra extra) {
   int r[4], p[4];
@@ -70,7 +72,8 @@ __device__ __forceinline__ void band_phases_idx(T* sU, int RS, const T* rows, co
   }
   for (int it = 0; it < eta; ++it) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int cc = 0; cc < 4; ++cc) {
+      const int c = REV ? 3 - cc : cc;
       if (p[c] >= 0) {
         const T* Up = sU + p[c];
         const T* W = rows + (size_t)r[c] * MG_ROW;

@@ -217,6 +217,8 @@ __device__ inline double c_triangle_h(double t1, double t2) {
 
 struct CellOut {
   double Ke[16], Gk[16], Mk[16], Nk[16];
+  double S[16];    // volume stiffness on K cap Omega_h (h-independent in 2D)
+  double Kn[16];   // int_{Gamma_h cap K} (n . grad phi_i)(n . grad phi_j), times h
   double C, lam;
   double area, length;
   int config;
@@ -230,7 +232,7 @@ __device__ inline void cut_cell_matrices(const double psi[4], double h, double g
   Geom g;
   build_geometry(psi, g);
   o.config = g.config;
-  double S[4][4] = {}, Mr[4][4] = {}, Ms[4][4] = {}, Bn[4][4] = {};
+  double S[4][4] = {}, Mr[4][4] = {}, Ms[4][4] = {}, Bn[4][4] = {}, Kn[4][4] = {};
   double M3[3][3] = {}, K3[3][3] = {};
   double gs[3], gw[3];
   gl3(gs, gw);
@@ -289,6 +291,7 @@ __device__ inline void cut_cell_matrices(const double psi[4], double h, double g
         for (int j = 0; j < 4; ++j) {
           Ms[i][j] += w * phi[i] * phi[j];
           Bn[i][j] += w * dn[j] * phi[i];
+          Kn[i][j] += w * dn[i] * dn[j];
         }
       double gb[3] = {nx, ny, (nx * (et - cb) + ny * (xi - ca)) / d};
       for (int i = 0; i < 3; ++i)
@@ -313,6 +316,8 @@ __device__ inline void cut_cell_matrices(const double psi[4], double h, double g
         o.Nk[i * 4 + j] = 0.0;
       }
       o.Mk[i * 4 + j] = h * h * Mr[i][j];
+      o.S[i * 4 + j] = S[i][j];
+      o.Kn[i * 4 + j] = neumann ? 0.0 : Kn[i][j];
     }
   // exact symmetry of Ke (the two halves are summed in different orders)
   for (int i = 0; i < 4; ++i)

@@ -39,9 +39,10 @@ __device__ __forceinline__ const T* row_of(const OpArgs<T>& op, int i, int j, in
 // MODE: kSweepPlain (u from uin), kSweepZero (u = 0: first pre-smoothing
 // step), kSweepProlong (u = uin + P e_2h: the prolongation of Sec. 5.1,
 // added while loading, with the same arithmetic as k_prolong).
-enum : int { kSweepPlain = 0, kSweepZero = 1, kSweepProlong = 2 };
 
-template <class T, int MODE>
+// REV: the colours in the reverse order (1,1), (0,1), (1,0), (0,0): the
+// transposed sweep of the transposed V-cycle.
+template <class T, int MODE, bool REV = false>
 __global__ void __launch_bounds__(kThreads)
 k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ uin,
            T* __restrict__ uout, const T* __restrict__ F, T* __restrict__ bval, Layout Lc,
@@ -115,7 +116,8 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
 
 #pragma unroll 1
   for (int k = 0; k < 4; ++k) {
-    const int ci = k & 1, cj = k >> 1;
+    const int col = REV ? 3 - k : k;
+    const int ci = col & 1, cj = col >> 1;
     T* P = sU + (cj * 2 + ci) * SW_PLANE;
     const T* PXn = sU + (cj * 2 + (ci ^ 1)) * SW_PLANE;
     const T* PYn = sU + ((cj ^ 1) * 2 + ci) * SW_PLANE;
@@ -191,12 +193,12 @@ __host__ __device__ inline int band_halo(int eta) { return 4 * eta + 1; }
 __host__ __device__ inline int band_region(int eta) { return 32 + 2 * band_halo(eta); }
 __host__ __device__ inline size_t band_a128(size_t b) { return (b + 127) & ~(size_t)127; }
 
-template <class T>
+template <class T, bool REV = false>
 __global__ void __launch_bounds__(kThreads)
 k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __restrict__ u,
        const T* __restrict__ F, const T* __restrict__ bval, const int* __restrict__ boff,
        const int2* __restrict__ bent, const __grid_constant__ BandMaps maps, int umap,
-       unsigned* err) {
+       unsigned* err, unsigned wait_polls) {
   griddep_launch_next();
   constexpr int EC = BandCap<T>::value;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
@@ -261,7 +263,7 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
     sS[MG_ROW * EC + e] = f;
     sS[(MG_ROW + 1) * EC + e] = bv;
   }
-  const bool ok = mbar_wait(&bar, 0);
+  const bool ok = mbar_wait(&bar, 0, wait_polls);
   if (__syncthreads_or(!ok || bad)) {
     if (threadIdx.x == 0 && !ok) {
       atomicOr(err, DEV_ERR_TIMEOUT);
@@ -314,7 +316,8 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
               w[8] * Up[RS + 1];
       sU[p] = Up[0] + (w[MG_ROW] - acc) * w[9];
     };
-    band_phases_reg<T>(sU, RS, g, eta, 32 * nw, fetch, extra);
+    band_phases_reg<T, decltype(fetch), decltype(extra), REV>(sU, RS, g, eta, 32 * nw, fetch,
+                                                               extra);
   }
   __syncthreads();
   // 4. owned listed nodes back to u
@@ -530,6 +533,19 @@ k_prolong(OpArgs<T> op, const int* __restrict__ tiles, T* __restrict__ uf, Layou
     else e = T(0.25) * ((E[0] + E[1]) + (E[Lc.pitch] + E[Lc.pitch + 1]));
     uf[op.L.idx(i, j)] = uu[b] + e;
   }
+}
+
+// bval[r] = u at boundary node r (bnode[r] = i | j << 16): the snapshot the
+// band kernel reads when no full sweep has just written it (transposed step)
+template <class T>
+__global__ void k_gather_bval(Layout L, const int* __restrict__ bnode, int nb,
+                              const T* __restrict__ u, T* __restrict__ bval) {
+  griddep_launch_next();
+  griddep_wait();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb) return;
+  const int p = bnode[r];
+  bval[r] = u[L.idx(p & 0xffff, p >> 16)];
 }
 
 template <class T>
@@ -805,9 +821,14 @@ cudaError_t configure_kernels(int eta) {
   e = cudaFuncSetAttribute(k_gs_sweep<T, kSweepProlong>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<T>());
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gs_sweep<T, kSweepPlain, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<T>());
+  if (e != cudaSuccess) return e;
   // the largest eta allowed by the ABI, so handles with different eta coexist
   (void)eta;
   e = raise_smem_limit(k_band<T>, (int)band_smem<T>(8));
+  if (e != cudaSuccess) return e;
+  e = raise_smem_limit(k_band<T, true>, (int)band_smem<T>(8));
   return e;
 }
 
@@ -816,10 +837,6 @@ void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T*
                      const T* F, T* bval, bool zero_in, const Layout* Lc, const T* ec,
                      cudaStream_t st) {
   if (!ntiles) return;
-  if constexpr (sizeof(T) == 4) {
-    launch_gs_sweep_f32(op, tiles, ntiles, uin, uout, F, bval, zero_in, Lc, ec, st);
-    return;
-  }
   const Layout L0 = Lc ? *Lc : op.L;
   if (ec)
     launch_pdl(k_gs_sweep<T, kSweepProlong>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles, uin,
@@ -833,12 +850,39 @@ void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T*
 }
 
 template <class T>
+void launch_gs_sweep_rev(const OpArgs<T>& op, const int* tiles, int ntiles, const T* uin,
+                         T* uout, const T* F, T* bval, cudaStream_t st) {
+  if (!ntiles) return;
+  launch_pdl(k_gs_sweep<T, kSweepPlain, true>, ntiles, kThreads, sweep_smem<T>(), st, op, tiles,
+             uin, uout, F, bval, op.L, (const T*)nullptr);
+}
+
+template <class T>
+void launch_gather_bval(const Layout& L, const int* bnode, int nb, const T* u, T* bval,
+                        cudaStream_t st) {
+  if (!nb) return;
+  launch_pdl(k_gather_bval<T>, (nb + kThreads - 1) / kThreads, kThreads, 0, st, L, bnode, nb, u,
+             bval);
+}
+
+template <class T>
+void launch_band_rev(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
+                     const T* F, const T* bval, const int* boff, const int2* bent,
+                     const BandMaps& maps, int umap, unsigned* err, unsigned wait_polls,
+                     cudaStream_t st) {
+  if (!nbt || eta <= 0) return;
+  launch_pdl(k_band<T, true>, nbt, kThreads, band_smem<T>(eta), st, op, btiles, nbx, eta, u, F,
+             bval, boff, bent, maps, umap, err, wait_polls);
+}
+
+template <class T>
 void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
                  const T* F, const T* bval, const int* boff, const int2* bent,
-                 const BandMaps& maps, int umap, unsigned* err, cudaStream_t st) {
+                 const BandMaps& maps, int umap, unsigned* err, unsigned wait_polls,
+                 cudaStream_t st) {
   if (!nbt || eta <= 0) return;
   launch_pdl(k_band<T>, nbt, kThreads, band_smem<T>(eta), st, op, btiles, nbx, eta, u, F, bval,
-             boff, bent, maps, umap, err);
+             boff, bent, maps, umap, err, wait_polls);
 }
 
 template <class T>
@@ -934,7 +978,7 @@ void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st) {
                                    bool, const Layout*, const T*, cudaStream_t);                 \
   template void launch_band<T>(const OpArgs<T>&, const int*, int, int, int, T*, const T*,        \
                                const T*, const int*, const int2*, const BandMaps&, int,          \
-                               unsigned*, cudaStream_t);                                         \
+                               unsigned*, unsigned, cudaStream_t);                               \
   template void launch_resid_restrict<T>(const OpArgs<T>&, const T*, const T*, const Layout&,    \
                                          const int*, int, T*, double*, cudaStream_t);            \
   template void launch_prolong<T>(const OpArgs<T>&, const int*, int, T*, const Layout&, const T*, \
@@ -946,6 +990,13 @@ void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st) {
 
 MG_INSTANTIATE(double)
 MG_INSTANTIATE(float)
+template void launch_gs_sweep_rev<double>(const OpArgs<double>&, const int*, int, const double*,
+                                          double*, const double*, double*, cudaStream_t);
+template void launch_gather_bval<double>(const Layout&, const int*, int, const double*, double*,
+                                         cudaStream_t);
+template void launch_band_rev<double>(const OpArgs<double>&, const int*, int, int, int, double*,
+                                      const double*, const double*, const int*, const int2*,
+                                      const BandMaps&, int, unsigned*, unsigned, cudaStream_t);
 template void launch_residual<double, float>(const OpArgs<double>&, const int*, int, const double*,
                                              const double*, float*, double, double*, cudaStream_t,
                                              bool);

@@ -38,20 +38,45 @@ template <class T> size_t sweep_smem();
 template <class T> size_t band_smem(int eta);
 template <class T> cudaError_t configure_kernels(int eta);
 
+// load modes of a sweep: u as stored, u = 0, u + P e_2h (Sec. 5.1)
+enum SweepMode : int { kSweepPlain = 0, kSweepZero = 1, kSweepProlong = 2 };
+
 template <class T>
 // One 4-colour sweep; ec != nullptr adds the prolongated coarse correction
-// P ec (coarse layout *Lc) to uin while loading.
+// P ec (coarse layout *Lc) to uin while loading.  (The fp32 sweep is
+// launch_gs_sweep_f32.)
 void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T* uin, T* uout,
                      const T* F, T* bval, bool zero_in, const Layout* Lc, const T* ec,
                      cudaStream_t st);
-// the fp32 instance of launch_gs_sweep (sweep32.cu)
+
+// The fp32 sweep (sweep32.cu): launch_gs_sweep's arguments plus the tiles'
+// region lists of boundary nodes (5 group offsets per listed tile, entries
+// {x | y << 16, row} in region coordinates of a 64 x 32 tile with a 4-node
+// halo; see build_region_lists).
 void launch_gs_sweep_f32(const OpArgs<float>& op, const int* tiles, int ntiles, const float* uin,
                          float* uout, const float* F, float* bval, bool zero_in,
-                         const Layout* Lc, const float* ec, cudaStream_t st);
+                         const Layout* Lc, const float* ec, const int* loff, const int2* lent,
+                         cudaStream_t st);
 template <class T>
 void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
                  const T* F, const T* bval, const int* boff, const int2* bent,
-                 const BandMaps& maps, int umap, unsigned* err, cudaStream_t st);
+                 const BandMaps& maps, int umap, unsigned* err, unsigned wait_polls,
+                 cudaStream_t st);
+// The transposed smoothing step's kernels (fp64; the transposed V-cycle of
+// the adjoint): a sweep with the colours in the reverse order, the snapshot
+// of the boundary values the band kernel reads (bnode[r] = i | j << 16), and
+// the band sweeps with the colours in the reverse order.
+template <class T>
+void launch_gs_sweep_rev(const OpArgs<T>& op, const int* tiles, int ntiles, const T* uin,
+                         T* uout, const T* F, T* bval, cudaStream_t st);
+template <class T>
+void launch_gather_bval(const Layout& L, const int* bnode, int nb, const T* u, T* bval,
+                        cudaStream_t st);
+template <class T>
+void launch_band_rev(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
+                     const T* F, const T* bval, const int* boff, const int2* bent,
+                     const BandMaps& maps, int umap, unsigned* err, unsigned wait_polls,
+                     cudaStream_t st);
 template <class T>
 void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const Layout& Lc,
                            const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st);

@@ -1,4 +1,5 @@
-// The fine-level fp32 Gauss-Seidel sweep, written for instruction economy.
+// The fp32 Gauss-Seidel sweep of the levels above the fused ones, written
+// for instruction economy.
 //
 // One 4-colour sweep (Sec. 4.1, colours (i mod 2, j mod 2) in the order
 // (0,0), (1,0), (0,1), (1,1)) of a 64 x 32 tile, recomputed on a 4-node halo
@@ -12,7 +13,11 @@
 //     and paired fp32 arithmetic (add/fma/mul .f32x2, each lane an ordinary
 //     IEEE fp32 operation, so results are bit for bit those of the scalar
 //     code), 384 threads so that each colour phase (19 rows of 18 pairs) is
-//     one pass of the block with no thread doing a second, and
+//     one pass of the block,
+//   * the region's boundary rows (cut-cell vertices) staged in shared memory
+//     from a setup-time list before the wait for the previous kernel, so the
+//     colour phases read no global memory: the list entry of each boundary
+//     node replaces its code in the code plane, and
 //   * the prolongation P e_2h (Sec. 5.1) added while loading, when asked.
 #include "cycle.cuh"
 
@@ -26,6 +31,8 @@ constexpr int PX = RX / 2, PY = RY / 2;    // parity plane 36 x 20
 constexpr int PL = PX * PY;
 constexpr int QX = RX / 4;                 // 16-byte groups per region row (18)
 constexpr int kLoadIt = (RY * QX + kT - 1) / kT;                  // 2
+constexpr int kRC = 384;                   // boundary rows staged in shared memory
+constexpr int kRS = MG_ROW + 1;            // odd stride: conflict-free row reads
 constexpr int kStoreIt = (MG_TY * (MG_TX / 4) + kT - 1) / kT;    // 2
 
 enum : int { kPlain = 0, kZero = 1, kProlong = 2 };
@@ -52,12 +59,23 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
   return as_f2(r);
 }
 
-// boundary row of node (i, j) with code cd >= 2, same arithmetic as k_gs_sweep
-__device__ __forceinline__ float boundary_update(const OpArgs<float>& op, int i, int j, int cd,
-                                                 float uc, float f, float w, float e, float s,
-                                                 float n, float sw, float se, float nw,
-                                                 float ne) {
-  const float* R = op.rows + (size_t)(op.tile_base[op.L.tile_of(i, j)] + cd - 2) * MG_ROW;
+// Row of list entry e of the region (code 2 + e in the code plane): staged
+// in shared memory for e < kRC, else from global memory.
+struct RowSrc {
+  const float* sRow;                       // kRC staged rows, stride kRS
+  const float* rows;                       // the level's boundary rows
+  const int2* ent;                         // the tile's list entries
+};
+__device__ __forceinline__ const float* row_ptr(const RowSrc& rs, int e) {
+  return e < kRC ? rs.sRow + e * kRS : rs.rows + (size_t)rs.ent[e].y * MG_ROW;
+}
+
+// boundary-row update of a node whose code is cd >= 2, same arithmetic as
+// k_gs_sweep
+__device__ __forceinline__ float boundary_update(const RowSrc& rs, int cd, float uc, float f,
+                                                 float w, float e, float s, float n, float sw,
+                                                 float se, float nw, float ne) {
+  const float* R = row_ptr(rs, cd - 2);
   float acc = R[0] * sw + R[1] * s + R[2] * se + R[3] * w + R[4] * uc + R[5] * e +
               R[6] * nw + R[7] * n + R[8] * ne;
   return uc + (f - acc) * R[9];
@@ -71,9 +89,8 @@ __device__ __forceinline__ float boundary_update(const OpArgs<float>& op, int i,
 // node per phase, so the owned tile is exact after the 4 phases.  The colour
 // is a template argument, so plane bases and neighbour offsets are constants.
 template <int CI, int CJ>
-__device__ __forceinline__ void colour_phase(const OpArgs<float>& op, float* sU,
-                                             const float* sF, const uint16_t* sC, int tb,
-                                             int ta, bool lane_on, int ri0, int rj0) {
+__device__ __forceinline__ void colour_phase(const RowSrc& rs, float* sU, const float* sF,
+                                             const uint16_t* sC, int tb, int ta, bool lane_on) {
   float* P = sU + (CJ * 2 + CI) * PL;
   const float* PXn = sU + (CJ * 2 + (CI ^ 1)) * PL;
   const float* PYn = sU + ((CJ ^ 1) * 2 + CI) * PL;
@@ -136,16 +153,13 @@ __device__ __forceinline__ void colour_phase(const OpArgs<float>& op, float* sU,
   }
   const uint32_t c0 = cc & 0xffffu, c1 = cc >> 16;
   const float2 uc = *reinterpret_cast<const float2*>(P + q);
-  const int rj = 2 * b + CJ;
   float r0 = uc.x, r1 = uc.y;
   if (c0 == 1u) r0 = in.x;
   else if (c0 >= 2u)
-    r0 = boundary_update(op, ri0 + 2 * a + CI, rj0 + rj, (int)c0, uc.x, f.x, W.x, E.x, S.x,
-                         N.x, SW.x, SE.x, NW.x, NE.x);
+    r0 = boundary_update(rs, (int)c0, uc.x, f.x, W.x, E.x, S.x, N.x, SW.x, SE.x, NW.x, NE.x);
   if (c1 == 1u) r1 = in.y;
   else if (c1 >= 2u)
-    r1 = boundary_update(op, ri0 + 2 * a + 2 + CI, rj0 + rj, (int)c1, uc.y, f.y, W.y, E.y,
-                         S.y, N.y, SW.y, SE.y, NW.y, NE.y);
+    r1 = boundary_update(rs, (int)c1, uc.y, f.y, W.y, E.y, S.y, N.y, SW.y, SE.y, NW.y, NE.y);
   *reinterpret_cast<float2*>(P + q) = make_float2(r0, r1);
 }
 
@@ -153,16 +167,34 @@ template <int MODE>
 __global__ void __launch_bounds__(kT)
 k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __restrict__ uin,
                float* __restrict__ uout, const float* __restrict__ F, float* __restrict__ bval,
-               Layout Lc, const float* __restrict__ ec) {
+               Layout Lc, const float* __restrict__ ec, const int* __restrict__ loff,
+               const int2* __restrict__ lent) {
   griddep_launch_next();
-  griddep_wait();
   __shared__ __align__(16) float sU[4 * PL];       // plane 2 (y parity) + (x parity)
   __shared__ __align__(16) float sF[4 * PL];
   __shared__ __align__(16) uint16_t sC[4 * PL];
+  __shared__ float sRow[kRC * kRS];
+  __shared__ int sGrow[kRC];                       // the staged entries' global rows
   const int t = tiles[blockIdx.x];
   const int i0 = (t % op.L.ntx) * MG_TX, j0 = (t / op.L.ntx) * MG_TY;
   const int ri0 = i0 - H, rj0 = j0 - H;            // both even
   const int n = op.L.n;
+  // 0. static data first (it may overlap the end of the previous kernel):
+  //    the region's boundary nodes (colour groups, not the rim) and their rows
+  const int e0 = loff[5 * blockIdx.x];
+  const int m = loff[5 * blockIdx.x + 4] - e0;
+  const RowSrc rs{sRow, op.rows, lent + e0};
+  for (int e = threadIdx.x; e < m && e < kRC; e += kT) {
+    const int2 en = lent[e0 + e];
+    const float* R = op.rows + (size_t)en.y * MG_ROW;
+    float v[MG_ROW];
+#pragma unroll
+    for (int k = 0; k < MG_ROW; ++k) v[k] = R[k];
+#pragma unroll
+    for (int k = 0; k < MG_ROW; ++k) sRow[e * kRS + k] = v[k];
+    sGrow[e] = en.y;
+  }
+  griddep_wait();
 
   // 1. region -> parity planes; item (rj, q) = nodes ri0 + 4q .. + 3 of row rj
   {
@@ -226,6 +258,13 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
     }
   }
   __syncthreads();
+  // each listed boundary node's code becomes 2 + its list entry
+  for (int e = threadIdx.x; e < m; e += kT) {
+    const int p = lent[e0 + e].x;
+    const int x = p & 0xffff, y = p >> 16;
+    sC[(y & 1) * 2 * PL + (x & 1) * PL + (y >> 1) * PX + (x >> 1)] = (uint16_t)(2 + e);
+  }
+  __syncthreads();
 
   // 2. the four colour phases, (0,0), (1,0), (0,1), (1,1)
   constexpr int kPairCols = PX / 2;                 // 18
@@ -234,17 +273,17 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
   const int tb = threadIdx.x / kPairCols;
   const int ta = 2 * (threadIdx.x - tb * kPairCols);
   const bool lane_on = tb < kRowStep;
-  colour_phase<0, 0>(op, sU, sF, sC, tb, ta, lane_on, ri0, rj0);
+  colour_phase<0, 0>(rs, sU, sF, sC, tb, ta, lane_on);
   __syncthreads();
-  colour_phase<1, 0>(op, sU, sF, sC, tb, ta, lane_on, ri0, rj0);
+  colour_phase<1, 0>(rs, sU, sF, sC, tb, ta, lane_on);
   __syncthreads();
-  colour_phase<0, 1>(op, sU, sF, sC, tb, ta, lane_on, ri0, rj0);
+  colour_phase<0, 1>(rs, sU, sF, sC, tb, ta, lane_on);
   __syncthreads();
-  colour_phase<1, 1>(op, sU, sF, sC, tb, ta, lane_on, ri0, rj0);
+  colour_phase<1, 1>(rs, sU, sF, sC, tb, ta, lane_on);
   __syncthreads();
 
-  // 3. owned tile out (16-byte stores), boundary values to bval
-  const int base = bval ? op.tile_base[t] : 0;
+  // 3. owned tile out (16-byte stores), boundary values to bval (the global
+  //    row of the node's list entry)
 #pragma unroll
   for (int k = 0; k < kStoreIt; ++k) {
     const int it = threadIdx.x + k * kT;
@@ -262,8 +301,11 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
       const uint32_t c[4] = {ce & 0xffffu, co & 0xffffu, ce >> 16, co >> 16};
       const float v[4] = {ve.x, vo.x, ve.y, vo.y};
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
-        if (c[m] >= 2u) bval[base + (int)c[m] - 2] = v[m];
+      for (int k2 = 0; k2 < 4; ++k2)
+        if (c[k2] >= 2u) {
+          const int e = (int)c[k2] - 2;
+          bval[e < kRC ? sGrow[e] : lent[e0 + e].y] = v[k2];
+        }
     }
   }
 }
@@ -272,13 +314,17 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
 
 void launch_gs_sweep_f32(const OpArgs<float>& op, const int* tiles, int ntiles, const float* uin,
                          float* uout, const float* F, float* bval, bool zero_in,
-                         const Layout* Lc, const float* ec, cudaStream_t st) {
+                         const Layout* Lc, const float* ec, const int* loff, const int2* lent,
+                         cudaStream_t st) {
   if (!ntiles) return;
   const Layout L0 = Lc ? *Lc : op.L;
   if (ec)
-    launch_pdl(k_gs_sweep_f32<kProlong>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec);
+    launch_pdl(k_gs_sweep_f32<kProlong>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec,
+               loff, lent);
   else if (zero_in)
-    launch_pdl(k_gs_sweep_f32<kZero>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec);
+    launch_pdl(k_gs_sweep_f32<kZero>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec,
+               loff, lent);
   else
-    launch_pdl(k_gs_sweep_f32<kPlain>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec);
+    launch_pdl(k_gs_sweep_f32<kPlain>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec,
+               loff, lent);
 }

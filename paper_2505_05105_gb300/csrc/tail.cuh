@@ -46,6 +46,8 @@ template <class T> struct TailArgs {
   int load_u0;
   int eta, nu1, nu2;
   unsigned* err;                              // DEV_ERR_TIMEOUT if the image copy stalls
+  unsigned wait_polls = kMbarSpinLimit;       // poll budget of the image copy's wait
+  int transposed = 0;                         // run the transposed V-cycle
 };
 
 // Device arrays a level contributes to the image.

@@ -121,6 +121,41 @@ __device__ void smooth(const TailArgs<T>& a, const Smem<T>& s, int k) {
   __syncthreads();
 }
 
+// the transposed smoothing step (transposed V-cycle): the eta sweeps over
+// the cut-cell vertices first, then the full sweep, all colours in the
+// reverse order
+template <class T>
+__device__ void smooth_transposed(const TailArgs<T>& a, const Smem<T>& s, int k) {
+  const Lvl<T> v = level(s, k);
+  if (a.eta > 0) {
+    int mc = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) mc = max(mc, v.o[c + 1] - v.o[c]);
+    const int nw = min((int)(blockDim.x >> 5), max(1, (mc + 31) / 32));
+    if ((int)(threadIdx.x >> 5) < nw) {
+      auto fetch = [&](int e, int& r, T& f, int& p) {
+        const int q = v.BL[e];
+        r = v.G[q];
+        f = v.F[q];
+        p = q;
+      };
+      auto extra = [&](int e) {
+        const int q = v.BL[e];
+        const T* w = v.rows + (size_t)v.G[q] * MG_ROW;
+        const T* Up = v.U + q;
+        const int S = v.S;
+        T acc = w[0] * Up[-S - 1] + w[1] * Up[-S] + w[2] * Up[-S + 1] + w[3] * Up[-1] +
+                w[4] * Up[0] + w[5] * Up[1] + w[6] * Up[S - 1] + w[7] * Up[S] + w[8] * Up[S + 1];
+        v.U[q] = Up[0] + (v.F[q] - acc) * w[9];
+      };
+      band_phases_idx<T, decltype(fetch), decltype(extra), true>(v.U, v.S, v.rows, v.o, a.eta,
+                                                                 32 * nw, fetch, extra);
+    }
+    __syncthreads();
+  }
+  for (int c = 3; c >= 0; --c) colour_phase(v, c, false);
+}
+
 template <class T>
 __device__ void residual_restrict(const Smem<T>& s, int k) {
   const Lvl<T> v = level(s, k);
@@ -281,7 +316,7 @@ __device__ void tail_vcycle(const TailArgs<T>& a, unsigned char* smem_raw, bool 
       }
     }
   }
-  const bool ok = mbar_wait(&bar, 0);
+  const bool ok = mbar_wait(&bar, 0, a.wait_polls);
   if (__syncthreads_or(!ok || bad)) {
     if (threadIdx.x == 0 && !ok) {
       atomicOr(a.err, DEV_ERR_TIMEOUT);
@@ -291,14 +326,28 @@ __device__ void tail_vcycle(const TailArgs<T>& a, unsigned char* smem_raw, bool 
     return;
   }
   if (threadIdx.x == 0) mbar_inval(&bar);
-  for (int k = 0; k + 1 < K; ++k) {
-    for (int r = 0; r < a.nu1; ++r) smooth(a, s, k);
-    residual_restrict(s, k);
-  }
-  coarsest(s, K - 1);
-  for (int k = K - 2; k >= 0; --k) {
-    prolong(s, k);
-    for (int r = 0; r < a.nu2; ++r) smooth(a, s, k);
+  if (!a.transposed) {
+    for (int k = 0; k + 1 < K; ++k) {
+      for (int r = 0; r < a.nu1; ++r) smooth(a, s, k);
+      residual_restrict(s, k);
+    }
+    coarsest(s, K - 1);
+    for (int k = K - 2; k >= 0; --k) {
+      prolong(s, k);
+      for (int r = 0; r < a.nu2; ++r) smooth(a, s, k);
+    }
+  } else {
+    // the transposed cycle: the same steps in the reverse order, each
+    // transposed (nu2 transposed steps down, nu1 up)
+    for (int k = 0; k + 1 < K; ++k) {
+      for (int r = 0; r < a.nu2; ++r) smooth_transposed(a, s, k);
+      residual_restrict(s, k);
+    }
+    coarsest(s, K - 1);
+    for (int k = K - 2; k >= 0; --k) {
+      prolong(s, k);
+      for (int r = 0; r < a.nu1; ++r) smooth_transposed(a, s, k);
+    }
   }
   const int n = lay.n[0], S = n + 3;
   for (int p = threadIdx.x; p < (n + 1) * (n + 1); p += blockDim.x) {

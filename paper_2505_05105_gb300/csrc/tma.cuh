@@ -10,8 +10,10 @@
 // kTmaAlign elements (8, i.e. 16 bytes for 16-bit data, 32 bytes for fp32)
 // and indexes shared memory from the remainder.
 //
-// Waits are bounded: after kMbarSpinLimit polls the waiting thread sets
-// DEV_ERR_TIMEOUT and the kernel returns without using the data.
+// Waits are bounded: after a poll budget (kMbarSpinLimit unless the handle
+// sets another, mg_set_wait_limit) the waiting thread sets DEV_ERR_TIMEOUT,
+// waits once more with the default budget for its copies still in flight,
+// and the kernel returns without using the data.
 #pragma once
 
 #include <cuda.h>
@@ -59,10 +61,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
-// true once the barrier completed phase `parity`; false after the spin limit
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// true once the barrier completed phase `parity`; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned limit = kMbarSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (unsigned it = 0; it < kMbarSpinLimit; ++it) {
+  for (unsigned it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

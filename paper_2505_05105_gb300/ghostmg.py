@@ -102,14 +102,18 @@ SIGNATURES = {
     "mg_adjoint_bc": (_I, [_P, _P, _P, _P, _P]),
     "mg_destroy": (None, [_P]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
+    "mg_get_c_global": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mg_set_wait_limit": (_I, [_P, ctypes.c_longlong]),
     "mg_get_counts": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                            ctypes.POINTER(_I)]),
     "mg_level_cells": (_I, [_P, _I]),
+    "mg_level_dofs": (_I, [_P, _I]),
     "mg_export_stencil": (_I, [_P, _I, _P]),
     "mg_export_cut_cells": (_I, [_P, _I, _P, _P, ctypes.POINTER(_I)]),
     "mg_rhs": (_I, [_P, _P, _P, _P]),
     "mg_rhs_bc": (_I, [_P, _P, _P, _P, _P]),
     "mg_cycles": (_I, [_P, _P, _P, _I, _I]),
+    "mg_cycles_transposed": (_I, [_P, _P, _P, _I]),
     "mg_residual": (_I, [_P, _P, _P, _P, _P]),
     "mg_residual_static": (_I, [_P, _P, _P, _P, _P]),
     "mg_set_profiling": (_I, [_P, _I]),
@@ -129,7 +133,8 @@ SIGNATURES = {
     "mg1d_cycles": (_I, [_I, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
 }
 
-PROF_SLOTS = ("sweep", "band", "restrict", "prolong", "residual", "update", "coarse", "io")
+PROF_SLOTS = ("sweep", "band", "restrict", "prolong", "residual", "update", "coarse", "io",
+              "levels", "fused", "tail")
 
 _lib = None
 
@@ -237,6 +242,19 @@ def mg_strerror(code: int) -> str:
     return load().mg_strerror(code).decode()
 
 
+def mg_get_c_global(handle: int):
+    """(c_global, Lanczos steps, CG iterations) of the handle (see the header)."""
+    c, st, it = _D(), _I(), _I()
+    _check(load().mg_get_c_global(handle, ctypes.byref(c), ctypes.byref(st), ctypes.byref(it)),
+           "mg_get_c_global")
+    return c.value, st.value, it.value
+
+
+def mg_set_wait_limit(handle: int, polls: int) -> int:
+    """Poll budget of the handle's bounded device waits (< 0: default)."""
+    return _check(load().mg_set_wait_limit(handle, int(polls)), "mg_set_wait_limit")
+
+
 def mg_get_counts(handle: int):
     vals = [_I() for _ in range(4)]
     _check(load().mg_get_counts(handle, *[ctypes.byref(v) for v in vals]), "mg_get_counts")
@@ -245,6 +263,10 @@ def mg_get_counts(handle: int):
 
 def mg_level_cells(handle: int, level: int) -> int:
     return load().mg_level_cells(handle, level)
+
+
+def mg_level_dofs(handle: int, level: int) -> int:
+    return load().mg_level_dofs(handle, level)
 
 
 def mg_export_stencil(handle: int, level: int, out) -> int:
@@ -264,6 +286,11 @@ def mg_rhs(handle: int, f, g, F) -> int:
 
 def mg_cycles(handle: int, F, u, k: int, precision: int = MG_FP64) -> int:
     return _check(load().mg_cycles(handle, _addr(F), _addr(u, True), k, precision), "mg_cycles")
+
+
+def mg_cycles_transposed(handle: int, F, u, k: int) -> int:
+    return _check(load().mg_cycles_transposed(handle, _addr(F), _addr(u, True), k),
+                  "mg_cycles_transposed")
 
 
 def mg_residual(handle: int, F, u, r=None):
@@ -393,7 +420,8 @@ class Solver:
         or a device tensor), nonzero where a cut cell's boundary piece is
         Neumann (MG_BC_MIXED); None: all Dirichlet.
         c_global: the global constant C of Sec. 5.2 (MG_LAMBDA_GLOBAL:
-        lambda = gamma c_global on every cut cell); None: local lambda_K.
+        lambda = gamma c_global on every cut cell); 0: computed by mg_setup
+        on the GPU; None: local lambda_K.
         fuse_max_tiles: mg_stab.fuse_max_tiles (0 default, -1 never fused)."""
         self.N = n_cells
         stab = mg_default_stab()
@@ -449,6 +477,10 @@ class Solver:
 
     def cycles(self, F, u, k: int, precision: str = "fp64"):
         mg_cycles(self.handle, F, u, k, {"fp64": MG_FP64, "mixed": MG_MIXED}[precision])
+        return u
+
+    def cycles_transposed(self, F, u, k: int):
+        mg_cycles_transposed(self.handle, F, u, k)
         return u
 
     def residual(self, F, u, r=None):

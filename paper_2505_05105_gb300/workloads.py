@@ -92,6 +92,15 @@ def flower(N: int = 256, k: int = 5, phase: float = 0.0,
                    meta={"k": k, "phase": phase})
 
 
+def adjoint_target(p: Problem, seed: int) -> np.ndarray:
+    """The adjoint workload's target u_t: the flower's manufactured solution
+    sin 3x cos 2y with seeded phases (nodal, (N+1)^2)."""
+    rng = np.random.default_rng(seed)
+    a, b = rng.uniform(0, 2 * np.pi, 2)
+    x, y = node_grid(p.N, p.x0, p.y0, p.h)
+    return np.sin(3 * x + a) * np.cos(2 * y + b)
+
+
 def fourier_source(X, Y, rng, modes: int = 8):
     """f = sum_m c_m sin(pi (p_m x + q_m y) + phi_m), c ~ N(0,1), p,q in 1..4."""
     c = rng.standard_normal(modes)

@@ -2,7 +2,8 @@
 
 A is symmetric (Sec. 4.1) and F = M f + G g is linear in f and g (Eq.
 disc_rhs), so for a loss L(u): w solves A w = dL/du, dL/df = M^T w and
-dL/dg = G^T w.  Checked against
+dL/dg = G^T w; mg_adjoint solves for w with the transposed V-cycle (held
+to the oracle's transposed cycle iterate by iterate below).  Checked against
   * the oracle's dense adjoint (direct solve, exact to fp64) at small N,
   * central differences of the GPU's own forward solves on the adjoint
     configuration (flower 512^2, loss 1/2 sum over internal nodes of
@@ -50,9 +51,10 @@ def test_adjoint_matches_oracle(name, precision):
     dLdu = rng.standard_normal(s.n_nodes)
     ref_f, ref_g = gf.adjoint(s, dLdu)
     S = G.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h, precision=precision)
-    # the adjoint solves to the last solve's tolerance
+    # the adjoint solves to the last solve's tolerance (1e-12: above the
+    # rounding floor of the unscaled right-hand side dL/du, ~2e-13 here)
     u = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
-    S.solve(dev(p.f), dev(p.g), u, tol=1e-13)
+    S.solve(dev(p.f), dev(p.g), u, tol=1e-12)
     dLdf = torch.zeros_like(u)
     dLdg = torch.zeros_like(u)
     S.adjoint(dev(dLdu), dLdf, dLdg)
@@ -64,6 +66,42 @@ def test_adjoint_matches_oracle(name, precision):
     S.adjoint(dLdu, None, gh)
     assert np.abs(gh - ref_g).max() <= 1e-9 * np.abs(ref_g).max()
     S.close()
+
+
+@pytest.mark.parametrize("name", ["circle64", "flower128", "discs256", "flower512"])
+def test_transposed_cycle_iterates(name):
+    """The transposed V-cycle mg_adjoint solves with (mg_cycles_transposed,
+    fp64) against the oracle's mg_cycle_transposed, whose operator is pinned
+    to be B^T (tests/test_oracle_multigrid.py): iterates after k = 1..3
+    cycles node by node, at the fp64 iterate bound of the forward cycle
+    (1e-10 max|w| + (64 k eps + ROW_REL) S_p), from w = 0 with a random
+    right-hand side on the DOFs (an adjoint dL/du has no smoothness)."""
+    from oracle import multigrid as mg
+    from paper_2505_05105_gb300 import ghostmg as G
+    from parity_tol import assert_nodewise, node_tolerance
+    p = {"circle64": lambda: wl.circle64(64), "flower128": lambda: wl.flower(128),
+         "discs256": lambda: wl.three_discs(256, seed=0),
+         "flower512": lambda: wl.flower(512, k=7, phase=0.3)}[name]()
+    s = gf.assemble_problem(p)
+    lev = mg.build_hierarchy(s)
+    d = np.random.default_rng(8).standard_normal(s.n_nodes) * s.dof
+    w_ref = np.zeros(s.n_nodes)
+    with G.Solver(dev(p.psi), p.N, p.x0, p.y0, p.h) as S:
+        w = torch.zeros(s.n_nodes, dtype=torch.float64, device="cuda")
+        dd = dev(d)
+        for k in range(1, 4):
+            w_ref = mg.mg_cycle_transposed(lev, 0, w_ref, d, nu1=2, nu2=1, eta=4)
+            S.cycles_transposed(dd, w, 1)
+            torch.cuda.synchronize()
+            assert_nodewise(host(w), w_ref, node_tolerance(s, d, w_ref, 1e-10, 64 * k),
+                            (name, k))
+        # and the bound tells the cycles apart: one forward cycle misses the
+        # transposed one by over 100 times the bound (1e3-1e5 measured)
+        u = torch.zeros_like(w)
+        S.cycles(dd, u, 1)
+        w1 = mg.mg_cycle_transposed(lev, 0, np.zeros(s.n_nodes), d, nu1=2, nu2=1, eta=4)
+        tol1 = node_tolerance(s, d, w1, 1e-10, 64)
+        assert (np.abs(host(u) - w1) / tol1)[s.dof].max() > 100
 
 
 def test_adjoint_rejects_bad_input():
@@ -88,10 +126,7 @@ def test_adjoint_rejects_bad_input():
 
 def target(p, seed):
     """u_t: the flower's manufactured solution sin 3x cos 2y with seeded phases."""
-    rng = np.random.default_rng(seed)
-    a, b = rng.uniform(0, 2 * np.pi, 2)
-    x, y = wl.node_grid(p.N, p.x0, p.y0, p.h)
-    return np.sin(3 * x + a) * np.cos(2 * y + b)
+    return wl.adjoint_target(p, seed)
 
 
 def test_adjoint_central_differences_flower512():

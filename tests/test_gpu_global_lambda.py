@@ -1,7 +1,8 @@
 """The global stabilisation parameter of Sec. 5.2 on the GPU
 (stab.lambda_mode = MG_LAMBDA_GLOBAL, lambda = gamma c_global on every cut
-cell), with c_global the oracle's largest generalized eigenvalue of the
-global pencil (a setup-time value the caller supplies).
+cell), with c_global the largest generalized eigenvalue of the global
+pencil: the oracle's value passed in, or (c_global = 0) computed by
+mg_setup on the GPU and held to the oracle's.
 
 * Cut-cell lambda and Ke, and the operator rows of every level, against the
   oracle assembled with the same c_global (1e-13, as tests/test_gpu_parity.py;
@@ -125,10 +126,40 @@ def test_rho_global_vs_local(name):
     assert got_g > 1.5 * got_l
 
 
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_computed_global_constant(name):
+    """c_global = 0: mg_setup solves the global eigenvalue problem itself
+    (Lanczos on M'^{-1} K with CG solves, global.cu); the value equals the
+    oracle's dense generalized eigenvalue (oracle.ghostfem.global_C, pinned
+    in tests/test_oracle_global_lambda.py) to 1e-8, and the handle it makes
+    contracts like one given the oracle's value (rho to 1e-6)."""
+    from paper_2505_05105_gb300 import ghostmg as G
+    p, C, s, lev = setup(name)
+    with solver(p, c_global=0.0) as S:
+        c, steps, cg_it = G.mg_get_c_global(S.handle)
+        cells, data = S.cut_cells()
+    print(f"{name}: computed C_global h = {c * p.h:.12f} (oracle {C * p.h:.12f}), "
+          f"{steps} Lanczos steps, {cg_it} CG iterations")
+    assert c == pytest.approx(C, rel=1e-8)
+    assert 0 < steps <= 100 and cg_it > 0
+    # every cut cell got lambda = gamma c
+    assert np.allclose(data[:, 1], 2.0 * c, rtol=1e-15, atol=0)
+    ref_g, _ = mg.convergence_factor(lev, cycles=30, first=21)
+    assert abs(gpu_rho(p, s.dof, c_global=0.0) - ref_g) <= 1e-6
+    # a given value is reported back as given; local handles report 0
+    with solver(p, c_global=C) as S:
+        assert G.mg_get_c_global(S.handle) == (C, 0, 0)
+    with solver(p) as S:
+        assert G.mg_get_c_global(S.handle)[0] == 0.0
+
+
 def test_refused_values():
     from paper_2505_05105_gb300 import ghostmg as G
     p = wl.circle64(64)
-    for bad in (0.0, -1.0, float("nan"), float("inf")):
+    with pytest.raises(G.GhostMGError) as e:
+        solver(p, c_global=0.0, box_sides=True)
+    assert e.value.code == G.MG_ERR_UNIMPLEMENTED
+    for bad in (-1.0, float("nan"), float("inf")):
         with pytest.raises(G.GhostMGError) as e:
             solver(p, c_global=bad)
         assert e.value.code == G.MG_ERR_INVALID_ARG
