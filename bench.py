@@ -108,26 +108,24 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# source file of each fine-level kernel class
-KERNEL_SOURCE = {"sweep": "sweep32.cu", "restrict": "cycle.cu", "prolong": "cycle.cu",
-                 "residual": "cycle.cu", "update": "cycle.cu", "batch": "batch.cu"}
-
-
-def profile_traffic(kernel_tag, kind):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source has not changed since it was captured."""
+def profile_traffic(kernel_tag, kind=None):
+    """DRAM bytes per launch from the committed ncu summary
+    profiles/<kernel_tag>.md, if every source file it lists still has the
+    hash recorded there (a change to any of them voids the figure)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    src = os.path.join(ROOT, "paper_2505_05105_gb300", "csrc", KERNEL_SOURCE.get(kind, "cycle.cu"))
     try:
         txt = open(path).read()
-        want = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+        srcs = re.findall(r"source: `([^`]+)`\s*\n\s*source_sha256:\s*([0-9a-f]{64})", txt)
         t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-        if m and t and m.group(1) == want:
-            return float(t.group(1))
+        if not srcs or not t:
+            return None
+        for rel, want in srcs:
+            got = hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()
+            if got != want:
+                return None
+        return float(t.group(1))
     except Exception:
-        pass
-    return None
+        return None
 
 
 class ClockSampler:

@@ -159,9 +159,9 @@ typedef struct {
  *                 the same either way): a level with at most this many
  *                 active 64 x 32-node tiles runs each smoothing step as one
  *                 fused kernel, a larger one runs the separate sweep, extra
- *                 sweep, restriction and prolongation kernels.  0 = twice
- *                 the device's SM count; -1 = never fused; >= -1 otherwise
- *                 (MG_ERR_INVALID_ARG). */
+ *                 sweep, restriction and prolongation kernels.  0 = the
+ *                 device's SM count (one wave of the fused kernel); -1 =
+ *                 never fused; >= -1 otherwise (MG_ERR_INVALID_ARG). */
 typedef struct {
   double gamma, alpha;
   int eta, nu1, nu2;
