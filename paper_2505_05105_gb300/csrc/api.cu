@@ -49,6 +49,15 @@ struct Level {
   // the fp32 sweep's region lists (active tiles, 4-node halo)
   int* soff = nullptr;
   int2* sent = nullptr;
+  // per block, whether its input region holds a boundary node that the band
+  // kernel launched directly before it writes (launch_touch_flags): the
+  // sweep's region (after this level's band kernel), the coarse nodes the
+  // prolongating sweep reads (after the next coarser level's band kernel),
+  // the residual + restriction region (after this level's band kernel)
+  uint8_t* sw_touch = nullptr;
+  uint8_t* pl_touch = nullptr;
+  uint8_t* rr_touch = nullptr;
+  unsigned long long band_seq = 0;  // launch number of this level's last band kernel
   int nbx = 0;
   int n_dof = 0;
   int n_rtiles = 0;
@@ -114,6 +123,9 @@ struct mg_ctx {
   // profiling: device time per kernel class between event pairs
   bool prof = false;
   long long launches = 0;
+  // kernel launches through Launch so far, never reset: a band kernel's
+  // launch number tells whether it is the launch directly before another
+  unsigned long long seq = 1;
   struct Pend { int cls; cudaEvent_t a, b; };
   std::vector<Pend> pend;
   std::vector<cudaEvent_t> evpool;
@@ -209,6 +221,7 @@ struct Launch {
   cudaEvent_t a = nullptr;
   Launch(mg_ctx* ctx, int k, int nk) : c(ctx), cls(k) {
     c->launches += nk;
+    if (nk) c->seq += 1;
     if (c->prof) {
       a = ev_get(c);
       cudaEventRecord(a, c->st);
@@ -373,12 +386,22 @@ void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine, Level* coarse = nullpt
   OpArgs<T> op = op_of<T>(v);
   int& cur = P<T>::cur(v);
   const int eta = c->stab.eta;
+  // directly after a band kernel that writes what this sweep reads (this
+  // level's, or the coarser level's when prolongating), blocks away from the
+  // boundary need not wait for it
+  const uint8_t* touch = nullptr;
+  if (coarse) {
+    if (coarse->band_seq == c->seq) touch = v.pl_touch;
+  } else if (!zero_in && v.band_seq == c->seq) {
+    touch = v.sw_touch;
+  }
   {
     Launch k(c, fine ? MG_PROF_SWEEP : MG_PROF_LEVELS, v.n_active > 0);
     if constexpr (sizeof(T) == 4) {
       launch_gs_sweep_f32(op, v.active, v.n_active, v.u32[cur], v.u32[cur ^ 1], v.F32,
                           eta > 0 ? v.bval32 : nullptr, zero_in, coarse ? &coarse->L : nullptr,
-                          coarse ? coarse->u32[coarse->cur32] : nullptr, v.soff, v.sent, c->st);
+                          coarse ? coarse->u32[coarse->cur32] : nullptr, v.soff, v.sent, touch,
+                          c->st);
     } else {
       launch_gs_sweep<T>(op, v.active, v.n_active, P<T>::u(v, cur), P<T>::u(v, cur ^ 1),
                          P<T>::F(v), eta > 0 ? P<T>::bval(v) : (T*)nullptr, zero_in,
@@ -393,6 +416,7 @@ void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine, Level* coarse = nullpt
     launch_band<T>(op, v.band, v.n_band, v.nbx, eta, P<T>::u(v, cur), P<T>::F(v), P<T>::bval(v),
                    v.band_off, v.band_ent, v.bmap[sizeof(T) == 8 ? 1 : 0], cur, c->d_err,
                    c->wait_polls, c->st);
+    v.band_seq = c->seq;
   }
 }
 
@@ -516,9 +540,10 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
   Level& w = c->lev[l + 1];
   OpArgs<T> op = op_of<T>(v);
   {
+    const uint8_t* touch = v.band_seq == c->seq ? v.rr_touch : nullptr;
     Launch k(c, fine ? MG_PROF_RESTRICT : MG_PROF_LEVELS, w.n_active > 0);
     launch_resid_restrict<T>(op, P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
-                             P<T>::F(w), nullptr, c->st);
+                             P<T>::F(w), nullptr, c->st, touch);
   }
   // gamma* cycles on the coarse level (Alg. 1: 1 V, 2 W), the first from zero
   const int gs = coarse_cycles(c, l);
@@ -1141,6 +1166,26 @@ static int setup_impl(mg_ctx* c, const double* levelset) {
       if (v.fused_ok || v.n_active == 0) continue;
       TRY(build_region_lists(c, v, v.active, v.n_active, v.L.ntx, MG_TX, MG_TY, 4, &v.soff,
                              &v.sent));
+    }
+    // which blocks of the kernels after a band kernel may start before it
+    // ends (levels whose smoothing runs the separate kernels)
+    for (int l = 0; l < end && c->stab.eta > 0; ++l) {
+      Level& v = c->lev[l];
+      if (v.fused_ok || v.n_active == 0) continue;
+      TRY(dalloc(c, &v.sw_touch, (size_t)v.n_active));
+      launch_touch_flags(TOUCH_SWEEP, v.L, v.code, v.active, v.L.ntx, v.n_active, v.sw_touch,
+                         c->st);
+      if (l + 1 < nlev) {
+        Level& w = c->lev[l + 1];
+        TRY(dalloc(c, &v.pl_touch, (size_t)v.n_active));
+        launch_touch_flags(TOUCH_PROLONG, w.L, w.code, v.active, v.L.ntx, v.n_active, v.pl_touch,
+                           c->st);
+        if (w.n_active > 0) {
+          TRY(dalloc(c, &v.rr_touch, 4 * (size_t)w.n_active));
+          launch_touch_flags(TOUCH_RESTRICT, v.L, v.code, w.active, w.L.ntx, 4 * w.n_active,
+                             v.rr_touch, c->st);
+        }
+      }
     }
   }
   TRY(sync_check(c));

@@ -125,6 +125,15 @@ __device__ __forceinline__ void block_norms_to_global(double vmax, double vsum, 
 // writes (u, F, bval, e, norms) and every global write comes after it.  The
 // wait returns once the previous kernel has completed and its writes are
 // visible (immediately when launched without the attribute).
+//
+// One exception: the band kernel (eta sweeps over the cut-cell vertices)
+// lets its dependents launch only after its own wait, so when it starts the
+// kernel after it, every kernel before the band kernel has completed.  A
+// block of that next kernel whose input region holds none of the nodes the
+// band kernel writes may then skip the wait (band_independent below); it
+// reads through L2 (ld.global.cg), never from a possibly stale L1 line.  At
+// least one block of such a launch always waits, so the launch completes
+// only after the band kernel.
 __device__ __forceinline__ void griddep_wait() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
@@ -132,6 +141,12 @@ __device__ __forceinline__ void griddep_wait() {
 // started (it still waits in griddep_wait for this kernel to complete).
 __device__ __forceinline__ void griddep_launch_next() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// touch: per block, nonzero when the block's input region holds a node the
+// directly preceding band kernel writes; nullptr when the launch does not
+// directly follow a band kernel (every block waits).  Block 0 always waits.
+__device__ __forceinline__ bool band_independent(const uint8_t* touch) {
+  return touch != nullptr && blockIdx.x != 0 && touch[blockIdx.x] == 0;
 }
 
 template <typename... KArgs, typename... Args>

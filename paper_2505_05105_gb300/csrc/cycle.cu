@@ -185,21 +185,24 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
 //      named barrier),
 //   4. writes the owned listed nodes back.
 template <class T> struct BandCap;
-template <> struct BandCap<float> { static constexpr int value = 512; };
+template <> struct BandCap<float> { static constexpr int value = 384; };
 template <> struct BandCap<double> { static constexpr int value = 256; };
 constexpr int kBandNS = MG_ROW + 2;    // staged per node: row, F, bval
+// 4 warps: the colour phases need at most a few (a 66 x 66 region holds a few
+// hundred boundary nodes), and small blocks let every band tile of a
+// 4096^2 level be resident at once (one wave)
+constexpr int kBandThreads = 128;
 
-__host__ __device__ inline int band_halo(int eta) { return 4 * eta + 1; }
-__host__ __device__ inline int band_region(int eta) { return 32 + 2 * band_halo(eta); }
+__host__ __device__ constexpr int band_halo(int eta) { return 4 * eta + 1; }
+__host__ __device__ constexpr int band_region(int eta) { return 32 + 2 * band_halo(eta); }
 __host__ __device__ inline size_t band_a128(size_t b) { return (b + 127) & ~(size_t)127; }
 
 template <class T, bool REV = false>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kBandThreads)
 k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __restrict__ u,
        const T* __restrict__ F, const T* __restrict__ bval, const int* __restrict__ boff,
        const int2* __restrict__ bent, const __grid_constant__ BandMaps maps, int umap,
        unsigned* err, unsigned wait_polls) {
-  griddep_launch_next();
   constexpr int EC = BandCap<T>::value;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem_raw = smem_align128(smem_dyn);
@@ -245,6 +248,9 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
   }
   __syncthreads();
   griddep_wait();
+  // dependents launch only now: when the next kernel starts, everything
+  // before this one has completed (see band_independent)
+  griddep_launch_next();
   if (threadIdx.x == 0) {
     if (!bad) {
       mbar_arrive_expect_tx(&bar, (uint32_t)((size_t)RS * RB * sizeof(T)));
@@ -358,9 +364,10 @@ constexpr int RR_X = 68, RR_Y = 36;   // region of a 64 x 32 fine block with 2-n
 template <class T, bool NORM>
 __global__ void __launch_bounds__(kThreads)
 k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F, Layout Lc,
-                 const int* __restrict__ ctiles, T* __restrict__ Fc, double* __restrict__ norms) {
+                 const int* __restrict__ ctiles, T* __restrict__ Fc, double* __restrict__ norms,
+                 const uint8_t* __restrict__ touch) {
   griddep_launch_next();
-  griddep_wait();
+  if (!band_independent(touch)) griddep_wait();
   typedef typename Vec2<T>::type T2;
   __shared__ __align__(16) T sU[RR_Y * RR_X];
   __shared__ __align__(16) T sR[RR_Y * RR_X];
@@ -380,7 +387,7 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
         int it = it0 + b * blockDim.x;
         int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
         size_t g = it < RR_Y * (RR_X / 2) ? op.L.idx(fi0 + 2 * a, fj0 + rj) : op.L.idx(0, 0);
-        u2[b] = *reinterpret_cast<const T2*>(u + g);
+        u2[b] = __ldcg(reinterpret_cast<const T2*>(u + g));
         c2[b] = *reinterpret_cast<const uint32_t*>(op.code + g);
       }
 #pragma unroll
@@ -404,7 +411,7 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
     T r = T(0);
     if (cd) {
       int gi = fi0 + ri, gj = fj0 + rj;
-      r = node_residual<T, RR_X>(op, sU + p, cd, F[op.L.idx(gi, gj)], gi, gj);
+      r = node_residual<T, RR_X>(op, sU + p, cd, __ldcg(F + op.L.idx(gi, gj)), gi, gj);
     }
     sR[p] = r;
     if (NORM && ri >= 2 && ri < RR_X - 2 && rj >= 2 && rj < RR_Y - 2) {
@@ -424,6 +431,52 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
     Fc[Lc.idx(I, J)] = rc;
   }
   if (NORM) block_norms_to_global(vmax, vsum, norms);
+}
+
+// One flag per block of a later launch: does the block's input region hold a
+// boundary node (code >= 2) of the level with layout L?  The regions are
+// those of k_gs_sweep_f32 (64 x 32 tile, 4-node halo), of the coarse nodes
+// its prolongation reads, and of k_resid_restrict (RR_X x RR_Y).  The
+// prolongation window is a superset: a flag set without need only makes a
+// block wait.
+__global__ void k_touch_flags(int mode, Layout L, const uint16_t* __restrict__ code,
+                              const int* __restrict__ tiles, int tpr, uint8_t* __restrict__ flag) {
+  __shared__ int any;
+  const int b = blockIdx.x;
+  int x0, y0, w, h;
+  if (mode == TOUCH_RESTRICT) {
+    const int t = tiles[b >> 2], sub = b & 3;
+    const int I0 = (t % tpr) * MG_TX + (sub & 1) * 32, J0 = (t / tpr) * MG_TY + (sub >> 1) * 16;
+    x0 = 2 * I0 - 2;
+    y0 = 2 * J0 - 2;
+    w = RR_X;
+    h = RR_Y;
+  } else {
+    const int t = tiles[b];
+    const int ri0 = (t % tpr) * MG_TX - 4, rj0 = (t / tpr) * MG_TY - 4;
+    if (mode == TOUCH_SWEEP) {
+      x0 = ri0;
+      y0 = rj0;
+      w = MG_TX + 8;
+      h = MG_TY + 8;
+    } else {
+      // fine nodes gi in [ri0, ri0 + MG_TX + 8) read coarse nodes gi / 2 .. gi / 2 + 2
+      x0 = (ri0 >> 1) - 1;
+      y0 = (rj0 >> 1) - 1;
+      w = (MG_TX + 8) / 2 + 4;
+      h = (MG_TY + 8) / 2 + 4;
+    }
+  }
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int hit = 0;
+  for (int p = threadIdx.x; p < w * h; p += blockDim.x) {
+    const int gi = x0 + p % w, gj = y0 + p / w;
+    if (gi >= 0 && gj >= 0 && gi <= L.n && gj <= L.n && code[L.idx(gi, gj)] >= 2) hit = 1;
+  }
+  if (hit) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) flag[b] = (uint8_t)any;
 }
 
 template <class T, class TR>
@@ -449,7 +502,7 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
         int it = it0 + b * blockDim.x;
         int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
         size_t g = it < RR_Y * (RR_X / 2) ? op.L.idx(fi0 + 2 * a, fj0 + rj) : op.L.idx(0, 0);
-        u2[b] = *reinterpret_cast<const T2*>(u + g);
+        u2[b] = __ldcg(reinterpret_cast<const T2*>(u + g));
         c2[b] = *reinterpret_cast<const uint32_t*>(op.code + g);
       }
 #pragma unroll
@@ -871,7 +924,7 @@ void launch_band_rev(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, i
                      const BandMaps& maps, int umap, unsigned* err, unsigned wait_polls,
                      cudaStream_t st) {
   if (!nbt || eta <= 0) return;
-  launch_pdl(k_band<T, true>, nbt, kThreads, band_smem<T>(eta), st, op, btiles, nbx, eta, u, F,
+  launch_pdl(k_band<T, true>, nbt, kBandThreads, band_smem<T>(eta), st, op, btiles, nbx, eta, u, F,
              bval, boff, bent, maps, umap, err, wait_polls);
 }
 
@@ -881,19 +934,26 @@ void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int e
                  const BandMaps& maps, int umap, unsigned* err, unsigned wait_polls,
                  cudaStream_t st) {
   if (!nbt || eta <= 0) return;
-  launch_pdl(k_band<T>, nbt, kThreads, band_smem<T>(eta), st, op, btiles, nbx, eta, u, F, bval,
+  launch_pdl(k_band<T>, nbt, kBandThreads, band_smem<T>(eta), st, op, btiles, nbx, eta, u, F, bval,
              boff, bent, maps, umap, err, wait_polls);
 }
 
 template <class T>
 void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const Layout& Lc,
-                           const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st) {
+                           const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st,
+                           const uint8_t* touch) {
   if (!nct) return;
   if (norms)
-    launch_pdl(k_resid_restrict<T, true>, nct * 4, kThreads, 0, st, op, u, F, Lc, ctiles, Fc, norms);
+    launch_pdl(k_resid_restrict<T, true>, nct * 4, kThreads, 0, st, op, u, F, Lc, ctiles, Fc, norms,
+               touch);
   else
     launch_pdl(k_resid_restrict<T, false>, nct * 4, kThreads, 0, st, op, u, F, Lc, ctiles, Fc,
-               norms);
+               norms, touch);
+}
+
+void launch_touch_flags(int mode, const Layout& L, const uint16_t* code, const int* tiles,
+                        int tpr, int nblocks, uint8_t* flag, cudaStream_t st) {
+  if (nblocks > 0) k_touch_flags<<<nblocks, kThreads, 0, st>>>(mode, L, code, tiles, tpr, flag);
 }
 
 template <class T, class TR>
@@ -980,7 +1040,8 @@ void launch_export_stencil(const OpArgs<T>& op, double* out, cudaStream_t st) {
                                const T*, const int*, const int2*, const BandMaps&, int,          \
                                unsigned*, unsigned, cudaStream_t);                               \
   template void launch_resid_restrict<T>(const OpArgs<T>&, const T*, const T*, const Layout&,    \
-                                         const int*, int, T*, double*, cudaStream_t);            \
+                                         const int*, int, T*, double*, cudaStream_t,             \
+                                         const uint8_t*);                                        \
   template void launch_prolong<T>(const OpArgs<T>&, const int*, int, T*, const Layout&, const T*, \
                                   cudaStream_t);                                                 \
   template void launch_coarse_solve<T>(const Layout&, const double*, const T*, T*, cudaStream_t); \

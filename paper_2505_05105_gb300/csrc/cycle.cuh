@@ -52,11 +52,14 @@ void launch_gs_sweep(const OpArgs<T>& op, const int* tiles, int ntiles, const T*
 // The fp32 sweep (sweep32.cu): launch_gs_sweep's arguments plus the tiles'
 // region lists of boundary nodes (5 group offsets per listed tile, entries
 // {x | y << 16, row} in region coordinates of a 64 x 32 tile with a 4-node
-// halo; see build_region_lists).
+// halo; see build_region_lists).  touch (or nullptr): per tile of the list,
+// whether its region holds a node the directly preceding band kernel writes
+// (launch_touch_flags, TOUCH_SWEEP; TOUCH_PROLONG when ec is given); blocks
+// of untouched tiles skip the wait for that kernel.
 void launch_gs_sweep_f32(const OpArgs<float>& op, const int* tiles, int ntiles, const float* uin,
                          float* uout, const float* F, float* bval, bool zero_in,
                          const Layout* Lc, const float* ec, const int* loff, const int2* lent,
-                         cudaStream_t st);
+                         const uint8_t* touch, cudaStream_t st);
 template <class T>
 void launch_band(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, int eta, T* u,
                  const T* F, const T* bval, const int* boff, const int2* bent,
@@ -77,9 +80,23 @@ void launch_band_rev(const OpArgs<T>& op, const int* btiles, int nbt, int nbx, i
                      const T* F, const T* bval, const int* boff, const int2* bent,
                      const BandMaps& maps, int umap, unsigned* err, unsigned wait_polls,
                      cudaStream_t st);
+// touch (or nullptr): per block (4 per coarse tile), whether its fine
+// region holds a node the directly preceding band kernel writes
+// (launch_touch_flags, TOUCH_RESTRICT).
 template <class T>
 void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const Layout& Lc,
-                           const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st);
+                           const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st,
+                           const uint8_t* touch = nullptr);
+// Which blocks of a later launch read a boundary node (code >= 2) of the
+// level with layout L and codes `code`, one flag per block:
+//   TOUCH_SWEEP    tiles of L (ntx tpr), the fp32 sweep's region (4-node halo);
+//   TOUCH_PROLONG  tiles of the next finer level (tpr its ntx), the coarse
+//                  nodes of L that the prolongating sweep's region reads;
+//   TOUCH_RESTRICT 4 blocks per coarse tile (tpr the coarse ntx), the fine
+//                  region of L that a residual + restriction block reads.
+enum TouchMode : int { TOUCH_SWEEP = 0, TOUCH_PROLONG = 1, TOUCH_RESTRICT = 2 };
+void launch_touch_flags(int mode, const Layout& L, const uint16_t* code, const int* tiles,
+                        int tpr, int nblocks, uint8_t* flag, cudaStream_t st);
 template <class T, class TR>
 // norms[0] gets max |r| (atomic max); with l2 norms[1] gets sum r^2
 void launch_residual(const OpArgs<T>& op, const int* tiles, int ntiles, const T* u, const T* F,

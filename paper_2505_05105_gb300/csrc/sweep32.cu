@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kT)
 k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __restrict__ uin,
                float* __restrict__ uout, const float* __restrict__ F, float* __restrict__ bval,
                Layout Lc, const float* __restrict__ ec, const int* __restrict__ loff,
-               const int2* __restrict__ lent) {
+               const int2* __restrict__ lent, const uint8_t* __restrict__ touch) {
   griddep_launch_next();
   __shared__ __align__(16) float sU[4 * PL];       // plane 2 (y parity) + (x parity)
   __shared__ __align__(16) float sF[4 * PL];
@@ -194,7 +194,7 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
     for (int k = 0; k < MG_ROW; ++k) sRow[e * kRS + k] = v[k];
     sGrow[e] = en.y;
   }
-  griddep_wait();
+  if (!band_independent(touch)) griddep_wait();
 
   // 1. region -> parity planes; item (rj, q) = nodes ri0 + 4q .. + 3 of row rj
   {
@@ -207,22 +207,22 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
       const bool ok = it < RY * QX;
       const int rj = it / QX, q = it - rj * QX;
       const size_t g = ok ? op.L.idx(ri0 + 4 * q, rj0 + rj) : op.L.idx(0, 0);
-      f4[k] = *reinterpret_cast<const float4*>(F + g);
+      f4[k] = __ldcg(reinterpret_cast<const float4*>(F + g));
       u4[k] = MODE == kZero ? make_float4(0.f, 0.f, 0.f, 0.f)
-                            : *reinterpret_cast<const float4*>(uin + g);
+                            : __ldcg(reinterpret_cast<const float4*>(uin + g));
       c4[k] = *reinterpret_cast<const uint2*>(op.code + g);
       if (MODE == kProlong) {
         // coarse nodes I .. I+2 of row J (and J+1 for odd j), I = gi / 2
         const int gi = ri0 + 4 * q, gj = rj0 + rj;
         const bool in = ok && gi >= 0 && gj >= 0 && gi <= n && gj <= n;
         const float* E = ec + (in ? Lc.idx(gi >> 1, gj >> 1) : Lc.idx(0, 0));
-        e0[k] = E[0];
-        e1[k] = E[1];
-        e2[k] = E[2];
+        e0[k] = __ldcg(E);
+        e1[k] = __ldcg(E + 1);
+        e2[k] = __ldcg(E + 2);
         const bool odd = gj & 1;
-        g0[k] = odd ? E[Lc.pitch] : 0.f;
-        g1[k] = odd ? E[Lc.pitch + 1] : 0.f;
-        g2[k] = odd ? E[Lc.pitch + 2] : 0.f;
+        g0[k] = odd ? __ldcg(E + Lc.pitch) : 0.f;
+        g1[k] = odd ? __ldcg(E + Lc.pitch + 1) : 0.f;
+        g2[k] = odd ? __ldcg(E + Lc.pitch + 2) : 0.f;
       }
     }
 #pragma unroll
@@ -315,16 +315,16 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
 void launch_gs_sweep_f32(const OpArgs<float>& op, const int* tiles, int ntiles, const float* uin,
                          float* uout, const float* F, float* bval, bool zero_in,
                          const Layout* Lc, const float* ec, const int* loff, const int2* lent,
-                         cudaStream_t st) {
+                         const uint8_t* touch, cudaStream_t st) {
   if (!ntiles) return;
   const Layout L0 = Lc ? *Lc : op.L;
   if (ec)
     launch_pdl(k_gs_sweep_f32<kProlong>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec,
-               loff, lent);
+               loff, lent, touch);
   else if (zero_in)
     launch_pdl(k_gs_sweep_f32<kZero>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec,
-               loff, lent);
+               loff, lent, (const uint8_t*)nullptr);
   else
     launch_pdl(k_gs_sweep_f32<kPlain>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec,
-               loff, lent);
+               loff, lent, touch);
 }

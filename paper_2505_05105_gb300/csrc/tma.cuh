@@ -26,7 +26,7 @@ constexpr unsigned kMbarSpinLimit = 1u << 22;
 // region's offset inside the box
 __host__ __device__ inline int tma_floor(int xs) { return xs & ~(kTmaAlign - 1); }
 // box width covering a region of w columns at any offset 0..kTmaAlign-1
-__host__ __device__ inline int tma_box_w(int w) {
+__host__ __device__ constexpr int tma_box_w(int w) {
   return (w + kTmaAlign - 1 + kTmaAlign - 1) / kTmaAlign * kTmaAlign;
 }
 
