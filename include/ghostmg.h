@@ -274,6 +274,17 @@ const char* mg_strerror(int code);
  * be NULL. */
 int mg_get_c_global(mg_handle h, double* c_global, int* lanczos_steps, int* cg_iterations);
 
+/* The bounds-checked debug build (a library variant compiled with
+ * -DMG_CHECK_BOUNDS; not a part of the method).  Its kernels check every
+ * node index, boundary-row index and boundary-list position where it is
+ * formed; a failed check sets a per-device word and the access is redirected
+ * inside its array (no fault), and every call that synchronizes then returns
+ * MG_ERR_INTERNAL.  *enabled = 1 in that build, 0 in the normal one (where
+ * *hits is always 0).  *hits: nonzero when a check failed on the current
+ * device since the last reset; reset != 0 clears it.  Synchronizes the
+ * current device.  Any output may be NULL.  Errors: MG_ERR_CUDA. */
+int mg_bounds_check(int* enabled, unsigned* hits, int reset);
+
 /* Poll budget of the handle's bounded device waits (the completion waits of
  * the shared-memory tensor and bulk copies; not a part of the method).
  * Every such wait gives up after `polls` polls of its mbarrier (polls < 0:

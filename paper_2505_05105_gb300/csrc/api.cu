@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -173,6 +174,43 @@ bool is_device_ptr(const void* p) {
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// --- bounds-checked build ------------------------------------------------------
+
+#ifdef MG_CHECK_BOUNDS
+constexpr bool kBoundsChecked = true;
+#else
+constexpr bool kBoundsChecked = false;
+#endif
+constexpr int kMaxDevices = 64;
+std::mutex g_bounds_mu;
+unsigned* g_bounds_word[kMaxDevices] = {};
+
+// The current device's bounds-check word, allocated and bound to every
+// translation unit on first use (checked builds; nullptr otherwise or on a
+// CUDA error).
+unsigned* bounds_word() {
+  if (!kBoundsChecked) return nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_bounds_mu);
+  if (!g_bounds_word[dev]) {
+    unsigned* w = nullptr;
+    if (cudaMalloc(&w, sizeof(unsigned)) != cudaSuccess) return nullptr;
+    cudaError_t (*const bind[])(unsigned*) = {
+        bind_bounds_api,   bind_bounds_batch, bind_bounds_cycle,   bind_bounds_fused,
+        bind_bounds_global, bind_bounds_noalloc, bind_bounds_oned, bind_bounds_scan,
+        bind_bounds_setup, bind_bounds_sweep32, bind_bounds_tail,  bind_bounds_tma};
+    bool ok = cudaMemset(w, 0, sizeof(unsigned)) == cudaSuccess;
+    for (auto f : bind) ok = ok && f(w) == cudaSuccess;
+    if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
+      cudaFree(w);
+      return nullptr;
+    }
+    g_bounds_word[dev] = w;
+  }
+  return g_bounds_word[dev];
+}
+
 int sync_check(mg_ctx* c) {
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return mg_cuda_fail(e);
@@ -188,6 +226,15 @@ int sync_check(mg_ctx* c) {
     if (err & (DEV_ERR_NAN | DEV_ERR_EDGE)) return MG_ERR_INVALID_ARG;
     if (err & DEV_ERR_TIMEOUT) return MG_ERR_TIMEOUT;
     return MG_ERR_INTERNAL;
+  }
+  if (kBoundsChecked) {
+    // a failed index check in any kernel of this device (the word stays
+    // set until mg_bounds_check resets it)
+    unsigned* w = bounds_word();
+    unsigned hits = 0;
+    if (!w || cudaMemcpy(&hits, w, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return MG_ERR_CUDA;
+    if (hits) return MG_ERR_INTERNAL;
   }
   return MG_OK;
 }
@@ -376,6 +423,7 @@ OpArgs<T> op_of(Level& v) {
   o.code = v.code;
   o.tile_base = v.tile_base;
   o.rows = P<T>::rows(v);
+  o.n_rows = v.n_bnd;
   return o;
 }
 
@@ -471,6 +519,7 @@ void fused_cycle(mg_ctx* c, int l, bool zero_init) {
   a.code = v.code;
   a.tile_base = v.tile_base;
   a.rows = P<T>::rows(v);
+  a.n_rows = v.n_bnd;
   a.loff = v.foff;
   a.lent = v.fent;
   a.eta = c->stab.eta;
@@ -1236,6 +1285,7 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
   if (s.coarse_op == MG_COARSE_REDISCRETISE && bc && bc->kind == MG_BC_MIXED)
     return MG_ERR_UNIMPLEMENTED;
   if (s.precision != MG_FP64 && s.precision != MG_MIXED) return MG_ERR_INVALID_ARG;
+  if (kBoundsChecked && !bounds_word()) return MG_ERR_CUDA;
   mg_ctx* c = new mg_ctx();
   c->st = (cudaStream_t)cuda_stream;
   c->grid = g;
@@ -1253,6 +1303,20 @@ int mg_setup(mg_handle* out, const double* levelset, const mg_grid* grid, const 
   }
   c->setup_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = c;
+  return MG_OK;
+}
+
+int mg_bounds_check(int* enabled, unsigned* hits, int reset) {
+  if (enabled) *enabled = kBoundsChecked ? 1 : 0;
+  if (hits) *hits = 0;
+  if (!kBoundsChecked) return MG_OK;
+  unsigned* w = bounds_word();
+  if (!w) return MG_ERR_CUDA;
+  MG_CUDA_TRY(cudaDeviceSynchronize());
+  unsigned v = 0;
+  MG_CUDA_TRY(cudaMemcpy(&v, w, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (hits) *hits = v;
+  if (reset) MG_CUDA_TRY(cudaMemset(w, 0, sizeof(unsigned)));
   return MG_OK;
 }
 
@@ -1551,6 +1615,7 @@ int mg_internal_fine_view(mg_handle c, FineOpView* out) {
   out->code = v.code;
   out->tile_base = v.tile_base;
   out->rows64 = v.rows64;
+  out->n_rows = v.n_bnd;
   out->active = v.active;
   out->n_active = v.n_active;
   out->N = c->N;
@@ -2112,6 +2177,7 @@ int mg_batch_setup(mg_batch* out, int count, const mg_grid* grids, const double*
   // one global constant per geometry would need a per-member value
   if (s.lambda_mode != MG_LAMBDA_LOCAL)
     return s.lambda_mode == MG_LAMBDA_GLOBAL ? MG_ERR_UNIMPLEMENTED : MG_ERR_INVALID_ARG;
+  if (kBoundsChecked && !bounds_word()) return MG_ERR_CUDA;
   mg_batch_ctx* b = new mg_batch_ctx();
   b->user_st = (cudaStream_t)cuda_stream;
   b->count = count;
@@ -2280,3 +2346,6 @@ void mg_batch_destroy(mg_batch b) {
 }
 
 }  // extern "C"
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_api)

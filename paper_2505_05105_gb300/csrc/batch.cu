@@ -837,3 +837,6 @@ void launch_batch_lists(const Layout& L, const uint16_t* code, const int* tile_b
                         int2* blist, int* boff, cudaStream_t st) {
   k_batch_lists<<<1, 1024, 0, st>>>(L, code, tile_base, blist, boff);
 }
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_batch)

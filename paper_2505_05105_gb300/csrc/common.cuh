@@ -36,6 +36,50 @@ enum : unsigned {
   DEV_ERR_ALIGN = 64u,       // a TMA / bulk copy operand failed its alignment check
 };
 
+// Bounds-checked build (compiled with -DMG_CHECK_BOUNDS, a debug variant of
+// the library): node indices (Layout::idx), boundary-row indices and the
+// region positions of the boundary-node lists are checked where they are
+// formed.  A failed check sets a device word (one per device, bound to every
+// translation unit by the MG_BOUNDS_BINDER function it defines) and redirects
+// the access to element 0 of its array, so the kernel reads and writes only
+// inside its allocations and finishes; the host reports the word as
+// MG_ERR_INTERNAL (mg_bounds_check).  In the normal build the checks compile
+// to nothing.
+#ifdef MG_CHECK_BOUNDS
+static __constant__ unsigned* c_bounds_word;
+__device__ __forceinline__ bool mg_checked(bool ok) {
+  if (!ok && c_bounds_word) atomicOr(c_bounds_word, 1u);
+  return ok;
+}
+#define MG_CHECKED(cond) mg_checked(cond)
+#define MG_BOUNDS_BINDER(name)                                                        \
+  cudaError_t name(unsigned* word) {                                                  \
+    return cudaMemcpyToSymbol(c_bounds_word, &word, sizeof(word));                    \
+  }
+#else
+#define MG_CHECKED(cond) true
+#define MG_BOUNDS_BINDER(name)                                                        \
+  cudaError_t name(unsigned*) { return cudaSuccess; }
+#endif
+// a boundary-row index r of a table of n rows (0 when out of range, checked
+// builds only)
+__device__ __forceinline__ int checked_row(int r, int n) {
+  (void)n;
+  return MG_CHECKED(r >= 0 && r < n) ? r : 0;
+}
+// region position {x, y} of a boundary-node list entry {x | y << 16, row}
+// of an RX x RY region; `inner`: a colour-group entry, which the phases
+// update and whose stencil must stay inside (checked builds only: (1, 1)
+// when out of range)
+__device__ __forceinline__ int2 region_pos(int2 en, bool inner, int RX, int RY) {
+  int x = en.x & 0xffff, y = en.x >> 16;
+  (void)inner; (void)RX; (void)RY;
+  if (!MG_CHECKED(x < RX && y < RY &&
+                  (!inner || (x >= 1 && y >= 1 && x < RX - 1 && y < RY - 1))))
+    x = y = 1;
+  return make_int2(x, y);
+}
+
 struct Layout {
   int n;       // cells per side
   int ntx;     // tiles along x covering nodes 0..n
@@ -43,6 +87,9 @@ struct Layout {
   int pitch;   // elements per padded row
   int rows;    // padded rows
   __host__ __device__ __forceinline__ size_t idx(int i, int j) const {
+#if defined(MG_CHECK_BOUNDS) && defined(__CUDA_ARCH__)
+    if (!MG_CHECKED(i >= -MG_G && j >= -MG_G && i + MG_G < pitch && j + MG_G < rows)) return 0;
+#endif
     return (size_t)(j + MG_G) * (size_t)pitch + (size_t)(i + MG_G);
   }
   __host__ __device__ __forceinline__ size_t size() const {

@@ -32,7 +32,9 @@ constexpr int kThreads = 256;
 
 template <class T>
 __device__ __forceinline__ const T* row_of(const OpArgs<T>& op, int i, int j, int cd) {
-  int r = op.tile_base[op.L.tile_of(i, j)] + cd - 2;
+  int t = op.L.tile_of(i, j);
+  if (!MG_CHECKED(t >= 0 && t < op.L.ntx * op.L.nty)) t = 0;
+  const int r = checked_row(op.tile_base[t] + cd - 2, op.n_rows);
   return op.rows + (size_t)r * MG_ROW;
 }
 
@@ -164,8 +166,8 @@ k_gs_sweep(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ ui
     *reinterpret_cast<T2*>(uout + op.L.idx(i0 + 2 * a2, j0 + rr)) = v;
     if (bval) {
       uint16_t c0 = sC[pl], c1 = sC[pl + SW_PLANE];
-      if (c0 >= 2) bval[base + c0 - 2] = v.x;
-      if (c1 >= 2) bval[base + c1 - 2] = v.y;
+      if (c0 >= 2) bval[checked_row(base + c0 - 2, op.n_rows)] = v.x;
+      if (c1 >= 2) bval[checked_row(base + c1 - 2, op.n_rows)] = v.y;
     }
   }
 }
@@ -232,10 +234,11 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
   //     for the previous kernel
   for (int e = threadIdx.x; e < m && e < EC; e += blockDim.x) {
     const int2 en = bent[e0 + e];
-    const int x = en.x & 0xffff, y = en.x >> 16;
+    const int2 xy = region_pos(en, e < nrim0, RB, RB);
+    const int x = xy.x, y = xy.y;
     T v[MG_ROW];
     if (e < nrim0) {
-      const T* R = op.rows + (size_t)en.y * MG_ROW;
+      const T* R = op.rows + (size_t)checked_row(en.y, op.n_rows) * MG_ROW;
 #pragma unroll
       for (int k = 0; k < MG_ROW; ++k) v[k] = R[k];
     } else {
@@ -263,9 +266,10 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
   // 1b. F and bval of the listed nodes, while the TMA runs
   for (int e = threadIdx.x; e < m && e < EC; e += blockDim.x) {
     const int2 en = bent[e0 + e];
-    const int x = en.x & 0xffff, y = en.x >> 16;
+    const int2 xy = region_pos(en, e < nrim0, RB, RB);
+    const int x = xy.x, y = xy.y;
     const T f = e < nrim0 ? F[op.L.idx(bi0 + x, bj0 + y)] : T(0);
-    const T bv = bval[en.y];
+    const T bv = bval[checked_row(en.y, op.n_rows)];
     sS[MG_ROW * EC + e] = f;
     sS[(MG_ROW + 1) * EC + e] = bv;
   }
@@ -284,7 +288,8 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
       sU[sP[e]] = sS[(MG_ROW + 1) * EC + e];
     } else {
       const int2 en = bent[e0 + e];
-      sU[(en.x >> 16) * RS + (en.x & 0xffff)] = bval[en.y];
+      const int2 xy = region_pos(en, e < nrim0, RB, RB);
+      sU[xy.y * RS + xy.x] = bval[checked_row(en.y, op.n_rows)];
     }
   }
   __syncthreads();
@@ -304,9 +309,10 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
         for (int k = 0; k <= MG_ROW; ++k) w[k] = sS[k * EC + e];
       } else {
         const int2 en = bent[e0 + e];
-        const int x = en.x & 0xffff, y = en.x >> 16;
+        const int2 xy = region_pos(en, true, RB, RB);
+        const int x = xy.x, y = xy.y;
         p = y * RS + x;
-        const T* R = op.rows + (size_t)en.y * MG_ROW;
+        const T* R = op.rows + (size_t)checked_row(en.y, op.n_rows) * MG_ROW;
 #pragma unroll
         for (int k = 0; k < MG_ROW; ++k) w[k] = R[k];
         w[MG_ROW] = F[op.L.idx(bi0 + x, bj0 + y)];
@@ -334,9 +340,9 @@ k_band(OpArgs<T> op, const int* __restrict__ btiles, int nbx, int eta, T* __rest
       y = p / RS;
       x = p - y * RS;
     } else {
-      const int2 en = bent[e0 + e];
-      x = en.x & 0xffff;
-      y = en.x >> 16;
+      const int2 xy = region_pos(bent[e0 + e], true, RB, RB);
+      x = xy.x;
+      y = xy.y;
     }
     if (x >= H && x < H + 32 && y >= H && y < H + 32)
       u[op.L.idx(bi0 + x, bj0 + y)] = sU[y * RS + x];
@@ -1064,3 +1070,6 @@ template void launch_residual<double, float>(const OpArgs<double>&, const int*, 
 template void launch_residual<double, double>(const OpArgs<double>&, const int*, int,
                                               const double*, const double*, double*, double,
                                               double*, cudaStream_t, bool);
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_cycle)

@@ -9,6 +9,7 @@ template <class T> struct OpArgs {
   const uint16_t* code;      // per node, padded layout
   const int* tile_base;      // per tile: first boundary row
   const T* rows;             // boundary rows, MG_ROW values each
+  int n_rows;                // rows in the table
 };
 
 // Level-0 data for the right-hand side F = M f + G g.

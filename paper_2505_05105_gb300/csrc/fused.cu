@@ -140,7 +140,9 @@ k_smooth_step(FusedArgs<float> a) {
   const int ri0 = i0 - HS, rj0 = j0 - HS;          // multiples of 4
   const int warp = threadIdx.x >> 5;
   auto row_base = [&](int gi, int gj) {
-    return sTB[((gj / MG_TY) - ty + 2) * kTBX + (gi / MG_TX) - tx + 1];
+    int k = ((gj / MG_TY) - ty + 2) * kTBX + (gi / MG_TX) - tx + 1;
+    if (!MG_CHECKED(k >= 0 && k < kTBX * kTBY)) k = 0;
+    return sTB[k];
   };
 
   // static data first (row bases, lists, rows, offsets): it may overlap the
@@ -163,8 +165,9 @@ k_smooth_step(FusedArgs<float> a) {
   const int m = a.loff[5 * t + 4] - e0;        // colour groups only: the rim is never updated
   for (int e = threadIdx.x; e < m && e < kRC; e += blockDim.x) {
     const int2 en = a.lent[e0 + e];
-    const int x = en.x & 0xffff, y = en.x >> 16;
-    const float* R = a.rows + (size_t)en.y * MG_ROW;
+    const int2 xy = region_pos(en, true, RX, RY);
+    const int x = xy.x, y = xy.y;
+    const float* R = a.rows + (size_t)checked_row(en.y, a.n_rows) * MG_ROW;
     float v[MG_ROW];
 #pragma unroll
     for (int k = 0; k < MG_ROW; ++k) v[k] = R[k];
@@ -257,8 +260,9 @@ k_smooth_step(FusedArgs<float> a) {
       for (int k = 0; k < MG_ROW; ++k) w[k] = sS[e * kRS + k];
     } else {
       const int2 en = a.lent[e0 + e];
-      q = ((en.x >> 16) >> 1) * PX + ((en.x & 0xffff) >> 1);
-      const float* R = a.rows + (size_t)en.y * MG_ROW;
+      const int2 xy = region_pos(en, true, RX, RY);
+      q = (xy.y >> 1) * PX + (xy.x >> 1);
+      const float* R = a.rows + (size_t)checked_row(en.y, a.n_rows) * MG_ROW;
 #pragma unroll
       for (int k = 0; k < MG_ROW; ++k) w[k] = R[k];
     }
@@ -419,7 +423,8 @@ k_smooth_step(FusedArgs<float> a) {
                      ((U[off[0]] + U[off[2]]) + (U[off[6]] + U[off[8]]));
           r = f - (8.f * U[off[4]] - s8) * (1.f / 3.f);
         } else {
-          const float* R = a.rows + (size_t)(row_base(ri0 + x, rj0 + y) + cd - 2) * MG_ROW;
+          const float* R =
+              a.rows + (size_t)checked_row(row_base(ri0 + x, rj0 + y) + cd - 2, a.n_rows) * MG_ROW;
           float acc = R[0] * U[off[0]] + R[1] * U[off[1]] + R[2] * U[off[2]] +
                       R[3] * U[off[3]] + R[4] * U[off[4]] + R[5] * U[off[5]] +
                       R[6] * U[off[6]] + R[7] * U[off[7]] + R[8] * U[off[8]];
@@ -497,3 +502,6 @@ template void launch_smooth_step<float>(const FusedArgs<float>&, int, bool, bool
                                         cudaStream_t);
 template void launch_smooth_step<double>(const FusedArgs<double>&, int, bool, bool, bool, size_t,
                                          cudaStream_t);
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_fused)

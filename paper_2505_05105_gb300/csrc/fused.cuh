@@ -8,6 +8,7 @@ template <class T> struct FusedArgs {
   const uint16_t* code;
   const int* tile_base;
   const T* rows;
+  int n_rows;               // rows in the table
   const int* tiles;         // tiles to process
   const int* loff;          // [5 tile id ..] group offsets of the region lists
   const int2* lent;         // region boundary nodes {x | y << 16, row}

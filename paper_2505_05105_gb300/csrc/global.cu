@@ -436,3 +436,6 @@ cudaError_t launch_lanczos(int n, const double* Mr, const double* Kr, const uint
   return cudaLaunchCooperativeKernel((const void*)k_lanczos, dim3(blocks), dim3(kThreads), args,
                                      0, st);
 }
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_global)

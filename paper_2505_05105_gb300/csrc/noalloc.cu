@@ -64,7 +64,8 @@ constexpr int kRX = MG_TX + 2, kRY = MG_TY + 2;   // owned tile + 1-node halo
 // (if given) and the tile's partial norms to part[2 * blockIdx.x].
 __global__ void __launch_bounds__(256)
 k_residual_static(Layout L, const uint16_t* __restrict__ code, const int* __restrict__ tile_base,
-                  const double* __restrict__ rows, const int* __restrict__ tiles, int N,
+                  const double* __restrict__ rows, int n_rows, const int* __restrict__ tiles,
+                  int N,
                   const double* __restrict__ F, const double* __restrict__ u,
                   double* __restrict__ r, double* __restrict__ part) {
   __shared__ double sU[kRY * kRX];
@@ -98,7 +99,7 @@ k_residual_static(Layout L, const uint16_t* __restrict__ code, const int* __rest
                     ((Up[-kRX - 1] + Up[-kRX + 1]) + (Up[kRX - 1] + Up[kRX + 1]));
         res = f - (8.0 * Up[0] - s8) * (1.0 / 3.0);
       } else {
-        const double* R = rows + (size_t)(tile_base[t] + cd - 2) * MG_ROW;
+        const double* R = rows + (size_t)checked_row(tile_base[t] + cd - 2, n_rows) * MG_ROW;
         double acc = R[0] * Up[-kRX - 1] + R[1] * Up[-kRX] + R[2] * Up[-kRX + 1] +
                      R[3] * Up[-1] + R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[kRX - 1] +
                      R[7] * Up[kRX] + R[8] * Up[kRX + 1];
@@ -187,8 +188,8 @@ int run_residual(const FineOpView& v, const double* F, const double* u, double* 
     if (e != cudaSuccess) return mg_cuda_fail(e);
   }
   if (v.n_active > 0)
-    k_residual_static<<<v.n_active, 256, 0, v.st>>>(v.L, v.code, v.tile_base, v.rows64, v.active,
-                                                     v.N, F, u, r, scratch);
+    k_residual_static<<<v.n_active, 256, 0, v.st>>>(v.L, v.code, v.tile_base, v.rows64, v.n_rows,
+                                                     v.active, v.N, F, u, r, scratch);
   k_reduce_partials<<<1, 1024, 0, v.st>>>(scratch, v.n_active, result);
   e = cudaGetLastError();
   if (e != cudaSuccess) return mg_cuda_fail(e);
@@ -202,3 +203,6 @@ int run_residual(const FineOpView& v, const double* F, const double* u, double* 
 }
 
 }  // namespace
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_noalloc)

@@ -354,3 +354,6 @@ extern "C" int mg1d_cycles(int count, const mg1d_problem* problems, int cycle, i
   if (herr & DEV_ERR_NOT_SPD) return MG_ERR_NOT_SPD;
   return MG_OK;
 }
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_oned)

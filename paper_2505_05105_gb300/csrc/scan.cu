@@ -137,3 +137,6 @@ void compact_flags_u8(const uint8_t* flag, int* list, int* count, size_t n, int*
   scan_sums<<<1, kThreads, 0, st>>>(tmp, nb, count);
   chunk_compact_write<<<nb, kThreads, 0, st>>>(a, n, tmp, list);
 }
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_scan)

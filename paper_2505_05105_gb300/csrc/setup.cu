@@ -511,3 +511,6 @@ void launch_coarsest(const CellData& cd, double* A, double* Ainv, unsigned* err,
 void launch_rows_to_f32(const double* r64, float* r32, size_t m, cudaStream_t st) {
   if (m) k_rows_to_f32<<<grid_for(m), 256, 0, st>>>(r64, r32, m);
 }
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_setup)

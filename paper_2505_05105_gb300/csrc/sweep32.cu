@@ -65,9 +65,11 @@ struct RowSrc {
   const float* sRow;                       // kRC staged rows, stride kRS
   const float* rows;                       // the level's boundary rows
   const int2* ent;                         // the tile's list entries
+  int n_rows;
 };
 __device__ __forceinline__ const float* row_ptr(const RowSrc& rs, int e) {
-  return e < kRC ? rs.sRow + e * kRS : rs.rows + (size_t)rs.ent[e].y * MG_ROW;
+  return e < kRC ? rs.sRow + e * kRS
+                 : rs.rows + (size_t)checked_row(rs.ent[e].y, rs.n_rows) * MG_ROW;
 }
 
 // boundary-row update of a node whose code is cd >= 2, same arithmetic as
@@ -183,16 +185,16 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
   //    the region's boundary nodes (colour groups, not the rim) and their rows
   const int e0 = loff[5 * blockIdx.x];
   const int m = loff[5 * blockIdx.x + 4] - e0;
-  const RowSrc rs{sRow, op.rows, lent + e0};
+  const RowSrc rs{sRow, op.rows, lent + e0, op.n_rows};
   for (int e = threadIdx.x; e < m && e < kRC; e += kT) {
     const int2 en = lent[e0 + e];
-    const float* R = op.rows + (size_t)en.y * MG_ROW;
+    const float* R = op.rows + (size_t)checked_row(en.y, op.n_rows) * MG_ROW;
     float v[MG_ROW];
 #pragma unroll
     for (int k = 0; k < MG_ROW; ++k) v[k] = R[k];
 #pragma unroll
     for (int k = 0; k < MG_ROW; ++k) sRow[e * kRS + k] = v[k];
-    sGrow[e] = en.y;
+    sGrow[e] = checked_row(en.y, op.n_rows);
   }
   if (!band_independent(touch)) griddep_wait();
 
@@ -260,8 +262,8 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
   __syncthreads();
   // each listed boundary node's code becomes 2 + its list entry
   for (int e = threadIdx.x; e < m; e += kT) {
-    const int p = lent[e0 + e].x;
-    const int x = p & 0xffff, y = p >> 16;
+    const int2 xy = region_pos(lent[e0 + e], true, RX, RY);
+    const int x = xy.x, y = xy.y;
     sC[(y & 1) * 2 * PL + (x & 1) * PL + (y >> 1) * PX + (x >> 1)] = (uint16_t)(2 + e);
   }
   __syncthreads();
@@ -304,7 +306,7 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
       for (int k2 = 0; k2 < 4; ++k2)
         if (c[k2] >= 2u) {
           const int e = (int)c[k2] - 2;
-          bval[e < kRC ? sGrow[e] : lent[e0 + e].y] = v[k2];
+          bval[e < kRC ? sGrow[e] : checked_row(lent[e0 + e].y, op.n_rows)] = v[k2];
         }
     }
   }
@@ -328,3 +330,6 @@ void launch_gs_sweep_f32(const OpArgs<float>& op, const int* tiles, int ntiles, 
     launch_pdl(k_gs_sweep_f32<kPlain>, ntiles, kT, 0, st, op, tiles, uin, uout, F, bval, L0, ec,
                loff, lent, touch);
 }
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_sweep32)

@@ -153,3 +153,6 @@ template cudaError_t configure_tail<float>(size_t);
 template cudaError_t configure_tail<double>(size_t);
 template void launch_tail<float>(const TailArgs<float>&, cudaStream_t);
 template void launch_tail<double>(const TailArgs<double>&, cudaStream_t);
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_tail)

@@ -17,6 +17,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 template <class T>
 struct Smem {
   int n[MG_TAIL_MAX_LEVELS];
+  int nb[MG_TAIL_MAX_LEVELS];             // boundary rows per level
   T* U[MG_TAIL_MAX_LEVELS];
   T* F[MG_TAIL_MAX_LEVELS];
   const int16_t* G[MG_TAIL_MAX_LEVELS];   // -2 not a DOF, -1 interior, >= 0 boundary row
@@ -30,7 +31,7 @@ struct Smem {
 // Level data used by the phases of one level, loaded once per smoothing step.
 template <class T>
 struct Lvl {
-  int n, S;
+  int n, S, nb;
   T* U;
   const T* F;
   const int16_t* G;
@@ -39,11 +40,19 @@ struct Lvl {
   int o[5];
 };
 
+// a listed node's bordered position (checked builds: its stencil inside the
+// (n + 3)^2 array)
+__device__ __forceinline__ int tail_pos(int q, int S) {
+  (void)S;
+  return MG_CHECKED(q >= S + 1 && q < S * S - S - 1) ? q : S + 1;
+}
+
 template <class T>
 __device__ __forceinline__ Lvl<T> level(const Smem<T>& s, int k) {
   Lvl<T> v;
   v.n = s.n[k];
   v.S = v.n + 3;
+  v.nb = s.nb[k];
   v.U = s.U[k];
   v.F = s.F[k];
   v.G = s.G[k];
@@ -78,8 +87,8 @@ __device__ __forceinline__ void colour_phase(const Lvl<T>& v, int c, bool bounda
   const int e0 = c == 0 ? v.o[0] : c == 1 ? v.o[1] : c == 2 ? v.o[2] : v.o[3];
   const int e1 = c == 0 ? v.o[1] : c == 1 ? v.o[2] : c == 2 ? v.o[3] : v.o[4];
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const int q = v.BL[e];
-    const T* R = v.rows + (size_t)v.G[q] * MG_ROW;
+    const int q = tail_pos(v.BL[e], v.S);
+    const T* R = v.rows + (size_t)checked_row(v.G[q], v.nb) * MG_ROW;
     const T* Up = U + q;
     T acc = R[0] * Up[-S - 1] + R[1] * Up[-S] + R[2] * Up[-S + 1] + R[3] * Up[-1] +
             R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[S - 1] + R[7] * Up[S] + R[8] * Up[S + 1];
@@ -102,14 +111,14 @@ __device__ void smooth(const TailArgs<T>& a, const Smem<T>& s, int k) {
   const int nw = min((int)(blockDim.x >> 5), max(1, (mc + 31) / 32));
   if ((int)(threadIdx.x >> 5) < nw) {
     auto fetch = [&](int e, int& r, T& f, int& p) {
-      const int q = v.BL[e];
-      r = v.G[q];
+      const int q = tail_pos(v.BL[e], v.S);
+      r = checked_row(v.G[q], v.nb);
       f = v.F[q];
       p = q;
     };
     auto extra = [&](int e) {
-      const int q = v.BL[e];
-      const T* w = v.rows + (size_t)v.G[q] * MG_ROW;
+      const int q = tail_pos(v.BL[e], v.S);
+      const T* w = v.rows + (size_t)checked_row(v.G[q], v.nb) * MG_ROW;
       const T* Up = v.U + q;
       const int S = v.S;
       T acc = w[0] * Up[-S - 1] + w[1] * Up[-S] + w[2] * Up[-S + 1] + w[3] * Up[-1] +
@@ -134,14 +143,14 @@ __device__ void smooth_transposed(const TailArgs<T>& a, const Smem<T>& s, int k)
     const int nw = min((int)(blockDim.x >> 5), max(1, (mc + 31) / 32));
     if ((int)(threadIdx.x >> 5) < nw) {
       auto fetch = [&](int e, int& r, T& f, int& p) {
-        const int q = v.BL[e];
-        r = v.G[q];
+        const int q = tail_pos(v.BL[e], v.S);
+        r = checked_row(v.G[q], v.nb);
         f = v.F[q];
         p = q;
       };
       auto extra = [&](int e) {
-        const int q = v.BL[e];
-        const T* w = v.rows + (size_t)v.G[q] * MG_ROW;
+        const int q = tail_pos(v.BL[e], v.S);
+        const T* w = v.rows + (size_t)checked_row(v.G[q], v.nb) * MG_ROW;
         const T* Up = v.U + q;
         const int S = v.S;
         T acc = w[0] * Up[-S - 1] + w[1] * Up[-S] + w[2] * Up[-S + 1] + w[3] * Up[-1] +
@@ -170,7 +179,7 @@ __device__ void residual_restrict(const Smem<T>& s, int k) {
                ((Up[-S - 1] + Up[-S + 1]) + (Up[S - 1] + Up[S + 1]));
         r = v.F[q] - (T(8) * Up[0] - s8) * T(1.0 / 3.0);
       } else {
-        const T* R = v.rows + (size_t)tag * MG_ROW;
+        const T* R = v.rows + (size_t)checked_row(tag, v.nb) * MG_ROW;
         T acc = R[0] * Up[-S - 1] + R[1] * Up[-S] + R[2] * Up[-S + 1] + R[3] * Up[-1] +
                 R[4] * Up[0] + R[5] * Up[1] + R[6] * Up[S - 1] + R[7] * Up[S] + R[8] * Up[S + 1];
         r = v.F[q] - acc;
@@ -253,6 +262,7 @@ __device__ void tail_vcycle(const TailArgs<T>& a, unsigned char* smem_raw, bool 
   if (threadIdx.x == 0) {
     for (int k = 0; k < K; ++k) {
       s.n[k] = lay.n[k];
+      s.nb[k] = lay.n_bnd[k];
       s.U[k] = reinterpret_cast<T*>(smem_raw + lay.U[k]);
       s.F[k] = reinterpret_cast<T*>(smem_raw + lay.F[k]);
       s.G[k] = reinterpret_cast<const int16_t*>(smem_raw + lay.G[k]);

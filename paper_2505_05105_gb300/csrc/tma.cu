@@ -41,3 +41,6 @@ int make_level_map(CUtensorMap* out, const void* base, size_t elem, const Layout
   if (r != CUDA_SUCCESS) return mg_cuda_fail(cudaErrorInvalidValue);
   return 0;
 }
+
+// binds the bounds-checked build's device error word (see common.cuh)
+MG_BOUNDS_BINDER(bind_bounds_tma)

@@ -14,7 +14,10 @@ from typing import Optional
 
 import numpy as np
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libghostmg.so")
+# GHOSTMG_CHECKED=1 loads the bounds-checked debug variant (build(checked=True))
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "libghostmg_checked.so" if os.environ.get("GHOSTMG_CHECKED") == "1"
+                        else "libghostmg.so")
 
 MG_OK = 0
 MG_ERR_INVALID_ARG = 1
@@ -131,6 +134,7 @@ SIGNATURES = {
     "mg_batch_timing": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "mg_batch_destroy": (None, [_P]),
     "mg1d_cycles": (_I, [_I, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "mg_bounds_check": (_I, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint), _I]),
 }
 
 PROF_SLOTS = ("sweep", "band", "restrict", "prolong", "residual", "update", "coarse", "io",
@@ -248,6 +252,14 @@ def mg_get_c_global(handle: int):
     _check(load().mg_get_c_global(handle, ctypes.byref(c), ctypes.byref(st), ctypes.byref(it)),
            "mg_get_c_global")
     return c.value, st.value, it.value
+
+
+def mg_bounds_check(reset: bool = False):
+    """(enabled, hits) of the bounds-checked build; (False, 0) in the normal one."""
+    en, hits = ctypes.c_int(), ctypes.c_uint()
+    _check(load().mg_bounds_check(ctypes.byref(en), ctypes.byref(hits), int(reset)),
+           "mg_bounds_check")
+    return bool(en.value), int(hits.value)
 
 
 def mg_set_wait_limit(handle: int, polls: int) -> int:
