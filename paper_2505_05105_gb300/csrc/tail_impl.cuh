@@ -86,7 +86,9 @@ __device__ __forceinline__ void colour_phase(const Lvl<T>& v, int c, bool bounda
   }
   const int e0 = c == 0 ? v.o[0] : c == 1 ? v.o[1] : c == 2 ? v.o[2] : v.o[3];
   const int e1 = c == 0 ? v.o[1] : c == 1 ? v.o[2] : c == 2 ? v.o[3] : v.o[4];
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+  // boundary nodes from the last threads, whose warps have the fewest (on the
+  // small levels no) interior rows: both kinds of work run side by side
+  for (int e = e0 + (int)(blockDim.x - 1 - threadIdx.x); e < e1; e += blockDim.x) {
     const int q = tail_pos(v.BL[e], v.S);
     const T* R = v.rows + (size_t)checked_row(v.G[q], v.nb) * MG_ROW;
     const T* Up = U + q;
@@ -221,22 +223,53 @@ __device__ void prolong(const Smem<T>& s, int k) {
   __syncthreads();
 }
 
-// u = A^{-1} F on the coarsest level in fp64: one row per thread (the
-// inverse is stored by columns, so a warp's rows read consecutive entries)
+// u = A^{-1} F on the coarsest level in fp64.  fp64 instructions are costly
+// on this part (a warp's fp64 instruction occupies the SM's fp64 pipe for
+// many cycles), so the solve issues as few as it can: F is converted once,
+// the columns are split into K slices whose partial row sums go to scratch
+// space (the residual buffer R, free at this point), and one pass adds the
+// K partials of each row.  With too little scratch, one thread per row.
+// The inverse is stored by columns.
 template <class T>
-__device__ void coarsest(const Smem<T>& s, int k) {
-  const int n = s.n[k], S = n + 3, m = (n + 1) * (n + 1);
+__device__ void coarsest(const Smem<T>& s, int k, size_t r_bytes) {
+  const int n = s.n[k], S = n + 3, W = n + 1, m = W * W;
   const T* F = s.F[k];
   const double* Ainv = s.Ainv;
-  for (int p = threadIdx.x; p < m; p += blockDim.x) {
-    double x = 0.0;
-    for (int cj = 0; cj <= n; ++cj) {
-      const T* Fr = F + (cj + 1) * S + 1;
-      const double* A = Ainv + (size_t)cj * (n + 1) * m + p;
-      for (int ci = 0; ci <= n; ++ci) x += A[(size_t)ci * m] * (double)Fr[ci];
+  T* U = s.U[k];
+  double* fd = reinterpret_cast<double*>(s.R);            // F in fp64, then the partials
+  const int cap = (int)(r_bytes / sizeof(double));
+  const int K = min((int)blockDim.x / m, cap / m - 1);
+  if (K < 1) {
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+      double x = 0.0;
+      for (int c = 0; c < m; ++c) {
+        const int cj = c / W, ci = c - cj * W;
+        x = fma(Ainv[(size_t)c * m + p], (double)F[(cj + 1) * S + ci + 1], x);
+      }
+      const int j = p / W, i = p - j * W;
+      U[(j + 1) * S + (i + 1)] = (T)x;
     }
-    const int j = p / (n + 1), i = p - j * (n + 1);
-    s.U[k][(j + 1) * S + (i + 1)] = (T)x;
+    __syncthreads();
+    return;
+  }
+  double* part = fd + m;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int cj = c / W, ci = c - cj * W;
+    fd[c] = (double)F[(cj + 1) * S + ci + 1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < K * m; t += blockDim.x) {
+    const int sl = t / m, p = t - sl * m;
+    double x = 0.0;
+    for (int c = sl; c < m; c += K) x = fma(Ainv[(size_t)c * m + p], fd[c], x);
+    part[sl * m + p] = x;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    double x = part[p];
+    for (int sl = 1; sl < K; ++sl) x += part[sl * m + p];
+    const int j = p / W, i = p - j * W;
+    U[(j + 1) * S + (i + 1)] = (T)x;
   }
   __syncthreads();
 }
@@ -259,6 +292,8 @@ __device__ void tail_vcycle(const TailArgs<T>& a, unsigned char* smem_raw, bool 
   __shared__ int bad;
   const TailLayout& lay = a.lay;
   const int K = lay.nlev;
+  // the residual buffer: (n_0 + 3)^2 values of the top level
+  const size_t s_rbytes = (size_t)(lay.n[0] + 3) * (lay.n[0] + 3) * sizeof(T);
   if (threadIdx.x == 0) {
     for (int k = 0; k < K; ++k) {
       s.n[k] = lay.n[k];
@@ -341,7 +376,7 @@ __device__ void tail_vcycle(const TailArgs<T>& a, unsigned char* smem_raw, bool 
       for (int r = 0; r < a.nu1; ++r) smooth(a, s, k);
       residual_restrict(s, k);
     }
-    coarsest(s, K - 1);
+    coarsest(s, K - 1, s_rbytes);
     for (int k = K - 2; k >= 0; --k) {
       prolong(s, k);
       for (int r = 0; r < a.nu2; ++r) smooth(a, s, k);
@@ -353,7 +388,7 @@ __device__ void tail_vcycle(const TailArgs<T>& a, unsigned char* smem_raw, bool 
       for (int r = 0; r < a.nu2; ++r) smooth_transposed(a, s, k);
       residual_restrict(s, k);
     }
-    coarsest(s, K - 1);
+    coarsest(s, K - 1, s_rbytes);
     for (int k = K - 2; k >= 0; --k) {
       prolong(s, k);
       for (int r = 0; r < a.nu1; ++r) smooth_transposed(a, s, k);
