@@ -141,23 +141,49 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
             (unsigned long long)__double_as_longlong(v));
 }
 
-// Reduce (max, sum) over the block and add to out[0] (max) / out[1] (sum).
-// Requires blockDim.x a multiple of 32, <= 1024.
-__device__ __forceinline__ void block_norms_to_global(double vmax, double vsum, double* out) {
-  __shared__ double s_max[32], s_sum[32];
-  vmax = warp_max(vmax);
+// Max |x| kept as the bit pattern of |x|: non-negative doubles order like
+// their bit patterns, so integer max replaces fmax (integer instructions
+// instead of the scarce fp64 pipe), and a NaN (above +Inf in this order) is
+// kept rather than dropped as fmax would.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ void max_abs(unsigned long long& m, double x) {
+  const unsigned long long b = abs_bits(x);
+  m = b > m ? b : m;
+}
+// finite (neither Inf nor NaN), by the exponent bits
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (abs_bits(x) >> 52) != 0x7ffull;
+}
+__device__ __forceinline__ unsigned long long warp_max_bits(unsigned long long m) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, m, o);
+    m = b > m ? b : m;
+  }
+  return m;
+}
+
+// Reduce (max |x| as bits, sum) over the block and take them into out[0]
+// (max, by atomic max on the bit pattern) / out[1] (sum).  Requires
+// blockDim.x a multiple of 32, <= 1024.
+__device__ __forceinline__ void block_norms_to_global(unsigned long long vmax, double vsum,
+                                                      double* out) {
+  __shared__ unsigned long long s_max[32];
+  __shared__ double s_sum[32];
+  vmax = warp_max_bits(vmax);
   vsum = warp_sum(vsum);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) { s_max[w] = vmax; s_sum[w] = vsum; }
   __syncthreads();
   if (w == 0) {
     int nw = blockDim.x >> 5;
-    vmax = l < nw ? s_max[l] : 0.0;
+    vmax = l < nw ? s_max[l] : 0ull;
     vsum = l < nw ? s_sum[l] : 0.0;
-    vmax = warp_max(vmax);
+    vmax = warp_max_bits(vmax);
     vsum = warp_sum(vsum);
     if (l == 0) {
-      atomic_max_nonneg(out, vmax);
+      atomicMax(reinterpret_cast<unsigned long long*>(out), vmax);
       atomicAdd(out + 1, vsum);
     }
   }

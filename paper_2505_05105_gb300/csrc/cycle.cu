@@ -409,7 +409,8 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
     }
   }
   __syncthreads();
-  double vmax = 0.0, vsum = 0.0;
+  unsigned long long vmax = 0ull;
+  double vsum = 0.0;
   for (int it = threadIdx.x; it < (RR_Y - 2) * (RR_X - 2); it += blockDim.x) {
     int rj = 1 + it / (RR_X - 2), ri = 1 + it % (RR_X - 2);
     int p = rj * RR_X + ri;
@@ -422,7 +423,7 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
     sR[p] = r;
     if (NORM && ri >= 2 && ri < RR_X - 2 && rj >= 2 && rj < RR_Y - 2) {
       double rd = (double)r;
-      vmax = fmax(vmax, fabs(rd));
+      max_abs(vmax, rd);
       vsum += rd * rd;
     }
   }
@@ -536,7 +537,8 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
     sH[it] = (r[-1] + r[0]) + r[1];
   }
   __syncthreads();
-  double vmax = 0.0, vsum = 0.0;
+  unsigned long long vmax = 0ull;
+  double vsum = 0.0;
   for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
     int rr = it / MG_TX, ii = it - rr * MG_TX;
     int p = (rr + 2) * RR_X + ii + 2;
@@ -552,7 +554,7 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
       r = cd ? node_residual<T, RR_X>(op, sU + p, cd, F[g], gi, gj) : T(0);
     }
     double rd = (double)r;
-    vmax = fmax(vmax, fabs(rd));
+    max_abs(vmax, rd);
     if (l2) vsum += rd * rd;
     if (rout) rout[g] = (TR)(r * scale);
   }
@@ -628,8 +630,7 @@ __global__ void k_coarse_solve(Layout Lc, const double* __restrict__ Ainv, const
 __global__ void __launch_bounds__(kThreads)
 k_rhs(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ f,
       const double* __restrict__ g, double* __restrict__ F, double* __restrict__ norms) {
-  const double vmax = rhs_tile(a, tiles[blockIdx.x], f, g, F);
-  block_norms_to_global(vmax, 0.0, norms);
+  block_norms_to_global(rhs_tile(a, tiles[blockIdx.x], f, g, F), 0.0, norms);
 }
 
 // Adjoint of the right-hand side map (f, g) -> F = M f + G g (Eq. disc_rhs):
@@ -729,36 +730,71 @@ k_rhs_adj(RhsArgs a, const int* __restrict__ tiles, const double* __restrict__ w
 
 // User layout (row-major (n+1)^2) -> padded layout, zero on nodes that are
 // not DOFs; flags NaN/Inf in a DOF entry (err) and any nonzero DOF value
-// (nz).  One block row per node row: blockIdx.y = j.
+// (nz).  One block per node row (blockIdx.x = j), kIoUnroll nodes of a
+// thread in flight; the checks are integer tests on the bit patterns (no
+// fp64 instructions) and one atomic per block at most.
+constexpr int kIoUnroll = 4;
 template <class T>
-__global__ void k_pack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
-                       T* __restrict__ dst, unsigned* err, unsigned* nz) {
-  const int n = L.n, j = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kThreads)
+k_pack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
+       T* __restrict__ dst, unsigned* err, unsigned* nz) {
+  const int n = L.n, j = blockIdx.x;
+  const size_t row = L.idx(0, j);
+  const double* s = src + (size_t)j * (n + 1);
   bool bad = false, any = false;
-  if (i <= n) {
-    const size_t g = L.idx(i, j);
+  for (int i0 = threadIdx.x; i0 <= n; i0 += kIoUnroll * blockDim.x) {
+    uint16_t cd[kIoUnroll];
+    double v[kIoUnroll];
+#pragma unroll
+    for (int k = 0; k < kIoUnroll; ++k) {
+      const int i = i0 + k * (int)blockDim.x;
+      cd[k] = i <= n ? code[row + i] : 0;
+    }
     // entries off the DOFs are neither read nor checked
-    const bool dof = code[g] != 0;
-    const double v = dof ? src[(size_t)j * (n + 1) + i] : 0.0;
-    bad = !isfinite(v);
-    any = v != 0.0;
-    dst[g] = (T)v;
+#pragma unroll
+    for (int k = 0; k < kIoUnroll; ++k) v[k] = cd[k] ? s[i0 + k * (int)blockDim.x] : 0.0;
+#pragma unroll
+    for (int k = 0; k < kIoUnroll; ++k) {
+      const int i = i0 + k * (int)blockDim.x;
+      if (i > n) continue;
+      bad |= !finite_bits(v[k]);
+      any |= abs_bits(v[k]) != 0ull;
+      dst[row + i] = (T)v[k];
+    }
   }
-  if (err && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, DEV_ERR_NAN);
-  if (nz && __any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(nz, 1u);
+  bad = __syncthreads_or(bad);
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    if (err && bad) atomicOr(err, DEV_ERR_NAN);
+    if (nz && any) atomicOr(nz, 1u);
+  }
 }
 
 // Padded layout -> user layout, zero on nodes that are not DOFs (box: the
-// box-side nodes are kept as well).
-__global__ void k_unpack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
-                         double* __restrict__ dst, int box) {
-  const int n = L.n, j = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > n) return;
-  const size_t g = L.idx(i, j);
-  const bool keep = code[g] || (box && (i == 0 || j == 0 || i == n || j == n));
-  dst[(size_t)j * (n + 1) + i] = keep ? src[g] : 0.0;
+// box-side nodes are kept as well).  One block per node row.
+__global__ void __launch_bounds__(kThreads)
+k_unpack(Layout L, const uint16_t* __restrict__ code, const double* __restrict__ src,
+         double* __restrict__ dst, int box) {
+  const int n = L.n, j = blockIdx.x;
+  const size_t row = L.idx(0, j);
+  double* d = dst + (size_t)j * (n + 1);
+  const bool edge_row = box && (j == 0 || j == n);
+  for (int i0 = threadIdx.x; i0 <= n; i0 += kIoUnroll * blockDim.x) {
+    bool keep[kIoUnroll];
+#pragma unroll
+    for (int k = 0; k < kIoUnroll; ++k) {
+      const int i = i0 + k * (int)blockDim.x;
+      keep[k] = i <= n && (code[row + i] || edge_row || (box && (i == 0 || i == n)));
+    }
+    double v[kIoUnroll];
+#pragma unroll
+    for (int k = 0; k < kIoUnroll; ++k) v[k] = keep[k] ? src[row + i0 + k * (int)blockDim.x] : 0.0;
+#pragma unroll
+    for (int k = 0; k < kIoUnroll; ++k) {
+      const int i = i0 + k * (int)blockDim.x;
+      if (i <= n) d[i] = v[k];
+    }
+  }
 }
 
 // k_unpack restricted to the listed tiles (64 x 32 nodes each, clipped to
@@ -998,14 +1034,12 @@ void launch_rhs_adj(const RhsArgs& a, const int* tiles, int ntiles, const double
 template <class T>
 void launch_pack(const Layout& L, const uint16_t* code, const double* src, T* dst, unsigned* err,
                  cudaStream_t st, unsigned* nz) {
-  dim3 grid((L.n + 1 + kThreads - 1) / kThreads, L.n + 1);
-  k_pack<T><<<grid, kThreads, 0, st>>>(L, code, src, dst, err, nz);
+  k_pack<T><<<L.n + 1, kThreads, 0, st>>>(L, code, src, dst, err, nz);
 }
 
 void launch_unpack(const Layout& L, const uint16_t* code, const double* src, double* dst,
                    cudaStream_t st, int box) {
-  dim3 grid((L.n + 1 + kThreads - 1) / kThreads, L.n + 1);
-  k_unpack<<<grid, kThreads, 0, st>>>(L, code, src, dst, box);
+  k_unpack<<<L.n + 1, kThreads, 0, st>>>(L, code, src, dst, box);
 }
 
 void launch_unpack_tiles(const Layout& L, const uint16_t* code, const int* tiles, int ntiles,

@@ -14,8 +14,9 @@ namespace {
 // the cut cells' Mk and Gk (Eq. disc_rhs with Q1 interpolants).
 constexpr int RHS_X = MG_TX + 2, RHS_Y = MG_TY + 2;
 // Block-wide over tile t, one tile per block (any block size that is a
-// multiple of 32); returns the thread's max |F| over the nodes it wrote.
-__device__ __forceinline__ double rhs_tile(const RhsArgs& a, int t, const double* __restrict__ f,
+// multiple of 32); returns the thread's max |F| over the nodes it wrote (as
+// the bit pattern of |F|, see abs_bits).
+__device__ __forceinline__ unsigned long long rhs_tile(const RhsArgs& a, int t, const double* __restrict__ f,
                                            const double* __restrict__ g, double* __restrict__ F) {
   __shared__ double sf[RHS_Y * RHS_X];       // f on the tile plus one ring
   __shared__ double st[RHS_Y * MG_TX];       // row pass f(i-1) + 4 f(i) + f(i+1)
@@ -46,7 +47,7 @@ __device__ __forceinline__ double rhs_tile(const RhsArgs& a, int t, const double
   }
   __syncthreads();
   const double h2 = a.h * a.h / 36.0;
-  double vmax = 0.0;
+  unsigned long long vmax = 0ull;
   for (int q = threadIdx.x; q < MG_TY * MG_TX; q += blockDim.x) {
     const int y = q / MG_TX, x = q - y * MG_TX;
     const int i = i0 + x, j = j0 + y;
@@ -118,8 +119,8 @@ __device__ __forceinline__ double rhs_tile(const RhsArgs& a, int t, const double
     F[gk] = s;
     // every f, g (and g_N) value that enters F_p is in s with a weight:
     // a NaN or Inf among them (0 * Inf included) leaves s not finite
-    if (a.err != nullptr && !isfinite(s)) atomicOr(a.err, DEV_ERR_NAN);
-    vmax = fmax(vmax, fabs(s));
+    if (a.err != nullptr && !finite_bits(s)) atomicOr(a.err, DEV_ERR_NAN);
+    max_abs(vmax, s);
   }
   return vmax;
 }
