@@ -198,7 +198,8 @@ unsigned* bounds_word() {
     if (cudaMalloc(&w, sizeof(unsigned)) != cudaSuccess) return nullptr;
     cudaError_t (*const bind[])(unsigned*) = {
         bind_bounds_api,   bind_bounds_batch, bind_bounds_cycle,   bind_bounds_fused,
-        bind_bounds_global, bind_bounds_noalloc, bind_bounds_oned, bind_bounds_scan,
+        bind_bounds_global, bind_bounds_noalloc, bind_bounds_oned, bind_bounds_restrict32,
+        bind_bounds_scan,
         bind_bounds_setup, bind_bounds_sweep32, bind_bounds_tail,  bind_bounds_tma};
     bool ok = cudaMemset(w, 0, sizeof(unsigned)) == cudaSuccess;
     for (auto f : bind) ok = ok && f(w) == cudaSuccess;

@@ -386,7 +386,7 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
   {
     constexpr int B = 4;
     for (int it0 = threadIdx.x; it0 < RR_Y * (RR_X / 2); it0 += B * blockDim.x) {
-      T2 u2[B];
+      T2 u2[B], f2[B];
       uint32_t c2[B];
 #pragma unroll
       for (int b = 0; b < B; ++b) {
@@ -394,6 +394,7 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
         int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
         size_t g = it < RR_Y * (RR_X / 2) ? op.L.idx(fi0 + 2 * a, fj0 + rj) : op.L.idx(0, 0);
         u2[b] = __ldcg(reinterpret_cast<const T2*>(u + g));
+        f2[b] = __ldcg(reinterpret_cast<const T2*>(F + g));
         c2[b] = *reinterpret_cast<const uint32_t*>(op.code + g);
       }
 #pragma unroll
@@ -403,6 +404,8 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
         int rj = it / (RR_X / 2), a = it - rj * (RR_X / 2);
         sU[rj * RR_X + 2 * a] = u2[b].x;
         sU[rj * RR_X + 2 * a + 1] = u2[b].y;
+        sR[rj * RR_X + 2 * a] = f2[b].x;       // F, replaced by r below
+        sR[rj * RR_X + 2 * a + 1] = f2[b].y;
         sC[rj * RR_X + 2 * a] = (uint16_t)(c2[b] & 0xffffu);
         sC[rj * RR_X + 2 * a + 1] = (uint16_t)(c2[b] >> 16);
       }
@@ -411,6 +414,7 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
   __syncthreads();
   unsigned long long vmax = 0ull;
   double vsum = 0.0;
+  // r = F - A u in place of F (the restriction below reads only these nodes)
   for (int it = threadIdx.x; it < (RR_Y - 2) * (RR_X - 2); it += blockDim.x) {
     int rj = 1 + it / (RR_X - 2), ri = 1 + it % (RR_X - 2);
     int p = rj * RR_X + ri;
@@ -418,7 +422,7 @@ k_resid_restrict(OpArgs<T> op, const T* __restrict__ u, const T* __restrict__ F,
     T r = T(0);
     if (cd) {
       int gi = fi0 + ri, gj = fj0 + rj;
-      r = node_residual<T, RR_X>(op, sU + p, cd, __ldcg(F + op.L.idx(gi, gj)), gi, gj);
+      r = node_residual<T, RR_X>(op, sU + p, cd, sR[p], gi, gj);
     }
     sR[p] = r;
     if (NORM && ri >= 2 && ri < RR_X - 2 && rj >= 2 && rj < RR_Y - 2) {
@@ -539,6 +543,8 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
   __syncthreads();
   unsigned long long vmax = 0ull;
   double vsum = 0.0;
+  // unrolled so that several nodes' loads of F are in flight at once
+#pragma unroll 4
   for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
     int rr = it / MG_TX, ii = it - rr * MG_TX;
     int p = (rr + 2) * RR_X + ii + 2;
@@ -985,6 +991,10 @@ void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const La
                            const int* ctiles, int nct, T* Fc, double* norms, cudaStream_t st,
                            const uint8_t* touch) {
   if (!nct) return;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    launch_resid_restrict_f32(op, u, F, Lc, ctiles, nct, Fc, norms, st, touch);
+    return;
+  }
   if (norms)
     launch_pdl(k_resid_restrict<T, true>, nct * 4, kThreads, 0, st, op, u, F, Lc, ctiles, Fc, norms,
                touch);

@@ -95,6 +95,10 @@ void launch_resid_restrict(const OpArgs<T>& op, const T* u, const T* F, const La
 //                  nodes of L that the prolongating sweep's region reads;
 //   TOUCH_RESTRICT 4 blocks per coarse tile (tpr the coarse ntx), the fine
 //                  region of L that a residual + restriction block reads.
+// The fp32 version (restrict32.cu), which launch_resid_restrict<float> runs.
+void launch_resid_restrict_f32(const OpArgs<float>& op, const float* u, const float* F,
+                               const Layout& Lc, const int* ctiles, int nct, float* Fc,
+                               double* norms, cudaStream_t st, const uint8_t* touch);
 enum TouchMode : int { TOUCH_SWEEP = 0, TOUCH_PROLONG = 1, TOUCH_RESTRICT = 2 };
 void launch_touch_flags(int mode, const Layout& L, const uint16_t* code, const int* tiles,
                         int tpr, int nblocks, uint8_t* flag, cudaStream_t st);

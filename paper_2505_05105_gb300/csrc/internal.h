@@ -29,6 +29,7 @@ cudaError_t bind_bounds_fused(unsigned* word);
 cudaError_t bind_bounds_global(unsigned* word);
 cudaError_t bind_bounds_noalloc(unsigned* word);
 cudaError_t bind_bounds_oned(unsigned* word);
+cudaError_t bind_bounds_restrict32(unsigned* word);
 cudaError_t bind_bounds_scan(unsigned* word);
 cudaError_t bind_bounds_setup(unsigned* word);
 cudaError_t bind_bounds_sweep32(unsigned* word);
