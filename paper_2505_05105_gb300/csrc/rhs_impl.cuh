@@ -58,12 +58,26 @@ __device__ __forceinline__ unsigned long long rhs_tile(const RhsArgs& a, int t, 
       const double* c = st + y * MG_TX + x;
       s = h2 * fma(4.0, c[MG_TX], c[0] + c[2 * MG_TX]);
     } else if (cd) {
+      // the four cells' classes, then the cut cells' indices, each as one
+      // batch of independent loads (three round trips to memory, not twelve)
+      uint8_t cl4[4];
+      int cut4[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ic = i - 1 + (k & 1), jc = j - 1 + (k >> 1);
+        const bool in = ic >= 0 && jc >= 0 && ic < n && jc < n;
+        cl4[k] = in ? a.cls[(size_t)jc * n + ic] : (uint8_t)CELL_EXT;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ic = i - 1 + (k & 1), jc = j - 1 + (k >> 1);
+        cut4[k] = cl4[k] == CELL_CUT ? a.cell_cut[(size_t)jc * n + ic] : 0;
+      }
+#pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int dx = k & 1, dy = k >> 1;
         const int ic = i - 1 + dx, jc = j - 1 + dy;
-        if (ic < 0 || jc < 0 || ic >= n || jc >= n) continue;
-        const size_t c = (size_t)jc * n + ic;
-        const uint8_t cl = a.cls[c];
+        const uint8_t cl = cl4[k];
         if (cl == CELL_EXT) continue;
         const int av = (1 - dx) + 2 * (1 - dy);
         // the cell's vertices (0,0),(1,0),(0,1),(1,1) in sf
@@ -77,14 +91,14 @@ __device__ __forceinline__ unsigned long long rhs_tile(const RhsArgs& a, int t, 
             s += h2 * wgt * fb[b];
           }
         } else {
-          const double* Mk = a.Mk + (size_t)a.cell_cut[c] * 16 + av * 4;
-          const double* Gk = a.Gk + (size_t)a.cell_cut[c] * 16 + av * 4;
+          const double* Mk = a.Mk + (size_t)cut4[k] * 16 + av * 4;
+          const double* Gk = a.Gk + (size_t)cut4[k] * 16 + av * 4;
           const size_t k0 = (size_t)jc * W + ic;
           const size_t vk[4] = {k0, k0 + 1, k0 + W, k0 + W + 1};
           for (int b = 0; b < 4; ++b) s += Mk[b] * fb[b] + Gk[b] * g[vk[b]];
           if (a.gN != nullptr && a.Nk != nullptr) {
             // Neumann load of the cell (zero on Dirichlet cells)
-            const double* Nk = a.Nk + (size_t)a.cell_cut[c] * 16 + av * 4;
+            const double* Nk = a.Nk + (size_t)cut4[k] * 16 + av * 4;
             for (int b = 0; b < 4; ++b) s += Nk[b] * a.gN[vk[b]];
           }
         }

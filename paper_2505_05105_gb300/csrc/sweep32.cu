@@ -297,7 +297,7 @@ k_gs_sweep_f32(OpArgs<float> op, const int* __restrict__ tiles, const float* __r
     const float2 vo = *reinterpret_cast<const float2*>(sU + po);
     *reinterpret_cast<float4*>(uout + op.L.idx(i0 + 4 * q, j0 + rr)) =
         make_float4(ve.x, vo.x, ve.y, vo.y);
-    if (bval) {
+    if (bval && m > 0) {          // m = 0: no boundary node in the tile
       const uint32_t ce = *reinterpret_cast<const uint32_t*>(sC + pe);
       const uint32_t co = *reinterpret_cast<const uint32_t*>(sC + po);
       const uint32_t c[4] = {ce & 0xffffu, co & 0xffffu, ce >> 16, co >> 16};
