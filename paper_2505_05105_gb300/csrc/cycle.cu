@@ -562,7 +562,14 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
     double rd = (double)r;
     max_abs(vmax, rd);
     if (l2) vsum += rd * rd;
-    if (rout) rout[g] = (TR)(r * scale);
+    // for an fp32 output with a power-of-two scale (the refinement's sigma)
+    // the scaling is exact in fp32 after the rounding to fp32, one fp64
+    // instruction fewer per node (identical unless r is below the fp32
+    // normal range)
+    if (rout) {
+      if (sizeof(TR) < sizeof(T)) rout[g] = (TR)r * (TR)scale;
+      else rout[g] = (TR)(r * scale);
+    }
   }
   if (norms) block_norms_to_global(vmax, vsum, norms);
 }

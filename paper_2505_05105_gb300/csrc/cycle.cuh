@@ -103,7 +103,9 @@ enum TouchMode : int { TOUCH_SWEEP = 0, TOUCH_PROLONG = 1, TOUCH_RESTRICT = 2 };
 void launch_touch_flags(int mode, const Layout& L, const uint16_t* code, const int* tiles,
                         int tpr, int nblocks, uint8_t* flag, cudaStream_t st);
 template <class T, class TR>
-// norms[0] gets max |r| (atomic max); with l2 norms[1] gets sum r^2
+// norms[0] gets max |r| (atomic max); with l2 norms[1] gets sum r^2; rout
+// (if given) gets scale r -- for an fp32 rout, scale must be a power of two
+// (it is applied after the rounding to fp32)
 void launch_residual(const OpArgs<T>& op, const int* tiles, int ntiles, const T* u, const T* F,
                      TR* rout, T scale, double* norms, cudaStream_t st, bool l2 = true);
 template <class T>
