@@ -854,8 +854,9 @@ __global__ void k_scale_to_f32(Layout L, const int* __restrict__ tiles,
     const int ii = 2 * (threadIdx.x & 31);
     const double2 v = *reinterpret_cast<const double2*>(src + g + ii);
     float2 o;
-    o.x = (float)(v.x * scale);
-    o.y = (float)(v.y * scale);
+    // scale is a power of two: exact in fp32 after the rounding
+    o.x = (float)v.x * (float)scale;
+    o.y = (float)v.y * (float)scale;
     *reinterpret_cast<float2*>(dst + g + ii) = o;
   }
 }

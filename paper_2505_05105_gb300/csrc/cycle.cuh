@@ -132,7 +132,7 @@ void launch_unpack_tiles(const Layout& L, const uint16_t* code, const int* tiles
 void launch_zero_inactive(const Layout& L, const uint8_t* tile_active, double* dst, int blocks,
                           cudaStream_t st);
 // dst = (float)(src * scale) on the DOFs of the tiles (the refinement
-// residual when u = 0: r = F)
+// residual when u = 0: r = F); scale a power of two
 void launch_scale_to_f32(const Layout& L, const int* tiles, int ntiles, const double* src,
                          float* dst, double scale, cudaStream_t st);
 void launch_update(const Layout& L, const int* tiles, int ntiles, const uint16_t* code, double* u,

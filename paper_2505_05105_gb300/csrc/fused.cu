@@ -337,7 +337,10 @@ k_smooth_step(FusedArgs<float> a) {
         else if (in0) P[b * PX + a2] = v.x;
         else P[b * PX + a2 + 1] = v.y;
       }
-      for (int e = gs[c] + threadIdx.x; e < gs[c + 1]; e += blockDim.x) listed(c, e);
+      // the colour's boundary nodes from the last threads, which make one
+      // pass of the pairs fewer than the first ones
+      for (int e = gs[c] + (int)(blockDim.x - 1 - threadIdx.x); e < gs[c + 1]; e += blockDim.x)
+        listed(c, e);
       __syncthreads();
     }
   }
