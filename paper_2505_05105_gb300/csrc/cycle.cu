@@ -535,6 +535,9 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
   // then three of them per node -- 6 fp64 operations per node instead of 10,
   // this kernel being bound by the fp64 rate.
   __shared__ __align__(16) T sH[(MG_TY + 2) * MG_TX];
+  __shared__ uint16_t s_list[MG_TY * MG_TX];
+  __shared__ int s_nl;
+  if (threadIdx.x == 0) s_nl = 0;
   for (int it = threadIdx.x; it < (MG_TY + 2) * MG_TX; it += blockDim.x) {
     const int y = it / MG_TX, x = it - y * MG_TX;     // region row y + 1, column x + 2
     const T* r = sU + (y + 1) * RR_X + x + 2;
@@ -543,22 +546,7 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
   __syncthreads();
   unsigned long long vmax = 0ull;
   double vsum = 0.0;
-  // unrolled so that several nodes' loads of F are in flight at once
-#pragma unroll 4
-  for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
-    int rr = it / MG_TX, ii = it - rr * MG_TX;
-    int p = (rr + 2) * RR_X + ii + 2;
-    int gi = i0 + ii, gj = j0 + rr;
-    size_t g = op.L.idx(gi, gj);
-    uint16_t cd = sC[p];
-    T r;
-    if (cd == 1) {
-      const T* h = sH + it;                            // rows rr .. rr + 2 of sH
-      const T box = (h[0] + h[MG_TX]) + h[2 * MG_TX];
-      r = fma(fma(T(9), sU[p], -box), T(-1.0 / 3.0), F[g]);
-    } else {
-      r = cd ? node_residual<T, RR_X>(op, sU + p, cd, F[g], gi, gj) : T(0);
-    }
+  auto finish = [&](size_t g, T r) {
     double rd = (double)r;
     max_abs(vmax, rd);
     if (l2) vsum += rd * rd;
@@ -570,6 +558,37 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
       if (sizeof(TR) < sizeof(T)) rout[g] = (TR)r * (TR)scale;
       else rout[g] = (TR)(r * scale);
     }
+  };
+  // interior nodes here (unrolled so that several nodes' loads of F are in
+  // flight at once); boundary nodes go to a list and are done after, a
+  // thread each, so that their row products do not hold up whole warps
+  // (s_nl was cleared before the barrier above)
+#pragma unroll 4
+  for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
+    int rr = it / MG_TX, ii = it - rr * MG_TX;
+    int p = (rr + 2) * RR_X + ii + 2;
+    uint16_t cd = sC[p];
+    if (cd >= 2) {
+      s_list[atomicAdd(&s_nl, 1)] = (uint16_t)it;
+      continue;
+    }
+    size_t g = op.L.idx(i0 + ii, j0 + rr);
+    T r = T(0);
+    if (cd == 1) {
+      const T* h = sH + it;                            // rows rr .. rr + 2 of sH
+      const T box = (h[0] + h[MG_TX]) + h[2 * MG_TX];
+      r = fma(fma(T(9), sU[p], -box), T(-1.0 / 3.0), F[g]);
+    }
+    finish(g, r);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < s_nl; e += blockDim.x) {
+    const int it = s_list[e];
+    const int rr = it / MG_TX, ii = it - rr * MG_TX;
+    const int p = (rr + 2) * RR_X + ii + 2;
+    const int gi = i0 + ii, gj = j0 + rr;
+    const size_t g = op.L.idx(gi, gj);
+    finish(g, node_residual<T, RR_X>(op, sU + p, sC[p], F[g], gi, gj));
   }
   if (norms) block_norms_to_global(vmax, vsum, norms);
 }

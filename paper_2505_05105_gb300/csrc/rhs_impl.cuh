@@ -48,7 +48,39 @@ __device__ __forceinline__ unsigned long long rhs_tile(const RhsArgs& a, int t, 
   __syncthreads();
   const double h2 = a.h * a.h / 36.0;
   unsigned long long vmax = 0ull;
+  // interior nodes here; vertices of cut cells (and, with box sides, nodes
+  // next to the box) go to a list and are done after, a thread each, so that
+  // their long fp64 path does not hold up whole warps of interior nodes
+  __shared__ uint16_t s_list[MG_TX * MG_TY];
+  __shared__ int s_nl;
+  if (threadIdx.x == 0) s_nl = 0;
+  __syncthreads();
+  auto finish = [&](size_t gk, double s) {
+    F[gk] = s;
+    // every f, g (and g_N) value that enters F_p is in s with a weight:
+    // a NaN or Inf among them (0 * Inf included) leaves s not finite
+    if (a.err != nullptr && !finite_bits(s)) atomicOr(a.err, DEV_ERR_NAN);
+    max_abs(vmax, s);
+  };
   for (int q = threadIdx.x; q < MG_TY * MG_TX; q += blockDim.x) {
+    const int y = q / MG_TX, x = q - y * MG_TX;
+    const int i = i0 + x, j = j0 + y;
+    const size_t gk = a.L.idx(i, j);
+    const uint16_t cd = a.code[gk];
+    if (cd >= 2 || (a.box && cd && (i == 1 || j == 1 || i == n - 1 || j == n - 1))) {
+      s_list[atomicAdd(&s_nl, 1)] = (uint16_t)q;
+      continue;
+    }
+    double s = 0.0;
+    if (cd == 1) {
+      const double* c = st + y * MG_TX + x;
+      s = h2 * fma(4.0, c[MG_TX], c[0] + c[2 * MG_TX]);
+    }
+    finish(gk, s);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < s_nl; e += blockDim.x) {
+    const int q = s_list[e];
     const int y = q / MG_TX, x = q - y * MG_TX;
     const int i = i0 + x, j = j0 + y;
     const size_t gk = a.L.idx(i, j);
@@ -57,7 +89,7 @@ __device__ __forceinline__ unsigned long long rhs_tile(const RhsArgs& a, int t, 
     if (cd == 1) {
       const double* c = st + y * MG_TX + x;
       s = h2 * fma(4.0, c[MG_TX], c[0] + c[2 * MG_TX]);
-    } else if (cd) {
+    } else {
       // the four cells' classes, then the cut cells' indices, each as one
       // batch of independent loads (three round trips to memory, not twelve)
       uint8_t cl4[4];
@@ -130,11 +162,7 @@ __device__ __forceinline__ unsigned long long rhs_tile(const RhsArgs& a, int t, 
         }
       }
     }
-    F[gk] = s;
-    // every f, g (and g_N) value that enters F_p is in s with a weight:
-    // a NaN or Inf among them (0 * Inf included) leaves s not finite
-    if (a.err != nullptr && !finite_bits(s)) atomicOr(a.err, DEV_ERR_NAN);
-    max_abs(vmax, s);
+    finish(gk, s);
   }
   return vmax;
 }
