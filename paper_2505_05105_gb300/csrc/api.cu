@@ -127,6 +127,7 @@ struct mg_ctx {
   // kernel launches through Launch so far, never reset: a band kernel's
   // launch number tells whether it is the launch directly before another
   unsigned long long seq = 1;
+  double* d_part = nullptr;     // per-tile partial sums of mg_residual's l2 norm
   struct Pend { int cls; cudaEvent_t a, b; };
   std::vector<Pend> pend;
   std::vector<cudaEvent_t> evpool;
@@ -1529,9 +1530,10 @@ int mg_residual(mg_handle c, const double* F, const double* u, double* r, double
   v.cur64 = 0;
   launch_pack<double>(v.L, v.code, su.dev, v.u64[0], c->d_err, c->st);
   MG_CUDA_TRY(cudaMemsetAsync(c->d_norms, 0, 2 * sizeof(double), c->st));
+  if (!c->d_part) TRY(dalloc(c, &c->d_part, (size_t)std::max(1, v.n_active)));
   OpArgs<double> op = op_of<double>(v);
   launch_residual<double, double>(op, v.active, v.n_active, v.u64[0], v.F64, v.u64[1], 1.0,
-                                  c->d_norms, c->st);
+                                  c->d_norms, c->st, true, c->d_part);
   if (r) {
     double* rd;
     bool rh;

@@ -189,6 +189,31 @@ __device__ __forceinline__ void block_norms_to_global(unsigned long long vmax, d
   }
 }
 
+// As block_norms_to_global, but the block's sum goes to *part (a slot of
+// its own) for a later fixed-order total (sum_partials): the same bits on
+// every run.
+__device__ __forceinline__ void block_norms_partial(unsigned long long vmax, double vsum,
+                                                    double* out, double* part) {
+  __shared__ unsigned long long p_max[32];
+  __shared__ double p_sum[32];
+  vmax = warp_max_bits(vmax);
+  vsum = warp_sum(vsum);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { p_max[w] = vmax; p_sum[w] = vsum; }
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    vmax = l < nw ? p_max[l] : 0ull;
+    vsum = l < nw ? p_sum[l] : 0.0;
+    vmax = warp_max_bits(vmax);
+    vsum = warp_sum(vsum);
+    if (l == 0) {
+      atomicMax(reinterpret_cast<unsigned long long*>(out), vmax);
+      *part = vsum;
+    }
+  }
+}
+
 // Programmatic dependent launch ---------------------------------------------
 //
 // The V-cycle kernels are launched with programmatic stream serialization:

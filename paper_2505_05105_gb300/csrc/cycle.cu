@@ -494,7 +494,7 @@ template <class T, class TR>
 __global__ void __launch_bounds__(kThreads)
 k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
            const T* __restrict__ F, TR* __restrict__ rout, T scale, double* __restrict__ norms,
-           int l2) {
+           int l2, double* __restrict__ part) {
   griddep_launch_next();
   griddep_wait();
   typedef typename Vec2<T>::type T2;
@@ -590,7 +590,27 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
     const size_t g = op.L.idx(gi, gj);
     finish(g, node_residual<T, RR_X>(op, sU + p, sC[p], F[g], gi, gj));
   }
-  if (norms) block_norms_to_global(vmax, vsum, norms);
+  if (norms) {
+    if (part) block_norms_partial(vmax, vsum, norms, part + blockIdx.x);
+    else block_norms_to_global(vmax, vsum, norms);
+  }
+}
+
+// norms[1] = the sum of part[0 .. n - 1] in a fixed order (one block)
+__global__ void __launch_bounds__(kThreads) k_sum_partials(const double* __restrict__ part, int n,
+                                                           double* __restrict__ norms) {
+  griddep_launch_next();
+  griddep_wait();
+  __shared__ double s[kThreads];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += kThreads) v += part[i];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) norms[1] = s[0];
 }
 
 template <class T>
@@ -1037,10 +1057,13 @@ void launch_touch_flags(int mode, const Layout& L, const uint16_t* code, const i
 
 template <class T, class TR>
 void launch_residual(const OpArgs<T>& op, const int* tiles, int ntiles, const T* u, const T* F,
-                     TR* rout, T scale, double* norms, cudaStream_t st, bool l2) {
+                     TR* rout, T scale, double* norms, cudaStream_t st, bool l2,
+                     double* part) {
   if (!ntiles) return;
+  if (!(norms && l2)) part = nullptr;
   launch_pdl(k_residual<T, TR>, ntiles, kThreads, 0, st, op, tiles, u, F, rout, scale, norms,
-             (int)l2);
+             (int)l2, part);
+  if (part) launch_pdl(k_sum_partials, 1, kThreads, 0, st, (const double*)part, ntiles, norms);
 }
 
 template <class T>
@@ -1137,10 +1160,10 @@ template void launch_band_rev<double>(const OpArgs<double>&, const int*, int, in
                                       const BandMaps&, int, unsigned*, unsigned, cudaStream_t);
 template void launch_residual<double, float>(const OpArgs<double>&, const int*, int, const double*,
                                              const double*, float*, double, double*, cudaStream_t,
-                                             bool);
+                                             bool, double*);
 template void launch_residual<double, double>(const OpArgs<double>&, const int*, int,
                                               const double*, const double*, double*, double,
-                                              double*, cudaStream_t, bool);
+                                              double*, cudaStream_t, bool, double*);
 
 // binds the bounds-checked build's device error word (see common.cuh)
 MG_BOUNDS_BINDER(bind_bounds_cycle)

@@ -105,9 +105,12 @@ void launch_touch_flags(int mode, const Layout& L, const uint16_t* code, const i
 template <class T, class TR>
 // norms[0] gets max |r| (atomic max); with l2 norms[1] gets sum r^2; rout
 // (if given) gets scale r -- for an fp32 rout, scale must be a power of two
-// (it is applied after the rounding to fp32)
+// (it is applied after the rounding to fp32).  part (ntiles doubles, or
+// nullptr): the l2 sum is taken through per-block partial sums added in a
+// fixed order, the same bits on every run (else by atomic adds).
 void launch_residual(const OpArgs<T>& op, const int* tiles, int ntiles, const T* u, const T* F,
-                     TR* rout, T scale, double* norms, cudaStream_t st, bool l2 = true);
+                     TR* rout, T scale, double* norms, cudaStream_t st, bool l2 = true,
+                     double* part = nullptr);
 template <class T>
 void launch_prolong(const OpArgs<T>& op, const int* tiles, int ntiles, T* uf, const Layout& Lc,
                     const T* ec, cudaStream_t st);

@@ -3,7 +3,8 @@
 // On the small levels (n <= 64 cells per side) every kernel of the V-cycle is
 // latency bound: a launch costs more than its work.  k_tail runs the whole
 // V-cycle below a given level (Alg. 1 applied recursively, Sec. 3.2) inside
-// one 1024-thread block, with every level's u, F and node tags in shared
+// one thread block (512 threads in fp32, 1024 in fp64), with every level's
+// u, F and node tags in shared
 // memory and __syncthreads() between the colour phases: for each level
 // nu1 smoothing steps (one 4-colour Gauss-Seidel sweep, Sec. 4.1, then eta
 // sweeps over the cut-cell vertices, Sec. 5.3), residual and restriction
@@ -22,12 +23,17 @@
 namespace {
 
 constexpr int kThreads = kTailThreads;
+// threads of k_tail: fp32 on 512 threads, which leaves the registers for the
+// band phases' rows (the fp64 rows would not fit: 1024 threads, rows read
+// from shared memory)
+template <class T> struct TailBlock { static constexpr int threads = 1024; };
+template <> struct TailBlock<float> { static constexpr int threads = 512; };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, 1) k_tail(TailArgs<T> a) {
+__global__ void __launch_bounds__(TailBlock<T>::threads, 1) k_tail(TailArgs<T> a) {
   griddep_launch_next();
   extern __shared__ __align__(128) unsigned char smem_dyn[];
-  tail_vcycle<T>(a, smem_align128(smem_dyn), a.load_u0 != 0, true);
+  tail_vcycle<T, sizeof(T) == sizeof(float)>(a, smem_align128(smem_dyn), a.load_u0 != 0, true);
 }
 
 // Setup: tags, colour-sorted boundary lists and their offsets of the image.
@@ -146,7 +152,7 @@ cudaError_t configure_tail(size_t smem) {
 
 template <class T>
 void launch_tail(const TailArgs<T>& a, cudaStream_t st) {
-  launch_pdl(k_tail<T>, 1, kThreads, a.lay.total, st, a);
+  launch_pdl(k_tail<T>, 1, TailBlock<T>::threads, a.lay.total, st, a);
 }
 
 template cudaError_t configure_tail<float>(size_t);

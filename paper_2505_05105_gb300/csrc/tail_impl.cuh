@@ -101,8 +101,9 @@ __device__ __forceinline__ void colour_phase(const Lvl<T>& v, int c, bool bounda
 
 // one smoothing step: the full 4-colour sweep, then the eta sweeps over the
 // cut-cell vertices on as many warps as the longest colour list needs, each
-// thread's nodes in registers
-template <class T>
+// thread's nodes in registers (REG: their rows too, for blocks small enough
+// to hold them)
+template <class T, bool REG = false>
 __device__ void smooth(const TailArgs<T>& a, const Smem<T>& s, int k) {
   const Lvl<T> v = level(s, k);
   for (int c = 0; c < 4; ++c) colour_phase(v, c, false);
@@ -112,12 +113,6 @@ __device__ void smooth(const TailArgs<T>& a, const Smem<T>& s, int k) {
   for (int c = 0; c < 4; ++c) mc = max(mc, v.o[c + 1] - v.o[c]);
   const int nw = min((int)(blockDim.x >> 5), max(1, (mc + 31) / 32));
   if ((int)(threadIdx.x >> 5) < nw) {
-    auto fetch = [&](int e, int& r, T& f, int& p) {
-      const int q = tail_pos(v.BL[e], v.S);
-      r = checked_row(v.G[q], v.nb);
-      f = v.F[q];
-      p = q;
-    };
     auto extra = [&](int e) {
       const int q = tail_pos(v.BL[e], v.S);
       const T* w = v.rows + (size_t)checked_row(v.G[q], v.nb) * MG_ROW;
@@ -127,7 +122,25 @@ __device__ void smooth(const TailArgs<T>& a, const Smem<T>& s, int k) {
               w[4] * Up[0] + w[5] * Up[1] + w[6] * Up[S - 1] + w[7] * Up[S] + w[8] * Up[S + 1];
       v.U[q] = Up[0] + (v.F[q] - acc) * w[9];
     };
-    band_phases_idx<T>(v.U, v.S, v.rows, v.o, a.eta, 32 * nw, fetch, extra);
+    if constexpr (REG) {
+      auto fetch = [&](int e, T* w, int& p) {
+        const int q = tail_pos(v.BL[e], v.S);
+        const T* R = v.rows + (size_t)checked_row(v.G[q], v.nb) * MG_ROW;
+#pragma unroll
+        for (int kk = 0; kk < MG_ROW; ++kk) w[kk] = R[kk];
+        w[MG_ROW] = v.F[q];
+        p = q;
+      };
+      band_phases_reg<T>(v.U, v.S, v.o, a.eta, 32 * nw, fetch, extra);
+    } else {
+      auto fetch = [&](int e, int& r, T& f, int& p) {
+        const int q = tail_pos(v.BL[e], v.S);
+        r = checked_row(v.G[q], v.nb);
+        f = v.F[q];
+        p = q;
+      };
+      band_phases_idx<T>(v.U, v.S, v.rows, v.o, a.eta, 32 * nw, fetch, extra);
+    }
   }
   __syncthreads();
 }
@@ -280,7 +293,7 @@ __device__ void coarsest(const Smem<T>& s, int k, size_t r_bytes) {
 // block.  load_u0: start from the top level's u in global memory (else from
 // zero; a.load_u0 is not read); load_image = false keeps the static image a
 // previous call of the same problem left in shared memory.
-template <class T>
+template <class T, bool REG = false>
 __device__ void tail_vcycle(const TailArgs<T>& a, unsigned char* smem_raw, bool load_u0,
                             bool load_image) {
   // order this block's earlier generic accesses of the shared memory before
@@ -373,13 +386,13 @@ __device__ void tail_vcycle(const TailArgs<T>& a, unsigned char* smem_raw, bool 
   if (threadIdx.x == 0) mbar_inval(&bar);
   if (!a.transposed) {
     for (int k = 0; k + 1 < K; ++k) {
-      for (int r = 0; r < a.nu1; ++r) smooth(a, s, k);
+      for (int r = 0; r < a.nu1; ++r) smooth<T, REG>(a, s, k);
       residual_restrict(s, k);
     }
     coarsest(s, K - 1, s_rbytes);
     for (int k = K - 2; k >= 0; --k) {
       prolong(s, k);
-      for (int r = 0; r < a.nu2; ++r) smooth(a, s, k);
+      for (int r = 0; r < a.nu2; ++r) smooth<T, REG>(a, s, k);
     }
   } else {
     // the transposed cycle: the same steps in the reverse order, each
