@@ -346,7 +346,8 @@ k_smooth_step(FusedArgs<float> a) {
   }
 
   // 4 eta phases on the cut-cell vertices only, on nw warps; each thread's
-  // node of every colour (position, F, staged row) stays in registers
+  // node of every colour (position, F and its row) stays in registers, and
+  // the stencil offsets of a colour are computed, not loaded
   if (a.eta > 0) {
     int g[5];
 #pragma unroll
@@ -357,18 +358,20 @@ k_smooth_step(FusedArgs<float> a) {
     const int nw = min(kWarps, max(1, (mc + 31) / 32));
     if (warp < nw) {
       const int nt = 32 * nw;
-      int q[4], r[4];
-      float fv[4];
+      int q[4];
+      float w[4][MG_ROW], fv[4];
       bool more = false;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int e = g[c] + threadIdx.x;
         q[c] = -1;
-        r[c] = 0;
         fv[c] = 0.f;
+#pragma unroll
+        for (int k = 0; k < MG_ROW; ++k) w[c][k] = 0.f;
         if (e < g[c + 1] && e < kRC) {
           q[c] = sP[e];
-          r[c] = e;
+#pragma unroll
+          for (int k = 0; k < MG_ROW; ++k) w[c][k] = sS[e * kRS + k];
           fv[c] = sF[c * PL + q[c]];
         }
         more |= g[c + 1] - g[c] > nt || g[c + 1] > kRC;
@@ -377,11 +380,15 @@ k_smooth_step(FusedArgs<float> a) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           if (q[c] >= 0) {
+            // neighbour (dx, dy) of colour c: as the table soff
             int off[9];
 #pragma unroll
-            for (int s = 0; s < 9; ++s) off[s] = soff[c][s];
+            for (int s = 0; s < 9; ++s) {
+              const int nx = (c & 1) + (s % 3) - 1, ny = (c >> 1) + (s / 3) - 1;
+              off[s] = ((ny & 1) * 2 + (nx & 1)) * PL + (ny >> 1) * PX + (nx >> 1);
+            }
             float* U = sU + q[c];
-            U[off[4]] = row_update(sS + r[c] * kRS, U, off, fv[c]);
+            U[off[4]] = row_update(w[c], U, off, fv[c]);
           }
           if (more)
             for (int e = g[c] + threadIdx.x; e < g[c + 1]; e += nt)
