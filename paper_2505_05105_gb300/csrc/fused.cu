@@ -131,7 +131,6 @@ k_smooth_step(FusedArgs<float> a) {
   int* sP = cv.sP;
   __shared__ int sTB[kTBX * kTBY];
   __shared__ int gs[6];
-  __shared__ int soff[4][9];            // stencil offsets (plane base + shift) per colour
   const Layout& L = a.L;
   const int n = L.n;
   const int t = a.tiles[blockIdx.x];
@@ -151,14 +150,6 @@ k_smooth_step(FusedArgs<float> a) {
     int ux = tx + threadIdx.x % kTBX - 1, uy = ty + threadIdx.x / kTBX - 2;
     sTB[threadIdx.x] =
         (ux >= 0 && uy >= 0 && ux < L.ntx && uy < L.nty) ? a.tile_base[uy * L.ntx + ux] : 0;
-  }
-  if (threadIdx.x < 36) {
-    // neighbour (dx, dy) of a node of colour c = px + 2 py: plane
-    // ((py + dy) & 1) * 2 + ((px + dx) & 1), row shift (py + dy) >> 1,
-    // column shift (px + dx) >> 1 (floor); s = (dx + 1) + 3 (dy + 1)
-    const int c = threadIdx.x / 9, s = threadIdx.x - 9 * (threadIdx.x / 9);
-    const int nx = (c & 1) + (s % 3) - 1, ny = (c >> 1) + (s / 3) - 1;
-    soff[c][s] = ((ny & 1) * 2 + (nx & 1)) * PL + (ny >> 1) * PX + (nx >> 1);
   }
   const int e0 = a.loff[5 * t];
   if (threadIdx.x < 6) gs[threadIdx.x] = a.loff[5 * t + threadIdx.x] - e0;
@@ -249,9 +240,15 @@ k_smooth_step(FusedArgs<float> a) {
 
   // one listed node (entry e, colour c), from shared memory when staged
   auto listed = [&](int c, int e) {
+    // neighbour (dx, dy) of a node of colour c = px + 2 py: plane
+    // ((py + dy) & 1) * 2 + ((px + dx) & 1), row shift (py + dy) >> 1,
+    // column shift (px + dx) >> 1 (floor); s = (dx + 1) + 3 (dy + 1)
     int off[9];
 #pragma unroll
-    for (int s = 0; s < 9; ++s) off[s] = soff[c][s];
+    for (int s = 0; s < 9; ++s) {
+      const int nx = (c & 1) + (s % 3) - 1, ny = (c >> 1) + (s / 3) - 1;
+      off[s] = ((ny & 1) * 2 + (nx & 1)) * PL + (ny >> 1) * PX + (nx >> 1);
+    }
     int q;
     float w[MG_ROW];
     if (e < kRC) {
@@ -380,7 +377,7 @@ k_smooth_step(FusedArgs<float> a) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           if (q[c] >= 0) {
-            // neighbour (dx, dy) of colour c: as the table soff
+            // neighbour (dx, dy) of colour c, as in listed()
             int off[9];
 #pragma unroll
             for (int s = 0; s < 9; ++s) {
@@ -425,7 +422,10 @@ k_smooth_step(FusedArgs<float> a) {
       if (cd) {
         int off[9];
 #pragma unroll
-        for (int s = 0; s < 9; ++s) off[s] = soff[c][s];
+        for (int s = 0; s < 9; ++s) {
+          const int nx = (c & 1) + (s % 3) - 1, ny = (c >> 1) + (s / 3) - 1;
+          off[s] = ((ny & 1) * 2 + (nx & 1)) * PL + (ny >> 1) * PX + (nx >> 1);
+        }
         const float* U = sU + q;
         const float f = sF[c * PL + q];
         if (cd == 1) {
