@@ -562,22 +562,27 @@ k_residual(OpArgs<T> op, const int* __restrict__ tiles, const T* __restrict__ u,
   // interior nodes here (unrolled so that several nodes' loads of F are in
   // flight at once); boundary nodes go to a list and are done after, a
   // thread each, so that their row products do not hold up whole warps
-  // (s_nl was cleared before the barrier above)
+  // (s_nl was cleared before the barrier above).  With the l2 sum they stay
+  // in place: the list's order varies from run to run, and so would the
+  // sum's last bits.
 #pragma unroll 4
   for (int it = threadIdx.x; it < MG_TY * MG_TX; it += blockDim.x) {
     int rr = it / MG_TX, ii = it - rr * MG_TX;
     int p = (rr + 2) * RR_X + ii + 2;
     uint16_t cd = sC[p];
-    if (cd >= 2) {
+    if (cd >= 2 && !l2) {
       s_list[atomicAdd(&s_nl, 1)] = (uint16_t)it;
       continue;
     }
-    size_t g = op.L.idx(i0 + ii, j0 + rr);
+    const int gi = i0 + ii, gj = j0 + rr;
+    size_t g = op.L.idx(gi, gj);
     T r = T(0);
     if (cd == 1) {
       const T* h = sH + it;                            // rows rr .. rr + 2 of sH
       const T box = (h[0] + h[MG_TX]) + h[2 * MG_TX];
       r = fma(fma(T(9), sU[p], -box), T(-1.0 / 3.0), F[g]);
+    } else if (cd >= 2) {
+      r = node_residual<T, RR_X>(op, sU + p, cd, F[g], gi, gj);
     }
     finish(g, r);
   }
