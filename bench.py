@@ -419,20 +419,37 @@ def run_ours(args):
             ent.update({"algorithmic_bytes_per_launch": per_launch_bytes[k],
                         "achieved_gbs": gbs, "frac": gbs / peak})
         kernel_roofline[k] = ent
-    coarse_ms = sum(slots[k][1] for k in ("levels", "fused", "tail", "coarse") if k in slots)
+    coarse_cls = ("levels", "levels_band", "levels_restrict", "fused", "tail", "coarse")
+    coarse_ms = sum(slots[k][1] for k in coarse_cls if k in slots)
     if coarse_ms > 0:
         gbs = per_step_bytes_coarse / (coarse_ms / args.steps / 1e3) / 1e9
         kernel_roofline["intermediate_levels_all"] = {
-            "classes": ["levels", "fused", "tail", "coarse"],
+            "classes": list(coarse_cls),
             "algorithmic_bytes_per_step": per_step_bytes_coarse, "achieved_gbs": gbs,
             "frac": gbs / peak, "level_dofs": lev_dofs}
-    dom = max((k for k in slots if slots[k][0] > 0), key=lambda k: slots[k][1])
+    # the dominant kernel: device time per kernel function over all the
+    # levels it runs on; its roofline is that of its largest (fine-level)
+    # launches, whose bytes are modelled and whose traffic ncu measured
+    kernel_classes = {"k_gs_sweep_f32": ("sweep", "levels"),
+                      "k_band<float>": ("band", "levels_band"),
+                      "k_resid_restrict_f32": ("restrict", "levels_restrict"),
+                      "k_smooth_step": ("fused",), "k_tail<float>": ("tail",),
+                      "k_residual<double,float>": ("residual",), "k_update": ("update",),
+                      "k_rhs, k_pack, k_unpack": ("io",), "k_prolong": ("prolong",),
+                      "coarsest solve": ("coarse",)}
+    kernel_ms = {kn: sum(slots[c][1] for c in cls if c in slots)
+                 for kn, cls in kernel_classes.items()}
+    dom_kernel = max(kernel_ms, key=kernel_ms.get)
+    dom = next((c for c in kernel_classes[dom_kernel] if c in slots and slots[c][0] > 0),
+               kernel_classes[dom_kernel][0])
     n_launch, dom_ms = slots[dom]
     per_launch_s = dom_ms / n_launch / 1e3
     names = {"sweep": "k_gs_sweep_f32 (fine level)", "band": "k_band<float> (fine level)",
-             "restrict": "k_resid_restrict<float> (fine level)",
+             "restrict": "k_resid_restrict_f32 (fine level)",
              "residual": "k_residual<double,float> (fp64 refinement residual)",
-             "update": "k_update", "levels": "separate kernels of the intermediate levels",
+             "update": "k_update", "levels": "k_gs_sweep_f32 (intermediate levels)",
+             "levels_band": "k_band<float> (intermediate levels)",
+             "levels_restrict": "k_resid_restrict_f32 (intermediate levels)",
              "fused": "k_smooth_step (fused smoothing steps)", "tail": "k_tail<float>",
              "coarse": "coarsest solve", "io": "right-hand side, pack, unpack",
              "prolong": "k_prolong"}
@@ -447,7 +464,10 @@ def run_ours(args):
     traffic = profile_traffic(f"{dom}_f32_flower{N}", dom)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": names.get(dom, dom),
-                "class": dom, "algorithmic_bytes_per_launch": algo, "launches": n_launch,
+                "class": dom, "dominant_kernel": dom_kernel,
+                "dominant_kernel_share": kernel_ms[dom_kernel] / total_ms,
+                "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items() if v > 0},
+                "algorithmic_bytes_per_launch": algo, "launches": n_launch,
                 "avg_launch_us": per_launch_s * 1e6, "peak_source": f"{peak_src} hbm_gbs",
                 "timing": f"CUDA events around each launch on the solver stream, over {args.steps} "
                           "profiled solves run after the timed ones"}

@@ -395,12 +395,13 @@ enum {
   MG_PROF_COARSE = 6,    /* other coarse-level kernels (coarsest solve,
                             the fp64 transposed cycle) */
   MG_PROF_IO = 7,        /* right-hand side, input checks, pack/unpack */
-  MG_PROF_LEVELS = 8,    /* sweeps, extra sweeps, restriction, prolongation
-                            on the levels between the finest and the tail
-                            that do not run fused steps */
+  MG_PROF_LEVELS = 8,    /* sweeps on the levels between the finest and the
+                            tail that do not run fused steps */
   MG_PROF_FUSED = 9,     /* fused smoothing steps (fp32 intermediate levels) */
   MG_PROF_TAIL = 10,     /* the single-block V-cycle of the smallest levels */
-  MG_PROF_SLOTS = 11
+  MG_PROF_LEVELS_BAND = 11,      /* extra sweeps on those levels */
+  MG_PROF_LEVELS_RESTRICT = 12,  /* residual + restriction, prolongation there */
+  MG_PROF_SLOTS = 13
 };
 
 /* enable != 0: clear the accumulators and start recording; 0: stop. */

@@ -462,7 +462,7 @@ void smooth(mg_ctx* c, Level& v, bool zero_in, bool fine, Level* coarse = nullpt
   }
   cur ^= 1;
   if (eta > 0 && v.n_band > 0) {
-    Launch k(c, fine ? MG_PROF_BAND : MG_PROF_LEVELS, 1);
+    Launch k(c, fine ? MG_PROF_BAND : MG_PROF_LEVELS_BAND, 1);
     launch_band<T>(op, v.band, v.n_band, v.nbx, eta, P<T>::u(v, cur), P<T>::F(v), P<T>::bval(v),
                    v.band_off, v.band_ent, v.bmap[sizeof(T) == 8 ? 1 : 0], cur, c->d_err,
                    c->wait_polls, c->st);
@@ -592,7 +592,7 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
   OpArgs<T> op = op_of<T>(v);
   {
     const uint8_t* touch = v.band_seq == c->seq ? v.rr_touch : nullptr;
-    Launch k(c, fine ? MG_PROF_RESTRICT : MG_PROF_LEVELS, w.n_active > 0);
+    Launch k(c, fine ? MG_PROF_RESTRICT : MG_PROF_LEVELS_RESTRICT, w.n_active > 0);
     launch_resid_restrict<T>(op, P<T>::u(v, cur), P<T>::F(v), w.L, w.active, w.n_active,
                              P<T>::F(w), nullptr, c->st, touch);
   }
@@ -600,7 +600,7 @@ void vcycle(mg_ctx* c, int l, bool zero_init) {
   const int gs = coarse_cycles(c, l);
   for (int k = 0; k < gs; ++k) vcycle<T>(c, l + 1, k == 0);
   if (c->stab.nu2 == 0) {
-    Launch k(c, fine ? MG_PROF_PROLONG : MG_PROF_LEVELS, v.n_active > 0);
+    Launch k(c, fine ? MG_PROF_PROLONG : MG_PROF_LEVELS_RESTRICT, v.n_active > 0);
     launch_prolong<T>(op, v.active, v.n_active, P<T>::u(v, cur), w.L, P<T>::u(w, P<T>::cur(w)),
                       c->st);
   }

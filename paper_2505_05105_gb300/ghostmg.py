@@ -138,7 +138,7 @@ SIGNATURES = {
 }
 
 PROF_SLOTS = ("sweep", "band", "restrict", "prolong", "residual", "update", "coarse", "io",
-              "levels", "fused", "tail")
+              "levels", "fused", "tail", "levels_band", "levels_restrict")
 
 _lib = None
 
