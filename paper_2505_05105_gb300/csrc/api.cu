@@ -1819,9 +1819,49 @@ bool build_window(const std::vector<int2>& bl, int P, size_t avail, std::vector<
   return true;
 }
 
+// The static image of the resident eta phases of one level for block `rank`
+// of nr (batch.cu, eta_resident): rows (srows: n entries by coefficient),
+// positions (blist) and the window indices of the three stencil rows (slot:
+// 10 per entry) of the entries j = k nr + rank of each colour group (boff),
+// laid out as eta_resident_layout places them from `rows` to `f`.
+std::vector<unsigned char> eta_image(int win_n, const int* boff, int nr, int rank,
+                                     const std::vector<float>& srows, int n,
+                                     const std::vector<int2>& blist,
+                                     const std::vector<uint16_t>& slot) {
+  int lb[5], le = 0;
+  lb[0] = 0;
+  for (int c = 0; c < 4; ++c) {
+    const int cnt = boff[c + 1] - boff[c];
+    le += (cnt + nr - 1) / nr;
+    lb[c + 1] = lb[c] + (cnt - rank + nr - 1) / nr;
+  }
+  const EtaResidentLayout lay = eta_resident_layout(win_n, le);
+  std::vector<unsigned char> img(lay.f - lay.rows, 0);
+  float* R = reinterpret_cast<float*>(img.data());
+  int* P = reinterpret_cast<int*>(img.data() + (lay.pos - lay.rows));
+  uint16_t* S = reinterpret_cast<uint16_t*>(img.data() + (lay.slot - lay.rows));
+  // each colour group in the order of the padded offsets, so that a warp's
+  // vertices lie close together in the window (the order of the updates in a
+  // colour phase is free: vertices of one colour are not stencil neighbours)
+  std::vector<int> ord((size_t)boff[4]);
+  for (int e = 0; e < boff[4]; ++e) ord[e] = e;
+  for (int c = 0; c < 4; ++c)
+    std::sort(ord.begin() + boff[c], ord.begin() + boff[c + 1],
+              [&](int x, int y) { return blist[x].x < blist[y].x; });
+  for (int c = 0; c < 4; ++c)
+    for (int k = 0; k < lb[c + 1] - lb[c]; ++k) {
+      const int x = lb[c] + k, e = ord[boff[c] + k * nr + rank];
+      for (int r = 0; r < MG_ROW; ++r) R[(size_t)r * le + x] = srows[(size_t)r * n + e];
+      P[x] = blist[e].x;
+      for (int q = 0; q < 3; ++q) S[(size_t)q * le + x] = slot[(size_t)e * 10 + 3 * q];
+    }
+  return img;
+}
+
 // the device table entry of one member (its hierarchy is set up, mixed);
-// win_bytes: shared memory the member's eta windows may use
-int batch_member(mg_batch_ctx* b, int p, BatchProblem* out, size_t win_bytes) {
+// win_bytes: shared memory the member's eta windows may use; res_cap: the
+// shared memory of the resident eta phases
+int batch_member(mg_batch_ctx* b, int p, BatchProblem* out, size_t win_bytes, size_t res_cap) {
   mg_ctx* c = b->mem[p];
   const int t = c->tail_level;
   if (t < 0 || t > MG_BATCH_MAX_TOP) return MG_ERR_UNIMPLEMENTED;
@@ -1871,6 +1911,25 @@ int batch_member(mg_batch_ctx* b, int p, BatchProblem* out, size_t win_bytes) {
       w.win = dw;
       w.wslot = ds;
       w.win_n = (int)hw.size();
+    }
+    w.rimg[0] = w.rimg[1] = w.rimg[2] = nullptr;
+    if (w.win_n > 0) {
+      const bool one = eta_resident_bytes(w.win_n, w.boff, 1) <= res_cap;
+      if (one || eta_resident_bytes(w.win_n, w.boff, 2) <= res_cap) {
+        std::vector<float> hr((size_t)v.n_bnd * MG_ROW);
+        MG_CUDA_TRY(cudaMemcpyAsync(hr.data(), srows, hr.size() * sizeof(float),
+                                    cudaMemcpyDeviceToHost, c->st));
+        MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+        for (int k = one ? 0 : 1; k < (one ? 1 : 3); ++k) {
+          const std::vector<unsigned char> img =
+              eta_image(w.win_n, w.boff, one ? 1 : 2, one ? 0 : k - 1, hr, v.n_bnd, hb, hs);
+          unsigned char* d;
+          TRY(dalloc(c, &d, img.size()));
+          MG_CUDA_TRY(cudaMemcpyAsync(d, img.data(), img.size(), cudaMemcpyHostToDevice, c->st));
+          MG_CUDA_TRY(cudaStreamSynchronize(c->st));
+          w.rimg[k] = d;
+        }
+      }
     }
     w.L = v.L;
     w.code = v.code;
@@ -2126,11 +2185,24 @@ int batch_setup_impl(mg_batch_ctx* b, const mg_grid* grids, const double* levels
   std::vector<int> tile_off(n + 1, 0);
   size_t smem = 0;
   for (int p = 0; p < n; ++p) smem = std::max(smem, (size_t)b->mem[p]->tail_lay[0].total);
+  // The resident eta phases take what the block's shared memory allows
+  // without a larger carve-out (which would shrink the L1 cache the level
+  // sweeps read through): 192 KB, or the tail's own need if larger.
+  {
+    int dev = 0, optin = 0;
+    MG_CUDA_TRY(cudaGetDevice(&dev));
+    MG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t target = 192 * 1024;                 // usable bytes, the slack apart
+    const size_t limit = (size_t)optin > 4096 + kSmemSlack ? (size_t)optin - 4096 - kSmemSlack : 0;
+    smem = std::max(smem, std::min(target, limit));
+  }
   for (int p = 0; p < n; ++p) {
     // the eta windows live in the tail's dynamic region, up to the end of
     // the batch's shared memory
     const size_t start = b->mem[p]->tail_lay[0].U[0];
-    TRY(batch_member(b, p, &probs[p], smem - kSmemSlack > start ? smem - kSmemSlack - start : 0));
+    TRY(batch_member(b, p, &probs[p], smem - kSmemSlack > start ? smem - kSmemSlack - start : 0,
+                     smem - kSmemSlack));
+    probs[p].res_cap = (int)(smem - kSmemSlack);
     tile_off[p + 1] = tile_off[p] + probs[p].n_active0;
   }
   b->total_tiles = tile_off[n];

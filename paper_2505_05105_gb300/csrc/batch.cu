@@ -62,6 +62,13 @@ __device__ __forceinline__ void dsmem_store_u32(void* p, unsigned rank, unsigned
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
 }
 
+// stores v into block `rank`'s shared word at the shared-window address a
+__device__ __forceinline__ void dsmem_store_f32(unsigned a, unsigned rank, float v) {
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ void dsmem_store_f64(void* p, unsigned rank, double v) {
   unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
@@ -182,21 +189,30 @@ __device__ __forceinline__ void colour_interior(const BatchLevel& v, int ci, int
   }
 }
 
-// Rows of the listed boundary nodes are read from a copy laid out by
-// coefficient (R[k * n + e] for list entry e of n), so that a warp's loads of
-// one coefficient are contiguous.  The expressions are those of row_apply.
-__device__ __forceinline__ float row_apply_soa(const float* __restrict__ R, int n, const float* U,
-                                               int P) {
-  return __ldg(R) * U[-P - 1] + __ldg(R + n) * U[-P] + __ldg(R + 2 * n) * U[-P + 1] +
-         __ldg(R + 3 * n) * U[-1] + __ldg(R + 4 * n) * U[0] + __ldg(R + 5 * n) * U[1] +
-         __ldg(R + 6 * n) * U[P - 1] + __ldg(R + 7 * n) * U[P] + __ldg(R + 8 * n) * U[P + 1];
+// The Gauss-Seidel update of one cut-cell vertex in the eta phases from its
+// row R (9 coefficients in row order, then the inverse diagonal), the 9
+// stencil values x (row order) and its right-hand side f.  Every eta path
+// evaluates this one expression, so that the result does not depend on the
+// path a launch shape selects.
+__device__ __forceinline__ float eta_row(const float (&R)[10], const float (&x)[9], float f) {
+  const float acc = R[0] * x[0] + R[1] * x[1] + R[2] * x[2] + R[3] * x[3] + R[4] * x[4] +
+                    R[5] * x[5] + R[6] * x[6] + R[7] * x[7] + R[8] * x[8];
+  return x[4] + (f - acc) * R[9];
 }
 
-__device__ __forceinline__ void row_update_soa(float* u, int g, const float* __restrict__ R, int n,
+// Rows of the listed boundary nodes are read from a copy laid out by
+// coefficient (R[k * n + e] for list entry e of n), so that a warp's loads of
+// one coefficient are contiguous.
+__device__ __forceinline__ void row_update_eta(float* u, int g, const float* __restrict__ R, int n,
                                                float f, int P) {
   const float* U = u + g;
-  const float acc = row_apply_soa(R, n, U, P);
-  u[g] = U[0] + (f - acc) * __ldg(R + 9 * n);
+  float r[10], x[9];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) r[k] = __ldg(R + k * n);
+  const int d[9] = {-P - 1, -P, -P + 1, -1, 0, 1, P - 1, P, P + 1};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) x[k] = U[d[k]];
+  u[g] = eta_row(r, x, f);
 }
 
 // The same update on values held in a shared-memory window: sl[k] is the
@@ -206,11 +222,139 @@ __device__ __forceinline__ void row_update_win(float* w, const uint16_t* __restr
   uint16_t q[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) q[k] = __ldg(sl + k);
-  const float acc = __ldg(R) * w[q[0]] + __ldg(R + n) * w[q[1]] + __ldg(R + 2 * n) * w[q[2]] +
-                    __ldg(R + 3 * n) * w[q[3]] + __ldg(R + 4 * n) * w[q[4]] +
-                    __ldg(R + 5 * n) * w[q[5]] + __ldg(R + 6 * n) * w[q[6]] +
-                    __ldg(R + 7 * n) * w[q[7]] + __ldg(R + 8 * n) * w[q[8]];
-  w[q[4]] = w[q[4]] + (f - acc) * __ldg(R + 9 * n);
+  float r[10], x[9];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) r[k] = __ldg(R + k * n);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) x[k] = w[q[k]];
+  w[q[4]] = eta_row(r, x, f);
+}
+
+// The eta phases of a level (Sec. 5.3) in shared memory.  A block holds the
+// window (the cut-cell vertices and their neighbours, gathered from u), the
+// right-hand sides of its vertices (gathered from F) and their static image,
+// built at setup and brought in by one bulk copy: their rows, positions and
+// the window indices of their three stencil rows (the three nodes of a
+// stencil row are consecutive in the sorted window).  With the solo image
+// the lead block does every vertex (a phase ends on its block barrier; the
+// team waits at the caller's team barrier).  With the pair images, in a team
+// of two blocks, each block holds the whole window and the vertices j mod 2 =
+// rank of each colour group: a vertex's new value goes to both windows (the
+// other's through distributed shared memory) and each phase ends on the team
+// barrier, which orders those stores before the next phase's loads.  At the
+// end the vertices are written back to u.  Returns false, doing nothing,
+// when the level has no image for this team; when it returns true, the
+// tail's static image in the same shared memory is gone.
+__device__ bool eta_resident(const BatchLevel& v, int eta, const Team& tm, unsigned char* smem,
+                             int cap, unsigned* err) {
+  const bool solo = v.rimg[0] != nullptr;
+  if (!solo && !(tm.nr == 2 && v.rimg[1] != nullptr)) return false;
+  const int nr = solo ? 1 : 2;
+  if (v.win_n <= 0 || eta_resident_bytes(v.win_n, v.boff, nr) > (size_t)cap) return false;
+  if (solo && tm.rank != 0) return true;
+  const int rank = solo ? 0 : tm.rank;
+  auto sync = [&]() {
+    if (solo) __syncthreads();
+    else team_sync(tm);
+  };
+  int lb[5], le = 0;
+  lb[0] = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int cnt = v.boff[c + 1] - v.boff[c];
+    le += (cnt + nr - 1) / nr;
+    lb[c + 1] = lb[c] + (cnt - rank + nr - 1) / nr;   // entries j = k nr + rank < cnt
+  }
+  const EtaResidentLayout lay = eta_resident_layout(v.win_n, le);
+  const unsigned char* img = v.rimg[solo ? 0 : 1 + rank];
+  float* sw = reinterpret_cast<float*>(smem);
+  const float* sR = reinterpret_cast<const float*>(smem + lay.rows);
+  const int* sP = reinterpret_cast<const int*>(smem + lay.pos);
+  const uint16_t* sS = reinterpret_cast<const uint16_t*>(smem + lay.slot);
+  float* sF = reinterpret_cast<float*>(smem + lay.f);
+  const int* gP = reinterpret_cast<const int*>(img + (lay.pos - lay.rows));
+  __shared__ uint64_t bar;
+  __shared__ int bad;
+  // earlier generic accesses of this shared memory before the bulk copy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    const size_t bytes = lay.f - lay.rows;
+    bad = !bulk_ok(smem + lay.rows, img, bytes);
+    if (bad) {
+      atomicOr(err, DEV_ERR_ALIGN);
+      mbar_arrive_expect_tx(&bar, 0);
+    } else {
+      mbar_arrive_expect_tx(&bar, (uint32_t)bytes);
+      for (size_t o = 0; o < bytes; o += 65536) {
+        const size_t n = bytes - o < 65536 ? bytes - o : 65536;
+        bulk_load(smem + lay.rows + o, img + o, (uint32_t)n, &bar);
+      }
+    }
+  }
+  // meanwhile the window and the right-hand sides, 8 nodes per thread in
+  // flight
+  constexpr int GU = 8;
+  const int ng = v.win_n + lb[4];
+  for (int k0 = threadIdx.x; k0 < ng; k0 += GU * blockDim.x) {
+    int a[GU];
+#pragma unroll
+    for (int q = 0; q < GU; ++q) {
+      const int k = k0 + q * blockDim.x;
+      a[q] = k < v.win_n ? __ldg(v.win + k) : k < ng ? __ldg(gP + (k - v.win_n)) : -1;
+    }
+    float x[GU];
+#pragma unroll
+    for (int q = 0; q < GU; ++q) {
+      const int k = k0 + q * blockDim.x;
+      x[q] = a[q] < 0 ? 0.f : k < v.win_n ? v.u[a[q]] : v.F[a[q]];
+    }
+#pragma unroll
+    for (int q = 0; q < GU; ++q) {
+      const int k = k0 + q * blockDim.x;
+      if (a[q] >= 0) {
+        if (k < v.win_n) sw[k] = x[q];
+        else sF[k - v.win_n] = x[q];
+      }
+    }
+  }
+  const bool ok = mbar_wait(&bar, 0, kMbarSpinLimit);
+  const bool fail = __syncthreads_or(!ok || bad) != 0;
+  if (threadIdx.x == 0) {
+    if (!ok) {
+      atomicOr(err, DEV_ERR_TIMEOUT);
+      mbar_wait(&bar, 0);        // bounded: let copies still in flight land
+    }
+    mbar_inval(&bar);
+  }
+  // every block's window complete before any block's first update lands in it
+  sync();
+  const unsigned swa = (unsigned)__cvta_generic_to_shared(sw);
+  for (int it = 0; it < eta; ++it) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      for (int x = lb[c] + threadIdx.x; x < lb[c + 1] && !fail; x += blockDim.x) {
+        const int b0 = sS[x], b1 = sS[le + x], b2 = sS[2 * le + x];
+        float r[10], xv[9];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) r[k] = sR[k * le + x];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          xv[k] = sw[b0 + k];
+          xv[3 + k] = sw[b1 + k];
+          xv[6 + k] = sw[b2 + k];
+        }
+        const float nv = eta_row(r, xv, sF[x]);
+        sw[b1 + 1] = nv;
+        if (!solo) dsmem_store_f32(swa + 4u * (unsigned)(b1 + 1), (unsigned)(rank ^ 1), nv);
+      }
+      sync();
+    }
+  }
+  if (!fail)
+    for (int x = threadIdx.x; x < lb[4]; x += blockDim.x) v.u[sP[x]] = sw[sS[le + x] + 1];
+  return true;
 }
 
 // One smoothing step of a level in global memory (Sec. 4.1, Sec. 5.3): four
@@ -223,9 +367,12 @@ __device__ __forceinline__ void row_update_win(float* w, const uint16_t* __restr
 // (sw): the cut-cell vertices and their neighbours are gathered once, the
 // phases update the window (only the vertices change: their neighbours that
 // are not vertices are constant during these phases), and the vertices are
-// written back.
+// written back.  The eta phases run on every block of the team from shared
+// memory (eta_resident) where the level's data fit in cap bytes; the return
+// value says whether they did (the tail's image at smem is then gone).
 template <int kU>
-__device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm, float* sw) {
+__device__ bool smooth_level(const BatchLevel& v, int eta, const Team& tm, float* sw,
+                             unsigned char* smem, int cap, unsigned* err) {
   const int P = v.L.pitch;
   const bool lead = tm.rank == 0;
   int mc = 0;
@@ -248,11 +395,11 @@ __device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm, float
     }
   }
   auto listed = [&](int c, int stride) {
-    if (pos[c] >= 0) row_update_soa(v.u, pos[c], v.srows + v.boff[c] + threadIdx.x, nb, fv[c], P);
+    if (pos[c] >= 0) row_update_eta(v.u, pos[c], v.srows + v.boff[c] + threadIdx.x, nb, fv[c], P);
     if (more)
       for (int e = v.boff[c] + nt + threadIdx.x; e < v.boff[c + 1]; e += stride) {
         const int g = __ldg(v.blist + e).x;
-        row_update_soa(v.u, g, v.srows + e, nb, v.F[g], P);
+        row_update_eta(v.u, g, v.srows + e, nb, v.F[g], P);
       }
   };
 #pragma unroll
@@ -261,7 +408,8 @@ __device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm, float
     if (own) listed(c, nt);
     team_sync(tm);
   }
-  if (eta > 0 && v.win_n > 0) {
+  const bool resident = eta > 0 && eta_resident(v, eta, tm, smem, cap, err);
+  if (!resident && eta > 0 && v.win_n > 0) {
     if (lead) {
       // gather: 8 nodes per thread in flight
       constexpr int GU = 8;
@@ -311,7 +459,7 @@ __device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm, float
           if (g[k] >= 0) v.u[g[k]] = sw[q[k]];
       }
     }
-  } else if (eta > 0 && own) {
+  } else if (!resident && eta > 0 && own) {
     for (int it = 0; it < eta; ++it)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -321,6 +469,7 @@ __device__ void smooth_level(const BatchLevel& v, int eta, const Team& tm, float
       }
   }
   if (eta > 0) team_sync(tm);
+  return resident;
 }
 
 __device__ void zero_level(const BatchLevel& v, const Team& tm) {
@@ -435,11 +584,12 @@ __device__ void prolong_level(const BatchLevel& v, const Layout& Lc, const float
   team_sync(tm);
 }
 
-// One fp32 V-cycle of problem p on the correction equation.  load_image: the
-// tail's static image is not yet in the lead block's shared memory.
+// One fp32 V-cycle of problem p on the correction equation.  image_ok: the
+// tail's static image is in the lead block's shared memory (the tail loads it
+// otherwise; resident eta phases overwrite it).
 template <int kU>
 __device__ void vcycle(const BatchProblem& p, bool zero_init, unsigned char* smem,
-                       bool load_image, const Team& tm) {
+                       bool& image_ok, const Team& tm) {
   // the eta windows use the tail's dynamic region (rewritten by every tail call)
   float* sw = reinterpret_cast<float*>(smem + p.tail.lay.U[0]);
   for (int l = 0; l < p.n_top; ++l) {
@@ -448,7 +598,8 @@ __device__ void vcycle(const BatchProblem& p, bool zero_init, unsigned char* sme
       zero_level(v, tm);
       team_sync(tm);
     }
-    for (int s = 0; s < p.nu1; ++s) smooth_level<kU>(v, p.eta, tm, sw);
+    for (int s = 0; s < p.nu1; ++s)
+      if (smooth_level<kU>(v, p.eta, tm, sw, smem, p.res_cap, p.tail.err)) image_ok = false;
     if (l + 1 < p.n_top) {
       const BatchLevel& w = p.lev[l + 1];
       resid_restrict_level<kU>(v, w.L, w.xy, w.n_active, w.F, tm);
@@ -457,14 +608,16 @@ __device__ void vcycle(const BatchProblem& p, bool zero_init, unsigned char* sme
       resid_restrict_level<kU>(v, p.tail.L0, p.tail_xy, p.tail_n_active, p.tail_F, tm);
     }
   }
-  if (tm.rank == 0) tail_vcycle<float>(p.tail, smem, p.n_top == 0 && !zero_init, load_image);
+  if (tm.rank == 0) tail_vcycle<float>(p.tail, smem, p.n_top == 0 && !zero_init, !image_ok);
+  image_ok = true;
   team_sync(tm);
   for (int l = p.n_top - 1; l >= 0; --l) {
     const BatchLevel& v = p.lev[l];
     const bool next_top = l + 1 < p.n_top;
     prolong_level<kU>(v, next_top ? p.lev[l + 1].L : p.tail.L0,
                   next_top ? p.lev[l + 1].u : p.tail.u0, tm);
-    for (int s = 0; s < p.nu2; ++s) smooth_level<kU>(v, p.eta, tm, sw);
+    for (int s = 0; s < p.nu2; ++s)
+      if (smooth_level<kU>(v, p.eta, tm, sw, smem, p.res_cap, p.tail.err)) image_ok = false;
   }
 }
 
@@ -557,11 +710,12 @@ __device__ void solve_member(const BatchProblem& p, int pi, const unsigned* bad,
     }
     team_sync(tm);
     rel = 1.0;
+    bool image_ok = false;                     // the tail's image is not loaded yet
     int kk = fixed > 0 ? fixed : first_group;
     while (rel > tol) {
       if (cycles >= max_cycles) { status = MG_ERR_NOT_CONVERGED; break; }
       kk = min(kk, max_cycles - cycles);
-      for (int s = 0; s < kk; ++s) vcycle<kU>(p, s == 0, smem, cycles + s == 0, tm);
+      for (int s = 0; s < kk; ++s) vcycle<kU>(p, s == 0, smem, image_ok, tm);
       cycles += kk;
       // u += e / sigma on the DOFs (same arithmetic as k_update)
       const double inv = 1.0 / sigma;

@@ -25,13 +25,45 @@ struct BatchLevel {
   const int* win;
   const uint16_t* wslot;
   int win_n;
+  // static images of the resident eta phases (eta_resident_layout from
+  // `rows` to `f`, or null): [0] the lead block alone, [1], [2] blocks 0 and 1
+  // of a team of two
+  const unsigned char* rimg[3];
   float* u;                    // iterate (in place)
   float* F;                    // right-hand side
   float* scr;                  // residual scratch (zero outside the active tiles)
 };
 
+// Shared memory of the resident eta phases of one level (batch.cu,
+// eta_resident) for le entries per block: the window (win_n floats), then per
+// entry its row (10 floats, by coefficient), position and the window indices
+// of its three stencil rows (by row) -- the static image, one bulk copy --
+// and its right-hand side.
+struct EtaResidentLayout {
+  size_t rows, pos, slot, f, total;
+};
+__host__ __device__ inline size_t eta_a16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline EtaResidentLayout eta_resident_layout(int win_n, int le) {
+  EtaResidentLayout l;
+  l.rows = eta_a16((size_t)win_n * sizeof(float));
+  l.pos = l.rows + eta_a16((size_t)le * 10 * sizeof(float));
+  l.slot = l.pos + eta_a16((size_t)le * sizeof(int));
+  l.f = l.slot + eta_a16((size_t)le * 3 * sizeof(uint16_t));
+  l.total = l.f + eta_a16((size_t)le * sizeof(float));
+  return l;
+}
+// bytes for a level with colour group offsets boff (5) shared by nr blocks
+// (entry j of a group to block j mod nr; the layout is that of the block
+// with the most entries)
+__host__ __device__ inline size_t eta_resident_bytes(int win_n, const int* boff, int nr) {
+  int le = 0;
+  for (int c = 0; c < 4; ++c) le += (boff[c + 1] - boff[c] + nr - 1) / nr;
+  return eta_resident_layout(win_n, le).total;
+}
+
 struct BatchProblem {
   int n_top;                   // levels 0 .. n_top-1 block-wide, the tail from level n_top
+  int res_cap;                 // shared memory the resident eta phases may use (bytes)
   BatchLevel lev[MG_BATCH_MAX_TOP];
   TailArgs<float> tail;        // the tail block's V-cycle (its top F and u: level n_top)
   const unsigned* tail_xy;     // active tiles of the tail's top level (i0 | j0 << 16)
