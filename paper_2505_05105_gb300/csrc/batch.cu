@@ -293,6 +293,8 @@ __device__ bool eta_resident(const BatchLevel& v, int eta, const Team& tm, unsig
       }
     }
   }
+  // the barrier initialised (and `bad` set) before any thread waits on it
+  __syncthreads();
   // meanwhile the window and the right-hand sides, 8 nodes per thread in
   // flight
   constexpr int GU = 8;
