@@ -14,7 +14,11 @@ leave the others bit for bit as in a clean batch; graph replays, host and
 device arrays and the zero-copy buffers give identical results; results do
 not depend on the block size; the autotuner returns a converging choice.
 The full-size case is the seeded 256-member batch (ellipses and flowers,
-N in {64, 128, 256, 512}) in the launch configuration bench.py times.
+N in {64, 128, 256, 512}) in the launch configuration bench.py times.  The
+batched fp32 V-cycle is also held to the oracle iterate by iterate (one
+refinement step against the oracle's fp64 V-cycles, within the fp32 step
+bound of test_gpu_mixed_parity.py) in launch shapes that select each of its
+eta paths.
 """
 import numpy as np
 import pytest
@@ -297,3 +301,58 @@ def test_batch_with_neumann_masks_and_box_sides():
         assert info[k].n_dof == int(s.dof.sum())
         assert_solution(out[k], gf.direct_solve(s, F), s, F, 1e-9, what=p.name)
 
+
+
+@pytest.fixture(scope="module")
+def step_members():
+    """Members for the step test and the oracle's V-cycles on them: the
+    7-petal flower at 512^2 (4576 cut-cell vertices on its finest level: more
+    eta data than one block's shared memory holds, so a team of two splits
+    them), the three discs at 256^2 and the flower at 128^2 (their levels'
+    eta data fit one block)."""
+    from oracle import multigrid as mg
+    ps = [wl.flower(512, k=7, phase=0.3), wl.three_discs(256, seed=0), wl.flower(128)]
+    out = []
+    for p in ps:
+        s = gf.assemble_problem(p)
+        lev = mg.build_hierarchy(s)
+        F = s.rhs(p.f, p.g)
+        refs = {}
+        u = np.zeros(s.n_nodes)
+        for k in (1, 2):
+            u = mg.mg_cycle(lev, 0, u, F, nu1=2, nu2=1, eta=4, order="color4")
+            refs[k] = u.copy()
+        out.append((p, s, F, refs))
+    return out
+
+
+@pytest.mark.parametrize("shape", [(1024, 4, 2, 0), (1024, 4, 1, 0), (512, 4, 4, 0)],
+                         ids=["pairs", "single_blocks", "clusters_of_4"])
+def test_batched_step_iterates(shape, step_members):
+    """The batched kernel's fp32 V-cycle held to the oracle iterate by
+    iterate: a batch solve stopped after its first refinement step (a fixed
+    group of `inner` fp32 V(2,1)-cycles on A e = sigma F from e = 0, then
+    u = e / sigma) equals `inner` fp64 V-cycles of the oracle from u = 0
+    (oracle.multigrid.mg_cycle: Sec. 4.1 smoother, Sec. 5.1 transfers, Sec.
+    5.3 extra cut-cell sweeps) up to the fp32 rounding of the correction
+    (parity_tol.fp32_step_tolerance, the bound of the single-problem step
+    test).  The launch shapes select the eta paths: a team of two splitting
+    the largest level's vertices (pairs), the lead block alone with its
+    shared-memory image or window (single blocks; clusters of 4)."""
+    from paper_2505_05105_gb300 import ghostmg as G
+    from parity_tol import assert_nodewise, fp32_step_tolerance
+    ps = [m[0] for m in step_members]
+    for inner in (1, 2):
+        with batch(ps, inner=inner, max_cycles=inner) as B:
+            B.set_shape(*shape)
+            f, g = B.pack([p.f for p in ps]), B.pack([p.g for p in ps])
+            u = np.zeros(B.total)
+            info = B.solve(f, g, u, tol=1e-300, allow_not_converged=True)
+            out = B.unpack(u)
+        for k, (p, s, F, refs) in enumerate(step_members):
+            assert info[k].status == G.MG_ERR_NOT_CONVERGED and info[k].cycles == inner
+            u_ref = refs[inner]
+            tol, e = fp32_step_tolerance(s, F, np.zeros(s.n_nodes), u_ref, cycles=inner)
+            got = out[k].ravel()
+            assert_nodewise(got, u_ref, tol, (p.name, shape, inner))
+            assert np.abs(got).max() >= 0.5 * np.abs(e).max()
